@@ -1,0 +1,196 @@
+/*
+ * sz_gb300.h -- C ABI of the GB300 (sm_103a) SZ-LV compressor.
+ *
+ * The library compresses 1D float32 particle arrays with an error bound, as in
+ * "In-Depth Exploration of Single-Snapshot Lossy Compression Techniques for
+ * N-Body Simulations" (arXiv 1711.03888).  The problem statement is Sec. III:
+ * every reconstructed value x'_i satisfies |x_i - x'_i| <= eb_abs, where the
+ * bound is absolute or relative to the value range R = max - min.  The method
+ * is SZ-LV (Sec. IV-A): last-value prediction on an integer lattice of step
+ * D ~ 2*eb_abs, quantization into 2^16 codes, and Huffman coding of the codes.
+ * For molecular dynamics (Sec. IV-B) the coordinates can first be reordered
+ * by a segment-wise partial radix sort of their R-index (best_tradeoff mode).
+ *
+ * Conventions for every call:
+ *   - Pointers named d_* are CUDA device pointers; h_* are host pointers.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   - Calls only enqueue work on `stream` and return.  Sizes that the device
+ *     computes (compressed bytes, element counts) are written through the
+ *     caller's host pointers by sz_sync(), which also reports device-side
+ *     errors.  The pointers must stay valid until that sz_sync().
+ *   - A context is not thread-safe and owns one workspace: issue its calls
+ *     from one host thread, on one stream at a time (use one context per
+ *     concurrent stream).
+ *   - No call aborts, traps or prints.  Each returns an sz_status; a device
+ *     error is latched in the context and returned by the next sz_sync().
+ *   - The caller owns every input and output buffer; the context owns its
+ *     workspace (device memory it allocates and grows on demand).
+ *
+ * Stream format: a 160-byte header followed by the codebook, chunk tables,
+ * sub-stream bit lengths, escape records and the Huffman payload.  No stream
+ * is longer than sz_max_compressed_bytes(n).
+ */
+#ifndef SZ_GB300_H
+#define SZ_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sz_ctx sz_ctx;
+
+typedef enum {
+    SZ_OK = 0,
+    SZ_ERR_ARG = 1,          /* invalid argument (NULL, bad bound, bad parameters) */
+    SZ_ERR_NOMEM = 2,        /* workspace allocation failed */
+    SZ_ERR_CAPACITY = 3,     /* output buffer too small; required size reported */
+    SZ_ERR_CORRUPT = 4,      /* malformed or truncated stream */
+    SZ_ERR_CUDA = 5,         /* a CUDA runtime call failed */
+    SZ_ERR_TIMEOUT = 6,      /* a bounded device wait expired */
+    SZ_ERR_UNSUPPORTED = 7,  /* stream parameters this decoder does not handle */
+    SZ_ERR_BUSY = 8          /* serving: no free slot or over the memory budget */
+} sz_status;
+
+/* Sec. III: absolute bound, or bound relative to the value range R. */
+typedef enum { SZ_EB_ABS = 0, SZ_EB_REL = 1 } sz_eb_kind;
+
+/* Sec. V: the three molecular-dynamics modes.  SZ_MODE_LV = best_speed (SZ-LV),
+ * SZ_MODE_LV_PRX = best_tradeoff (SZ-LV-PRX), SZ_MODE_CPC2000 = best_compression
+ * (SZ-CPC2000, not built: returns SZ_ERR_UNSUPPORTED). */
+typedef enum { SZ_MODE_LV = 0, SZ_MODE_LV_PRX = 1, SZ_MODE_CPC2000 = 2 } sz_mode;
+
+/* Sec. III: the six particle fields. */
+typedef enum {
+    SZ_FIELD_XX = 0, SZ_FIELD_YY = 1, SZ_FIELD_ZZ = 2,
+    SZ_FIELD_VX = 3, SZ_FIELD_VY = 4, SZ_FIELD_VZ = 5, SZ_FIELD_OTHER = 6
+} sz_field;
+
+/* Tuning parameters; a NULL pointer or a zero field selects the default.
+ *   chunk_elems    elements per chunk: 2048, 4096, 8192 or 16384
+ *                  (0 = chosen from n by the built-in tuner).
+ *   sub_elems      elements per sub-stream; must be chunk_elems / 64 (or 0).
+ *   segment        MD mode: elements per sorted segment (Table 4), 1..65536
+ *                  (0 = 16384).
+ *   ignored_digits MD mode: 3-bit R-index digits ignored by the sort
+ *                  (Table 5), 0..21 (the default 6 applies when segment is 0
+ *                  too; set segment explicitly to request 0). */
+typedef struct {
+    uint32_t chunk_elems;
+    uint32_t sub_elems;
+    uint32_t segment;
+    uint32_t ignored_digits;
+} sz_params;
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes caps the device
+ * memory the serving loop may admit at once (0 = no cap).  The workspace grows
+ * with the largest array seen.  Errors: SZ_ERR_ARG (NULL ctx), SZ_ERR_CUDA,
+ * SZ_ERR_NOMEM. */
+sz_status sz_ctx_create(sz_ctx** ctx, int device, size_t hbm_budget_bytes);
+
+/* Synchronize the context's device work and free the context and its workspace. */
+sz_status sz_ctx_destroy(sz_ctx* ctx);
+
+/* Largest stream any call can produce for n elements: 160 + 16*ceil(n/4). */
+size_t sz_max_compressed_bytes(size_t n);
+
+/* Compress d_in[0..n) (float32, device) into d_out (device, out_cap bytes).
+ * Sec. III / IV-A: eb is absolute (SZ_EB_ABS) or relative to the value range
+ * of the finite elements (SZ_EB_REL); it must be finite and >= 0.  n < 2^32.
+ * On sz_sync(), *out_bytes holds the stream size, or the required size when
+ * the call failed with SZ_ERR_CAPACITY (then d_out holds no valid stream).
+ * Errors now: SZ_ERR_ARG; at sz_sync(): SZ_ERR_CAPACITY, SZ_ERR_TIMEOUT. */
+sz_status sz_compress(sz_ctx* ctx, const float* d_in, size_t n, double eb, sz_eb_kind kind,
+                      const sz_params* params, void* d_out, size_t out_cap, size_t* out_bytes,
+                      void* stream);
+
+/* Decompress a stream (device, in_bytes) into d_out (device, room for n_cap
+ * floats).  Sec. III: every finite element is within the stream's eb_abs of
+ * the original; non-finite elements come back bit-exact.  On sz_sync(),
+ * *n_out holds the element count.  Errors at sz_sync(): SZ_ERR_CORRUPT
+ * (malformed stream; no read leaves the in_bytes buffer), SZ_ERR_CAPACITY
+ * (n_cap too small), SZ_ERR_UNSUPPORTED (sub-stream count other than 64). */
+sz_status sz_decompress(sz_ctx* ctx, const void* d_in, size_t in_bytes, float* d_out, size_t n_cap,
+                        size_t* n_out, void* stream);
+
+/* Compress k independent arrays (the per-rank fields of a snapshot; Sec. V
+ * compresses each in-memory array independently).  Arrays may have different
+ * sizes and bounds; each stream is byte-identical to sz_compress on that
+ * array.  Arrays are processed together so per-array fixed costs overlap.
+ * Arguments are host arrays of k entries; out_bytes[i] is set by sz_sync(). */
+sz_status sz_compress_batch(sz_ctx* ctx, int k, const float* const* d_in, const size_t* n,
+                            const double* eb, sz_eb_kind kind, const sz_params* params,
+                            void* const* d_out, const size_t* out_cap, size_t* out_bytes,
+                            void* stream);
+
+/* Decompress k streams; each result equals sz_decompress of that stream. */
+sz_status sz_decompress_batch(sz_ctx* ctx, int k, const void* const* d_in, const size_t* in_bytes,
+                              float* const* d_out, const size_t* n_cap, size_t* n_out, void* stream);
+
+/* Molecular-dynamics snapshot (Sec. IV-B).  fields[0..2] must be XX, YY, ZZ;
+ * further fields (velocities) follow the same reordering.  mode SZ_MODE_LV
+ * compresses each field in stored order; SZ_MODE_LV_PRX first reorders every
+ * field by one permutation: R-index keys from the lattice coordinates of the
+ * three positions (Fig. 3a), stably sorted by key >> 3p within consecutive
+ * segments (Tables 4-5).  No index array is stored (Sec. IV-B), so the
+ * streams decode to the reordered arrays.  d_perm (device, n uint32, may be
+ * NULL) receives the permutation: position j holds original index perm[j]. */
+sz_status sz_compress_snapshot(sz_ctx* ctx, int nfields, const sz_field* fields,
+                               const float* const* d_in, size_t n, const double* eb, sz_eb_kind kind,
+                               sz_mode mode, const sz_params* params, void* const* d_out,
+                               const size_t* out_cap, size_t* out_bytes, uint32_t* d_perm,
+                               void* stream);
+
+/* Wait for the context's work on `stream`, fill the pending host results
+ * (out_bytes, n_out) and return the first device error since the last sync
+ * (SZ_OK if none), then clear it. */
+sz_status sz_sync(sz_ctx* ctx, void* stream);
+
+/* Human-readable name of a status code (static string). */
+const char* sz_status_string(sz_status s);
+
+/* ---- serving: continuous batching of compress / decompress requests ---- */
+
+typedef enum { SZ_OP_COMPRESS = 0, SZ_OP_DECOMPRESS = 1 } sz_op;
+
+/* One request.  Buffers are device pointers owned by the caller and must stay
+ * valid until the request completes.  For SZ_OP_COMPRESS: in = float data of
+ * n elements, out = stream buffer of out_cap bytes.  For SZ_OP_DECOMPRESS:
+ * in = stream of in_bytes, out = float buffer of n (capacity) elements. */
+typedef struct {
+    sz_op op;
+    const void* in;
+    size_t n;
+    size_t in_bytes;
+    void* out;
+    size_t out_cap;
+    double eb;
+    sz_eb_kind kind;
+} sz_request;
+
+typedef struct {
+    sz_status status;     /* SZ_OK once done; SZ_ERR_BUSY while pending */
+    size_t out_size;      /* stream bytes (compress) or elements (decompress) */
+    double latency_s;     /* completion time - submit time */
+} sz_result;
+
+/* Start the serving loop on a context: up to `slots` requests in flight, at
+ * most hbm_budget_bytes (from sz_ctx_create) of workspace admitted at once. */
+sz_status sz_serve_start(sz_ctx* ctx, int slots);
+
+/* Queue a request; *ticket identifies it.  Returns SZ_ERR_ARG for a bad
+ * request, SZ_ERR_BUSY if it could never fit the memory budget. */
+sz_status sz_serve_submit(sz_ctx* ctx, const sz_request* req, uint64_t* ticket);
+
+/* Non-blocking: fills *res; res->status is SZ_ERR_BUSY while pending. */
+sz_status sz_serve_poll(sz_ctx* ctx, uint64_t ticket, sz_result* res);
+
+/* Drain all queued requests and stop the loop. */
+sz_status sz_serve_stop(sz_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SZ_GB300_H */

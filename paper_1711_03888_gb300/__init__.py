@@ -1,0 +1,265 @@
+"""Python binding of the GB300 SZ-LV compressor (C ABI in include/sz_gb300.h).
+
+Argument marshalling only: tensors become device pointers, the current torch
+stream becomes the CUDA stream, and sizes come back through sz_sync().  Every
+step of compression and decompression runs in the CUDA kernels of
+libsz_gb300.so; there is no CPU fallback.  If the shared library is missing,
+importing this package raises.  Build it with build.build() (or
+__graft_entry__.build()).
+
+The functions keep the C names.  A `Context` wraps an sz_ctx* and keeps the
+host size holders alive until sz_sync().
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsz_gb300.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: the GB300 library must be built (paper_1711_03888_gb300.build)")
+
+_lib = C.CDLL(LIB_PATH)
+
+SZ_OK, SZ_ERR_ARG, SZ_ERR_NOMEM, SZ_ERR_CAPACITY, SZ_ERR_CORRUPT, SZ_ERR_CUDA, SZ_ERR_TIMEOUT, \
+    SZ_ERR_UNSUPPORTED, SZ_ERR_BUSY = range(9)
+SZ_EB_ABS, SZ_EB_REL = 0, 1
+SZ_MODE_LV, SZ_MODE_LV_PRX, SZ_MODE_CPC2000 = 0, 1, 2
+SZ_FIELD_XX, SZ_FIELD_YY, SZ_FIELD_ZZ, SZ_FIELD_VX, SZ_FIELD_VY, SZ_FIELD_VZ, SZ_FIELD_OTHER = range(7)
+SZ_OP_COMPRESS, SZ_OP_DECOMPRESS = 0, 1
+HEADER_BYTES = 160
+
+EXPORTS = ("sz_ctx_create", "sz_ctx_destroy", "sz_max_compressed_bytes", "sz_compress", "sz_decompress",
+           "sz_compress_batch", "sz_decompress_batch", "sz_compress_snapshot", "sz_sync", "sz_status_string",
+           "sz_serve_start", "sz_serve_submit", "sz_serve_poll", "sz_serve_stop")
+
+
+class sz_params(C.Structure):
+    _fields_ = [("chunk_elems", C.c_uint32), ("sub_elems", C.c_uint32),
+                ("segment", C.c_uint32), ("ignored_digits", C.c_uint32)]
+
+
+class sz_request(C.Structure):
+    _fields_ = [("op", C.c_int), ("input", C.c_void_p), ("n", C.c_size_t), ("in_bytes", C.c_size_t),
+                ("out", C.c_void_p), ("out_cap", C.c_size_t), ("eb", C.c_double), ("kind", C.c_int)]
+
+
+class sz_result(C.Structure):
+    _fields_ = [("status", C.c_int), ("out_size", C.c_size_t), ("latency_s", C.c_double)]
+
+
+_vp, _sz, _st = C.c_void_p, C.c_size_t, C.c_int
+_sig = {
+    "sz_ctx_create": (_st, [C.POINTER(_vp), C.c_int, _sz]),
+    "sz_ctx_destroy": (_st, [_vp]),
+    "sz_max_compressed_bytes": (_sz, [_sz]),
+    "sz_compress": (_st, [_vp, _vp, _sz, C.c_double, C.c_int, C.POINTER(sz_params), _vp, _sz,
+                          C.POINTER(_sz), _vp]),
+    "sz_decompress": (_st, [_vp, _vp, _sz, _vp, _sz, C.POINTER(_sz), _vp]),
+    "sz_compress_batch": (_st, [_vp, C.c_int, C.POINTER(_vp), C.POINTER(_sz), C.POINTER(C.c_double), C.c_int,
+                                C.POINTER(sz_params), C.POINTER(_vp), C.POINTER(_sz), C.POINTER(_sz), _vp]),
+    "sz_decompress_batch": (_st, [_vp, C.c_int, C.POINTER(_vp), C.POINTER(_sz), C.POINTER(_vp), C.POINTER(_sz),
+                                  C.POINTER(_sz), _vp]),
+    "sz_compress_snapshot": (_st, [_vp, C.c_int, C.POINTER(C.c_int), C.POINTER(_vp), _sz, C.POINTER(C.c_double),
+                                   C.c_int, C.c_int, C.POINTER(sz_params), C.POINTER(_vp), C.POINTER(_sz),
+                                   C.POINTER(_sz), _vp, _vp]),
+    "sz_sync": (_st, [_vp, _vp]),
+    "sz_status_string": (C.c_char_p, [C.c_int]),
+    "sz_serve_start": (_st, [_vp, C.c_int]),
+    "sz_serve_submit": (_st, [_vp, C.POINTER(sz_request), C.POINTER(C.c_uint64)]),
+    "sz_serve_poll": (_st, [_vp, C.c_uint64, C.POINTER(sz_result)]),
+    "sz_serve_stop": (_st, [_vp]),
+}
+for _name, (_res, _args) in _sig.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+class SzError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        msg = _lib.sz_status_string(status).decode()
+        super().__init__(f"{what}: {msg} (status {status})" if what else msg)
+        self.status = status
+
+
+def _check(status: int, what: str):
+    if status != SZ_OK:
+        raise SzError(status, what)
+
+
+def _ptr(t) -> int:
+    return 0 if t is None else int(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is not None:
+        return C.c_void_p(int(stream))
+    import torch
+    return C.c_void_p(int(torch.cuda.current_stream().cuda_stream))
+
+
+def _params(chunk: int = 0, sub: int = 0, segment: int = 0, ignored_digits: int = 0):
+    return sz_params(chunk, sub, segment, ignored_digits)
+
+
+class Context:
+    """Owns an sz_ctx* and the host size holders of pending calls."""
+
+    def __init__(self, device: int = 0, budget: int = 0):
+        h = C.c_void_p()
+        _check(_lib.sz_ctx_create(C.byref(h), device, budget), "sz_ctx_create")
+        self.handle = h
+        self.device = device
+        self._keep = []
+
+    def close(self):
+        if self.handle:
+            _lib.sz_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def hold(self, obj):
+        self._keep.append(obj)
+        return obj
+
+
+def sz_ctx_create(device: int = 0, budget: int = 0) -> Context:
+    return Context(device, budget)
+
+
+def sz_ctx_destroy(ctx: Context):
+    ctx.close()
+
+
+def sz_max_compressed_bytes(n: int) -> int:
+    return int(_lib.sz_max_compressed_bytes(n))
+
+
+def sz_compress(ctx: Context, x, eb: float, kind: int = SZ_EB_REL, params=None, out=None, out_cap=None,
+                stream=None):
+    """Enqueue compression of the float32 CUDA tensor x into `out` (uint8 CUDA
+    tensor; allocated with the maximum size when None).  Returns
+    (out, size_holder); size_holder.value is valid after sz_sync."""
+    import torch
+    n = x.numel()
+    if out is None:
+        out = torch.empty(sz_max_compressed_bytes(n), dtype=torch.uint8, device=x.device)
+    cap = out.numel() if out_cap is None else out_cap
+    nb = ctx.hold(C.c_size_t(0))
+    p = params if params is not None else _params()
+    _check(_lib.sz_compress(ctx.handle, _ptr(x), n, eb, kind, C.byref(p), _ptr(out), cap, C.byref(nb),
+                            _stream(stream)), "sz_compress")
+    return out, nb
+
+
+def sz_decompress(ctx: Context, stream_buf, in_bytes: int, out, n_cap=None, stream=None):
+    """Enqueue decompression of a stream (uint8 CUDA tensor) into the float32
+    CUDA tensor `out`.  Returns a holder whose .value is n after sz_sync."""
+    no = ctx.hold(C.c_size_t(0))
+    cap = out.numel() if n_cap is None else n_cap
+    _check(_lib.sz_decompress(ctx.handle, _ptr(stream_buf), in_bytes, _ptr(out), cap, C.byref(no),
+                              _stream(stream)), "sz_decompress")
+    return no
+
+
+def sz_compress_batch(ctx: Context, xs, ebs, kind: int = SZ_EB_REL, params=None, outs=None, stream=None):
+    import torch
+    k = len(xs)
+    if outs is None:
+        outs = [torch.empty(sz_max_compressed_bytes(x.numel()), dtype=torch.uint8, device=x.device) for x in xs]
+    ins = (C.c_void_p * k)(*[_ptr(x) for x in xs])
+    ns = (C.c_size_t * k)(*[x.numel() for x in xs])
+    e = (C.c_double * k)(*ebs)
+    o = (C.c_void_p * k)(*[_ptr(t) for t in outs])
+    caps = (C.c_size_t * k)(*[t.numel() for t in outs])
+    nb = ctx.hold((C.c_size_t * k)())
+    p = params if params is not None else _params()
+    _check(_lib.sz_compress_batch(ctx.handle, k, ins, ns, e, kind, C.byref(p), o, caps, nb, _stream(stream)),
+           "sz_compress_batch")
+    return outs, nb
+
+
+def sz_decompress_batch(ctx: Context, streams, in_bytes, outs, stream=None):
+    k = len(streams)
+    ins = (C.c_void_p * k)(*[_ptr(s) for s in streams])
+    ib = (C.c_size_t * k)(*in_bytes)
+    o = (C.c_void_p * k)(*[_ptr(t) for t in outs])
+    caps = (C.c_size_t * k)(*[t.numel() for t in outs])
+    no = ctx.hold((C.c_size_t * k)())
+    _check(_lib.sz_decompress_batch(ctx.handle, k, ins, ib, o, caps, no, _stream(stream)), "sz_decompress_batch")
+    return no
+
+
+def sz_compress_snapshot(ctx: Context, fields, xs, n: int, ebs, kind: int = SZ_EB_REL, mode: int = SZ_MODE_LV_PRX,
+                         params=None, outs=None, perm=None, stream=None):
+    import torch
+    k = len(xs)
+    if outs is None:
+        outs = [torch.empty(sz_max_compressed_bytes(n), dtype=torch.uint8, device=xs[0].device) for _ in xs]
+    f = (C.c_int * k)(*fields)
+    ins = (C.c_void_p * k)(*[_ptr(x) for x in xs])
+    e = (C.c_double * k)(*ebs)
+    o = (C.c_void_p * k)(*[_ptr(t) for t in outs])
+    caps = (C.c_size_t * k)(*[t.numel() for t in outs])
+    nb = ctx.hold((C.c_size_t * k)())
+    p = params if params is not None else _params()
+    _check(_lib.sz_compress_snapshot(ctx.handle, k, f, ins, n, e, kind, mode, C.byref(p), o, caps, nb,
+                                     _ptr(perm), _stream(stream)), "sz_compress_snapshot")
+    return outs, nb
+
+
+def sz_sync(ctx: Context, stream=None, check: bool = True) -> int:
+    st = _lib.sz_sync(ctx.handle, _stream(stream))
+    ctx._keep.clear()
+    if check:
+        _check(st, "sz_sync")
+    return st
+
+
+def sz_status_string(status: int) -> str:
+    return _lib.sz_status_string(status).decode()
+
+
+def sz_serve_start(ctx: Context, slots: int):
+    _check(_lib.sz_serve_start(ctx.handle, slots), "sz_serve_start")
+
+
+def sz_serve_submit(ctx: Context, req: sz_request) -> int:
+    t = C.c_uint64(0)
+    _check(_lib.sz_serve_submit(ctx.handle, C.byref(req), C.byref(t)), "sz_serve_submit")
+    return t.value
+
+
+def sz_serve_poll(ctx: Context, ticket: int) -> sz_result:
+    r = sz_result()
+    _lib.sz_serve_poll(ctx.handle, ticket, C.byref(r))
+    return r
+
+
+def sz_serve_stop(ctx: Context):
+    _check(_lib.sz_serve_stop(ctx.handle), "sz_serve_stop")
+
+
+# ---- convenience (still only marshalling) ----------------------------------
+
+def compress(ctx: Context, x, eb: float, kind: int = SZ_EB_REL, chunk: int = 0):
+    """Compress and synchronize; returns the stream as a uint8 CUDA tensor."""
+    out, nb = sz_compress(ctx, x, eb, kind, _params(chunk))
+    sz_sync(ctx)
+    return out[: nb.value]
+
+
+def decompress(ctx: Context, stream_buf, n: int):
+    import torch
+    out = torch.empty(max(n, 1), dtype=torch.float32, device=stream_buf.device)
+    no = sz_decompress(ctx, stream_buf, stream_buf.numel(), out, n)
+    sz_sync(ctx)
+    return out[: no.value]

@@ -1,0 +1,60 @@
+// sz_ctx.h -- the context object behind the opaque sz_ctx handle.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <vector>
+#include "../../include/sz_gb300.h"
+#include "sz_internal.h"
+
+struct sz_serve_state;
+
+struct sz_ctx {
+    int device = 0;
+    size_t budget = 0;
+    // workspace (one block of device memory, grown on demand)
+    uint8_t* ws = nullptr;
+    size_t ws_bytes = 0;
+    int cap_arrays = 0;
+    uint64_t cap_chunks = 0;
+    szg::ArrayState* d_state = nullptr;
+    uint32_t* d_hist = nullptr;
+    uint32_t* d_enc = nullptr;
+    uint32_t* d_chunk_esc = nullptr;
+    unsigned long long* d_chunk_status = nullptr;
+    uint32_t* d_cb = nullptr;
+    uint32_t* d_lut = nullptr;
+    uint16_t* d_bylen = nullptr;
+    uint32_t* d_err = nullptr;
+    // pinned result slots and where sz_sync delivers them
+    uint64_t* h_res = nullptr;
+    uint32_t* h_err = nullptr;
+    std::vector<size_t*> pend_dst;
+    uint32_t n_pending = 0, cap_pending = 0;
+    // MD reordering buffers
+    uint8_t* md = nullptr;
+    size_t md_bytes = 0;
+    // serving loop
+    sz_serve_state* serve = nullptr;
+
+    void free_workspace();
+    void free_extra();
+};
+
+namespace szg {
+uint32_t tune_chunk(uint64_t n);
+sz_status resolve_params(const sz_params* p, uint64_t n, uint32_t* C, uint32_t* G);
+sz_status ctx_reserve(sz_ctx* ctx, int arrays, uint64_t max_chunks);
+CompressArgs make_compress_args(sz_ctx* ctx, int slot, const float* in, uint64_t n, double eb, int kind,
+                                uint32_t C, uint32_t G, uint32_t extra_flags, void* out, uint64_t cap);
+DecompressArgs make_decompress_args(sz_ctx* ctx, int slot, const void* in, uint64_t in_bytes, float* out,
+                                    uint64_t n_cap);
+sz_status queue_result(sz_ctx* ctx, const void* dsrc, size_t* dst, cudaStream_t s);
+sz_status validate_compress(const float* d_in, size_t n, double eb, sz_eb_kind kind, void* d_out);
+sz_status enqueue_compress(sz_ctx* ctx, const CompressArgs& a, size_t* out_bytes, cudaStream_t s);
+sz_status enqueue_decompress(sz_ctx* ctx, const DecompressArgs& d, size_t* n_out, cudaStream_t s);
+sz_status batch_compress(sz_ctx* ctx, int k, const float* const* d_in, const size_t* n, const double* eb,
+                         sz_eb_kind kind, const sz_params* params, void* const* d_out, const size_t* out_cap,
+                         size_t* out_bytes, cudaStream_t s);
+sz_status batch_decompress(sz_ctx* ctx, int k, const void* const* d_in, const size_t* in_bytes, float* const* d_out,
+                           const size_t* n_cap, size_t* n_out, cudaStream_t s);
+}  // namespace szg

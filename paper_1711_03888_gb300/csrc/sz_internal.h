@@ -1,0 +1,135 @@
+// sz_internal.h -- structures shared by the GB300 kernels and the C-ABI layer.
+//
+// Stream layout (version 1, little-endian), restated for the CUDA side:
+//   header 160 B | symbols u16[m] | lengths u8[m] | chunk words u64[nc+1] |
+//   chunk anchors i64[nc] | chunk escape bases u64[nc+1] |
+//   sub-stream bit lengths u16[nc*C/G] | escapes 16 B each | payload u32[]
+// Every section starts on a 16-byte boundary; padding bytes are zero.
+#pragma once
+#include <stdint.h>
+#include <stddef.h>
+
+namespace szg {
+
+constexpr uint32_t kMagic = 0x564C5A53u;        // "SZLV"
+constexpr uint32_t kVersion = 1;
+constexpr uint32_t kHeaderBytes = 160;
+constexpr int kMaxLen = 24;                       // longest codeword (bits)
+constexpr int kRadius = 32768;                    // code = delta + radius, 0 = escape
+constexpr int kNumCodes = 65536;
+constexpr uint32_t kFlagRaw = 1u;
+constexpr uint32_t kFlagReordered = 2u;
+constexpr uint32_t kEscBytes = 16;
+constexpr int kSubPerChunk = 64;                  // sub-streams per chunk on the GPU path
+constexpr int kRangeBlocks = 1216;                // 8 x 152 SMs
+constexpr int kLutBits = 11;                      // decoder direct-lookup width
+
+// header byte offsets
+constexpr int H_MAGIC = 0, H_VERSION = 4, H_HDRBYTES = 6, H_N = 8, H_EB = 16, H_D = 24,
+              H_FLAGS = 28, H_C = 32, H_G = 36, H_M = 40, H_MAXLEN = 42, H_PRED = 43,
+              H_NCHUNKS = 48, H_NSYM = 56, H_NESC = 64, H_PWORDS = 72, H_OFF = 80,
+              H_TOTAL = 144;
+enum { S_SYMS = 0, S_LENS, S_CWORD, S_ANCHOR, S_CESC, S_SUBLEN, S_ESC, S_PAYLOAD };
+
+// error word bits (per context, set with atomicOr by kernels)
+enum : uint32_t {
+    E_CAPACITY = 1u, E_CORRUPT = 2u, E_TIMEOUT = 4u, E_UNSUPPORTED = 8u, E_INTERNAL = 16u
+};
+
+// Quantities every kernel derives the same way from the range (Sec. III).
+struct LatticeParams {
+    double eb_abs;      // absolute bound
+    float D;            // lattice step: largest float <= 2*eb_abs
+    float inv;          // ~1/D (candidate only)
+    float thr_lo;       // RD32(D*(1/2 - 2^-20)): |x - qD| below -> q is certain
+    float thr_hi;       // RU32(D*(1/2 + 2^-20)): |x - qD| above -> q is off by one
+    float ebf;          // RD32(eb_abs): exact float form of the verbatim test
+    int fast;           // D normal and in [2^-100, 2^100]
+    int raw;            // D == 0: stream is a raw copy
+};
+
+// Per-array device state (workspace-resident).  Kernels of one call read and
+// write it in stream order.
+struct ArrayState {
+    // range (set by the last range block)
+    uint32_t min_key, max_key, any_finite, range_done;
+    uint32_t acc_min, acc_max, acc_any, acc_blocks;   // accumulators, self-resetting
+    // codebook / layout (set by the codebook kernel)
+    uint64_t off[8];
+    uint64_t n_escapes;
+    uint64_t bound_bits;
+    uint32_t n_used;
+    uint32_t raw;
+    uint32_t ticket;           // encoder chunk ticket (reset by the codebook kernel)
+    uint32_t pad0;
+    uint64_t total_bytes;      // final stream size (set by the encoder)
+    uint64_t n_out;            // decoder: element count from the header
+    // decoder tables
+    uint32_t first[kMaxLen + 2];
+    uint32_t count[kMaxLen + 2];
+    uint32_t base[kMaxLen + 2];
+    uint32_t dec_ok;
+    uint32_t pad1;
+};
+
+// Arguments of one array's compression (passed by value to kernels).
+struct CompressArgs {
+    const float* in;
+    uint8_t* out;
+    uint64_t n;
+    uint64_t out_cap;
+    double eb;
+    int eb_kind;                // 0 abs, 1 rel
+    uint32_t C, G;
+    uint32_t n_chunks;
+    uint32_t extra_flags;
+    ArrayState* st;
+    uint32_t* hist;             // 65536
+    uint32_t* enc;              // 65536: codeword << 5 | length
+    uint32_t* chunk_esc;        // n_chunks: escapes per chunk
+    unsigned long long* chunk_status;  // n_chunks: look-back words
+    uint32_t* cb_scratch;       // codebook scratch (kCbScratchWords words)
+    uint32_t* err;              // context error word
+};
+
+struct DecompressArgs {
+    const uint8_t* in;
+    uint64_t in_bytes;
+    float* out;
+    uint64_t n_cap;
+    ArrayState* st;
+    uint32_t* lut;              // 1 << kLutBits entries: sym << 8 | len, 0 = long/invalid
+    uint16_t* by_len;           // 65536: symbols in (length, symbol) order
+    uint32_t* cb_scratch;
+    uint32_t* err;
+};
+
+// codebook scratch: 9 arrays of 65536 words and 5 of 131072 (see k_codebook.cu)
+constexpr size_t kCbScratchWords = 65536u * 20u;
+
+// ---- host-side launchers (defined in the kernel files) ----
+void launch_range(const CompressArgs* a, int k, void* stream);
+void launch_quant(const CompressArgs* a, int k, void* stream);
+void launch_codebook(const CompressArgs* a, int k, void* stream);
+void launch_encode(const CompressArgs* a, int k, void* stream);
+void launch_decode_setup(const DecompressArgs* a, int k, void* stream);
+void launch_decode(const DecompressArgs* a, int k, void* stream);
+
+// MD reordering
+struct ReorderArgs {
+    const float* pos[3];        // xx, yy, zz (device)
+    uint64_t n;
+    double eb[3];
+    int eb_kind;
+    uint32_t segment;
+    uint32_t p;
+    ArrayState* st[3];          // range state of the three coordinates
+    unsigned long long* keys;   // n
+    uint32_t* perm;             // n
+    uint32_t* err;
+};
+void launch_rindex_keys(const ReorderArgs& a, void* stream);
+void launch_segment_sort(const ReorderArgs& a, void* stream);
+void launch_gather(const float* src, float* dst, const uint32_t* perm, uint64_t n, void* stream);
+
+}  // namespace szg

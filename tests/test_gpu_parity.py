@@ -1,0 +1,240 @@
+"""GPU parity: the CUDA path, called through the C ABI, against the CPU
+oracle on the same seeded inputs.  Integer/byte work must be bit-exact: the
+compressed stream must equal the oracle's byte for byte, and the
+reconstruction must equal the oracle's bit for bit (which implies the error
+bound |x - x'| <= eb_abs the oracle pins establish)."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sz():
+    import __graft_entry__ as g
+    g.build()
+    import paper_1711_03888_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(sz):
+    c = sz.Context(0)
+    yield c
+    c.close()
+
+
+def _gpu_stream(sz, ctx, x_cpu, eb, kind, chunk):
+    x = x_cpu.cuda()
+    out, nb = sz.sz_compress(ctx, x, eb, kind, sz._params(chunk))
+    sz.sz_sync(ctx)
+    return out[: nb.value].cpu().numpy().tobytes()
+
+
+def _gpu_decode(sz, ctx, stream_bytes, n):
+    buf = torch.frombuffer(bytearray(stream_bytes), dtype=torch.uint8).cuda()
+    out = torch.full((max(n, 1),), float("nan"), dtype=torch.float32, device="cuda")
+    no = sz.sz_decompress(ctx, buf, len(stream_bytes), out, n)
+    sz.sz_sync(ctx)
+    assert no.value == n
+    return out[:n].cpu().numpy()
+
+
+def _bits(a):
+    return np.ascontiguousarray(a, np.float32).view(np.uint32)
+
+
+def _check(sz, ctx, oracle, x_cpu, eb, kind, chunk):
+    x_cpu = x_cpu.contiguous()
+    ref = oracle.compress(x_cpu.numpy(), eb, kind, chunk, chunk // 64)
+    got = _gpu_stream(sz, ctx, x_cpu, eb, kind, chunk)
+    if got != ref:
+        h1, h2 = oracle.parse_header(got) if len(got) >= 160 else {}, oracle.parse_header(ref)
+        diff = next((i for i in range(min(len(got), len(ref))) if got[i] != ref[i]), None)
+        raise AssertionError(f"stream mismatch: len {len(got)} vs {len(ref)}, first diff at byte {diff}, "
+                             f"gpu header {h1}, oracle header {h2}")
+    yr = oracle.decompress(ref)
+    yg = _gpu_decode(sz, ctx, ref, x_cpu.numel())
+    assert np.array_equal(_bits(yg), _bits(yr))
+    return ref
+
+
+CASES = [
+    ("walk", 1, 2048), ("walk", 3, 2048), ("walk", 100, 2048), ("walk", 2047, 2048), ("walk", 2048, 2048),
+    ("walk", 2049, 2048), ("walk", 3 * 4096 + 17, 4096), ("walk", 70001, 8192), ("walk", 16384 * 5 + 1, 16384),
+    ("uniform", 50000, 4096), ("cosmo_xx", 1 << 16, 4096), ("cosmo_vy", 1 << 16, 8192),
+    ("md_zz", 60000, 8192), ("wild", 30000, 2048), ("spiky", 40000, 4096), ("const", 5000, 2048),
+]
+
+
+def _make(kind, n):
+    if kind == "walk":
+        return synth.random_walk_f32(n, 21)
+    if kind == "uniform":
+        return synth.uniform_f32(n, 6, -3.0, 5.0)
+    if kind.startswith("cosmo"):
+        return synth.cosmology(n, 8, 1)[kind.split("_")[1]]
+    if kind.startswith("md"):
+        return synth.md_fcc(cells=25, seed=2)[kind.split("_")[1]][:n].clone()
+    if kind == "wild":
+        w = synth.uniform_f32(n, 7, -1e30, 1e30).numpy().copy()
+        w[::97] = np.nan
+        w[5::211] = np.inf
+        w[7::223] = -np.inf
+        w[9::50] = np.float32(1e-42)
+        w[11::50] = -0.0
+        return torch.from_numpy(w)
+    if kind == "spiky":
+        x = synth.random_walk_f32(n, 8, 1e-3).numpy().copy()
+        x[::777] = 1e6
+        return torch.from_numpy(x)
+    if kind == "const":
+        return torch.full((n,), 2.5, dtype=torch.float32)
+    raise ValueError(kind)
+
+
+@pytest.mark.parametrize("kind,n,chunk", CASES)
+@pytest.mark.parametrize("eb", [1e-3, 1e-5])
+def test_stream_parity_relative(sz, ctx, oracle, kind, n, chunk, eb):
+    _check(sz, ctx, oracle, _make(kind, n), eb, 1, chunk)
+
+
+@pytest.mark.parametrize("eb_abs", [0.0, 1e-7, 0.05, 3.0])
+def test_stream_parity_absolute(sz, ctx, oracle, eb_abs):
+    _check(sz, ctx, oracle, _make("walk", 30000), eb_abs, 0, 4096)
+    _check(sz, ctx, oracle, _make("spiky", 30000), eb_abs, 0, 2048)
+
+
+def test_empty_array(sz, ctx, oracle):
+    x = torch.zeros(0, dtype=torch.float32)
+    ref = oracle.compress(x.numpy(), 1e-4, 1, 2048, 32)
+    got = _gpu_stream(sz, ctx, x, 1e-4, 1, 2048)
+    assert got == ref and len(got) == 160
+    assert _gpu_decode(sz, ctx, ref, 0).size == 0
+
+
+def test_near_ties_and_large_lattice(sz, ctx, oracle):
+    """Values on and next to lattice half-points exercise the binary64 slow
+    path; values with |q| > 2^22 exercise the out-of-range candidate path."""
+    D = 2.0 ** -8
+    k = np.arange(-20000, 20000)
+    halves = ((k + 0.5) * D).astype(np.float32)
+    nxt = np.nextafter(halves, np.float32(np.inf))
+    prv = np.nextafter(halves, np.float32(-np.inf))
+    x = np.stack([halves, nxt, prv], 1).ravel()
+    _check(sz, ctx, oracle, torch.from_numpy(x), D / 2, 0, 4096)
+    big = (1000.0 + np.cumsum(np.random.default_rng(8).normal(0, 1e-4, 20000))).astype(np.float32)
+    _check(sz, ctx, oracle, torch.from_numpy(big), 1e-6, 0, 4096)
+    _check(sz, ctx, oracle, torch.from_numpy(big), 1e-9, 0, 4096)
+
+
+def test_unaligned_input(sz, ctx, oracle):
+    base = _make("walk", 20001)
+    for off in (1, 2, 3):
+        x = base.cuda()[off:]
+        ref = oracle.compress(base[off:].numpy(), 1e-4, 1, 2048, 32)
+        out, nb = sz.sz_compress(ctx, x, 1e-4, 1, sz._params(2048))
+        sz.sz_sync(ctx)
+        assert out[: nb.value].cpu().numpy().tobytes() == ref
+
+
+def test_decoder_reads_oracle_streams_and_reuse(sz, ctx, oracle):
+    """Several calls back to back on one context reuse the workspace."""
+    for seed in range(4):
+        x = synth.random_walk_f32(10000 + 999 * seed, seed)
+        _check(sz, ctx, oracle, x, 10.0 ** -(2 + seed), 1, 2048)
+
+
+def test_capacity_error_reports_size(sz, ctx, oracle):
+    x_cpu = _make("walk", 50000)
+    ref = oracle.compress(x_cpu.numpy(), 1e-4, 1, 4096, 64)
+    x = x_cpu.cuda()
+    for cap in (100, 1000, len(ref) - 16):
+        out = torch.full((len(ref) + 4096,), 0xAB, dtype=torch.uint8, device="cuda")
+        _, nb = sz.sz_compress(ctx, x, 1e-4, 1, sz._params(4096), out=out, out_cap=cap)
+        st = sz.sz_sync(ctx, check=False)
+        assert st == sz.SZ_ERR_CAPACITY
+        assert nb.value == len(ref)
+        assert (out[cap:].cpu().numpy() == 0xAB).all()       # nothing written past the cap
+    out = torch.empty(len(ref), dtype=torch.uint8, device="cuda")
+    _, nb = sz.sz_compress(ctx, x, 1e-4, 1, sz._params(4096), out=out)
+    sz.sz_sync(ctx)
+    assert out.cpu().numpy().tobytes() == ref
+    small = torch.empty(10, dtype=torch.float32, device="cuda")
+    buf = torch.frombuffer(bytearray(ref), dtype=torch.uint8).cuda()
+    no = sz.sz_decompress(ctx, buf, len(ref), small, 10)
+    assert sz.sz_sync(ctx, check=False) == sz.SZ_ERR_CAPACITY and no.value == 50000
+
+
+def test_corrupt_streams_are_rejected(sz, ctx, oracle):
+    x_cpu = _make("cosmo_vx", 1 << 15)
+    ref = bytearray(oracle.compress(x_cpu.numpy(), 1e-4, 1, 2048, 32))
+    h = oracle.parse_header(bytes(ref))
+    out = torch.empty(1 << 15, dtype=torch.float32, device="cuda")
+
+    def run(buf, nbytes=None):
+        t = torch.frombuffer(bytearray(buf), dtype=torch.uint8).cuda()
+        sz.sz_decompress(ctx, t, len(buf) if nbytes is None else nbytes, out, out.numel())
+        return sz.sz_sync(ctx, check=False)
+
+    assert run(ref) == sz.SZ_OK
+    assert run(ref, 100) == sz.SZ_ERR_CORRUPT                  # truncated below the header
+    assert run(ref, len(ref) - 16) == sz.SZ_ERR_CORRUPT        # truncated payload
+    bad = bytearray(ref); bad[0] ^= 1
+    assert run(bad) == sz.SZ_ERR_CORRUPT                       # magic
+    bad = bytearray(ref); bad[h["off_lens"]] = 30
+    assert run(bad) == sz.SZ_ERR_CORRUPT                       # code length > 24
+    bad = bytearray(ref); bad[h["off_chunk_word"] + 8 * 3: h["off_chunk_word"] + 8 * 4] = (1 << 50).to_bytes(8, "little")
+    assert run(bad) == sz.SZ_ERR_CORRUPT                       # chunk offset out of range
+    bad = bytearray(ref); bad[h["off_sublen"]: h["off_sublen"] + 2] = (60000).to_bytes(2, "little")
+    assert run(bad) == sz.SZ_ERR_CORRUPT                       # sub-stream length inconsistent
+    rng = np.random.default_rng(1)
+    for trial in range(8):                                      # random payload damage: no fault, no hang
+        bad = bytearray(ref)
+        pos = rng.integers(h["off_payload"], len(ref), 64)
+        for p in pos:
+            bad[p] = rng.integers(0, 256)
+        assert run(bad) in (sz.SZ_OK, sz.SZ_ERR_CORRUPT)
+    assert run(ref) == sz.SZ_OK
+
+
+def test_batch_equals_plain(sz, ctx, oracle):
+    xs = [synth.random_walk_f32(n, i) for i, n in enumerate([1, 5000, 2048, 123457, 0, 70000])]
+    ebs = [1e-3, 1e-4, 1e-2, 1e-5, 1e-4, 1e-3]
+    outs, nb = sz.sz_compress_batch(ctx, [x.cuda() for x in xs], ebs, 1)
+    sz.sz_sync(ctx)
+    for i, x in enumerate(xs):
+        C = 2048 if x.numel() <= (1 << 17) else 4096
+        ref = oracle.compress(x.numpy(), ebs[i], 1, C, C // 64)
+        assert outs[i][: nb[i]].cpu().numpy().tobytes() == ref
+    bufs = [outs[i][: nb[i]] for i in range(len(xs))]
+    ys = [torch.empty(max(x.numel(), 1), dtype=torch.float32, device="cuda") for x in xs]
+    no = sz.sz_decompress_batch(ctx, bufs, [nb[i] for i in range(len(xs))], ys)
+    sz.sz_sync(ctx)
+    for i, x in enumerate(xs):
+        assert no[i] == x.numel()
+        yr = oracle.decompress(outs[i][: nb[i]].cpu().numpy().tobytes())
+        assert np.array_equal(_bits(ys[i][: x.numel()].cpu().numpy()), _bits(yr))
+
+
+@pytest.mark.parametrize("field", ["xx", "vz"])
+def test_full_size_large_cosmology_array(sz, ctx, oracle, field):
+    """One array of the large cosmology snapshot (2^27 particles, 4096 halos)
+    at the size and launch configuration the benchmark uses."""
+    snap = synth.cosmology(1 << 27, 4096, 3, device="cuda")
+    x = snap[field]
+    del snap
+    out, nb = sz.sz_compress(ctx, x, 1e-4, 1)
+    sz.sz_sync(ctx)
+    got = out[: nb.value].cpu().numpy().tobytes()
+    x_cpu = x.cpu()
+    ref = oracle.compress(x_cpu.numpy(), 1e-4, 1, 8192, 128)
+    assert got == ref
+    y = torch.empty_like(x)
+    sz.sz_decompress(ctx, out[: nb.value], nb.value, y)
+    sz.sz_sync(ctx)
+    yr = oracle.decompress(ref)
+    assert np.array_equal(_bits(y.cpu().numpy()), _bits(yr))
