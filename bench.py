@@ -1,0 +1,406 @@
+"""Benchmark of the SZ-LV hot path on GB300.
+
+Workload (default): the large cosmology snapshot -- 2^27 particles, six
+float32 fields (3.2 GB), relative error bound 1e-4, 4096 halos.  One step is
+the whole hot path: compress the six arrays (range, quantize + histogram,
+codebook, encode) and decompress the six streams (decoder setup, decode), all
+on device-resident data.  Inputs (3.2 GB) exceed the 129 MB L2, so no flush is
+needed between steps.
+
+value       = uncompressed bytes / step time (compress + decompress), all ranks.
+e2e         = the same round trip through the C ABI from pinned host buffers:
+              H2D inputs, compress, D2H streams, H2D streams, decompress,
+              D2H outputs, all inside the timed region.
+roofline    = the dominant kernel's algorithmic bytes per launch over its
+              average launch time (CUDA events on its stream, inside the
+              timed region), against the measured HBM copy bandwidth.
+cpu_baseline= the CPU oracle on a bounded sample of the same arrays.
+
+Multi-GPU: one process per GPU (torchrun); each rank compresses its own
+snapshot (independent seeds, no collective on the data path; weak scaling).
+`--impl reference` times the CPU oracle instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FIELDS = ("xx", "yy", "zz", "vx", "vy", "vz")
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(v: float, ws: int) -> float:
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _sum_over_ranks(v: float, ws: int) -> float:
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def _traffic(kernel: str):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if the
+    kernel source is unchanged since the capture; else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+        e = d.get(kernel)
+        if not e:
+            return None
+        src = os.path.join(ROOT, "paper_1711_03888_gb300", "csrc", e["source"])
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if h != e["source_sha256_16"]:
+            return None
+        return float(e["bytes_per_launch_full"])
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline leg / reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_round_trip(arrays, eb):
+    """Round trip of each array through the oracle, one thread per array (the
+    paper's one-process-per-array model); returns (seconds, bytes)."""
+    import oracle
+    oracle.build()
+    from concurrent.futures import ThreadPoolExecutor
+
+    def one(x):
+        s = oracle.compress(x, eb, 1, 8192, 128)
+        oracle.decompress(s)
+        return len(s)
+
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=len(arrays)) as ex:
+        list(ex.map(one, arrays))
+    return time.perf_counter() - t0, sum(4 * a.size for a in arrays)
+
+
+def cpu_sample(snap, n_sample):
+    import numpy as np
+    return [np.ascontiguousarray(snap[f][:n_sample].cpu().numpy()) for f in FIELDS]
+
+
+# ---------------------------------------------------------------------------
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--log2n", type=int, default=27)
+    ap.add_argument("--eb", type=float, default=1e-4)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-log2n", type=int, default=24)
+    args = ap.parse_args()
+
+    ws, rank, local = _dist()
+    n = 1 << args.log2n
+    halos = 4096 if args.log2n == 27 else max(1, int(round(64 * n / (1 << 20))))
+    workload = f"large cosmology snapshot: 2^{args.log2n} particles x 6 float32 fields, {halos} halos, rel eb {args.eb:g}"
+    config = {"workload": workload, "particles": n, "fields": 6, "eb_rel": args.eb, "eb_kind": "relative",
+              "step": "compress 6 arrays + decompress 6 streams", "l2": "inputs (3.2 GB) larger than L2",
+              "parallelism": f"replicas x{ws} (independent snapshots, no data-path collective)"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        import synth
+        import torch
+        snap = synth.cosmology(n, halos, 3, device="cuda" if torch.cuda.is_available() else "cpu")
+        arrays = cpu_sample(snap, 1 << args.cpu_log2n)
+        del snap
+        for _ in range(args.warmup):
+            oracle_round_trip(arrays, args.eb)
+        tt, b = 0.0, 0
+        for _ in range(args.steps):
+            t, b = oracle_round_trip(arrays, args.eb)
+            tt += t
+        v = b * args.steps / tt / 1e9
+        sample = f"first 2^{args.cpu_log2n} elements of each of the 6 fields, one thread per field"
+        print(json.dumps({"impl": "reference", "metric": "round-trip (compress+decompress) throughput, uncompressed float32",
+                          "value": v, "unit": "GB/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                          "ms_per_step": 1e3 * tt / args.steps, "higher_is_better": True, "scaling": "weak",
+                          "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config,
+                          "cpu_baseline": {"value": v, "unit": "GB/s", "cores": len(arrays), "kind": "oracle",
+                                           "sample": sample},
+                          "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+        return
+
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import synth
+    import paper_1711_03888_gb300 as sz
+
+    snap = synth.cosmology(n, halos, 3 + rank, device="cuda")
+    xs = [snap[f] for f in FIELDS]
+    raw_bytes = 4 * n * len(xs)
+    ctx = sz.Context(local)
+    outs = [torch.empty(sz.sz_max_compressed_bytes(n), dtype=torch.uint8, device="cuda") for _ in xs]
+    ys = [torch.empty(n, dtype=torch.float32, device="cuda") for _ in xs]
+    stream = torch.cuda.current_stream()
+
+    def step(ev_mid=None):
+        # fully asynchronous: the decoder reads each stream's size from its
+        # header, so in_bytes is the buffer capacity and no host sync is needed
+        holders = []
+        for x, o in zip(xs, outs):
+            holders.append(sz.sz_compress(ctx, x, args.eb, sz.SZ_EB_REL, None, o)[1])
+        if ev_mid is not None:
+            ev_mid.record(stream)
+        for o, y in zip(outs, ys):
+            sz.sz_decompress(ctx, o, o.numel(), y)
+        return holders
+
+    # correctness guard on the benchmarked configuration: max error <= eb_abs
+    holders = step()
+    sz.sz_sync(ctx)
+    sizes = [h.value for h in holders]
+    for x, y in zip(xs, ys):
+        fin = torch.isfinite(x)
+        R = (x[fin].max().double() - x[fin].min().double()).item()
+        err = (x.double() - y.double()).abs().max().item()
+        assert err <= args.eb * R * (1 + 1e-12), f"error bound violated: {err} > {args.eb * R}"
+    ratio = raw_bytes / sum(sizes)
+
+    for _ in range(args.warmup):
+        step()
+        sz.sz_sync(ctx)
+    torch.cuda.synchronize()
+    _barrier(ws)
+    clocks = ClockSampler(local)
+    clocks.start()
+    sz.sz_profile_enable(ctx, True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    _barrier(ws)
+    t_wall0 = time.perf_counter()
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        holders = step(ev[i][1])
+        ev[i][2].record(stream)
+    sz.sz_sync(ctx)
+    sizes = [h.value for h in holders]
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    _barrier(ws)
+    prof = sz.sz_profile_read(ctx)
+    sz.sz_profile_enable(ctx, False)
+    clk = clocks.stop()
+    t_c = sum(e[0].elapsed_time(e[1]) for e in ev) / 1e3
+    t_d = sum(e[1].elapsed_time(e[2]) for e in ev) / 1e3
+    t_step = (t_c + t_d) / args.steps
+    t_step_max = _max_over_ranks(t_step, ws)
+    total_bytes = _sum_over_ranks(raw_bytes, ws)
+    value = total_bytes / t_step_max / 1e9
+    comp_gbs = raw_bytes / (t_c / args.steps) / 1e9
+    decomp_gbs = raw_bytes / (t_d / args.steps) / 1e9
+
+    # ---- roofline of the dominant kernel -----------------------------------
+    peak, peak_kind = _peaks()
+    stream_bytes = sum(sizes)
+    algo = {  # algorithmic bytes per launch (one array): reads + writes the kernel must make
+        "range": 4 * n,
+        "quant": 4 * n,
+        "encode": 4 * n + stream_bytes / len(xs),
+        "decode": stream_bytes / len(xs) + 4 * n,
+    }
+    kernels = {}
+    for ph, (cnt, ms) in prof.items():
+        if cnt == 0:
+            continue
+        avg = ms / cnt / 1e3
+        e = {"launches": cnt, "avg_ms": 1e3 * avg, "share": ms / sum(v[1] for v in prof.values())}
+        if ph in algo:
+            e["achieved_gbs"] = algo[ph] / avg / 1e9
+            e["frac"] = e["achieved_gbs"] / peak
+        kernels[ph] = e
+    dom = max((p for p in kernels if p in algo), key=lambda p: prof[p][1])
+    kname = {"encode": "encode_kernel", "decode": "decode_kernel", "quant": "quant_kernel",
+             "range": "range_kernel"}[dom]
+    roofline = {"bound": "hbm", "kernel": kname, "achieved": kernels[dom]["achieved_gbs"], "peak": peak,
+                "peak_kind": peak_kind, "unit": "GB/s", "frac": kernels[dom]["frac"],
+                "traffic": _traffic(kname),
+                "algorithmic_bytes_per_launch": algo[dom]}
+    launches = sum(c for c, _ in prof.values())
+
+    # ---- end to end through host buffers ------------------------------------
+    e2e = None
+    if not args.no_e2e:
+        hx = [x.cpu().pin_memory() for x in xs]
+        hs = [torch.empty(sz.sz_max_compressed_bytes(n), dtype=torch.uint8).pin_memory() for _ in xs]
+        hy = [torch.empty(n, dtype=torch.float32).pin_memory() for _ in xs]
+        dx = [torch.empty(n, dtype=torch.float32, device="cuda") for _ in xs]
+        ds = [torch.empty_like(o) for o in outs]
+        h2d = d2h = 0
+
+        def e2e_step():
+            nonlocal h2d, d2h
+            h2d = d2h = 0
+            hold = []
+            for a, b, o in zip(hx, dx, outs):
+                b.copy_(a, non_blocking=True)
+                hold.append(sz.sz_compress(ctx, b, args.eb, sz.SZ_EB_REL, None, o)[1])
+                h2d += 4 * n
+            sz.sz_sync(ctx)
+            sz_ = [h.value for h in hold]
+            for o, h, s_ in zip(outs, hs, sz_):
+                h[:s_].copy_(o[:s_], non_blocking=True)
+                d2h += s_
+            for h, d, s_ in zip(hs, ds, sz_):
+                d[:s_].copy_(h[:s_], non_blocking=True)
+                h2d += s_
+            for d, y, s_ in zip(ds, ys, sz_):
+                sz.sz_decompress(ctx, d, s_, y)
+            for y, h in zip(ys, hy):
+                h.copy_(y, non_blocking=True)
+                d2h += 4 * n
+            sz.sz_sync(ctx)
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        _barrier(ws)
+        k2 = max(1, min(args.steps, 3))
+        t0 = time.perf_counter()
+        for _ in range(k2):
+            e2e_step()
+        torch.cuda.synchronize()
+        te = _max_over_ranks((time.perf_counter() - t0) / k2, ws)
+        assert np.array_equal(hy[0][: 1 << 16].numpy().view(np.uint32), ys[0][: 1 << 16].cpu().numpy().view(np.uint32))
+        e2e = {"value": total_bytes / te / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "ms_per_step": 1e3 * te}
+        del hx, hs, hy, dx, ds
+
+    # ---- CPU oracle on a bounded sample (rank 0) -------------------------------
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        arrays = cpu_sample(snap, 1 << args.cpu_log2n)
+        t, b = oracle_round_trip(arrays, args.eb)
+        cpu = {"value": b / t / 1e9, "unit": "GB/s", "cores": len(arrays), "kind": "oracle",
+               "sample": f"first 2^{args.cpu_log2n} elements of each of the 6 fields, compress + decompress, "
+                         f"one thread per field"}
+
+    if rank == 0:
+        line = {
+            "metric": "round-trip (compress+decompress) throughput, uncompressed float32",
+            "value": value, "unit": "GB/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t_step_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config,
+            "compress_gbs": comp_gbs, "decompress_gbs": decomp_gbs,
+            "compress_frac_hbm": comp_gbs / peak, "decompress_frac_hbm": decomp_gbs / peak,
+            "ratio": ratio, "roofline": roofline, "kernels": kernels, "gpu_launches": launches,
+            "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "wall_s_timed": t_wall,
+        }
+        print(json.dumps(line))
+    ctx.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -151,6 +151,28 @@ sz_status sz_sync(sz_ctx* ctx, void* stream);
 /* Human-readable name of a status code (static string). */
 const char* sz_status_string(sz_status s);
 
+/* ---- tracing: per-phase kernel timing ------------------------------------ */
+
+/* Kernel phases of the path: range (a1), lattice + histogram (a2-a4),
+ * codebook + layout (a5, a8), encode (a6-a7), decoder setup, decode
+ * (a9-a11), MD reordering (R-index keys + segment sort + gather), and the
+ * batched persistent kernel. */
+typedef enum {
+    SZ_PHASE_RANGE = 0, SZ_PHASE_QUANT = 1, SZ_PHASE_CODEBOOK = 2, SZ_PHASE_ENCODE = 3,
+    SZ_PHASE_DECODE_SETUP = 4, SZ_PHASE_DECODE = 5, SZ_PHASE_REORDER = 6, SZ_PHASE_BATCH = 7,
+    SZ_NUM_PHASES = 8
+} sz_phase;
+
+/* Enable (on != 0) or disable tracing.  While enabled, the context records a
+ * CUDA event pair around every kernel it launches.  Enabling clears the
+ * counters. */
+sz_status sz_profile_enable(sz_ctx* ctx, int on);
+
+/* Wait for the recorded events and return, for each of the first nphases
+ * phases, the number of kernel launches and their summed device time in
+ * milliseconds (host arrays of nphases entries).  Clears the counters. */
+sz_status sz_profile_read(sz_ctx* ctx, uint64_t* launches, double* ms, int nphases);
+
 /* ---- serving: continuous batching of compress / decompress requests ---- */
 
 typedef enum { SZ_OP_COMPRESS = 0, SZ_OP_DECOMPRESS = 1 } sz_op;

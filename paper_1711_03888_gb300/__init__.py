@@ -33,7 +33,9 @@ HEADER_BYTES = 160
 
 EXPORTS = ("sz_ctx_create", "sz_ctx_destroy", "sz_max_compressed_bytes", "sz_compress", "sz_decompress",
            "sz_compress_batch", "sz_decompress_batch", "sz_compress_snapshot", "sz_sync", "sz_status_string",
+           "sz_profile_enable", "sz_profile_read",
            "sz_serve_start", "sz_serve_submit", "sz_serve_poll", "sz_serve_stop")
+PHASES = ("range", "quant", "codebook", "encode", "decode_setup", "decode", "reorder", "batch")
 
 
 class sz_params(C.Structure):
@@ -67,6 +69,8 @@ _sig = {
                                    C.POINTER(_sz), _vp, _vp]),
     "sz_sync": (_st, [_vp, _vp]),
     "sz_status_string": (C.c_char_p, [C.c_int]),
+    "sz_profile_enable": (_st, [_vp, C.c_int]),
+    "sz_profile_read": (_st, [_vp, C.POINTER(C.c_uint64), C.POINTER(C.c_double), C.c_int]),
     "sz_serve_start": (_st, [_vp, C.c_int]),
     "sz_serve_submit": (_st, [_vp, C.POINTER(sz_request), C.POINTER(C.c_uint64)]),
     "sz_serve_poll": (_st, [_vp, C.c_uint64, C.POINTER(sz_result)]),
@@ -226,6 +230,19 @@ def sz_sync(ctx: Context, stream=None, check: bool = True) -> int:
 
 def sz_status_string(status: int) -> str:
     return _lib.sz_status_string(status).decode()
+
+
+def sz_profile_enable(ctx: Context, on: bool = True):
+    _check(_lib.sz_profile_enable(ctx.handle, 1 if on else 0), "sz_profile_enable")
+
+
+def sz_profile_read(ctx: Context) -> dict:
+    """{phase: (launches, milliseconds)} since tracing was enabled or last read."""
+    k = len(PHASES)
+    n = (C.c_uint64 * k)()
+    ms = (C.c_double * k)()
+    _check(_lib.sz_profile_read(ctx.handle, n, ms, k), "sz_profile_read")
+    return {PHASES[i]: (int(n[i]), float(ms[i])) for i in range(k)}
 
 
 def sz_serve_start(ctx: Context, slots: int):

@@ -149,20 +149,19 @@ __global__ void __launch_bounds__(kSetupThreads) decode_setup_kernel(DecompressA
     if (tid == 0) st->dec_ok = 1;
 }
 
-// bit reader over the chunk payload (global, bounds-checked)
+// bit reader over the chunk payload (global, bounds-checked: words at or past
+// `end` read as zero, so a bad stream cannot read outside it)
 struct BitReader {
     const uint32_t* words;
     uint64_t pos, end;            // word index of the next refill, end (exclusive)
     unsigned long long win;       // bits MSB-aligned
     uint32_t avail;
-    bool bad;
     __device__ __forceinline__ void init(const uint32_t* w, uint64_t begin_bit, uint64_t end_word) {
         words = w;
         end = end_word;
         pos = begin_bit >> 5;
         win = 0;
         avail = 0;
-        bad = false;
         uint32_t skip = (uint32_t)(begin_bit & 31u);
         refill();
         refill();
@@ -183,13 +182,40 @@ struct BitReader {
     }
 };
 
-__global__ void __launch_bounds__(kDecThreads) decode_kernel(DecompressArgs a) {
+// Team-level primitives: a team is 64 threads (2 warps) with its own named
+// barrier (id team + 1) decoding one chunk at a time.
+__device__ __forceinline__ void team_sync(int team) {
+    asm volatile("bar.sync %0, %1;" :: "r"(team + 1), "r"(kDecThreads) : "memory");
+}
+
+template <typename T>
+__device__ __forceinline__ T team_exclusive_scan(T v, T* ws, int team, int k, T* total) {
+    T inc = warp_inclusive_scan(v);
+    if ((k & 31) == 31) ws[k >> 5] = inc;
+    team_sync(team);
+    T w0 = ws[0];
+    T r = inc - v + ((k >> 5) ? w0 : T(0));
+    *total = w0 + ws[1];
+    team_sync(team);
+    return r;
+}
+
+constexpr int kTeams = 6;
+constexpr int kDecBlock = kTeams * kDecThreads;        // 384
+constexpr int kDecLutBits = 12;
+
+struct DecSmem {
+    uint32_t lut[1 << kDecLutBits];       // sym << 8 | len for codes of <= 12 bits, else 0
+    uint32_t lim[kMaxLen + 2];            // left-justified (24-bit) end of each length's codes
+    uint32_t first[kMaxLen + 2], base[kMaxLen + 2];
+    uint32_t ws32[kTeams][2], ws32b[kTeams][2];
+    long long ws64[kTeams][2];
+    uint32_t bad[kTeams];
+};
+
+__global__ void __launch_bounds__(kDecBlock, 1) decode_kernel(DecompressArgs a) {
+    __shared__ DecSmem sm;
     extern __shared__ uint4 dyn_smem[];
-    uint32_t* xs = reinterpret_cast<uint32_t*>(dyn_smem);
-    __shared__ uint32_t ws32[4], ws32b[4];
-    __shared__ unsigned long long ws64[4];
-    __shared__ uint32_t s_first[kMaxLen + 2], s_count[kMaxLen + 2], s_base[kMaxLen + 2];
-    __shared__ uint32_t s_bad, s_bad_hdr;
     const ArrayState* st = a.st;
     const int tid = threadIdx.x;
     if (!st->dec_ok) return;
@@ -212,33 +238,55 @@ __global__ void __launch_bounds__(kDecThreads) decode_kernel(DecompressArgs a) {
     const uint16_t* sublen = reinterpret_cast<const uint16_t*>(in + st->off[S_SUBLEN]);
     const uint8_t* escs = in + st->off[S_ESC];
     const uint32_t* payload = reinterpret_cast<const uint32_t*>(in + st->off[S_PAYLOAD]);
-    for (int l = tid; l < kMaxLen + 2; l += kDecThreads) {
-        s_first[l] = st->first[l];
-        s_count[l] = st->count[l];
-        s_base[l] = st->base[l];
+
+    // block-wide: direct lookup table for codes of <= 12 bits, limits for the rest
+    for (uint32_t i = tid; i < (1u << kDecLutBits); i += kDecBlock) sm.lut[i] = 0u;
+    __syncthreads();
+    if (tid < kMaxLen + 2) {
+        const uint32_t l = tid;
+        sm.first[l] = st->first[l];
+        sm.base[l] = st->base[l];
+        sm.lim[l] = (l >= 1 && l <= (uint32_t)kMaxLen) ? ((st->first[l] + st->count[l]) << (kMaxLen - l)) : 0u;
     }
-    const bool vec = ((uintptr_t)a.out & 15u) == 0;
+    {
+        const uint32_t m = (uint32_t)rd64(in + H_NSYM);
+        for (uint32_t p = tid; p < m; p += kDecBlock) {
+            // symbols in (length, symbol) order: find this position's length
+            uint32_t l = 1;
+            while (l < (uint32_t)kMaxLen && p >= st->base[l] + st->count[l]) ++l;
+            if (l <= (uint32_t)kDecLutBits) {
+                uint32_t code = st->first[l] + (p - st->base[l]);
+                uint32_t lo = code << (kDecLutBits - l), hi = (code + 1) << (kDecLutBits - l);
+                uint32_t v = ((uint32_t)a.by_len[p] << 8) | l;
+                for (uint32_t e = lo; e < hi; ++e) sm.lut[e] = v;
+            }
+        }
+    }
     __syncthreads();
 
-    for (uint64_t c = blockIdx.x; c < nc; c += gridDim.x) {
+    const int team = tid / kDecThreads, k = tid % kDecThreads;
+    const int teams_active = umin32(kTeams, (uint32_t)(kTeams * 8192u) / C);
+    if (team >= teams_active) return;
+    uint32_t* xs = reinterpret_cast<uint32_t*>(dyn_smem) + (size_t)team * C;
+    const bool vec = ((uintptr_t)a.out & 15u) == 0;
+    const uint64_t stride = (uint64_t)gridDim.x * teams_active;
+
+    for (uint64_t c = (uint64_t)blockIdx.x * teams_active + team; c < nc; c += stride) {
         const uint64_t base = c * C;
         const uint32_t cnt = (uint32_t)umin64(C, n - base);
         const uint64_t wb = cword[c], we = cword[c + 1];
         const uint64_t eb = cesc[c], ee = cesc[c + 1];
-        if (tid == 0) {
-            s_bad_hdr = (wb > we || we > pw || eb > ee || ee > E) ? 1u : 0u;
-            s_bad = 0u;
-        }
-        const uint32_t k = tid, e0 = k * G;
-        const uint32_t nsym = e0 < cnt ? min(G, cnt - e0) : 0u;
+        const bool hdr_bad = (wb > we || we > pw || eb > ee || ee > E);
+        const uint32_t e0 = k * G;
+        const uint32_t nsym = e0 < cnt ? umin32(G, cnt - e0) : 0u;
         const uint32_t sl = sublen[c * kSubPerChunk + k];
         uint32_t tot_bits;
-        const uint32_t start = block_exclusive_scan<kDecThreads>(sl, ws32, &tot_bits);
-        if (s_bad_hdr || (uint64_t)tot_bits > 32ull * (we - wb)) {
-            if (tid == 0) raise_err(a.err, E_CORRUPT);
+        const uint32_t start = team_exclusive_scan<uint32_t>(sl, sm.ws32[team], team, k, &tot_bits);
+        if (hdr_bad || (uint64_t)tot_bits > 32ull * (we - wb)) {
+            if (k == 0) raise_err(a.err, E_CORRUPT);
             return;
         }
-        // ---- phase 1: decode the sub-stream, 4 symbols per shared store --------------
+        // ---- phase 1: decode the sub-stream ------------------------------------------
         BitReader br;
         br.init(payload, 32ull * wb + start, we);
         int dsum = 0;
@@ -248,45 +296,42 @@ __global__ void __launch_bounds__(kDecThreads) decode_kernel(DecompressArgs a) {
             uint32_t sy[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
-                if (j4 + t < nsym && !bad) {
-                    uint32_t top = (uint32_t)(br.win >> (64 - kLutBits));
-                    uint32_t ent = __ldg(a.lut + top);
+                if (j4 + t < nsym) {
+                    const uint32_t w24 = (uint32_t)(br.win >> 40);
+                    uint32_t ent = sm.lut[w24 >> (kMaxLen - kDecLutBits)];
                     uint32_t sym, len;
                     if (ent) {
                         sym = ent >> 8;
                         len = ent & 255u;
                     } else {
-                        sym = 0; len = 0;
-                        for (uint32_t l = kLutBits + 1; l <= (uint32_t)kMaxLen; ++l) {
-                            uint32_t code = (uint32_t)(br.win >> (64 - l));
-                            uint32_t d = code - s_first[l];
-                            if (d < s_count[l]) { sym = a.by_len[s_base[l] + d]; len = l; break; }
-                        }
-                        if (!len) bad = true;
+                        len = kDecLutBits + 1;
+                        while (len <= (uint32_t)kMaxLen && w24 >= sm.lim[len]) ++len;
+                        if (len > (uint32_t)kMaxLen) { bad = true; len = 0; sym = 0; }
+                        else sym = a.by_len[sm.base[len] + (w24 >> (kMaxLen - len)) - sm.first[len]];
                     }
                     br.consume(len);
                     used += len;
                     sy[t] = sym;
-                    if (sym == 0u) ++nesc;
-                    else dsum += (int)sym - kRadius;
+                    nesc += (sym == 0u);
+                    dsum += (sym == 0u) ? 0 : (int)sym - kRadius;
                 }
             }
             *reinterpret_cast<uint4*>(&xs[swz(e0 + j4, gshift)]) = make_uint4(sy[0], sy[1], sy[2], sy[3]);
         }
         bad = bad || used != sl;
         // ---- escapes and the block-wide prefix ----------------------------------------
-        if (bad) atomicOr(&s_bad, 1u);
         uint32_t tot_esc;
-        const uint32_t eoff = block_exclusive_scan<kDecThreads>(nesc, ws32b, &tot_esc);
-        if (s_bad || eb + tot_esc != ee) {
-            if (tid == 0) raise_err(a.err, E_CORRUPT);
+        const uint32_t eoff = team_exclusive_scan<uint32_t>(nesc + (bad ? 0x10000u : 0u), sm.ws32b[team], team, k,
+                                                             &tot_esc);
+        if ((tot_esc >> 16) || eb + tot_esc != ee) {
+            if (k == 0) raise_err(a.err, E_CORRUPT);
             return;
         }
         long long sum = dsum;
         for (uint32_t t = 0; t < nesc; ++t)
             sum += *reinterpret_cast<const long long*>(escs + (uint64_t)kEscBytes * (eb + eoff + t));
         long long tot_sum;
-        const long long pre = block_exclusive_scan<kDecThreads, long long>(sum, reinterpret_cast<long long*>(ws64), &tot_sum);
+        const long long pre = team_exclusive_scan<long long>(sum, sm.ws64[team], team, k, &tot_sum);
         // ---- phase 2: reconstruct in place -----------------------------------------
         long long q = anchor[c] + pre;
         uint64_t ecur = eb + eoff;
@@ -313,10 +358,10 @@ __global__ void __launch_bounds__(kDecThreads) decode_kernel(DecompressArgs a) {
             }
             *slot = make_uint4(ov[0], ov[1], ov[2], ov[3]);
         }
-        __syncthreads();
+        team_sync(team);
         // ---- phase 3: coalesced store ---------------------------------------------
         float* dst = a.out + base;
-        for (uint32_t e = 4 * tid; e < cnt; e += 4 * kDecThreads) {
+        for (uint32_t e = 4 * k; e < cnt; e += 4 * kDecThreads) {
             uint4 v = *reinterpret_cast<const uint4*>(&xs[swz(e, gshift)]);
             if (vec && e + 3 < cnt) {
                 *reinterpret_cast<uint4*>(dst + e) = v;
@@ -325,7 +370,7 @@ __global__ void __launch_bounds__(kDecThreads) decode_kernel(DecompressArgs a) {
                 for (int j = 0; j < 4 && e + j < cnt; ++j) dst[e + j] = __uint_as_float(vv[j]);
             }
         }
-        __syncthreads();
+        team_sync(team);
     }
 }
 
@@ -341,13 +386,13 @@ void launch_decode(const DecompressArgs* a, int k, void* stream) {
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (sms <= 0) sms = 148;
     }
-    const size_t smem = 16384u * 4u;
+    const size_t smem = (size_t)kTeams * 8192u * 4u;
     static bool configured = false;
     if (!configured) {
         cudaFuncSetAttribute(decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         configured = true;
     }
-    for (int i = 0; i < k; ++i) decode_kernel<<<sms * 8, kDecThreads, smem, (cudaStream_t)stream>>>(a[i]);
+    for (int i = 0; i < k; ++i) decode_kernel<<<sms, kDecBlock, smem, (cudaStream_t)stream>>>(a[i]);
 }
 
 }  // namespace szg

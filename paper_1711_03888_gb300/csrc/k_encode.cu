@@ -1,27 +1,27 @@
 // k_encode.cu -- a6 + a7: Huffman encoding of the codes into chunked
 // sub-streams, the chunk tables and the escape records.
 //
-// One 64-thread block per chunk of C elements; thread k owns sub-stream k
-// (G = C/64 consecutive elements).  The chunk is staged in shared memory with
-// the XOR swizzle of sz_device.cuh, so the coalesced float4 copy-in and the
-// per-thread float4 walk are both conflict-free.  Pass A recomputes the
-// lattice codes (a2-a3) and looks up (codeword, length); a block scan gives
-// every thread its start bit, and a decoupled look-back over chunk tickets
-// gives the chunk's word offset in the payload.  Pass B packs codewords
-// MSB-first into a shared buffer (interior words by plain stores, the two
-// boundary words of each thread by atomicOr) and the chunk is copied out
-// with 128-bit stores.  Escape records are rebuilt from global memory (rare).
+// One block of C/32 threads per chunk of C elements (chunks are taken in
+// ticket order so the decoupled look-back always waits on running blocks).
+//  pass 1 (coalesced): each thread takes one float4 per 4*blockDim step,
+//    recomputes the lattice codes (a2-a3; the predecessor comes from the
+//    neighbouring lane), looks up (codeword, length) and stores the packed
+//    entry in shared memory, swizzled so the next pass is conflict-free;
+//  pass 2: thread t loads the 32 consecutive entries t*32 .. t*32+31 into
+//    registers; block scans give its start bit and escape index; the chunk's
+//    word offset comes from the look-back over preceding chunks;
+//  pass 3: thread t packs its 32 codewords MSB-first into the (now free)
+//    shared buffer -- interior words by plain stores, its first and last
+//    word by atomicOr -- and the chunk leaves with 128-bit stores.
+// Sub-stream k (G = C/64 elements) is threads [kG/32, (k+1)G/32), so its bit
+// length is a shuffle reduction over G/32 lanes.  Escape records are rebuilt
+// from global memory (rare).
 #include "sz_device.cuh"
 
 namespace szg {
 
-constexpr int kEncThreads = kSubPerChunk;     // 64
 constexpr uint32_t kLookbackSpins = 1u << 22;
-
-__device__ __forceinline__ void flush_word(uint32_t* pay, uint32_t w, uint32_t v, bool shared_word) {
-    if (shared_word) atomicOr(&pay[w], v);
-    else pay[w] = v;
-}
+constexpr int kRun = 32;                    // consecutive elements per thread in passes 2-3
 
 __device__ void raw_copy(const CompressArgs& a) {
     const ArrayState* st = a.st;
@@ -34,86 +34,91 @@ __device__ void raw_copy(const CompressArgs& a) {
         dst[i] = (i < n) ? __ldg(src + i) : 0u;
 }
 
-__global__ void __launch_bounds__(kEncThreads) encode_kernel(CompressArgs a) {
+template <int NT>
+__global__ void __launch_bounds__(NT, (NT >= 256 ? 1024 / NT : 8)) encode_kernel(CompressArgs a) {
+    constexpr int C = NT * kRun;
     extern __shared__ uint4 dyn_smem[];
-    uint32_t* xs = reinterpret_cast<uint32_t*>(dyn_smem);   // C words, swizzled
-    uint32_t* pay = xs + a.C;                                 // payload words of the chunk
-    __shared__ uint32_t ws32[4], ws32b[4];
+    uint32_t* buf = reinterpret_cast<uint32_t*>(dyn_smem);   // C words: codes, then payload
+    __shared__ uint32_t ws32[NT / 32 + 1], ws32b[NT / 32 + 1];
     __shared__ uint32_t s_c;
     __shared__ unsigned long long s_prefix;
     ArrayState* st = a.st;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31;
     if (st->raw) { raw_copy(a); return; }
-    if (a.n == 0) return;
     if (tid == 0) s_c = atomicAdd(&st->ticket, 1u);
     __syncthreads();
     const uint32_t c = s_c;
     if (c >= a.n_chunks) return;
 
     const LatticeParams P = make_params(range_eb_abs(a.eb, a.eb_kind, st->min_key, st->max_key, st->any_finite));
-    const uint32_t C = a.C, G = a.G, gshift = 31 - __clz(G);
     const uint64_t n = a.n, base = (uint64_t)c * C;
     const uint32_t cnt = (uint32_t)umin64(C, n - base);
     const float* in = a.in;
     const bool vec = ((uintptr_t)in & 15u) == 0;
+    const uint32_t* enc = a.enc;
 
-    // ---- stage the chunk -------------------------------------------------------
-    for (uint32_t e = 4 * tid; e < C; e += 4 * kEncThreads) {
-        float4 v;
+    // ---- pass 1: codes and (codeword, length), coalesced -----------------------
+    long long anchor = 0;
+#pragma unroll 2
+    for (uint32_t e = 4 * tid; e < (uint32_t)C; e += 4 * NT) {
+        float x[4];
         if (vec && e + 3 < cnt) {
-            v = __ldg(reinterpret_cast<const float4*>(in + base + e));
+            float4 v = __ldg(reinterpret_cast<const float4*>(in + base + e));
+            x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
         } else {
-            v.x = (e + 0 < cnt) ? __ldg(in + base + e + 0) : 0.0f;
-            v.y = (e + 1 < cnt) ? __ldg(in + base + e + 1) : 0.0f;
-            v.z = (e + 2 < cnt) ? __ldg(in + base + e + 2) : 0.0f;
-            v.w = (e + 3 < cnt) ? __ldg(in + base + e + 3) : 0.0f;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) x[j] = (e + j < cnt) ? __ldg(in + base + e + j) : 0.0f;
         }
-        *reinterpret_cast<float4*>(&xs[swz(e, gshift)]) = v;
-    }
-    __syncthreads();
-
-    // ---- pass A: codes, lengths, escapes ------------------------------------------
-    const uint32_t k = tid, e0 = k * G;
-    long long qprev = 0;
-    if (e0 < cnt) {
-        bool vv;
-        if (e0 == 0) {
-            if (base > 0) lattice_q(__ldg(in + base - 1), P, qprev, vv);
-        } else {
-            lattice_q(__uint_as_float(xs[swz(e0 - 1, gshift)]), P, qprev, vv);
+        long long q[4];
+        bool vb[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) lattice_q(x[j], P, q[j], vb[j]);
+        long long qprev = __shfl_up_sync(0xffffffffu, q[3], 1);
+        if (lane == 0) {
+            qprev = 0;
+            if (base + e > 0 && e < cnt) {
+                bool vv;
+                lattice_q(__ldg(in + base + e - 1), P, qprev, vv);
+            }
+            if (e == 0) anchor = qprev;
         }
-    }
-    __syncthreads();   // everyone has read its predecessor before slots are overwritten
-    const long long anchor = qprev;
-    uint32_t bits = 0, escs = 0;
-    for (uint32_t m4 = 0; m4 < G; m4 += 4) {
-        const uint32_t e = e0 + m4;
-        uint4* slot = reinterpret_cast<uint4*>(&xs[swz(e, gshift)]);
-        float4 v = *reinterpret_cast<float4*>(slot);
-        float xv[4] = {v.x, v.y, v.z, v.w};
         uint32_t pk[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             pk[j] = 0u;
             if (e + j < cnt) {
-                long long q;
-                bool vb;
-                lattice_q(xv[j], P, q, vb);
-                uint32_t code = make_code(q, qprev, vb);
-                qprev = q;
-                uint32_t ent = __ldg(&a.enc[code]);
-                uint32_t len = ent & 31u;
-                bits += len;
-                escs += (code == 0u);
-                pk[j] = ((ent >> 5) << 6) | (len << 1) | (code == 0u ? 1u : 0u);
+                uint32_t code = make_code(q[j], j == 0 ? qprev : q[j - 1], vb[j]);
+                uint32_t ent = __ldg(enc + code);
+                pk[j] = ((ent >> 5) << 6) | ((ent & 31u) << 1) | (code == 0u ? 1u : 0u);
             }
         }
-        *slot = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        *reinterpret_cast<uint4*>(&buf[swz(e, 5)]) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    }
+    __syncthreads();
+
+    // ---- pass 2: this thread's 32 consecutive entries ---------------------------
+    const uint32_t e0 = tid * kRun;
+    uint32_t r[kRun];
+#pragma unroll
+    for (int m = 0; m < kRun / 4; ++m) {
+        uint4 v = *reinterpret_cast<const uint4*>(&buf[swz(e0 + 4 * m, 5)]);
+        r[4 * m] = v.x; r[4 * m + 1] = v.y; r[4 * m + 2] = v.z; r[4 * m + 3] = v.w;
+    }
+    uint32_t bits = 0, escs = 0;
+#pragma unroll
+    for (int j = 0; j < kRun; ++j) {
+        bits += (r[j] >> 1) & 31u;
+        escs += r[j] & 1u;
     }
     uint32_t chunk_bits, chunk_escs;
-    const uint32_t start = block_exclusive_scan<kEncThreads>(bits, ws32, &chunk_bits);
-    const uint32_t eoff = block_exclusive_scan<kEncThreads>(escs, ws32b, &chunk_escs);
+    const uint32_t start = block_exclusive_scan<NT>(bits, ws32, &chunk_bits);
+    const uint32_t eoff = block_exclusive_scan<NT>(escs, ws32b, &chunk_escs);
     const uint32_t chunk_words = ((chunk_bits + 127u) >> 7) << 2;
+    // sub-stream bit length: reduce over the G/32 lanes that share sub-stream
+    constexpr int kLanesPerSub = C / kSubPerChunk / kRun;   // 1, 2, 4 or 8
+    uint32_t sub_bits = bits;
+#pragma unroll
+    for (int o = 1; o < kLanesPerSub; o <<= 1) sub_bits += __shfl_xor_sync(0xffffffffu, sub_bits, o);
 
     // ---- decoupled look-back: word offset of this chunk ------------------------
     if (tid == 0) {
@@ -150,6 +155,8 @@ __global__ void __launch_bounds__(kEncThreads) encode_kernel(CompressArgs a) {
         }
         s_prefix = bad ? ~0ull : excl;
     }
+    // zero the payload area (the code entries are in registers now)
+    for (uint32_t w = tid; w < chunk_words; w += NT) buf[w] = 0u;
     __syncthreads();
     const unsigned long long prefix = s_prefix;
     if (prefix == ~0ull) return;
@@ -160,8 +167,11 @@ __global__ void __launch_bounds__(kEncThreads) encode_kernel(CompressArgs a) {
     const bool tables_ok = off_payload <= a.out_cap;
     const uint64_t chunk_end = off_payload + 4ull * (prefix + chunk_words);
     if (tables_ok) {
-        reinterpret_cast<uint16_t*>(out + st->off[S_SUBLEN])[(uint64_t)c * kSubPerChunk + k] =
-            (uint16_t)(e0 < cnt ? bits : 0u);
+        if ((tid % kLanesPerSub) == 0) {
+            const uint32_t k = tid / kLanesPerSub;
+            reinterpret_cast<uint16_t*>(out + st->off[S_SUBLEN])[(uint64_t)c * kSubPerChunk + k] =
+                (uint16_t)(e0 < cnt ? sub_bits : 0u);
+        }
         if (tid == 0) {
             reinterpret_cast<uint64_t*>(out + st->off[S_CWORD])[c] = prefix;
             reinterpret_cast<long long*>(out + st->off[S_ANCHOR])[c] = anchor;
@@ -182,71 +192,77 @@ __global__ void __launch_bounds__(kEncThreads) encode_kernel(CompressArgs a) {
     if (escs) {
         uint8_t* esc_base = out + st->off[S_ESC] + (uint64_t)kEscBytes * (a.chunk_esc[c] + eoff);
         uint32_t idx = 0;
-        for (uint32_t m1 = 0; m1 < G && e0 + m1 < cnt; ++m1) {
-            if (xs[swz(e0 + m1, gshift)] & 1u) {
-                uint64_t i = base + e0 + m1;
+#pragma unroll
+        for (int j = 0; j < kRun; ++j) {
+            if (r[j] & 1u) {
+                uint64_t i = base + e0 + j;
                 float x = __ldg(in + i);
                 long long q, qp = 0;
                 bool vb, vv;
                 lattice_q(x, P, q, vb);
                 if (i > 0) lattice_q(__ldg(in + i - 1), P, qp, vv);
-                uint8_t* r = esc_base + (uint64_t)kEscBytes * idx++;
-                *reinterpret_cast<long long*>(r) = q - qp;
-                *reinterpret_cast<uint32_t*>(r + 8) = vb ? __float_as_uint(x) : 0u;
-                *reinterpret_cast<uint32_t*>(r + 12) = vb ? 1u : 0u;
+                uint8_t* rec = esc_base + (uint64_t)kEscBytes * idx++;
+                *reinterpret_cast<long long*>(rec) = q - qp;
+                *reinterpret_cast<uint32_t*>(rec + 8) = vb ? __float_as_uint(x) : 0u;
+                *reinterpret_cast<uint32_t*>(rec + 12) = vb ? 1u : 0u;
             }
         }
     }
 
-    // ---- pass B: pack --------------------------------------------------------------
-    for (uint32_t w = tid; w < chunk_words; w += kEncThreads) pay[w] = 0u;
-    __syncthreads();
+    // ---- pass 3: pack ---------------------------------------------------------------
     {
         uint32_t word = start >> 5, fill = start & 31u, cur = 0u;
         bool first = true;
-        for (uint32_t m4 = 0; m4 < G; m4 += 4) {
-            uint4 p4 = *reinterpret_cast<const uint4*>(&xs[swz(e0 + m4, gshift)]);
-            uint32_t pk[4] = {p4.x, p4.y, p4.z, p4.w};
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                uint32_t len = (pk[j] >> 1) & 31u;
-                if (len == 0u) continue;
-                uint32_t cw = pk[j] >> 6;
-                uint32_t room = 32u - fill;
-                if (len < room) {
-                    cur |= cw << (room - len);
-                    fill += len;
-                } else {
-                    uint32_t spill = len - room;          // 0..23
-                    cur |= cw >> spill;
-                    flush_word(pay, word, cur, first);
-                    first = false;
-                    ++word;
-                    cur = spill ? (cw << (32u - spill)) : 0u;
-                    fill = spill;
-                }
+        for (int j = 0; j < kRun; ++j) {
+            const uint32_t len = (r[j] >> 1) & 31u;
+            const uint32_t cw = r[j] >> 6;
+            const uint32_t room = 32u - fill;
+            if (len < room) {
+                cur |= cw << (room - len);   // len == 0 leaves cur unchanged
+                fill += len;
+            } else {
+                const uint32_t spill = len - room;   // 0..23
+                cur |= cw >> spill;
+                if (first) atomicOr(&buf[word], cur); else buf[word] = cur;
+                first = false;
+                ++word;
+                cur = spill ? (cw << (32u - spill)) : 0u;
+                fill = spill;
             }
         }
-        if (fill) flush_word(pay, word, cur, true);
+        if (fill) atomicOr(&buf[word], cur);
     }
     __syncthreads();
     if (chunk_end <= a.out_cap) {
         uint4* dst = reinterpret_cast<uint4*>(out + off_payload + 4ull * prefix);
-        const uint4* src = reinterpret_cast<const uint4*>(pay);
-        for (uint32_t w4 = tid; w4 < chunk_words / 4; w4 += kEncThreads) dst[w4] = src[w4];
+        const uint4* src = reinterpret_cast<const uint4*>(buf);
+        for (uint32_t w4 = tid; w4 < chunk_words / 4; w4 += NT) dst[w4] = src[w4];
     }
 }
 
+template <int NT>
+static void launch_encode_t(const CompressArgs& a, cudaStream_t s) {
+    const size_t smem = (size_t)NT * kRun * 4u;
+    static bool configured = false;
+    if (!configured) {
+        cudaFuncSetAttribute(encode_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        configured = true;
+    }
+    encode_kernel<NT><<<a.n_chunks, NT, smem, s>>>(a);
+}
+
 void launch_encode(const CompressArgs* a, int k, void* stream) {
+    cudaStream_t s = (cudaStream_t)stream;
     for (int i = 0; i < k; ++i) {
         if (a[i].n == 0) continue;
-        size_t smem = (size_t)a[i].C * 4u + ((size_t)a[i].C * 3u / 4u + 4u) * 4u;
-        static size_t configured = 0;
-        if (smem > configured) {
-            cudaFuncSetAttribute(encode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            configured = smem;
+        switch (a[i].C) {
+            case 2048: launch_encode_t<64>(a[i], s); break;
+            case 4096: launch_encode_t<128>(a[i], s); break;
+            case 8192: launch_encode_t<256>(a[i], s); break;
+            case 16384: launch_encode_t<512>(a[i], s); break;
+            default: break;
         }
-        encode_kernel<<<a[i].n_chunks, kEncThreads, smem, (cudaStream_t)stream>>>(a[i]);
     }
 }
 

@@ -143,20 +143,40 @@ sz_status validate_compress(const float* d_in, size_t n, double eb, sz_eb_kind k
     return SZ_OK;
 }
 
+static cudaEvent_t prof_event(sz_ctx* ctx) {
+    if (ctx->prof_used < ctx->ev_pool.size()) return ctx->ev_pool[ctx->prof_used++];
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+    ctx->ev_pool.push_back(e);
+    ctx->prof_used++;
+    return e;
+}
+
+ProfScope::ProfScope(sz_ctx* c, int ph, cudaStream_t st) : ctx(c), s(st), phase(ph) {
+    if (ctx->prof_on && (a = prof_event(ctx))) cudaEventRecord(a, s);
+}
+ProfScope::~ProfScope() {
+    if (!a) return;
+    cudaEvent_t b = prof_event(ctx);
+    if (!b) return;
+    cudaEventRecord(b, s);
+    ctx->prof.push_back({phase, a, b});
+}
+
 // The four launches of one array's compression (range, quantize + histogram,
 // codebook + layout, encode) followed by the result copy.
 sz_status enqueue_compress(sz_ctx* ctx, const CompressArgs& a, size_t* out_bytes, cudaStream_t s) {
-    launch_range(&a, 1, s);
-    launch_quant(&a, 1, s);
-    launch_codebook(&a, 1, s);
-    launch_encode(&a, 1, s);
+    { ProfScope p(ctx, SZ_PHASE_RANGE, s); launch_range(&a, 1, s); }
+    { ProfScope p(ctx, SZ_PHASE_QUANT, s); launch_quant(&a, 1, s); }
+    { ProfScope p(ctx, SZ_PHASE_CODEBOOK, s); launch_codebook(&a, 1, s); }
+    if (a.n) { ProfScope p(ctx, SZ_PHASE_ENCODE, s); launch_encode(&a, 1, s); }
     if (cudaPeekAtLastError() != cudaSuccess) { cudaGetLastError(); return SZ_ERR_CUDA; }
     return queue_result(ctx, &a.st->total_bytes, out_bytes, s);
 }
 
 sz_status enqueue_decompress(sz_ctx* ctx, const DecompressArgs& d, size_t* n_out, cudaStream_t s) {
-    launch_decode_setup(&d, 1, s);
-    launch_decode(&d, 1, s);
+    { ProfScope p(ctx, SZ_PHASE_DECODE_SETUP, s); launch_decode_setup(&d, 1, s); }
+    { ProfScope p(ctx, SZ_PHASE_DECODE, s); launch_decode(&d, 1, s); }
     if (cudaPeekAtLastError() != cudaSuccess) { cudaGetLastError(); return SZ_ERR_CUDA; }
     return queue_result(ctx, &d.st->n_out, n_out, s);
 }
@@ -202,6 +222,7 @@ sz_status sz_ctx_destroy(sz_ctx* ctx) {
     cudaDeviceSynchronize();
     ctx->free_workspace();
     ctx->free_extra();
+    for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
     if (ctx->d_err) cudaFree(ctx->d_err);
     if (ctx->h_res) cudaFreeHost(ctx->h_res);
     delete ctx;
@@ -265,6 +286,32 @@ sz_status sz_sync(sz_ctx* ctx, void* stream) {
     if (err & E_CAPACITY) return SZ_ERR_CAPACITY;
     if (err) return SZ_ERR_CUDA;
     return SZ_OK;
+}
+
+sz_status sz_profile_enable(sz_ctx* ctx, int on) {
+    if (!ctx) return SZ_ERR_ARG;
+    cudaSetDevice(ctx->device);
+    if (!ctx->prof.empty()) cudaEventSynchronize(ctx->prof.back().b);
+    ctx->prof.clear();
+    ctx->prof_used = 0;
+    ctx->prof_on = on != 0;
+    return SZ_OK;
+}
+
+sz_status sz_profile_read(sz_ctx* ctx, uint64_t* launches, double* ms, int nphases) {
+    if (!ctx || nphases < 0 || (nphases && (!launches || !ms))) return SZ_ERR_ARG;
+    cudaSetDevice(ctx->device);
+    for (int i = 0; i < nphases; ++i) { launches[i] = 0; ms[i] = 0.0; }
+    sz_status st = SZ_OK;
+    if (!ctx->prof.empty() && cudaEventSynchronize(ctx->prof.back().b) != cudaSuccess) st = SZ_ERR_CUDA;
+    for (auto& r : ctx->prof) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess) { cudaGetLastError(); st = SZ_ERR_CUDA; continue; }
+        if (r.phase < nphases) { launches[r.phase]++; ms[r.phase] += t; }
+    }
+    ctx->prof.clear();
+    ctx->prof_used = 0;
+    return st;
 }
 
 const char* sz_status_string(sz_status s) {

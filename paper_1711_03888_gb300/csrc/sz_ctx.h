@@ -35,12 +35,27 @@ struct sz_ctx {
     size_t md_bytes = 0;
     // serving loop
     sz_serve_state* serve = nullptr;
+    // tracing: event pairs around launches
+    bool prof_on = false;
+    struct ProfRec { int phase; cudaEvent_t a, b; };
+    std::vector<ProfRec> prof;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t prof_used = 0;
 
     void free_workspace();
     void free_extra();
 };
 
 namespace szg {
+// Records an event before a launch and after it when tracing is on.
+struct ProfScope {
+    sz_ctx* ctx;
+    cudaStream_t s;
+    int phase;
+    cudaEvent_t a = nullptr;
+    ProfScope(sz_ctx* c, int ph, cudaStream_t st);
+    ~ProfScope();
+};
 uint32_t tune_chunk(uint64_t n);
 sz_status resolve_params(const sz_params* p, uint64_t n, uint32_t* C, uint32_t* G);
 sz_status ctx_reserve(sz_ctx* ctx, int arrays, uint64_t max_chunks);

@@ -65,14 +65,21 @@ __device__ __forceinline__ double range_eb_abs(double eb, int kind, uint32_t min
 // Near-ties (thr_lo < |r| < thr_hi, probability ~2^-19) and out-of-range
 // candidates fall back to the binary64 definition.
 // ---------------------------------------------------------------------------
-static __device__ __noinline__ void lattice_slow(float x, const LatticeParams& P, long long& q, bool& verb) {
-    if (!finite_f(x) || P.raw) { q = 0; verb = true; return; }
-    double t = __ddiv_rn((double)x, (double)P.D);
-    if (!(fabs(t) < 9007199254740992.0)) { q = 0; verb = true; return; }
+struct LatticeOut {
+    long long q;
+    int verb;
+};
+
+static __device__ __noinline__ LatticeOut lattice_slow(float x, double eb_abs, float D, int raw) {
+    LatticeOut o;
+    if (!finite_f(x) || raw) { o.q = 0; o.verb = 1; return o; }
+    double t = __ddiv_rn((double)x, (double)D);
+    if (!(fabs(t) < 9007199254740992.0)) { o.q = 0; o.verb = 1; return o; }
     long long k = __double2ll_rn(t);
-    float xr = __double2float_rn(__dmul_rn((double)k, (double)P.D));
-    q = k;
-    verb = fabs(__dsub_rn((double)x, (double)xr)) > P.eb_abs;
+    float xr = __double2float_rn(__dmul_rn((double)k, (double)D));
+    o.q = k;
+    o.verb = fabs(__dsub_rn((double)x, (double)xr)) > eb_abs;
+    return o;
 }
 
 __device__ __forceinline__ void lattice_q(float x, const LatticeParams& P, long long& q, bool& verb) {
@@ -81,20 +88,22 @@ __device__ __forceinline__ void lattice_q(float x, const LatticeParams& P, long 
         float qc = rintf(t);
         float r = fmaf(-qc, P.D, x);
         float ar = fabsf(r);
-        if (ar > P.thr_lo) {
-            if (ar >= P.thr_hi) {
-                qc += (r > 0.0f) ? 1.0f : -1.0f;
-                r = fmaf(-qc, P.D, x);
-                ar = fabsf(r);
-            }
-            if (ar > P.thr_lo) { lattice_slow(x, P, q, verb); return; }
+        bool ok = ar <= P.thr_lo;
+        if (!ok && ar >= P.thr_hi) {
+            qc += (r > 0.0f) ? 1.0f : -1.0f;
+            r = fmaf(-qc, P.D, x);
+            ok = fabsf(r) <= P.thr_lo;
         }
-        float xr = __fmul_rn(qc, P.D);
-        q = (long long)(int)qc;
-        verb = fabsf(__fsub_rn(x, xr)) > P.ebf;
-        return;
+        if (ok) {
+            float xr = __fmul_rn(qc, P.D);
+            q = (long long)(int)qc;
+            verb = fabsf(__fsub_rn(x, xr)) > P.ebf;
+            return;
+        }
     }
-    lattice_slow(x, P, q, verb);
+    LatticeOut o = lattice_slow(x, P.eb_abs, P.D, P.raw);
+    q = o.q;
+    verb = o.verb != 0;
 }
 
 // Lattice -> value (a11): RN32(RN64(q*D)); one fmul while |q| <= 2^24.
