@@ -151,6 +151,30 @@ sz_status sz_sync(sz_ctx* ctx, void* stream);
 /* Human-readable name of a status code (static string). */
 const char* sz_status_string(sz_status s);
 
+/* ---- compression without allocation -------------------------------------- */
+
+/* The paper has no counterpart to this call; it serves callers that cannot
+ * let a library allocate device memory -- for example an in-situ simulation
+ * whose own pool owns the GPU's memory, or code running where a cudaMalloc
+ * would stall other streams.  It produces the same stream as sz_compress with
+ * default parameters, byte for byte, but needs no context and allocates
+ * nothing: its scratch (array state, histogram, codeword table, per-chunk
+ * tables, codebook work arrays, error word; about 5.9 MB) is one fixed array
+ * in device memory that every GPU loading this library keeps until exit.
+ *   - n may be at most 2^26 elements; larger n returns SZ_ERR_ARG.
+ *   - The call is synchronous: it enqueues the kernels on `stream`, waits for
+ *     them and sets *out_bytes (host) before returning; device errors come
+ *     back as its return value (SZ_ERR_CAPACITY: out_cap too small, with the
+ *     required size in *out_bytes).
+ *   - The first call on a device also looks up the scratch array's device
+ *     address and initializes it; make that first call before any stream
+ *     capture.
+ *   - All calls on a device share the one array, which keeps the previous
+ *     call's contents.  Calls that overlap on the GPU (other host threads or
+ *     streams) race on it and must be serialized by the caller. */
+sz_status sz_compress_noalloc(const float* d_in, size_t n, double eb, sz_eb_kind kind, void* d_out,
+                              size_t out_cap, size_t* out_bytes, void* stream);
+
 /* ---- tracing: per-phase kernel timing ------------------------------------ */
 
 /* Kernel phases of the path: range (a1), lattice + histogram (a2-a4),

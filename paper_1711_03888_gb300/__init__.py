@@ -33,7 +33,7 @@ HEADER_BYTES = 160
 
 EXPORTS = ("sz_ctx_create", "sz_ctx_destroy", "sz_max_compressed_bytes", "sz_compress", "sz_decompress",
            "sz_compress_batch", "sz_decompress_batch", "sz_compress_snapshot", "sz_sync", "sz_status_string",
-           "sz_profile_enable", "sz_profile_read",
+           "sz_profile_enable", "sz_profile_read", "sz_compress_noalloc",
            "sz_serve_start", "sz_serve_submit", "sz_serve_poll", "sz_serve_stop")
 PHASES = ("range", "quant", "codebook", "encode", "decode_setup", "decode", "reorder", "batch")
 
@@ -69,6 +69,7 @@ _sig = {
                                    C.POINTER(_sz), _vp, _vp]),
     "sz_sync": (_st, [_vp, _vp]),
     "sz_status_string": (C.c_char_p, [C.c_int]),
+    "sz_compress_noalloc": (_st, [_vp, _sz, C.c_double, C.c_int, _vp, _sz, C.POINTER(_sz), _vp]),
     "sz_profile_enable": (_st, [_vp, C.c_int]),
     "sz_profile_read": (_st, [_vp, C.POINTER(C.c_uint64), C.POINTER(C.c_double), C.c_int]),
     "sz_serve_start": (_st, [_vp, C.c_int]),
@@ -230,6 +231,20 @@ def sz_sync(ctx: Context, stream=None, check: bool = True) -> int:
 
 def sz_status_string(status: int) -> str:
     return _lib.sz_status_string(status).decode()
+
+
+def sz_compress_noalloc(x, eb: float, kind: int = SZ_EB_REL, out=None, out_cap=None, stream=None):
+    """Compression that allocates nothing in the library (fixed device scratch;
+    n <= 2^26).  Synchronous; returns (status, out, out_bytes).  `out` is
+    allocated here by torch when None -- pass it to allocate nothing at all."""
+    import torch
+    n = x.numel()
+    if out is None:
+        out = torch.empty(sz_max_compressed_bytes(n), dtype=torch.uint8, device=x.device)
+    cap = out.numel() if out_cap is None else out_cap
+    nb = C.c_size_t(0)
+    st = _lib.sz_compress_noalloc(_ptr(x), n, eb, kind, _ptr(out), cap, C.byref(nb), _stream(stream))
+    return st, out, nb.value
 
 
 def sz_profile_enable(ctx: Context, on: bool = True):
