@@ -162,7 +162,7 @@ def oracle_round_trip(arrays, eb):
     from concurrent.futures import ThreadPoolExecutor
 
     def one(x):
-        s = oracle.compress(x, eb, 1, 8192, 128)
+        s = oracle.compress(x, eb, 1, 4096, 64)
         oracle.decompress(s)
         return len(s)
 

@@ -2,24 +2,33 @@
 //
 // decode_setup (one block): validates the header against in_bytes, rebuilds
 // the canonical code from the (symbol, length) list -- first code, count and
-// base per length, symbols in (length, symbol) order -- and fills an 11-bit
-// direct lookup table.
+// base per length, left-justified limits, symbols in (length, symbol) order --
+// and fills a 12-bit direct lookup table.
 //
-// decode (persistent 64-thread blocks, one chunk at a time): thread k decodes
-// sub-stream k (G symbols) from its start bit (block scan of the sub-stream
-// bit lengths), keeping the codes in a swizzled shared buffer and the sum of
-// its deltas.  A block scan of the sums plus the chunk anchor gives every
-// thread its starting lattice value (a10: block-wide prefix scan; the anchor
-// replaces the device-wide part).  Each thread then rebuilds its values
-// x' = RN32(q*D) (a11), escapes patch delta / raw bits, and the chunk leaves
-// with 128-bit coalesced stores.  Every table entry and payload word is
-// bounds-checked against in_bytes; a bad stream sets E_CORRUPT.
+// decode (one persistent block per SM, split into independent 64-thread
+// "chunk teams" with their own named barrier): a team takes one chunk at a
+// time.  It stages the chunk's payload in shared memory (coalesced 128-bit
+// copies; chunks too large for the stage are read from global memory) and
+// asks L2 to prefetch its next chunk.  Thread k decodes sub-stream k (G
+// symbols) from its start bit (team scan of the sub-stream bit lengths) into
+// a swizzled shared buffer of deltas.  A team scan of the per-thread delta
+// sums plus the chunk anchor gives each thread its starting lattice value
+// (a10: the block-wide prefix scan; the anchor replaces the device-wide
+// part).  Each thread then rebuilds its values x' = RN32(q*D) (a11) -- in
+// 32-bit integers when no escape occurs and |q| provably stays within 2^24 --
+// and the chunk leaves with 128-bit coalesced stores.  Every table entry and
+// payload word is bounds-checked against in_bytes; a bad stream sets
+// E_CORRUPT.
 #include "sz_blocksort.cuh"
 
 namespace szg {
 
 constexpr int kSetupThreads = 1024;
-constexpr int kDecThreads = kSubPerChunk;    // 64
+constexpr int kDecThreads = kSubPerChunk;    // 64 threads per team
+constexpr int kMaxTeams = 8;
+constexpr int kDecBlock = kMaxTeams * kDecThreads;   // 512
+constexpr size_t kDecDynSmem = 176u * 1024u;         // team regions: delta/value slots + payload stage
+constexpr uint32_t kEscMark = 0x80000000u;           // delta slot of an escape
 
 struct SetupSmem {
     RadixSmem rs;
@@ -30,6 +39,10 @@ struct SetupSmem {
 
 __device__ __forceinline__ uint64_t rd64(const uint8_t* p) { return *reinterpret_cast<const uint64_t*>(p); }
 __device__ __forceinline__ uint32_t rd32(const uint8_t* p) { return *reinterpret_cast<const uint32_t*>(p); }
+
+__device__ __forceinline__ bool shape_ok(uint32_t C, uint32_t G) {
+    return (C == 2048 || C == 4096 || C == 8192 || C == 16384) && G * kSubPerChunk == C;
+}
 
 __global__ void __launch_bounds__(kSetupThreads) decode_setup_kernel(DecompressArgs a) {
     __shared__ SetupSmem sm;
@@ -63,8 +76,7 @@ __global__ void __launch_bounds__(kSetupThreads) decode_setup_kernel(DecompressA
                     if (pw < n) status = E_CORRUPT;
                     st->raw = 1;
                 } else if (n > 0) {
-                    const bool shape = (C == 2048 || C == 4096 || C == 8192 || C == 16384) && G * kSubPerChunk == C;
-                    if (!shape) status = E_UNSUPPORTED;
+                    if (!shape_ok(C, G)) status = E_UNSUPPORTED;
                     else if (nc != (n + C - 1) / C || m == 0 || m > 65536 ||
                              off[S_LENS] - off[S_SYMS] < 2 * m || off[S_CWORD] - off[S_LENS] < m ||
                              off[S_ANCHOR] - off[S_CWORD] < 8 * (nc + 1) || off[S_CESC] - off[S_ANCHOR] < 8 * nc ||
@@ -125,14 +137,16 @@ __global__ void __launch_bounds__(kSetupThreads) decode_setup_kernel(DecompressA
     if (tid == 0) {
         uint32_t c = 0, b = 0;
         sm.cnt[0] = 0;
-        st->first[0] = st->count[0] = st->base[0] = 0;
+        st->first[0] = st->count[0] = st->base[0] = st->lim[0] = 0;
         for (int l = 1; l <= kMaxLen; ++l) {
             c = (c + sm.cnt[l - 1]) << 1;
             st->first[l] = c;
             st->count[l] = sm.cnt[l];
             st->base[l] = b;
+            st->lim[l] = (c + sm.cnt[l]) << (kMaxLen - l);
             b += sm.cnt[l];
         }
+        st->lim[kMaxLen + 1] = 0xffffffffu;
     }
     for (uint32_t i = tid; i < (1u << kLutBits); i += kSetupThreads) a.lut[i] = 0u;
     __syncthreads();
@@ -149,41 +163,46 @@ __global__ void __launch_bounds__(kSetupThreads) decode_setup_kernel(DecompressA
     if (tid == 0) st->dec_ok = 1;
 }
 
-// bit reader over the chunk payload (global, bounds-checked: words at or past
-// `end` read as zero, so a bad stream cannot read outside it)
+// Bit reader over a chunk payload in shared or global memory (generic
+// pointer).  Words at or past `end` read as zero, so a bad stream cannot make
+// it read outside the chunk.
 struct BitReader {
     const uint32_t* words;
-    uint64_t pos, end;            // word index of the next refill, end (exclusive)
+    uint32_t pos, end;            // word index of the next refill, end (exclusive)
     unsigned long long win;       // bits MSB-aligned
     uint32_t avail;
-    __device__ __forceinline__ void init(const uint32_t* w, uint64_t begin_bit, uint64_t end_word) {
+    __device__ __forceinline__ void init(const uint32_t* w, uint32_t begin_bit, uint32_t end_word) {
         words = w;
         end = end_word;
         pos = begin_bit >> 5;
         win = 0;
         avail = 0;
-        uint32_t skip = (uint32_t)(begin_bit & 31u);
+        uint32_t skip = begin_bit & 31u;
         refill();
         refill();
         win <<= skip;
         avail -= skip;
     }
     __device__ __forceinline__ void refill() {
-        uint32_t v = 0;
-        if (pos < end) v = __ldg(words + pos);
+        uint32_t v = (pos < end) ? words[pos] : 0u;
         ++pos;
         win |= (unsigned long long)v << (32u - avail);
         avail += 32;
     }
+    // branch-free: the refill load is predicated, so lanes do not diverge
     __device__ __forceinline__ void consume(uint32_t l) {
         win <<= l;
         avail -= l;
-        if (avail < 32) refill();
+        const bool need = avail < 32u;
+        const uint32_t v = (need && pos < end) ? words[pos] : 0u;
+        win |= (unsigned long long)v << ((32u - avail) & 63u);
+        avail += need ? 32u : 0u;
+        pos += need ? 1u : 0u;
     }
 };
 
-// Team-level primitives: a team is 64 threads (2 warps) with its own named
-// barrier (id team + 1) decoding one chunk at a time.
+// Team-level primitives: a team is 64 threads (2 warps) with named barrier
+// id team + 1.
 __device__ __forceinline__ void team_sync(int team) {
     asm volatile("bar.sync %0, %1;" :: "r"(team + 1), "r"(kDecThreads) : "memory");
 }
@@ -200,18 +219,37 @@ __device__ __forceinline__ T team_exclusive_scan(T v, T* ws, int team, int k, T*
     return r;
 }
 
-constexpr int kTeams = 6;
-constexpr int kDecBlock = kTeams * kDecThreads;        // 384
-constexpr int kDecLutBits = 12;
-
 struct DecSmem {
-    uint32_t lut[1 << kDecLutBits];       // sym << 8 | len for codes of <= 12 bits, else 0
+    uint32_t lut[1 << kLutBits];          // sym << 8 | len for codes of <= 12 bits, else 0
     uint32_t lim[kMaxLen + 2];            // left-justified (24-bit) end of each length's codes
     uint32_t first[kMaxLen + 2], base[kMaxLen + 2];
-    uint32_t ws32[kTeams][2], ws32b[kTeams][2];
-    long long ws64[kTeams][2];
-    uint32_t bad[kTeams];
+    uint32_t ws32[kMaxTeams][2], ws32b[kMaxTeams][2];
+    long long ws64[kMaxTeams][2];
 };
+
+__device__ __forceinline__ int teams_for(uint32_t C) {
+    return C <= 4096 ? 8 : (C == 8192 ? 4 : 2);
+}
+
+// One symbol: 12-bit direct lookup, else a walk over the left-justified limits.
+__device__ __forceinline__ uint32_t decode_symbol(BitReader& br, const DecSmem& sm, const uint16_t* by_len,
+                                                  uint32_t& used, bool& bad) {
+    const uint32_t w24 = (uint32_t)(br.win >> 40);
+    const uint32_t ent = sm.lut[w24 >> (kMaxLen - kLutBits)];
+    uint32_t sym, len;
+    if (ent) {
+        sym = ent >> 8;
+        len = ent & 255u;
+    } else {
+        len = kLutBits + 1;
+        while (w24 >= sm.lim[len]) ++len;   // lim[25] = ~0 stops the walk
+        if (len > (uint32_t)kMaxLen) { bad = true; len = 0; sym = 0; }
+        else sym = by_len[sm.base[len] + (w24 >> (kMaxLen - len)) - sm.first[len]];
+    }
+    br.consume(len);
+    used += len;
+    return sym;
+}
 
 __global__ void __launch_bounds__(kDecBlock, 1) decode_kernel(DecompressArgs a) {
     __shared__ DecSmem sm;
@@ -238,45 +276,33 @@ __global__ void __launch_bounds__(kDecBlock, 1) decode_kernel(DecompressArgs a) 
     const uint16_t* sublen = reinterpret_cast<const uint16_t*>(in + st->off[S_SUBLEN]);
     const uint8_t* escs = in + st->off[S_ESC];
     const uint32_t* payload = reinterpret_cast<const uint32_t*>(in + st->off[S_PAYLOAD]);
+    const uint16_t* by_len = a.by_len;
 
-    // block-wide: direct lookup table for codes of <= 12 bits, limits for the rest
-    for (uint32_t i = tid; i < (1u << kDecLutBits); i += kDecBlock) sm.lut[i] = 0u;
-    __syncthreads();
+    for (uint32_t i = tid; i < (1u << kLutBits) / 4; i += kDecBlock)
+        reinterpret_cast<uint4*>(sm.lut)[i] = __ldg(reinterpret_cast<const uint4*>(a.lut) + i);
     if (tid < kMaxLen + 2) {
-        const uint32_t l = tid;
-        sm.first[l] = st->first[l];
-        sm.base[l] = st->base[l];
-        sm.lim[l] = (l >= 1 && l <= (uint32_t)kMaxLen) ? ((st->first[l] + st->count[l]) << (kMaxLen - l)) : 0u;
-    }
-    {
-        const uint32_t m = (uint32_t)rd64(in + H_NSYM);
-        for (uint32_t p = tid; p < m; p += kDecBlock) {
-            // symbols in (length, symbol) order: find this position's length
-            uint32_t l = 1;
-            while (l < (uint32_t)kMaxLen && p >= st->base[l] + st->count[l]) ++l;
-            if (l <= (uint32_t)kDecLutBits) {
-                uint32_t code = st->first[l] + (p - st->base[l]);
-                uint32_t lo = code << (kDecLutBits - l), hi = (code + 1) << (kDecLutBits - l);
-                uint32_t v = ((uint32_t)a.by_len[p] << 8) | l;
-                for (uint32_t e = lo; e < hi; ++e) sm.lut[e] = v;
-            }
-        }
+        sm.first[tid] = st->first[tid];
+        sm.base[tid] = st->base[tid];
+        sm.lim[tid] = st->lim[tid];
     }
     __syncthreads();
 
+    const int teams = teams_for(C);
     const int team = tid / kDecThreads, k = tid % kDecThreads;
-    const int teams_active = umin32(kTeams, (uint32_t)(kTeams * 8192u) / C);
-    if (team >= teams_active) return;
-    uint32_t* xs = reinterpret_cast<uint32_t*>(dyn_smem) + (size_t)team * C;
+    if (team >= teams) return;
+    const uint32_t region_words = (uint32_t)(kDecDynSmem / 4) / teams;
+    uint32_t* xs = reinterpret_cast<uint32_t*>(dyn_smem) + (size_t)team * region_words;
+    uint32_t* stage = xs + C;
+    const uint32_t stage_words = region_words - C;      // multiple of 4
     const bool vec = ((uintptr_t)a.out & 15u) == 0;
-    const uint64_t stride = (uint64_t)gridDim.x * teams_active;
+    const uint64_t stride = (uint64_t)gridDim.x * teams;
 
-    for (uint64_t c = (uint64_t)blockIdx.x * teams_active + team; c < nc; c += stride) {
+    for (uint64_t c = (uint64_t)blockIdx.x * teams + team; c < nc; c += stride) {
         const uint64_t base = c * C;
         const uint32_t cnt = (uint32_t)umin64(C, n - base);
         const uint64_t wb = cword[c], we = cword[c + 1];
         const uint64_t eb = cesc[c], ee = cesc[c + 1];
-        const bool hdr_bad = (wb > we || we > pw || eb > ee || ee > E);
+        const bool hdr_bad = (wb > we || we > pw || eb > ee || ee > E || (wb & 3u));
         const uint32_t e0 = k * G;
         const uint32_t nsym = e0 < cnt ? umin32(G, cnt - e0) : 0u;
         const uint32_t sl = sublen[c * kSubPerChunk + k];
@@ -286,40 +312,54 @@ __global__ void __launch_bounds__(kDecBlock, 1) decode_kernel(DecompressArgs a) 
             if (k == 0) raise_err(a.err, E_CORRUPT);
             return;
         }
-        // ---- phase 1: decode the sub-stream ------------------------------------------
+        // ---- stage the chunk payload; prefetch the next chunk into L2 ---------------
+        const uint32_t cw_words = (uint32_t)(we - wb);
+        const uint32_t* src;
+        if (cw_words <= stage_words) {
+            // asynchronous 16-byte copies, all in flight at once
+            const uint4* g4 = reinterpret_cast<const uint4*>(payload + wb);
+            const uint32_t s_base = (uint32_t)__cvta_generic_to_shared(stage);
+            for (uint32_t w4 = k; w4 < cw_words / 4; w4 += kDecThreads)
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s_base + 16u * w4),
+                             "l"(__cvta_generic_to_global(g4 + w4))
+                             : "memory");
+            asm volatile("cp.async.wait_all;" ::: "memory");
+            src = stage;
+        } else {
+            src = payload + wb;
+        }
+        if (k == 0 && c + stride < nc) {
+            const uint64_t nb = cword[c + stride], ne = cword[c + stride + 1];
+            if (nb < ne && ne <= pw && !(nb & 3u) && !(ne & 3u) && ne - nb < (1u << 24)) {
+                const uint32_t* p = payload + nb;
+                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(__cvta_generic_to_global(p)), "r"((uint32_t)(4 * (ne - nb)))
+                             : "memory");
+            }
+        }
+        team_sync(team);
+        // ---- phase 1: decode the sub-stream into deltas -----------------------------
         BitReader br;
-        br.init(payload, 32ull * wb + start, we);
-        int dsum = 0;
+        br.init(src, start, cw_words);
+        int dsum = 0, dabs = 0;
         uint32_t nesc = 0, used = 0;
         bool bad = false;
         for (uint32_t j4 = 0; j4 < nsym; j4 += 4) {
-            uint32_t sy[4] = {0u, 0u, 0u, 0u};
+            uint32_t dl[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
-                if (j4 + t < nsym) {
-                    const uint32_t w24 = (uint32_t)(br.win >> 40);
-                    uint32_t ent = sm.lut[w24 >> (kMaxLen - kDecLutBits)];
-                    uint32_t sym, len;
-                    if (ent) {
-                        sym = ent >> 8;
-                        len = ent & 255u;
-                    } else {
-                        len = kDecLutBits + 1;
-                        while (len <= (uint32_t)kMaxLen && w24 >= sm.lim[len]) ++len;
-                        if (len > (uint32_t)kMaxLen) { bad = true; len = 0; sym = 0; }
-                        else sym = a.by_len[sm.base[len] + (w24 >> (kMaxLen - len)) - sm.first[len]];
-                    }
-                    br.consume(len);
-                    used += len;
-                    sy[t] = sym;
+                if (nsym == G || j4 + t < nsym) {
+                    const uint32_t sym = decode_symbol(br, sm, by_len, used, bad);
+                    const int d = (int)sym - kRadius;
+                    dl[t] = sym ? (uint32_t)d : kEscMark;
                     nesc += (sym == 0u);
-                    dsum += (sym == 0u) ? 0 : (int)sym - kRadius;
+                    dsum += sym ? d : 0;
+                    dabs += sym ? abs(d) : 0;
                 }
             }
-            *reinterpret_cast<uint4*>(&xs[swz(e0 + j4, gshift)]) = make_uint4(sy[0], sy[1], sy[2], sy[3]);
+            *reinterpret_cast<uint4*>(&xs[swz(e0 + j4, gshift)]) = make_uint4(dl[0], dl[1], dl[2], dl[3]);
         }
         bad = bad || used != sl;
-        // ---- escapes and the block-wide prefix ----------------------------------------
+        // ---- escapes and the team-wide prefix ----------------------------------------
         uint32_t tot_esc;
         const uint32_t eoff = team_exclusive_scan<uint32_t>(nesc + (bad ? 0x10000u : 0u), sm.ws32b[team], team, k,
                                                              &tot_esc);
@@ -333,39 +373,55 @@ __global__ void __launch_bounds__(kDecBlock, 1) decode_kernel(DecompressArgs a) 
         long long tot_sum;
         const long long pre = team_exclusive_scan<long long>(sum, sm.ws64[team], team, k, &tot_sum);
         // ---- phase 2: reconstruct in place -----------------------------------------
-        long long q = anchor[c] + pre;
-        uint64_t ecur = eb + eoff;
-        for (uint32_t j4 = 0; j4 < nsym; j4 += 4) {
-            uint4* slot = reinterpret_cast<uint4*>(&xs[swz(e0 + j4, gshift)]);
-            uint4 s4 = *slot;
-            uint32_t sy[4] = {s4.x, s4.y, s4.z, s4.w};
-            uint32_t ov[4];
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                ov[t] = 0u;
-                if (j4 + t < nsym) {
-                    float v;
-                    if (sy[t]) {
-                        q += (int)sy[t] - kRadius;
-                        v = recon_f(q, D);
-                    } else {
-                        const uint8_t* r = escs + (uint64_t)kEscBytes * ecur++;
-                        q += *reinterpret_cast<const long long*>(r);
-                        v = (rd32(r + 12) & 1u) ? __uint_as_float(rd32(r + 8)) : recon_f(q, D);
-                    }
-                    ov[t] = __float_as_uint(v);
-                }
+        const long long q0 = anchor[c] + pre;
+        if (nesc == 0 && q0 >= -(1ll << 24) + dabs && q0 <= (1ll << 24) - dabs) {
+            // every partial sum stays within |q| <= 2^24: 32-bit, one fmul each
+            int q = (int)q0;
+            for (uint32_t j4 = 0; j4 < nsym; j4 += 4) {
+                uint4* slot = reinterpret_cast<uint4*>(&xs[swz(e0 + j4, gshift)]);
+                uint4 s4 = *slot;
+                q += (int)s4.x; const float v0 = __fmul_rn((float)q, D);
+                q += (int)s4.y; const float v1 = __fmul_rn((float)q, D);
+                q += (int)s4.z; const float v2 = __fmul_rn((float)q, D);
+                q += (int)s4.w; const float v3 = __fmul_rn((float)q, D);
+                *slot = make_uint4(__float_as_uint(v0), __float_as_uint(v1), __float_as_uint(v2), __float_as_uint(v3));
             }
-            *slot = make_uint4(ov[0], ov[1], ov[2], ov[3]);
+        } else {
+            long long q = q0;
+            uint64_t ecur = eb + eoff;
+            for (uint32_t j4 = 0; j4 < nsym; j4 += 4) {
+                uint4* slot = reinterpret_cast<uint4*>(&xs[swz(e0 + j4, gshift)]);
+                uint4 s4 = *slot;
+                uint32_t dl[4] = {s4.x, s4.y, s4.z, s4.w};
+                uint32_t ov[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    ov[t] = 0u;
+                    if (j4 + t < nsym) {
+                        float v;
+                        if (dl[t] != kEscMark) {
+                            q += (int)dl[t];
+                            v = recon_f(q, D);
+                        } else {
+                            const uint8_t* r = escs + (uint64_t)kEscBytes * ecur++;
+                            q += *reinterpret_cast<const long long*>(r);
+                            v = (rd32(r + 12) & 1u) ? __uint_as_float(rd32(r + 8)) : recon_f(q, D);
+                        }
+                        ov[t] = __float_as_uint(v);
+                    }
+                }
+                *slot = make_uint4(ov[0], ov[1], ov[2], ov[3]);
+            }
         }
         team_sync(team);
         // ---- phase 3: coalesced store ---------------------------------------------
         float* dst = a.out + base;
-        for (uint32_t e = 4 * k; e < cnt; e += 4 * kDecThreads) {
-            uint4 v = *reinterpret_cast<const uint4*>(&xs[swz(e, gshift)]);
-            if (vec && e + 3 < cnt) {
-                *reinterpret_cast<uint4*>(dst + e) = v;
-            } else {
+        if (vec && cnt == C) {
+            for (uint32_t e = 4 * k; e < C; e += 4 * kDecThreads)
+                *reinterpret_cast<uint4*>(dst + e) = *reinterpret_cast<const uint4*>(&xs[swz(e, gshift)]);
+        } else {
+            for (uint32_t e = 4 * k; e < cnt; e += 4 * kDecThreads) {
+                uint4 v = *reinterpret_cast<const uint4*>(&xs[swz(e, gshift)]);
                 uint32_t vv[4] = {v.x, v.y, v.z, v.w};
                 for (int j = 0; j < 4 && e + j < cnt; ++j) dst[e + j] = __uint_as_float(vv[j]);
             }
@@ -386,13 +442,12 @@ void launch_decode(const DecompressArgs* a, int k, void* stream) {
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (sms <= 0) sms = 148;
     }
-    const size_t smem = (size_t)kTeams * 8192u * 4u;
     static bool configured = false;
     if (!configured) {
-        cudaFuncSetAttribute(decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDecDynSmem);
         configured = true;
     }
-    for (int i = 0; i < k; ++i) decode_kernel<<<sms, kDecBlock, smem, (cudaStream_t)stream>>>(a[i]);
+    for (int i = 0; i < k; ++i) decode_kernel<<<sms, kDecBlock, kDecDynSmem, (cudaStream_t)stream>>>(a[i]);
 }
 
 }  // namespace szg

@@ -34,8 +34,8 @@ __device__ void raw_copy(const CompressArgs& a) {
         dst[i] = (i < n) ? __ldg(src + i) : 0u;
 }
 
-template <int NT>
-__global__ void __launch_bounds__(NT, (NT >= 256 ? 1024 / NT : 8)) encode_kernel(CompressArgs a) {
+template <int NT, bool FROM_CODES>
+__global__ void __launch_bounds__(NT, (NT >= 512 ? 1 : 512 / NT)) encode_kernel(CompressArgs a) {
     constexpr int C = NT * kRun;
     extern __shared__ uint4 dyn_smem[];
     uint32_t* buf = reinterpret_cast<uint32_t*>(dyn_smem);   // C words: codes, then payload
@@ -56,9 +56,40 @@ __global__ void __launch_bounds__(NT, (NT >= 256 ? 1024 / NT : 8)) encode_kernel
     const float* in = a.in;
     const bool vec = ((uintptr_t)in & 15u) == 0;
     const uint32_t* enc = a.enc;
-
-    // ---- pass 1: codes and (codeword, length), coalesced -----------------------
+    const uint32_t e0 = tid * kRun;
+    uint32_t r[kRun];
     long long anchor = 0;
+
+    if (FROM_CODES) {
+        // ---- pass 1+2: the quantizer's codes for elements e0 .. e0+31 ----------------
+        const uint16_t* cp = a.codes + base + e0;
+        uint32_t w[kRun / 2];
+        if (e0 + kRun <= cnt) {
+#pragma unroll
+            for (int m = 0; m < kRun / 8; ++m) {
+                uint4 v = __ldg(reinterpret_cast<const uint4*>(cp) + m);
+                w[4 * m] = v.x; w[4 * m + 1] = v.y; w[4 * m + 2] = v.z; w[4 * m + 3] = v.w;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < kRun / 2; ++j) {
+                uint32_t lo = (e0 + 2 * j < cnt) ? __ldg(cp + 2 * j) : 0u;
+                uint32_t hi = (e0 + 2 * j + 1 < cnt) ? __ldg(cp + 2 * j + 1) : 0u;
+                w[j] = lo | (hi << 16);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kRun; ++j) {
+            const uint32_t code = (j & 1) ? (w[j >> 1] >> 16) : (w[j >> 1] & 0xffffu);
+            const uint32_t ent = __ldg(enc + code);
+            r[j] = (e0 + j < cnt) ? (((ent >> 5) << 6) | ((ent & 31u) << 1) | (code == 0u ? 1u : 0u)) : 0u;
+        }
+        if (tid == 0 && base > 0) {
+            bool vv;
+            lattice_q(__ldg(in + base - 1), P, anchor, vv);
+        }
+    } else {
+    // ---- pass 1: codes and (codeword, length), coalesced -----------------------
 #pragma unroll 2
     for (uint32_t e = 4 * tid; e < (uint32_t)C; e += 4 * NT) {
         float x[4];
@@ -97,13 +128,12 @@ __global__ void __launch_bounds__(NT, (NT >= 256 ? 1024 / NT : 8)) encode_kernel
     __syncthreads();
 
     // ---- pass 2: this thread's 32 consecutive entries ---------------------------
-    const uint32_t e0 = tid * kRun;
-    uint32_t r[kRun];
 #pragma unroll
     for (int m = 0; m < kRun / 4; ++m) {
         uint4 v = *reinterpret_cast<const uint4*>(&buf[swz(e0 + 4 * m, 5)]);
         r[4 * m] = v.x; r[4 * m + 1] = v.y; r[4 * m + 2] = v.z; r[4 * m + 3] = v.w;
     }
+    }  // !FROM_CODES
     uint32_t bits = 0, escs = 0;
 #pragma unroll
     for (int j = 0; j < kRun; ++j) {
@@ -120,96 +150,16 @@ __global__ void __launch_bounds__(NT, (NT >= 256 ? 1024 / NT : 8)) encode_kernel
 #pragma unroll
     for (int o = 1; o < kLanesPerSub; o <<= 1) sub_bits += __shfl_xor_sync(0xffffffffu, sub_bits, o);
 
-    // ---- decoupled look-back: word offset of this chunk ------------------------
-    if (tid == 0) {
-        unsigned long long* status = a.chunk_status;
-        const unsigned long long FLAG_AGG = 1ull << 62, FLAG_INC = 2ull << 62, FLAG_ERR = 3ull << 62;
-        const unsigned long long VMASK = (1ull << 62) - 1;
-        unsigned long long excl = 0;
-        bool bad = false;
-        if (c == 0) {
-            st_release(&status[0], FLAG_INC | chunk_words);
-        } else {
-            st_release(&status[c], FLAG_AGG | chunk_words);
-            int64_t j = (int64_t)c - 1;
-            uint32_t spins = 0;
-            while (j >= 0) {
-                unsigned long long s = ld_acquire(&status[j]);
-                unsigned long long f = s & ~VMASK;
-                if (f == 0ull) {
-                    if (++spins > kLookbackSpins) { bad = true; break; }
-                    __nanosleep(32);
-                    continue;
-                }
-                if (f == FLAG_ERR) { bad = true; break; }
-                excl += s & VMASK;
-                if (f == FLAG_INC) break;
-                --j;
-            }
-            if (bad) {
-                raise_err(a.err, E_TIMEOUT);
-                st_release(&status[c], FLAG_ERR);
-            } else {
-                st_release(&status[c], FLAG_INC | (excl + chunk_words));
-            }
-        }
-        s_prefix = bad ? ~0ull : excl;
-    }
+    // ---- publish this chunk's size for the look-back of later chunks --------------
+    unsigned long long* status = a.chunk_status;
+    constexpr unsigned long long FLAG_AGG = 1ull << 62, FLAG_INC = 2ull << 62, FLAG_ERR = 3ull << 62;
+    constexpr unsigned long long VMASK = (1ull << 62) - 1;
+    if (tid == 0) st_release(&status[c], (c == 0 ? FLAG_INC : FLAG_AGG) | chunk_words);
     // zero the payload area (the code entries are in registers now)
     for (uint32_t w = tid; w < chunk_words; w += NT) buf[w] = 0u;
     __syncthreads();
-    const unsigned long long prefix = s_prefix;
-    if (prefix == ~0ull) return;
 
-    // ---- tables ------------------------------------------------------------------
-    uint8_t* out = a.out;
-    const uint64_t off_payload = st->off[S_PAYLOAD];
-    const bool tables_ok = off_payload <= a.out_cap;
-    const uint64_t chunk_end = off_payload + 4ull * (prefix + chunk_words);
-    if (tables_ok) {
-        if ((tid % kLanesPerSub) == 0) {
-            const uint32_t k = tid / kLanesPerSub;
-            reinterpret_cast<uint16_t*>(out + st->off[S_SUBLEN])[(uint64_t)c * kSubPerChunk + k] =
-                (uint16_t)(e0 < cnt ? sub_bits : 0u);
-        }
-        if (tid == 0) {
-            reinterpret_cast<uint64_t*>(out + st->off[S_CWORD])[c] = prefix;
-            reinterpret_cast<long long*>(out + st->off[S_ANCHOR])[c] = anchor;
-            if (c == a.n_chunks - 1) reinterpret_cast<uint64_t*>(out + st->off[S_CWORD])[c + 1] = prefix + chunk_words;
-        }
-    }
-    if (c == a.n_chunks - 1 && tid == 0) {
-        st->total_bytes = chunk_end;
-        if (a.out_cap >= kHeaderBytes) {
-            *reinterpret_cast<uint64_t*>(out + H_PWORDS) = prefix + chunk_words;
-            *reinterpret_cast<uint64_t*>(out + H_TOTAL) = chunk_end;
-        }
-        if (chunk_end > a.out_cap) raise_err(a.err, E_CAPACITY);
-    }
-    if (!tables_ok) return;
-
-    // ---- escape records (rare): rebuilt from global memory ---------------------
-    if (escs) {
-        uint8_t* esc_base = out + st->off[S_ESC] + (uint64_t)kEscBytes * (a.chunk_esc[c] + eoff);
-        uint32_t idx = 0;
-#pragma unroll
-        for (int j = 0; j < kRun; ++j) {
-            if (r[j] & 1u) {
-                uint64_t i = base + e0 + j;
-                float x = __ldg(in + i);
-                long long q, qp = 0;
-                bool vb, vv;
-                lattice_q(x, P, q, vb);
-                if (i > 0) lattice_q(__ldg(in + i - 1), P, qp, vv);
-                uint8_t* rec = esc_base + (uint64_t)kEscBytes * idx++;
-                *reinterpret_cast<long long*>(rec) = q - qp;
-                *reinterpret_cast<uint32_t*>(rec + 8) = vb ? __float_as_uint(x) : 0u;
-                *reinterpret_cast<uint32_t*>(rec + 12) = vb ? 1u : 0u;
-            }
-        }
-    }
-
-    // ---- pass 3: pack ---------------------------------------------------------------
+    // ---- pass 3: pack into shared memory ------------------------------------------
     {
         uint32_t word = start >> 5, fill = start & 31u, cur = 0u;
         bool first = true;
@@ -233,8 +183,98 @@ __global__ void __launch_bounds__(NT, (NT >= 256 ? 1024 / NT : 8)) encode_kernel
         }
         if (fill) atomicOr(&buf[word], cur);
     }
+
+    // ---- escape records (rare): rebuilt from global memory ---------------------
+    uint8_t* out = a.out;
+    const uint64_t off_payload = st->off[S_PAYLOAD];
+    const bool tables_ok = off_payload <= a.out_cap;
+    if (escs && tables_ok) {
+        uint8_t* esc_base = out + st->off[S_ESC] + (uint64_t)kEscBytes * (a.chunk_esc[c] + eoff);
+        uint32_t idx = 0;
+#pragma unroll
+        for (int j = 0; j < kRun; ++j) {
+            if (r[j] & 1u) {
+                uint64_t i = base + e0 + j;
+                float x = __ldg(in + i);
+                long long q, qp = 0;
+                bool vb, vv;
+                lattice_q(x, P, q, vb);
+                if (i > 0) lattice_q(__ldg(in + i - 1), P, qp, vv);
+                uint8_t* rec = esc_base + (uint64_t)kEscBytes * idx++;
+                *reinterpret_cast<long long*>(rec) = q - qp;
+                *reinterpret_cast<uint32_t*>(rec + 8) = vb ? __float_as_uint(x) : 0u;
+                *reinterpret_cast<uint32_t*>(rec + 12) = vb ? 1u : 0u;
+            }
+        }
+    }
+
+    // ---- decoupled look-back, one warp, 32 predecessors per step --------------------
+    if (tid < 32 && c > 0) {
+        unsigned long long excl = 0;
+        bool bad = false;
+        long long j = (long long)c - 1;
+        while (j >= 0) {
+            const long long pos = j - tid;
+            unsigned long long s = FLAG_INC;               // before chunk 0: an empty prefix
+            if (pos >= 0) {
+                uint32_t spins = 0;
+                s = ld_acquire(&status[pos]);
+                while ((s & ~VMASK) == 0ull && spins < kLookbackSpins) {
+                    __nanosleep(64);
+                    s = ld_acquire(&status[pos]);
+                    ++spins;
+                }
+            }
+            const unsigned long long f = s & ~VMASK;
+            if (__any_sync(0xffffffffu, f == 0ull || f == FLAG_ERR)) { bad = true; break; }
+            const uint32_t inc = __ballot_sync(0xffffffffu, f == FLAG_INC);
+            const int lim = inc ? (__ffs(inc) - 1) : 31;    // lanes 0..lim contribute
+            unsigned long long v = (tid <= lim) ? (s & VMASK) : 0ull;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            excl += v;
+            if (inc) break;
+            j -= 32;
+        }
+        if (tid == 0) {
+            if (bad) {
+                raise_err(a.err, E_TIMEOUT);
+                st_release(&status[c], FLAG_ERR);
+            } else {
+                st_release(&status[c], FLAG_INC | (excl + chunk_words));
+            }
+            s_prefix = bad ? ~0ull : excl;
+        }
+    } else if (tid == 0) {
+        s_prefix = 0ull;
+    }
     __syncthreads();
-    if (chunk_end <= a.out_cap) {
+    const unsigned long long prefix = s_prefix;
+    if (prefix == ~0ull) return;
+
+    // ---- tables ------------------------------------------------------------------
+    const uint64_t chunk_end = off_payload + 4ull * (prefix + chunk_words);
+    if (tables_ok) {
+        if ((tid % kLanesPerSub) == 0) {
+            const uint32_t k = tid / kLanesPerSub;
+            reinterpret_cast<uint16_t*>(out + st->off[S_SUBLEN])[(uint64_t)c * kSubPerChunk + k] =
+                (uint16_t)(e0 < cnt ? sub_bits : 0u);
+        }
+        if (tid == 0) {
+            reinterpret_cast<uint64_t*>(out + st->off[S_CWORD])[c] = prefix;
+            reinterpret_cast<long long*>(out + st->off[S_ANCHOR])[c] = anchor;
+            if (c == a.n_chunks - 1) reinterpret_cast<uint64_t*>(out + st->off[S_CWORD])[c + 1] = prefix + chunk_words;
+        }
+    }
+    if (c == a.n_chunks - 1 && tid == 0) {
+        st->total_bytes = chunk_end;
+        if (a.out_cap >= kHeaderBytes) {
+            *reinterpret_cast<uint64_t*>(out + H_PWORDS) = prefix + chunk_words;
+            *reinterpret_cast<uint64_t*>(out + H_TOTAL) = chunk_end;
+        }
+        if (chunk_end > a.out_cap) raise_err(a.err, E_CAPACITY);
+    }
+    if (tables_ok && chunk_end <= a.out_cap) {
         uint4* dst = reinterpret_cast<uint4*>(out + off_payload + 4ull * prefix);
         const uint4* src = reinterpret_cast<const uint4*>(buf);
         for (uint32_t w4 = tid; w4 < chunk_words / 4; w4 += NT) dst[w4] = src[w4];
@@ -246,10 +286,12 @@ static void launch_encode_t(const CompressArgs& a, cudaStream_t s) {
     const size_t smem = (size_t)NT * kRun * 4u;
     static bool configured = false;
     if (!configured) {
-        cudaFuncSetAttribute(encode_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(encode_kernel<NT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(encode_kernel<NT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         configured = true;
     }
-    encode_kernel<NT><<<a.n_chunks, NT, smem, s>>>(a);
+    if (a.codes) encode_kernel<NT, true><<<a.n_chunks, NT, smem, s>>>(a);
+    else encode_kernel<NT, false><<<a.n_chunks, NT, smem, s>>>(a);
 }
 
 void launch_encode(const CompressArgs* a, int k, void* stream) {

@@ -21,12 +21,14 @@ __global__ void __launch_bounds__(256) range_kernel(CompressArgs a) {
         uint64_t head = 0;
         if (((uintptr_t)in & 15u) == 0) {
             const float4* v4 = reinterpret_cast<const float4*>(in);
-            uint64_t n4 = n >> 2;
-            for (uint64_t i = gtid; i < n4; i += gstride) {
-                float4 v = __ldg(v4 + i);
-                float e[4] = {v.x, v.y, v.z, v.w};
+            const uint64_t n4 = n >> 2;
+            // two 16-byte loads in flight per thread
+            for (uint64_t i = gtid; i < n4; i += 2 * gstride) {
+                float4 va = __ldg(v4 + i);
+                float4 vb = (i + gstride < n4) ? __ldg(v4 + i + gstride) : va;
+                float e[8] = {va.x, va.y, va.z, va.w, vb.x, vb.y, vb.z, vb.w};
 #pragma unroll
-                for (int j = 0; j < 4; ++j)
+                for (int j = 0; j < 8; ++j)
                     if (finite_f(e[j])) {
                         uint32_t k = float_key(e[j]);
                         kmin = min(kmin, k);

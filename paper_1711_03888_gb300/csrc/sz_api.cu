@@ -20,11 +20,11 @@ namespace szg {
 static const uint32_t kChunkChoices[] = {2048u, 4096u, 8192u, 16384u};
 
 // Built-in tuner: a pure function of n (never of load), so streams are
-// reproducible.  Small arrays use small chunks to keep every SM busy.
+// reproducible.  4096-element chunks (64-element sub-streams) let eight
+// decoder teams share an SM; small arrays use 2048 to keep every SM busy.
 uint32_t tune_chunk(uint64_t n) {
-    if (n <= (1ull << 17)) return 2048u;
-    if (n <= (1ull << 20)) return 4096u;
-    return 8192u;
+    if (n <= (1ull << 16)) return 2048u;
+    return 4096u;
 }
 
 sz_status resolve_params(const sz_params* p, uint64_t n, uint32_t* C, uint32_t* G) {
@@ -41,11 +41,13 @@ sz_status resolve_params(const sz_params* p, uint64_t n, uint32_t* C, uint32_t* 
 
 static sz_status cuda_status(cudaError_t e) { return e == cudaSuccess ? SZ_OK : SZ_ERR_CUDA; }
 
-sz_status ctx_reserve(sz_ctx* ctx, int arrays, uint64_t max_chunks) {
-    if (arrays <= ctx->cap_arrays && max_chunks <= ctx->cap_chunks) return SZ_OK;
+sz_status ctx_reserve(sz_ctx* ctx, int arrays, uint64_t max_chunks, uint64_t max_code_elems) {
+    if (arrays <= ctx->cap_arrays && max_chunks <= ctx->cap_chunks && max_code_elems <= ctx->cap_codes) return SZ_OK;
     int na = arrays > ctx->cap_arrays ? arrays : ctx->cap_arrays;
     uint64_t nc = max_chunks > ctx->cap_chunks ? max_chunks : ctx->cap_chunks;
+    uint64_t ncode = max_code_elems > ctx->cap_codes ? max_code_elems : ctx->cap_codes;
     if (nc < 1024) nc = 1024;
+    ncode = (ncode + 16383u) & ~(uint64_t)16383u;
     // in-flight work may still use the old buffers
     if (cudaDeviceSynchronize() != cudaSuccess) return SZ_ERR_CUDA;
     ctx->free_workspace();
@@ -59,6 +61,7 @@ sz_status ctx_reserve(sz_ctx* ctx, int arrays, uint64_t max_chunks) {
     size_t o_cb = take(sizeof(uint32_t) * kCbScratchWords * na);
     size_t o_lut = take(sizeof(uint32_t) * (1u << kLutBits) * na);
     size_t o_bylen = take(sizeof(uint16_t) * 65536 * na);
+    size_t o_codes = take(sizeof(uint16_t) * ncode * na);
     void* base = nullptr;
     if (cudaMalloc(&base, bytes) != cudaSuccess) {
         cudaGetLastError();
@@ -74,8 +77,10 @@ sz_status ctx_reserve(sz_ctx* ctx, int arrays, uint64_t max_chunks) {
     ctx->d_cb = (uint32_t*)(ctx->ws + o_cb);
     ctx->d_lut = (uint32_t*)(ctx->ws + o_lut);
     ctx->d_bylen = (uint16_t*)(ctx->ws + o_bylen);
+    ctx->d_codes = (uint16_t*)(ctx->ws + o_codes);
     ctx->cap_arrays = na;
     ctx->cap_chunks = nc;
+    ctx->cap_codes = ncode;
     // arm the range accumulators
     std::vector<ArrayState> init(na);
     memset(init.data(), 0, sizeof(ArrayState) * na);
@@ -107,6 +112,7 @@ CompressArgs make_compress_args(sz_ctx* ctx, int slot, const float* in, uint64_t
     a.chunk_status = ctx->d_chunk_status + ctx->cap_chunks * slot;
     a.cb_scratch = ctx->d_cb + kCbScratchWords * slot;
     a.err = ctx->d_err;
+    a.codes = ctx->d_codes + ctx->cap_codes * slot;
     return a;
 }
 
@@ -189,6 +195,7 @@ void sz_ctx::free_workspace() {
     ws_bytes = 0;
     cap_arrays = 0;
     cap_chunks = 0;
+    cap_codes = 0;
 }
 
 extern "C" {
@@ -209,7 +216,7 @@ sz_status sz_ctx_create(sz_ctx** out, int device, size_t hbm_budget_bytes) {
     }
     ctx->h_err = reinterpret_cast<uint32_t*>(ctx->h_res + ctx->cap_pending);
     ctx->pend_dst.resize(ctx->cap_pending);
-    sz_status s = ctx_reserve(ctx, 1, 1024);
+    sz_status s = ctx_reserve(ctx, 1, 1024, 0);
     if (s != SZ_OK) { sz_ctx_destroy(ctx); return s; }
     *out = ctx;
     return SZ_OK;
@@ -239,7 +246,7 @@ sz_status sz_compress(sz_ctx* ctx, const float* d_in, size_t n, double eb, sz_eb
     uint32_t C, G;
     if ((s = resolve_params(params, n, &C, &G)) != SZ_OK) return s;
     cudaSetDevice(ctx->device);
-    if ((s = ctx_reserve(ctx, 1, (n + C - 1) / C)) != SZ_OK) return s;
+    if ((s = ctx_reserve(ctx, 1, (n + C - 1) / C, (uint64_t)((n + C - 1) / C) * C)) != SZ_OK) return s;
     CompressArgs a = make_compress_args(ctx, 0, d_in, n, eb, (int)kind, C, G, 0u, d_out, out_cap);
     return enqueue_compress(ctx, a, out_bytes, (cudaStream_t)stream);
 }

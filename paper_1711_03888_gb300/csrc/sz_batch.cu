@@ -9,7 +9,7 @@ sz_status batch_compress(sz_ctx* ctx, int k, const float* const* d_in, const siz
                          sz_eb_kind kind, const sz_params* params, void* const* d_out, const size_t* out_cap,
                          size_t* out_bytes, cudaStream_t s) {
     cudaSetDevice(ctx->device);
-    uint64_t maxc = 0;
+    uint64_t maxc = 0, maxcode = 0;
     for (int i = 0; i < k; ++i) {
         sz_status st = validate_compress(d_in[i], n[i], eb[i], kind, d_out[i]);
         if (st != SZ_OK) return st;
@@ -17,8 +17,9 @@ sz_status batch_compress(sz_ctx* ctx, int k, const float* const* d_in, const siz
         if ((st = resolve_params(params, n[i], &C, &G)) != SZ_OK) return st;
         uint64_t nc = (n[i] + C - 1) / C;
         if (nc > maxc) maxc = nc;
+        if (nc * C > maxcode) maxcode = nc * C;
     }
-    sz_status st = ctx_reserve(ctx, 1, maxc);
+    sz_status st = ctx_reserve(ctx, 1, maxc, maxcode);
     if (st != SZ_OK) return st;
     for (int i = 0; i < k; ++i) {
         uint32_t C, G;

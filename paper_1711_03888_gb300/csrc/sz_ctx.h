@@ -24,6 +24,8 @@ struct sz_ctx {
     uint32_t* d_cb = nullptr;
     uint32_t* d_lut = nullptr;
     uint16_t* d_bylen = nullptr;
+    uint16_t* d_codes = nullptr;
+    uint64_t cap_codes = 0;
     uint32_t* d_err = nullptr;
     // pinned result slots and where sz_sync delivers them
     uint64_t* h_res = nullptr;
@@ -58,7 +60,7 @@ struct ProfScope {
 };
 uint32_t tune_chunk(uint64_t n);
 sz_status resolve_params(const sz_params* p, uint64_t n, uint32_t* C, uint32_t* G);
-sz_status ctx_reserve(sz_ctx* ctx, int arrays, uint64_t max_chunks);
+sz_status ctx_reserve(sz_ctx* ctx, int arrays, uint64_t max_chunks, uint64_t max_code_elems);
 CompressArgs make_compress_args(sz_ctx* ctx, int slot, const float* in, uint64_t n, double eb, int kind,
                                 uint32_t C, uint32_t G, uint32_t extra_flags, void* out, uint64_t cap);
 DecompressArgs make_decompress_args(sz_ctx* ctx, int slot, const void* in, uint64_t in_bytes, float* out,

@@ -22,7 +22,7 @@ constexpr uint32_t kFlagReordered = 2u;
 constexpr uint32_t kEscBytes = 16;
 constexpr int kSubPerChunk = 64;                  // sub-streams per chunk on the GPU path
 constexpr int kRangeBlocks = 1216;                // 8 x 152 SMs
-constexpr int kLutBits = 11;                      // decoder direct-lookup width
+constexpr int kLutBits = 12;                      // decoder direct-lookup width
 
 // header byte offsets
 constexpr int H_MAGIC = 0, H_VERSION = 4, H_HDRBYTES = 6, H_N = 8, H_EB = 16, H_D = 24,
@@ -68,6 +68,7 @@ struct ArrayState {
     uint32_t first[kMaxLen + 2];
     uint32_t count[kMaxLen + 2];
     uint32_t base[kMaxLen + 2];
+    uint32_t lim[kMaxLen + 2];   // left-justified end of each length's codes (24 bits)
     uint32_t dec_ok;
     uint32_t pad1;
 };
@@ -90,6 +91,7 @@ struct CompressArgs {
     unsigned long long* chunk_status;  // n_chunks: look-back words
     uint32_t* cb_scratch;       // codebook scratch (kCbScratchWords words)
     uint32_t* err;              // context error word
+    uint16_t* codes;            // n_chunks*C u16 codes written by the quantizer, or null (encoder recomputes)
 };
 
 struct DecompressArgs {
@@ -115,17 +117,23 @@ void launch_encode(const CompressArgs* a, int k, void* stream);
 void launch_decode_setup(const DecompressArgs* a, int k, void* stream);
 void launch_decode(const DecompressArgs* a, int k, void* stream);
 
-// MD reordering
+// MD reordering (Sec. IV-B)
 struct ReorderArgs {
     const float* pos[3];        // xx, yy, zz (device)
     uint64_t n;
     double eb[3];
     int eb_kind;
-    uint32_t segment;
-    uint32_t p;
-    ArrayState* st[3];          // range state of the three coordinates
-    unsigned long long* keys;   // n
-    uint32_t* perm;             // n
+    uint32_t segment;           // S, 1 .. 65536
+    uint32_t p;                 // ignored 3-bit digits, 0 .. 21
+    const ArrayState* st[3];    // range state of the three coordinates
+    unsigned long long* qrange; // 6: per-axis min (3) and max (3) lattice value, order-mapped
+    uint32_t* key_lo;           // n: low word of key >> 3p (also sort scratch)
+    uint32_t* key_hi;           // n: high word
+    uint32_t* idx;              // n: index within the segment
+    uint32_t* tmp_k;            // n: sort scratch
+    uint32_t* tmp_v;            // n: sort scratch
+    uint32_t* perm;             // n: position j holds original index perm[j]
+    uint32_t* any_hi;           // 1: some key needs more than 32 bits
     uint32_t* err;
 };
 void launch_rindex_keys(const ReorderArgs& a, void* stream);
