@@ -1,429 +1,15 @@
-// k_codebook.cu -- a5 + a8: Huffman codebook of the quantization codes
-// (Sec. II / IV-A: Huffman coding of the codes) and the stream layout.
-//
-// One 1024-thread block per array.
-//  1. compact the used symbols (ascending) from the 65536-bin histogram;
-//  2. stable radix sort by frequency -> leaves in (frequency, symbol) order;
-//  3. two-queue Huffman, round-parallel: with s = weight of the two smallest
-//     nodes, every remaining leaf of weight <= s and every pending internal
-//     node (all of weight <= s) precede the new node s in the sequential pick
-//     order, so they pair up in merged order in one round.  Merged ranks come
-//     from binary searches (a leaf precedes an internal node of equal weight).
-//     This is exactly the sequential two-queue tree, round by round;
-//  4. depths by pointer jumping; if the deepest leaf exceeds 24 bits every
-//     frequency f becomes (f >> 1) | 1 and steps 2-4 repeat;
-//  5. canonical codes in (length, symbol) order (stable radix pass on length);
-//  6. escape bases (exclusive scan of the per-chunk escape counts), section
-//     offsets, the raw rule, header, codebook and escape-base sections.
-#include "sz_blocksort.cuh"
+// k_codebook.cu -- stand-alone launch of the codebook phase (body in sz_codebook.cuh).
+#include "sz_codebook.cuh"
 
 namespace szg {
 
-constexpr int kCbThreads = 1024;
-
-// scratch layout (u32 words)
-constexpr size_t SC_SYM = 0;
-constexpr size_t SC_FRQ = SC_SYM + 65536;
-constexpr size_t SC_WRK = SC_FRQ + 65536;
-constexpr size_t SC_KA = SC_WRK + 65536;
-constexpr size_t SC_VA = SC_KA + 65536;
-constexpr size_t SC_KB = SC_VA + 65536;
-constexpr size_t SC_VB = SC_KB + 65536;
-constexpr size_t SC_WI = SC_VB + 65536;
-constexpr size_t SC_LEN = SC_WI + 65536;
-constexpr size_t SC_PAR = SC_LEN + 65536;
-constexpr size_t SC_DA = SC_PAR + 131072;
-constexpr size_t SC_JA = SC_DA + 131072;
-constexpr size_t SC_DB = SC_JA + 131072;
-constexpr size_t SC_JB = SC_DB + 131072;
-constexpr size_t SC_END = SC_JB + 131072;
-static_assert(SC_END <= kCbScratchWords, "codebook scratch too small");
-
-struct CbSmem {
-    RadixSmem rs;
-    uint32_t ws32[kCbThreads / 32 + 1];
-    unsigned long long ws64[kCbThreads / 32 + 1];
-    uint32_t m, lf, ifr, iend, a, b, done, left_leaf, changed, maxd;
-    unsigned long long s;
-    uint32_t cnt_len[kMaxLen + 2];
-    uint32_t first[kMaxLen + 2];
-    uint32_t base[kMaxLen + 2];
-    unsigned long long off[8];
-    uint32_t raw, tables_ok;
-};
-
-__device__ __forceinline__ uint64_t pad16(uint64_t b) { return (b + 15u) & ~(uint64_t)15u; }
-
-// header writer (thread 0); payload_words / total may be patched later
-__device__ void write_header(uint8_t* out, uint64_t n, double eb_abs, float D, uint32_t flags, uint32_t C,
-                             uint32_t G, uint64_t nc, uint64_t nsym, uint64_t nesc, uint64_t pwords,
-                             const unsigned long long* off, uint64_t total) {
-    uint32_t* w32 = reinterpret_cast<uint32_t*>(out);
-    for (int i = 0; i < (int)(kHeaderBytes / 4); ++i) w32[i] = 0u;
-    *reinterpret_cast<uint32_t*>(out + H_MAGIC) = kMagic;
-    *reinterpret_cast<uint16_t*>(out + H_VERSION) = (uint16_t)kVersion;
-    *reinterpret_cast<uint16_t*>(out + H_HDRBYTES) = (uint16_t)kHeaderBytes;
-    *reinterpret_cast<uint64_t*>(out + H_N) = n;
-    *reinterpret_cast<double*>(out + H_EB) = eb_abs;
-    *reinterpret_cast<float*>(out + H_D) = D;
-    *reinterpret_cast<uint32_t*>(out + H_FLAGS) = flags;
-    *reinterpret_cast<uint32_t*>(out + H_C) = C;
-    *reinterpret_cast<uint32_t*>(out + H_G) = G;
-    *reinterpret_cast<uint16_t*>(out + H_M) = 16;
-    out[H_MAXLEN] = (uint8_t)kMaxLen;
-    out[H_PRED] = 1;
-    *reinterpret_cast<uint64_t*>(out + H_NCHUNKS) = nc;
-    *reinterpret_cast<uint64_t*>(out + H_NSYM) = nsym;
-    *reinterpret_cast<uint64_t*>(out + H_NESC) = nesc;
-    *reinterpret_cast<uint64_t*>(out + H_PWORDS) = pwords;
-    for (int s = 0; s < 8; ++s) *reinterpret_cast<uint64_t*>(out + H_OFF + 8 * s) = off[s];
-    *reinterpret_cast<uint64_t*>(out + H_TOTAL) = total;
-}
-
-// lower_bound count: number of elements < v in sorted p[0..len)
-__device__ __forceinline__ uint32_t count_less(const uint32_t* p, uint32_t len, uint64_t v) {
-    uint32_t lo = 0, hi = len;
-    while (lo < hi) {
-        uint32_t mid = (lo + hi) >> 1;
-        if ((uint64_t)p[mid] < v) lo = mid + 1; else hi = mid;
-    }
-    return lo;
-}
-// upper_bound count: number of elements <= v
-__device__ __forceinline__ uint32_t count_le(const uint32_t* p, uint32_t len, uint64_t v) {
-    uint32_t lo = 0, hi = len;
-    while (lo < hi) {
-        uint32_t mid = (lo + hi) >> 1;
-        if ((uint64_t)p[mid] <= v) lo = mid + 1; else hi = mid;
-    }
-    return lo;
-}
-
-__global__ void __launch_bounds__(kCbThreads) codebook_kernel(CompressArgs a) {
-    __shared__ CbSmem sm;
-    const int tid = threadIdx.x;
-    ArrayState* st = a.st;
-    const LatticeParams P = make_params(range_eb_abs(a.eb, a.eb_kind, st->min_key, st->max_key, st->any_finite));
-    uint8_t* out = a.out;
-    const uint64_t n = a.n;
-    const uint32_t flags = a.extra_flags & kFlagReordered;
-
-    // -------- degenerate streams: empty, or raw copy ------------------------
-    if (n == 0 || P.raw) {
-        if (tid == 0) {
-            unsigned long long off[8];
-            uint64_t words = n ? ((n + 3u) & ~(uint64_t)3u) : 0u;
-            for (int s = 0; s < 8; ++s) off[s] = kHeaderBytes;
-            uint64_t total = kHeaderBytes + 4u * words;
-            if (a.out_cap >= total)
-                write_header(out, n, P.eb_abs, P.D, flags | (n ? kFlagRaw : 0u), a.C, a.G, 0, 0, 0, words, off, total);
-            else
-                raise_err(a.err, E_CAPACITY);
-            st->raw = n ? 1u : 0u;
-            st->total_bytes = total;
-            st->ticket = 0u;
-            for (int s = 0; s < 8; ++s) st->off[s] = off[s];
-        }
-        return;
-    }
-
-    uint32_t* scr = a.cb_scratch;
-    uint32_t* sym = scr + SC_SYM;
-    uint32_t* frq = scr + SC_FRQ;
-    uint32_t* wrk = scr + SC_WRK;
-    uint32_t* lenA = scr + SC_LEN;
-
-    // -------- 1. used symbols, ascending --------------------------------------
-    {
-        const uint4* h4 = reinterpret_cast<const uint4*>(a.hist) + tid * 16;
-        uint32_t c = 0;
-#pragma unroll 4
-        for (int j = 0; j < 16; ++j) {
-            uint4 v = h4[j];
-            c += (v.x != 0) + (v.y != 0) + (v.z != 0) + (v.w != 0);
-        }
-        uint32_t tot;
-        uint32_t pos = block_exclusive_scan<kCbThreads>(c, sm.ws32, &tot);
-        for (int j = 0; j < 16; ++j) {
-            uint4 v = h4[j];
-            uint32_t e[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-            for (int t = 0; t < 4; ++t)
-                if (e[t]) {
-                    sym[pos] = (uint32_t)(tid * 64 + j * 4 + t);
-                    frq[pos] = e[t];
-                    wrk[pos] = e[t];
-                    ++pos;
-                }
-        }
-        if (tid == 0) sm.m = tot;
-        __syncthreads();
-    }
-    const uint32_t m = sm.m;
-
-    // -------- 2-4. Huffman lengths with the length limit ------------------------
-    if (m == 1) {
-        if (tid == 0) lenA[0] = 1u;
-        __syncthreads();
-    } else {
-        uint32_t* wi = scr + SC_WI;
-        uint32_t* par = scr + SC_PAR;
-        for (;;) {
-            // keys: working weights; values: ascending-symbol index
-            uint32_t wmax = 0;
-            for (uint32_t k = tid; k < m; k += kCbThreads) {
-                scr[SC_KA + k] = wrk[k];
-                scr[SC_VA + k] = k;
-                wmax = max(wmax, wrk[k]);
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
-            if ((tid & 31) == 0) sm.ws32[tid >> 5] = wmax;
-            __syncthreads();
-            if (tid == 0) {
-                uint32_t mx = 0;
-                for (int w = 0; w < kCbThreads / 32; ++w) mx = max(mx, sm.ws32[w]);
-                sm.maxd = 32 - __clz(mx);   // key bits
-            }
-            __syncthreads();
-            uint32_t *wl, *vl;
-            radix_sort<kCbThreads>(scr + SC_KA, scr + SC_VA, scr + SC_KB, scr + SC_VB, m, (int)sm.maxd, sm.rs, &wl, &vl);
-
-            // round-parallel two-queue merge
-            for (uint32_t k = tid; k < m; k += kCbThreads) wi[k] = 0u;
-            if (tid == 0) { sm.lf = 0; sm.ifr = m; sm.iend = m; }
-            __syncthreads();
-            for (;;) {
-                if (tid == 0) {
-                    uint32_t lf = sm.lf, ifr = sm.ifr, iend = sm.iend;
-                    uint32_t rem = (m - lf) + (iend - ifr);
-                    if (rem <= 1) {
-                        sm.done = 1;
-                    } else {
-                        uint32_t l = lf, i = ifr;
-                        unsigned long long s = 0;
-                        for (int t = 0; t < 2; ++t) {
-                            if (l < m && (i == iend || wl[l] <= wi[i - m])) s += wl[l++];
-                            else s += wi[(i++) - m];
-                        }
-                        sm.s = s;
-                        sm.a = count_le(wl + lf, m - lf, s);
-                        sm.b = iend - ifr;
-                        sm.done = 0;
-                    }
-                }
-                __syncthreads();
-                if (sm.done) break;
-                const uint32_t lf = sm.lf, ifr = sm.ifr, iend = sm.iend, na = sm.a, nb = sm.b;
-                const uint32_t c = na + nb, pairs = c >> 1;
-                for (uint32_t j = tid; j < na; j += kCbThreads) {
-                    uint32_t w = wl[lf + j];
-                    uint32_t r = j + count_less(wi + (ifr - m), nb, w);
-                    if (r < 2 * pairs) {
-                        uint32_t p = iend + (r >> 1);
-                        par[lf + j] = p;
-                        atomicAdd(&wi[p - m], w);
-                    } else {
-                        sm.left_leaf = 1;
-                    }
-                }
-                for (uint32_t i = tid; i < nb; i += kCbThreads) {
-                    uint32_t w = wi[ifr - m + i];
-                    uint32_t r = i + count_le(wl + lf, na, w);
-                    if (r < 2 * pairs) {
-                        uint32_t p = iend + (r >> 1);
-                        par[ifr + i] = p;
-                        atomicAdd(&wi[p - m], w);
-                    } else {
-                        sm.left_leaf = 0;
-                    }
-                }
-                __syncthreads();
-                if (tid == 0) {
-                    if (c & 1u) {
-                        if (sm.left_leaf) { sm.lf = lf + na - 1; sm.ifr = iend; }
-                        else { sm.lf = lf + na; sm.ifr = iend - 1; }
-                    } else {
-                        sm.lf = lf + na;
-                        sm.ifr = iend;
-                    }
-                    sm.iend = iend + pairs;
-                }
-                __syncthreads();
-            }
-            // depths by pointer jumping (root = 2m-2)
-            const uint32_t nodes = 2 * m - 1, root = 2 * m - 2;
-            uint32_t *DA = scr + SC_DA, *JA = scr + SC_JA, *DB = scr + SC_DB, *JB = scr + SC_JB;
-            for (uint32_t v = tid; v < nodes; v += kCbThreads) {
-                DA[v] = (v == root) ? 0u : 1u;
-                JA[v] = (v == root) ? root : par[v];
-            }
-            __syncthreads();
-            for (int it = 0; it < 40; ++it) {
-                if (tid == 0) sm.changed = 0;
-                __syncthreads();
-                uint32_t ch = 0;
-                for (uint32_t v = tid; v < nodes; v += kCbThreads) {
-                    uint32_t j = JA[v];
-                    if (j != root) {
-                        DB[v] = DA[v] + DA[j];
-                        JB[v] = JA[j];
-                        ch = 1;
-                    } else {
-                        DB[v] = DA[v];
-                        JB[v] = j;
-                    }
-                }
-                if (ch) sm.changed = 1;
-                __syncthreads();
-                uint32_t* t = DA; DA = DB; DB = t;
-                t = JA; JA = JB; JB = t;
-                if (!sm.changed) break;
-                __syncthreads();
-            }
-            uint32_t md = 0;
-            for (uint32_t j = tid; j < m; j += kCbThreads) md = max(md, DA[j]);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) md = max(md, __shfl_xor_sync(0xffffffffu, md, o));
-            if ((tid & 31) == 0) sm.ws32[tid >> 5] = md;
-            __syncthreads();
-            if (tid == 0) {
-                uint32_t mx = 0;
-                for (int w = 0; w < kCbThreads / 32; ++w) mx = max(mx, sm.ws32[w]);
-                sm.maxd = mx;
-            }
-            __syncthreads();
-            if (sm.maxd <= (uint32_t)kMaxLen) {
-                for (uint32_t j = tid; j < m; j += kCbThreads) lenA[vl[j]] = DA[j];
-                __syncthreads();
-                break;
-            }
-            for (uint32_t k = tid; k < m; k += kCbThreads) wrk[k] = (wrk[k] >> 1) | 1u;
-            __syncthreads();
-        }
-    }
-
-    // -------- 5. canonical codes in (length, symbol) order --------------------
-    for (int l = tid; l < kMaxLen + 2; l += kCbThreads) sm.cnt_len[l] = 0;
-    __syncthreads();
-    for (uint32_t k = tid; k < m; k += kCbThreads) {
-        scr[SC_KA + k] = lenA[k];
-        scr[SC_VA + k] = k;
-        atomicAdd(&sm.cnt_len[lenA[k]], 1u);
-    }
-    __syncthreads();
-    uint32_t *kl = scr + SC_KA, *vlx = scr + SC_VA;
-    if (radix_pass<kCbThreads>(scr + SC_KA, scr + SC_VA, scr + SC_KB, scr + SC_VB, m, 0, sm.rs)) {
-        kl = scr + SC_KB;
-        vlx = scr + SC_VB;
-    }
-    __syncthreads();
-    if (tid == 0) {
-        uint32_t c = 0, b = 0;
-        sm.cnt_len[0] = 0;
-        for (int l = 1; l <= kMaxLen; ++l) {
-            c = (c + sm.cnt_len[l - 1]) << 1;
-            sm.first[l] = c;
-            sm.base[l] = b;
-            b += sm.cnt_len[l];
-        }
-    }
-    __syncthreads();
-    for (uint32_t p = tid; p < m; p += kCbThreads) {
-        uint32_t l = kl[p], k = vlx[p];
-        uint32_t code = sm.first[l] + (p - sm.base[l]);
-        a.enc[sym[k]] = (code << 5) | l;
-    }
-
-    // -------- total code bits --------------------------------------------------
-    unsigned long long bits = 0;
-    for (uint32_t k = tid; k < m; k += kCbThreads) bits += (unsigned long long)frq[k] * lenA[k];
-    bits = warp_reduce_sum(bits);
-    if ((tid & 31) == 0) sm.ws64[tid >> 5] = bits;
-    __syncthreads();
-    if (tid == 0) {
-        unsigned long long t = 0;
-        for (int w = 0; w < kCbThreads / 32; ++w) t += sm.ws64[w];
-        sm.s = t;
-    }
-    __syncthreads();
-    const unsigned long long B = sm.s;
-
-    // -------- 6. escape bases (exclusive scan, in place) ----------------------
-    const uint32_t nc = a.n_chunks;
-    uint32_t carry = 0;
-    for (uint32_t t0 = 0; t0 < nc; t0 += kCbThreads) {
-        uint32_t i = t0 + tid;
-        uint32_t v = (i < nc) ? a.chunk_esc[i] : 0u;
-        uint32_t tot;
-        uint32_t ex = block_exclusive_scan<kCbThreads>(v, sm.ws32, &tot);
-        if (i < nc) a.chunk_esc[i] = carry + ex;
-        carry += tot;
-    }
-    const uint64_t E = carry;
-
-    // -------- layout and the raw rule -----------------------------------------
-    if (tid == 0) {
-        unsigned long long* off = sm.off;
-        uint64_t o = kHeaderBytes;
-        off[S_SYMS] = o;   o = pad16(o + 2ull * m);
-        off[S_LENS] = o;   o = pad16(o + m);
-        off[S_CWORD] = o;  o = pad16(o + 8ull * (nc + 1));
-        off[S_ANCHOR] = o; o = pad16(o + 8ull * nc);
-        off[S_CESC] = o;   o = pad16(o + 8ull * (nc + 1));
-        off[S_SUBLEN] = o; o = pad16(o + 2ull * nc * (a.C / a.G));
-        off[S_ESC] = o;    o = pad16(o + (uint64_t)kEscBytes * E);
-        off[S_PAYLOAD] = o;
-        uint64_t raw_total = kHeaderBytes + 4ull * ((n + 3u) & ~(uint64_t)3u);
-        uint64_t bound = o + (B + 128ull * nc + 7ull) / 8ull;
-        sm.raw = bound >= raw_total;
-        if (sm.raw) {
-            for (int s = 0; s < 8; ++s) off[s] = kHeaderBytes;
-            uint64_t words = (n + 3u) & ~(uint64_t)3u;
-            if (a.out_cap >= raw_total)
-                write_header(out, n, P.eb_abs, P.D, flags | kFlagRaw, a.C, a.G, 0, 0, 0, words, off, raw_total);
-            else
-                raise_err(a.err, E_CAPACITY);
-            st->total_bytes = raw_total;
-            sm.tables_ok = 0;
-        } else {
-            sm.tables_ok = off[S_PAYLOAD] <= a.out_cap;
-            if (a.out_cap >= kHeaderBytes)
-                write_header(out, n, P.eb_abs, P.D, flags, a.C, a.G, nc, m, E, 0, off, 0);
-        }
-        for (int s = 0; s < 8; ++s) st->off[s] = off[s];
-        st->raw = sm.raw;
-        st->n_escapes = E;
-        st->n_used = m;
-        st->bound_bits = B;
-        st->ticket = 0u;
-    }
-    __syncthreads();
-    if (sm.raw || !sm.tables_ok) return;
-
-    // -------- codebook and escape-base sections ---------------------------------
-    const unsigned long long* off = sm.off;
-    uint16_t* osym = reinterpret_cast<uint16_t*>(out + off[S_SYMS]);
-    uint8_t* olen = out + off[S_LENS];
-    for (uint32_t k = tid; k < m; k += kCbThreads) {
-        osym[k] = (uint16_t)sym[k];
-        olen[k] = (uint8_t)lenA[k];
-    }
-    uint64_t* oce = reinterpret_cast<uint64_t*>(out + off[S_CESC]);
-    for (uint32_t c = tid; c < nc; c += kCbThreads) oce[c] = a.chunk_esc[c];
-    if (tid == 0) {
-        oce[nc] = E;
-        // zero the padding bytes of the sections this kernel and the encoder write
-        for (uint64_t b = off[S_SYMS] + 2ull * m; b < off[S_LENS]; ++b) out[b] = 0;
-        for (uint64_t b = off[S_LENS] + m; b < off[S_CWORD]; ++b) out[b] = 0;
-        for (uint64_t b = off[S_CWORD] + 8ull * (nc + 1); b < off[S_ANCHOR]; ++b) out[b] = 0;
-        for (uint64_t b = off[S_ANCHOR] + 8ull * nc; b < off[S_CESC]; ++b) out[b] = 0;
-        for (uint64_t b = off[S_CESC] + 8ull * (nc + 1); b < off[S_SUBLEN]; ++b) out[b] = 0;
-    }
+__global__ void __launch_bounds__(kCbBlock) codebook_kernel(CompressArgs a) {
+    __shared__ CbSmem<kCbBlock> sm;
+    codebook_body<kCbBlock>(a, sm);
 }
 
 void launch_codebook(const CompressArgs* a, int k, void* stream) {
-    for (int i = 0; i < k; ++i) codebook_kernel<<<1, kCbThreads, 0, (cudaStream_t)stream>>>(a[i]);
+    for (int i = 0; i < k; ++i) codebook_kernel<<<1, kCbBlock, 0, (cudaStream_t)stream>>>(a[i]);
 }
 
 }  // namespace szg

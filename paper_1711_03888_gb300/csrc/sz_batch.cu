@@ -1,32 +1,235 @@
-// sz_batch.cu -- many arrays per call (the per-rank fields of a snapshot).
-// Each array's stream is byte-identical to sz_compress on that array.
+// sz_batch.cu -- many arrays per call (a15).
+//
+// Compression: one persistent launch (k_batch.cu) over every array's range,
+// quantize, codebook and encode items.  The context keeps a batch pool with
+// each array's own state, histogram, codeword table, codebook scratch and
+// per-chunk tables, sliced by that array's size.  Each stream is
+// byte-identical to sz_compress on the same array.  Arrays whose chunk size
+// is above 4096 (set explicitly through params) go through the per-array
+// path instead.
+// Decompression: the setup and decode kernels per stream, enqueued back to
+// back (each decode launch already spans the whole GPU).
 #include <string.h>
+#include <vector>
 #include "sz_ctx.h"
 
 namespace szg {
+
+namespace {
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+sz_status pool_reserve(sz_ctx* ctx, size_t bytes) {
+    if (bytes <= ctx->batch_bytes) return SZ_OK;
+    if (cudaDeviceSynchronize() != cudaSuccess) return SZ_ERR_CUDA;
+    if (ctx->batch_pool) cudaFree(ctx->batch_pool);
+    ctx->batch_pool = nullptr;
+    ctx->batch_bytes = 0;
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) { cudaGetLastError(); return SZ_ERR_NOMEM; }
+    ctx->batch_pool = (uint8_t*)p;
+    ctx->batch_bytes = bytes;
+    ctx->batch_states_armed = 0;
+    return SZ_OK;
+}
+
+}  // namespace
 
 sz_status batch_compress(sz_ctx* ctx, int k, const float* const* d_in, const size_t* n, const double* eb,
                          sz_eb_kind kind, const sz_params* params, void* const* d_out, const size_t* out_cap,
                          size_t* out_bytes, cudaStream_t s) {
     cudaSetDevice(ctx->device);
-    uint64_t maxc = 0, maxcode = 0;
+    std::vector<uint32_t> Cs(k), Gs(k);
+    std::vector<int> batched;
     for (int i = 0; i < k; ++i) {
         sz_status st = validate_compress(d_in[i], n[i], eb[i], kind, d_out[i]);
         if (st != SZ_OK) return st;
-        uint32_t C, G;
-        if ((st = resolve_params(params, n[i], &C, &G)) != SZ_OK) return st;
-        uint64_t nc = (n[i] + C - 1) / C;
-        if (nc > maxc) maxc = nc;
-        if (nc * C > maxcode) maxcode = nc * C;
+        if ((st = resolve_params(params, n[i], &Cs[i], &Gs[i])) != SZ_OK) return st;
+        if (Cs[i] <= 4096) batched.push_back(i);
     }
-    sz_status st = ctx_reserve(ctx, 1, maxc, maxcode);
-    if (st != SZ_OK) return st;
+    // arrays with large explicit chunks: the per-array path
     for (int i = 0; i < k; ++i) {
-        uint32_t C, G;
-        resolve_params(params, n[i], &C, &G);
-        CompressArgs a = make_compress_args(ctx, 0, d_in[i], n[i], eb[i], (int)kind, C, G, 0u, d_out[i], out_cap[i]);
-        if ((st = enqueue_compress(ctx, a, out_bytes ? &out_bytes[i] : nullptr, s)) != SZ_OK) return st;
+        if (Cs[i] <= 4096) continue;
+        sz_status st = sz_compress(ctx, d_in[i], n[i], eb[i], kind, params, d_out[i], out_cap[i],
+                                   out_bytes ? &out_bytes[i] : nullptr, s);
+        if (st != SZ_OK) return st;
     }
+    const uint32_t kb = (uint32_t)batched.size();
+    if (kb == 0) return SZ_OK;
+
+    // ---- pool layout: plan | counters | states | per-array buffers ------------------
+    size_t bytes = 0;
+    auto take = [&](size_t b) { size_t o = bytes; bytes += align256(b); return o; };
+    const size_t o_args = take(sizeof(CompressArgs) * kb);
+    const size_t o_tiles = take(sizeof(uint32_t) * kb);
+    const size_t o_groups = take(sizeof(uint32_t) * kb);
+    const size_t o_off = take(sizeof(uint32_t) * 4 * (kb + 1));
+    const size_t plan_bytes = bytes;
+    const size_t cnt_bytes = sizeof(BatchCounters) * kb + 256;
+    const size_t o_cnt = take(cnt_bytes);
+    const size_t o_state = take(sizeof(ArrayState) * kb);
+    std::vector<size_t> o_hist(kb), o_enc(kb), o_cb(kb), o_cesc(kb), o_cst(kb), o_codes(kb);
+    for (uint32_t j = 0; j < kb; ++j) {
+        const int i = batched[j];
+        const uint64_t nc = (n[i] + Cs[i] - 1) / Cs[i];
+        o_hist[j] = take(sizeof(uint32_t) * kNumCodes);
+        o_enc[j] = take(sizeof(uint32_t) * kNumCodes);
+        o_cb[j] = take(sizeof(uint32_t) * kCbScratchWords);
+        o_cesc[j] = take(sizeof(uint32_t) * (nc + 1));
+        o_cst[j] = take(sizeof(unsigned long long) * (nc + 1));
+        o_codes[j] = take(sizeof(uint16_t) * (nc * Cs[i] + 8));
+    }
+    sz_status st = pool_reserve(ctx, bytes);
+    if (st != SZ_OK) return st;
+    uint8_t* base = ctx->batch_pool;
+
+    // ---- plan -------------------------------------------------------------------
+    std::vector<CompressArgs> args(kb);
+    std::vector<uint32_t> tiles(kb), groups(kb), off(4 * (kb + 1));
+    uint32_t item = 0;
+    for (int ph = 0; ph < 4; ++ph) {
+        for (uint32_t j = 0; j < kb; ++j) {
+            const int i = batched[j];
+            const uint64_t nc = (n[i] + Cs[i] - 1) / Cs[i];
+            off[ph * (kb + 1) + j] = item;
+            uint32_t cnt;
+            if (ph == 0) cnt = tiles[j] = (uint32_t)((n[i] + kRangeTile - 1) / kRangeTile) + (n[i] == 0 ? 1u : 0u);
+            else if (ph == 1) cnt = groups[j] = (uint32_t)((nc + kQuantGroup - 1) / kQuantGroup);
+            else if (ph == 2) cnt = 1;
+            else cnt = (uint32_t)nc;
+            item += cnt;
+        }
+        off[ph * (kb + 1) + kb] = item;
+    }
+    uint64_t key = 1469598103934665603ull;      // FNV-1a over everything the graph bakes in
+    auto mix = [&](const void* p, size_t b) {
+        const uint8_t* c = (const uint8_t*)p;
+        for (size_t t = 0; t < b; ++t) key = (key ^ c[t]) * 1099511628211ull;
+    };
+    mix(&base, sizeof(base));
+    mix(&bytes, sizeof(bytes));
+    for (uint32_t j = 0; j < kb; ++j) {
+        const int i = batched[j];
+        CompressArgs& a = args[j];
+        memset(&a, 0, sizeof(a));
+        a.in = d_in[i];
+        a.out = (uint8_t*)d_out[i];
+        a.n = n[i];
+        a.out_cap = out_cap[i];
+        a.eb = eb[i];
+        a.eb_kind = (int)kind;
+        a.C = Cs[i];
+        a.G = Gs[i];
+        a.n_chunks = (uint32_t)((n[i] + Cs[i] - 1) / Cs[i]);
+        a.st = (ArrayState*)(base + o_state) + j;
+        a.hist = (uint32_t*)(base + o_hist[j]);
+        a.enc = (uint32_t*)(base + o_enc[j]);
+        a.cb_scratch = (uint32_t*)(base + o_cb[j]);
+        a.chunk_esc = (uint32_t*)(base + o_cesc[j]);
+        a.chunk_status = (unsigned long long*)(base + o_cst[j]);
+        a.codes = (uint16_t*)(base + o_codes[j]);
+        a.err = ctx->d_err;
+        mix(&a, sizeof(a));
+    }
+
+    if (key != ctx->bg_key || !ctx->bg_exec) {
+        // a new batch: wait for the previous graph before reusing its staging
+        if (ctx->bg_done && cudaEventSynchronize(ctx->bg_done) != cudaSuccess) { cudaGetLastError(); return SZ_ERR_CUDA; }
+        if (!ctx->bg_done && cudaEventCreateWithFlags(&ctx->bg_done, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            return SZ_ERR_CUDA;
+        }
+        if (plan_bytes > ctx->batch_host_bytes) {
+            if (ctx->batch_host) cudaFreeHost(ctx->batch_host);
+            ctx->batch_host = nullptr;
+            ctx->batch_host_bytes = 0;
+            void* h = nullptr;
+            if (cudaMallocHost(&h, plan_bytes) != cudaSuccess) { cudaGetLastError(); return SZ_ERR_NOMEM; }
+            ctx->batch_host = (uint8_t*)h;
+            ctx->batch_host_bytes = plan_bytes;
+        }
+        uint8_t* hp = ctx->batch_host;
+        memcpy(hp + o_args, args.data(), sizeof(CompressArgs) * kb);
+        memcpy(hp + o_tiles, tiles.data(), sizeof(uint32_t) * kb);
+        memcpy(hp + o_groups, groups.data(), sizeof(uint32_t) * kb);
+        memcpy(hp + o_off, off.data(), sizeof(uint32_t) * off.size());
+        // arm the per-array range accumulators of a new layout
+        if (ctx->batch_layout_bytes != bytes || ctx->batch_k != kb || !ctx->batch_states_armed) {
+            std::vector<ArrayState> init(kb);
+            memset(init.data(), 0, sizeof(ArrayState) * kb);
+            for (auto& a : init) { a.acc_min = 0xffffffffu; a.min_key = 0xffffffffu; }
+            if (cudaMemcpy(base + o_state, init.data(), sizeof(ArrayState) * kb, cudaMemcpyHostToDevice) != cudaSuccess) {
+                cudaGetLastError();
+                return SZ_ERR_CUDA;
+            }
+            ctx->batch_states_armed = 1;
+            ctx->batch_layout_bytes = bytes;
+            ctx->batch_k = kb;
+        }
+        BatchPlan plan;
+        plan.args = (const CompressArgs*)(base + o_args);
+        plan.cnt = (BatchCounters*)(base + o_cnt);
+        plan.range_tiles = (const uint32_t*)(base + o_tiles);
+        plan.quant_groups = (const uint32_t*)(base + o_groups);
+        plan.item_off = (const uint32_t*)(base + o_off);
+        plan.k = kb;
+        plan.next = (uint32_t*)(base + o_cnt + sizeof(BatchCounters) * kb);
+        plan.err = ctx->d_err;
+        // graph: plan copy and counter reset, then the persistent kernel
+        if (ctx->bg_exec) cudaGraphExecDestroy(ctx->bg_exec);
+        if (ctx->bg_graph) cudaGraphDestroy(ctx->bg_graph);
+        ctx->bg_exec = nullptr;
+        ctx->bg_graph = nullptr;
+        ctx->bg_key = 0;
+        cudaGraph_t g = nullptr;
+        cudaGraphNode_t n_copy, n_reset, n_kern;
+        void* func;
+        unsigned grid, block;
+        size_t smem;
+        batch_compress_config(&func, &grid, &block, &smem);
+        cudaMemsetParams ms;
+        memset(&ms, 0, sizeof(ms));
+        ms.dst = base + o_cnt;
+        ms.value = 0;
+        ms.elementSize = 4;
+        ms.width = cnt_bytes / 4;
+        ms.height = 1;
+        cudaKernelNodeParams kp;
+        memset(&kp, 0, sizeof(kp));
+        void* kargs[] = {&plan};
+        kp.func = func;
+        kp.gridDim = dim3(grid);
+        kp.blockDim = dim3(block);
+        kp.sharedMemBytes = (unsigned)smem;
+        kp.kernelParams = kargs;
+        cudaGraphNode_t deps[2];
+        if (cudaGraphCreate(&g, 0) != cudaSuccess ||
+            cudaGraphAddMemcpyNode1D(&n_copy, g, nullptr, 0, base, hp, plan_bytes, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaGraphAddMemsetNode(&n_reset, g, nullptr, 0, &ms) != cudaSuccess) {
+            cudaGetLastError();
+            if (g) cudaGraphDestroy(g);
+            return SZ_ERR_CUDA;
+        }
+        deps[0] = n_copy;
+        deps[1] = n_reset;
+        if (cudaGraphAddKernelNode(&n_kern, g, deps, 2, &kp) != cudaSuccess ||
+            cudaGraphInstantiate(&ctx->bg_exec, g, 0) != cudaSuccess) {
+            cudaGetLastError();
+            cudaGraphDestroy(g);
+            ctx->bg_exec = nullptr;
+            return SZ_ERR_CUDA;
+        }
+        ctx->bg_graph = g;
+        ctx->bg_key = key;
+    }
+    {
+        ProfScope pr(ctx, SZ_PHASE_BATCH, s);
+        if (cudaGraphLaunch(ctx->bg_exec, s) != cudaSuccess) { cudaGetLastError(); return SZ_ERR_CUDA; }
+    }
+    if (cudaEventRecord(ctx->bg_done, s) != cudaSuccess) { cudaGetLastError(); return SZ_ERR_CUDA; }
+    if (out_bytes)
+        for (uint32_t j = 0; j < kb; ++j)
+            if ((st = queue_result(ctx, &args[j].st->total_bytes, &out_bytes[batched[j]], s)) != SZ_OK) return st;
     return SZ_OK;
 }
 

@@ -35,6 +35,19 @@ struct sz_ctx {
     // MD reordering buffers
     uint8_t* md = nullptr;
     size_t md_bytes = 0;
+    // batched form: per-array slices of one pool
+    uint8_t* batch_pool = nullptr;
+    size_t batch_bytes = 0;
+    size_t batch_layout_bytes = 0;
+    uint32_t batch_k = 0;
+    int batch_states_armed = 0;
+    // cached CUDA graph of the last batch (plan copy + counter reset + persistent kernel)
+    uint64_t bg_key = 0;
+    cudaGraph_t bg_graph = nullptr;
+    cudaGraphExec_t bg_exec = nullptr;
+    cudaEvent_t bg_done = nullptr;
+    uint8_t* batch_host = nullptr;      // pinned plan staging
+    size_t batch_host_bytes = 0;
     // serving loop
     sz_serve_state* serve = nullptr;
     // tracing: event pairs around launches

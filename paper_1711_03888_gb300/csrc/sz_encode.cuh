@@ -1,0 +1,285 @@
+// sz_encode.cuh -- a6 + a7: Huffman encoding of the codes into chunked
+// sub-streams, the chunk tables and the escape records.
+//
+// One block of C/32 threads per chunk of C elements (chunks are taken in
+// ticket order so the decoupled look-back always waits on running blocks).
+//  pass 1 (coalesced): each thread takes one float4 per 4*blockDim step,
+//    recomputes the lattice codes (a2-a3; the predecessor comes from the
+//    neighbouring lane), looks up (codeword, length) and stores the packed
+//    entry in shared memory, swizzled so the next pass is conflict-free;
+//  pass 2: thread t loads the 32 consecutive entries t*32 .. t*32+31 into
+//    registers; block scans give its start bit and escape index; the chunk's
+//    word offset comes from the look-back over preceding chunks;
+//  pass 3: thread t packs its 32 codewords MSB-first into the (now free)
+//    shared buffer -- interior words by plain stores, its first and last
+//    word by atomicOr -- and the chunk leaves with 128-bit stores.
+// Sub-stream k (G = C/64 elements) is threads [kG/32, (k+1)G/32), so its bit
+// length is a shuffle reduction over G/32 lanes.  Escape records are rebuilt
+// from global memory (rare).
+#pragma once
+#include "sz_device.cuh"
+
+namespace szg {
+
+constexpr uint32_t kLookbackSpins = 1u << 22;
+
+// raw stream: words [wb, we) of the payload are the input bits (zero past n)
+__device__ __forceinline__ void raw_copy_words(const CompressArgs& a, uint64_t wb, uint64_t we, uint64_t t0,
+                                               uint64_t tstride) {
+    if (a.st->total_bytes > a.out_cap) return;
+    uint32_t* dst = reinterpret_cast<uint32_t*>(a.out + kHeaderBytes);
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(a.in);
+    for (uint64_t i = wb + t0; i < we; i += tstride) dst[i] = (i < a.n) ? __ldg(src + i) : 0u;
+}
+
+template <int NT>
+struct EncSmem {
+    uint32_t ws32[NT / 32 + 1], ws32b[NT / 32 + 1];
+    unsigned long long prefix;
+};
+
+// Encode chunk c of array a with a block of NT threads, kRun = C / NT
+// consecutive elements per thread.  buf: C words of shared memory.
+template <int NT, int kRun, bool FROM_CODES>
+__device__ void encode_chunk(const CompressArgs& a, const uint32_t c, uint32_t* buf, EncSmem<NT>& esm) {
+    constexpr int C = NT * kRun;
+    constexpr int kRunShift = kRun == 8 ? 3 : (kRun == 16 ? 4 : 5);
+    static_assert(kRun == 8 || kRun == 16 || kRun == 32, "run length");
+    uint32_t* ws32 = esm.ws32;
+    uint32_t* ws32b = esm.ws32b;
+    unsigned long long& s_prefix = esm.prefix;
+    ArrayState* st = a.st;
+    const int tid = threadIdx.x, lane = tid & 31;
+
+    const LatticeParams P = make_params(range_eb_abs(a.eb, a.eb_kind, st->min_key, st->max_key, st->any_finite));
+    const uint64_t n = a.n, base = (uint64_t)c * C;
+    const uint32_t cnt = (uint32_t)umin64(C, n - base);
+    const float* in = a.in;
+    const bool vec = ((uintptr_t)in & 15u) == 0;
+    const uint32_t* enc = a.enc;
+    const uint32_t e0 = tid * kRun;
+    uint32_t r[kRun];
+    long long anchor = 0;
+
+    if (FROM_CODES) {
+        // ---- pass 1+2: the quantizer's codes for elements e0 .. e0+31 ----------------
+        const uint16_t* cp = a.codes + base + e0;
+        uint32_t w[kRun / 2];
+        if (e0 + kRun <= cnt) {
+#pragma unroll
+            for (int m = 0; m < kRun / 8; ++m) {
+                uint4 v = __ldg(reinterpret_cast<const uint4*>(cp) + m);
+                w[4 * m] = v.x; w[4 * m + 1] = v.y; w[4 * m + 2] = v.z; w[4 * m + 3] = v.w;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < kRun / 2; ++j) {
+                uint32_t lo = (e0 + 2 * j < cnt) ? __ldg(cp + 2 * j) : 0u;
+                uint32_t hi = (e0 + 2 * j + 1 < cnt) ? __ldg(cp + 2 * j + 1) : 0u;
+                w[j] = lo | (hi << 16);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kRun; ++j) {
+            const uint32_t code = (j & 1) ? (w[j >> 1] >> 16) : (w[j >> 1] & 0xffffu);
+            const uint32_t ent = __ldg(enc + code);
+            r[j] = (e0 + j < cnt) ? (((ent >> 5) << 6) | ((ent & 31u) << 1) | (code == 0u ? 1u : 0u)) : 0u;
+        }
+        if (tid == 0 && base > 0) {
+            bool vv;
+            lattice_q(__ldg(in + base - 1), P, anchor, vv);
+        }
+    } else {
+    // ---- pass 1: codes and (codeword, length), coalesced -----------------------
+#pragma unroll 2
+    for (uint32_t e = 4 * tid; e < (uint32_t)C; e += 4 * NT) {
+        float x[4];
+        if (vec && e + 3 < cnt) {
+            float4 v = __ldg(reinterpret_cast<const float4*>(in + base + e));
+            x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) x[j] = (e + j < cnt) ? __ldg(in + base + e + j) : 0.0f;
+        }
+        long long q[4];
+        bool vb[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) lattice_q(x[j], P, q[j], vb[j]);
+        long long qprev = __shfl_up_sync(0xffffffffu, q[3], 1);
+        if (lane == 0) {
+            qprev = 0;
+            if (base + e > 0 && e < cnt) {
+                bool vv;
+                lattice_q(__ldg(in + base + e - 1), P, qprev, vv);
+            }
+            if (e == 0) anchor = qprev;
+        }
+        uint32_t pk[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            pk[j] = 0u;
+            if (e + j < cnt) {
+                uint32_t code = make_code(q[j], j == 0 ? qprev : q[j - 1], vb[j]);
+                uint32_t ent = __ldg(enc + code);
+                pk[j] = ((ent >> 5) << 6) | ((ent & 31u) << 1) | (code == 0u ? 1u : 0u);
+            }
+        }
+        *reinterpret_cast<uint4*>(&buf[swz(e, kRunShift)]) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    }
+    __syncthreads();
+
+    // ---- pass 2: this thread's 32 consecutive entries ---------------------------
+#pragma unroll
+    for (int m = 0; m < kRun / 4; ++m) {
+        uint4 v = *reinterpret_cast<const uint4*>(&buf[swz(e0 + 4 * m, kRunShift)]);
+        r[4 * m] = v.x; r[4 * m + 1] = v.y; r[4 * m + 2] = v.z; r[4 * m + 3] = v.w;
+    }
+    }  // !FROM_CODES
+    uint32_t bits = 0, escs = 0;
+#pragma unroll
+    for (int j = 0; j < kRun; ++j) {
+        bits += (r[j] >> 1) & 31u;
+        escs += r[j] & 1u;
+    }
+    uint32_t chunk_bits, chunk_escs;
+    const uint32_t start = block_exclusive_scan<NT>(bits, ws32, &chunk_bits);
+    const uint32_t eoff = block_exclusive_scan<NT>(escs, ws32b, &chunk_escs);
+    const uint32_t chunk_words = ((chunk_bits + 127u) >> 7) << 2;
+    // sub-stream bit length: reduce over the G/32 lanes that share sub-stream
+    constexpr int kLanesPerSub = C / kSubPerChunk / kRun;   // 1, 2, 4 or 8
+    uint32_t sub_bits = bits;
+#pragma unroll
+    for (int o = 1; o < kLanesPerSub; o <<= 1) sub_bits += __shfl_xor_sync(0xffffffffu, sub_bits, o);
+
+    // ---- publish this chunk's size for the look-back of later chunks --------------
+    unsigned long long* status = a.chunk_status;
+    constexpr unsigned long long FLAG_AGG = 1ull << 62, FLAG_INC = 2ull << 62, FLAG_ERR = 3ull << 62;
+    constexpr unsigned long long VMASK = (1ull << 62) - 1;
+    if (tid == 0) st_release(&status[c], (c == 0 ? FLAG_INC : FLAG_AGG) | chunk_words);
+    // zero the payload area (the code entries are in registers now)
+    for (uint32_t w = tid; w < chunk_words; w += NT) buf[w] = 0u;
+    __syncthreads();
+
+    // ---- pass 3: pack into shared memory ------------------------------------------
+    {
+        uint32_t word = start >> 5, fill = start & 31u, cur = 0u;
+        bool first = true;
+#pragma unroll
+        for (int j = 0; j < kRun; ++j) {
+            const uint32_t len = (r[j] >> 1) & 31u;
+            const uint32_t cw = r[j] >> 6;
+            const uint32_t room = 32u - fill;
+            if (len < room) {
+                cur |= cw << (room - len);   // len == 0 leaves cur unchanged
+                fill += len;
+            } else {
+                const uint32_t spill = len - room;   // 0..23
+                cur |= cw >> spill;
+                if (first) atomicOr(&buf[word], cur); else buf[word] = cur;
+                first = false;
+                ++word;
+                cur = spill ? (cw << (32u - spill)) : 0u;
+                fill = spill;
+            }
+        }
+        if (fill) atomicOr(&buf[word], cur);
+    }
+
+    // ---- escape records (rare): rebuilt from global memory ---------------------
+    uint8_t* out = a.out;
+    const uint64_t off_payload = st->off[S_PAYLOAD];
+    const bool tables_ok = off_payload <= a.out_cap;
+    if (escs && tables_ok) {
+        uint8_t* esc_base = out + st->off[S_ESC] + (uint64_t)kEscBytes * (a.chunk_esc[c] + eoff);
+        uint32_t idx = 0;
+#pragma unroll
+        for (int j = 0; j < kRun; ++j) {
+            if (r[j] & 1u) {
+                uint64_t i = base + e0 + j;
+                float x = __ldg(in + i);
+                long long q, qp = 0;
+                bool vb, vv;
+                lattice_q(x, P, q, vb);
+                if (i > 0) lattice_q(__ldg(in + i - 1), P, qp, vv);
+                uint8_t* rec = esc_base + (uint64_t)kEscBytes * idx++;
+                *reinterpret_cast<long long*>(rec) = q - qp;
+                *reinterpret_cast<uint32_t*>(rec + 8) = vb ? __float_as_uint(x) : 0u;
+                *reinterpret_cast<uint32_t*>(rec + 12) = vb ? 1u : 0u;
+            }
+        }
+    }
+
+    // ---- decoupled look-back, one warp, 32 predecessors per step --------------------
+    if (tid < 32 && c > 0) {
+        unsigned long long excl = 0;
+        bool bad = false;
+        long long j = (long long)c - 1;
+        while (j >= 0) {
+            const long long pos = j - tid;
+            unsigned long long s = FLAG_INC;               // before chunk 0: an empty prefix
+            if (pos >= 0) {
+                uint32_t spins = 0;
+                s = ld_acquire(&status[pos]);
+                while ((s & ~VMASK) == 0ull && spins < kLookbackSpins) {
+                    __nanosleep(64);
+                    s = ld_acquire(&status[pos]);
+                    ++spins;
+                }
+            }
+            const unsigned long long f = s & ~VMASK;
+            if (__any_sync(0xffffffffu, f == 0ull || f == FLAG_ERR)) { bad = true; break; }
+            const uint32_t inc = __ballot_sync(0xffffffffu, f == FLAG_INC);
+            const int lim = inc ? (__ffs(inc) - 1) : 31;    // lanes 0..lim contribute
+            unsigned long long v = (tid <= lim) ? (s & VMASK) : 0ull;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            excl += v;
+            if (inc) break;
+            j -= 32;
+        }
+        if (tid == 0) {
+            if (bad) {
+                raise_err(a.err, E_TIMEOUT);
+                st_release(&status[c], FLAG_ERR);
+            } else {
+                st_release(&status[c], FLAG_INC | (excl + chunk_words));
+            }
+            s_prefix = bad ? ~0ull : excl;
+        }
+    } else if (tid == 0) {
+        s_prefix = 0ull;
+    }
+    __syncthreads();
+    const unsigned long long prefix = s_prefix;
+    if (prefix == ~0ull) return;
+
+    // ---- tables ------------------------------------------------------------------
+    const uint64_t chunk_end = off_payload + 4ull * (prefix + chunk_words);
+    if (tables_ok) {
+        if ((tid % kLanesPerSub) == 0) {
+            const uint32_t k = tid / kLanesPerSub;
+            reinterpret_cast<uint16_t*>(out + st->off[S_SUBLEN])[(uint64_t)c * kSubPerChunk + k] =
+                (uint16_t)(e0 < cnt ? sub_bits : 0u);
+        }
+        if (tid == 0) {
+            reinterpret_cast<uint64_t*>(out + st->off[S_CWORD])[c] = prefix;
+            reinterpret_cast<long long*>(out + st->off[S_ANCHOR])[c] = anchor;
+            if (c == a.n_chunks - 1) reinterpret_cast<uint64_t*>(out + st->off[S_CWORD])[c + 1] = prefix + chunk_words;
+        }
+    }
+    if (c == a.n_chunks - 1 && tid == 0) {
+        st->total_bytes = chunk_end;
+        if (a.out_cap >= kHeaderBytes) {
+            *reinterpret_cast<uint64_t*>(out + H_PWORDS) = prefix + chunk_words;
+            *reinterpret_cast<uint64_t*>(out + H_TOTAL) = chunk_end;
+        }
+        if (chunk_end > a.out_cap) raise_err(a.err, E_CAPACITY);
+    }
+    if (tables_ok && chunk_end <= a.out_cap) {
+        uint4* dst = reinterpret_cast<uint4*>(out + off_payload + 4ull * prefix);
+        const uint4* src = reinterpret_cast<const uint4*>(buf);
+        for (uint32_t w4 = tid; w4 < chunk_words / 4; w4 += NT) dst[w4] = src[w4];
+    }
+}
+
+}  // namespace szg

@@ -117,6 +117,30 @@ void launch_encode(const CompressArgs* a, int k, void* stream);
 void launch_decode_setup(const DecompressArgs* a, int k, void* stream);
 void launch_decode(const DecompressArgs* a, int k, void* stream);
 
+// Batched form: one persistent launch over every array's work items.
+constexpr uint32_t kRangeTile = 1u << 16;   // elements per range item
+constexpr uint32_t kQuantGroup = 8;         // chunks per quantize item
+
+struct BatchCounters {          // per array, zeroed before the launch
+    uint32_t range_done;        // range tiles finished
+    uint32_t range_ready;       // 1 once the last tile published min / max
+    uint32_t quant_done;        // quantize groups finished (histogram flushed)
+    uint32_t cb_ready;          // 1 once the codebook and layout are written
+};
+
+struct BatchPlan {
+    const CompressArgs* args;   // k (device)
+    BatchCounters* cnt;         // k (device)
+    const uint32_t* range_tiles;   // k
+    const uint32_t* quant_groups;  // k
+    const uint32_t* item_off;   // 4 x (k + 1): cumulative item offsets per phase, phase-major
+    uint32_t k;
+    uint32_t* next;             // item counter (zeroed before the launch)
+    uint32_t* err;
+};
+void launch_batch_compress(const BatchPlan& plan, void* stream);
+void batch_compress_config(void** func, unsigned* grid, unsigned* block, size_t* smem);
+
 // MD reordering (Sec. IV-B)
 struct ReorderArgs {
     const float* pos[3];        // xx, yy, zz (device)

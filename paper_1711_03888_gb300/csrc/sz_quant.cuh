@@ -1,0 +1,161 @@
+// sz_quant.cuh -- a2-a4 body: one chunk of value -> lattice, last-value
+// prediction on the lattice, linear-scaling quantization into 2^16 codes
+// (Sec. IV-A) and the code histogram, for a block of 256 threads.
+//
+// Each of the 8 warps owns a contiguous span of C/8 elements and walks it
+// 256 elements per step (two 128-element groups, both float4 loads issued
+// first), carrying the last lattice value from lane 31 to lane 0 of the next
+// group, so only the first group of a span recomputes a predecessor.  The
+// common case runs in 32-bit arithmetic: a refined FP32 candidate (x*inv
+// corrected by one fma residual) is exact except within 2^-20 of a
+// half-integer, which the residual test detects; any warp step holding such
+// an element, or a candidate beyond 2^22, takes the general binary64 path
+// for that step.  Codes near the centre go to a shared-memory window of the
+// histogram, the rest to global atomics.  When `codes` is set the u16 codes
+// are stored for the encoder.  The chunk's escape count is recorded and the
+// encoder's look-back word re-armed.
+#pragma once
+#include "sz_device.cuh"
+
+namespace szg {
+
+constexpr int kQuantThreads = 256;
+constexpr int kWin = 8192;                 // shared histogram window (codes 28672..36863)
+constexpr uint32_t kWinLo = kRadius - kWin / 2;
+
+__device__ __forceinline__ void hist_add(uint32_t code, uint32_t* sh, uint32_t* gh) {
+    uint32_t w = code - kWinLo;
+    if (w < (uint32_t)kWin) atomicAdd(&sh[w], 1u);
+    else atomicAdd(&gh[code], 1u);
+}
+
+// FP32 fast path: returns false when the element needs the general path.
+__device__ __forceinline__ bool lattice_fast32(float x, const LatticeParams& P, int& q, bool& verb) {
+    float t1 = x * P.inv;
+    float e = fmaf(-t1, P.D, x);
+    float t = fmaf(e, P.inv, t1);
+    float qc = rintf(t);
+    float r = fmaf(-qc, P.D, x);
+    float xr = __fmul_rn(qc, P.D);
+    verb = fabsf(__fsub_rn(x, xr)) > P.ebf;
+    q = __float2int_rz(qc);
+    return (fabsf(r) <= P.thr_lo) & (fabsf(t) < 4194304.0f);
+}
+
+__device__ __forceinline__ uint32_t code32(int q, int qprev, bool verb) {
+    int d = q - qprev;
+    return (verb || (uint32_t)(d + (kRadius - 1)) > (uint32_t)(2 * kRadius - 2)) ? 0u : (uint32_t)(d + kRadius);
+}
+
+__device__ __forceinline__ void hist_window_zero(uint32_t* sh) {
+    for (int i = threadIdx.x; i < kWin; i += kQuantThreads) sh[i] = 0u;
+}
+
+__device__ __forceinline__ void hist_window_flush(uint32_t* sh, uint32_t* gh) {
+    for (int i = threadIdx.x; i < kWin; i += kQuantThreads) {
+        uint32_t v = sh[i];
+        if (v) atomicAdd(&gh[kWinLo + i], v);
+    }
+}
+
+template <bool STORE>
+__device__ void quant_chunk(const CompressArgs& a, const LatticeParams& P, uint32_t c, uint32_t* sh,
+                            uint32_t* s_esc) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const float* in = a.in;
+    const bool vec = ((uintptr_t)in & 15u) == 0;
+    const bool fast_ok = P.fast != 0;
+    const uint64_t n = a.n;
+    const uint32_t span = a.C / 8;
+    uint16_t* codes = a.codes;
+    const uint64_t s0 = (uint64_t)c * a.C + (uint64_t)warp * span;
+    const uint64_t s1 = umin64(n, s0 + span);
+    uint32_t esc = 0;
+    long long carry = 0;
+    if (s0 < s1 && s0 > 0 && lane == 0) {
+        bool vv;
+        lattice_q(__ldg(in + s0 - 1), P, carry, vv);
+    }
+    carry = __shfl_sync(0xffffffffu, carry, 0);
+    for (uint64_t ib = s0; ib < s1; ib += 256) {
+        float xg[2][4];
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {
+            const uint64_t i = ib + 128 * g + 4 * (uint64_t)lane;
+            if (vec && ib + 128 * g + 128 <= s1) {
+                float4 v = __ldg(reinterpret_cast<const float4*>(in + i));
+                xg[g][0] = v.x; xg[g][1] = v.y; xg[g][2] = v.z; xg[g][3] = v.w;
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) xg[g][j] = (i + j < s1) ? __ldg(in + i + j) : 0.0f;
+            }
+        }
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {
+            const uint64_t i0 = ib + 128 * g;
+            if (i0 >= s1) break;
+            const uint64_t i = i0 + 4 * (uint64_t)lane;
+            const bool full = (i0 + 128 <= s1);
+            float x[4] = {xg[g][0], xg[g][1], xg[g][2], xg[g][3]};
+            uint32_t cd[4];
+            int q32[4];
+            bool vb[4];
+            bool ok = fast_ok;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) ok &= lattice_fast32(x[j], P, q32[j], vb[j]);
+            if (__all_sync(0xffffffffu, ok) && carry >= -(1ll << 30) && carry <= (1ll << 30)) {
+                int qp = __shfl_up_sync(0xffffffffu, q32[3], 1);
+                if (lane == 0) qp = (int)carry;
+                cd[0] = code32(q32[0], qp, vb[0]);
+                cd[1] = code32(q32[1], q32[0], vb[1]);
+                cd[2] = code32(q32[2], q32[1], vb[2]);
+                cd[3] = code32(q32[3], q32[2], vb[3]);
+                carry = __shfl_sync(0xffffffffu, q32[3], 31);
+            } else {
+                long long q[4];
+                bool v2[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) lattice_q(x[j], P, q[j], v2[j]);
+                long long qp = __shfl_up_sync(0xffffffffu, q[3], 1);
+                if (lane == 0) qp = carry;
+                cd[0] = make_code(q[0], qp, v2[0]);
+                cd[1] = make_code(q[1], q[0], v2[1]);
+                cd[2] = make_code(q[2], q[1], v2[2]);
+                cd[3] = make_code(q[3], q[2], v2[3]);
+                // only full groups continue, so lane 31's q[3] is the last element
+                carry = __shfl_sync(0xffffffffu, q[3], 31);
+            }
+            if (full) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    esc += (cd[j] == 0u);
+                    hist_add(cd[j], sh, a.hist);
+                }
+                if (STORE) {
+                    uint2 pk = make_uint2(cd[0] | (cd[1] << 16), cd[2] | (cd[3] << 16));
+                    *reinterpret_cast<uint2*>(codes + i) = pk;
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (i + j < s1) {
+                        esc += (cd[j] == 0u);
+                        hist_add(cd[j], sh, a.hist);
+                        if (STORE) codes[i + j] = (uint16_t)cd[j];
+                    }
+            }
+        }
+    }
+    esc = warp_reduce_sum(esc);
+    if (lane == 0) s_esc[warp] = esc;
+    __syncthreads();
+    if (tid == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < kQuantThreads / 32; ++w) t += s_esc[w];
+        a.chunk_esc[c] = t;
+        a.chunk_status[c] = 0ull;
+    }
+    __syncthreads();
+}
+
+}  // namespace szg

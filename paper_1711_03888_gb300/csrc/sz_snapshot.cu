@@ -13,6 +13,21 @@ void sz_ctx::free_extra() {
     if (md) cudaFree(md);
     md = nullptr;
     md_bytes = 0;
+    if (batch_pool) cudaFree(batch_pool);
+    batch_pool = nullptr;
+    batch_bytes = 0;
+    batch_layout_bytes = 0;
+    batch_states_armed = 0;
+    if (bg_exec) cudaGraphExecDestroy(bg_exec);
+    if (bg_graph) cudaGraphDestroy(bg_graph);
+    if (bg_done) cudaEventDestroy(bg_done);
+    if (batch_host) cudaFreeHost(batch_host);
+    bg_exec = nullptr;
+    bg_graph = nullptr;
+    bg_done = nullptr;
+    batch_host = nullptr;
+    batch_host_bytes = 0;
+    bg_key = 0;
 }
 
 namespace {

@@ -1,0 +1,91 @@
+"""GPU parity of the batched form (one persistent launch over many arrays):
+every array's stream must be byte-identical to sz_compress on that array
+(and to the oracle), whatever the mix of sizes, bounds and degenerate cases."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sz():
+    import __graft_entry__ as g
+    g.build()
+    import paper_1711_03888_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(sz):
+    c = sz.Context(0)
+    yield c
+    c.close()
+
+
+def _plain(sz, ctx, x, eb, kind):
+    out, nb = sz.sz_compress(ctx, x, eb, kind)
+    sz.sz_sync(ctx)
+    return out[: nb.value].cpu().numpy().tobytes()
+
+
+def _batch(sz, ctx, xs, ebs, kind):
+    outs, nb = sz.sz_compress_batch(ctx, xs, ebs, kind)
+    sz.sz_sync(ctx)
+    return [outs[i][: nb[i]].cpu().numpy().tobytes() for i in range(len(xs))]
+
+
+def _edge_arrays():
+    rng = np.random.default_rng(3)
+    xs = []
+    for n in [0, 1, 5, 2047, 2049, 70001, 200000, 65536, 65537]:
+        xs.append(synth.random_walk_f32(n, int(rng.integers(1 << 20))))
+    xs.append(torch.full((9000,), 7.0, dtype=torch.float32))           # R = 0: raw
+    w = synth.uniform_f32(30000, 7, -1e30, 1e30).numpy().copy()
+    w[::97] = np.nan
+    w[5::211] = np.inf
+    xs.append(torch.from_numpy(w))                                    # NaN / Inf
+    s = synth.random_walk_f32(40000, 8, 1e-3).numpy().copy()
+    s[::777] = 1e6
+    xs.append(torch.from_numpy(s))                                    # escapes
+    xs.append(synth.uniform_f32(1 << 15, 9, -1.0, 1.0))               # raw by the size rule at tiny eb
+    return xs
+
+
+def test_batch_edge_mix_matches_oracle(sz, ctx, oracle):
+    xs = _edge_arrays()
+    ebs = [1e-3, 1e-4, 1e-2, 1e-5, 1e-4, 1e-3, 1e-4, 1e-3, 1e-4, 1e-4, 1e-4, 1e-6, 1e-9]
+    for kind in (sz.SZ_EB_REL, sz.SZ_EB_ABS):
+        got = _batch(sz, ctx, [x.cuda() for x in xs], ebs, kind)
+        for x, e, g in zip(xs, ebs, got):
+            h = oracle.parse_header(g)
+            assert g == oracle.compress(x.numpy(), e, kind, h["chunk"], h["sub"])
+
+
+def test_batch_repeated_calls_and_shapes(sz, ctx):
+    """The pool is reused across calls and re-laid out for new shapes."""
+    a = [synth.random_walk_f32(n, n).cuda() for n in (3000, 500000, 12345)]
+    b = [synth.random_walk_f32(n, n + 1).cuda() for n in (70000, 10, 999999, 4096, 1)]
+    for xs in (a, a, b, a, b):
+        ebs = [1e-4] * len(xs)
+        got = _batch(sz, ctx, xs, ebs, sz.SZ_EB_REL)
+        assert got == [_plain(sz, ctx, x, 1e-4, sz.SZ_EB_REL) for x in xs]
+
+
+def test_batch_full_config_many_ranks(sz, ctx, oracle):
+    """The batched workload: 128 simulated ranks x 6 fields, sizes 2^14..2^24,
+    relative bounds from {1e-3, 1e-4}.  Every stream equals the plain path's;
+    a sample is checked against the oracle."""
+    arrays = synth.batch_ranks(device="cuda")
+    xs = [t for _, _, t, _ in arrays]
+    ebs = [e for _, _, _, e in arrays]
+    assert len(xs) == 768
+    got = _batch(sz, ctx, xs, ebs, sz.SZ_EB_REL)
+    for x, e, g in zip(xs, ebs, got):
+        assert g == _plain(sz, ctx, x, e, sz.SZ_EB_REL)
+    rng = np.random.default_rng(0)
+    for i in rng.choice(768, 6, replace=False):
+        h = oracle.parse_header(got[i])
+        assert got[i] == oracle.compress(xs[i].cpu().numpy(), ebs[i], 1, h["chunk"], h["sub"])
