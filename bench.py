@@ -190,6 +190,164 @@ def cpu_sample(snap, n_sample):
 
 # ---------------------------------------------------------------------------
 
+# ---------------------------------------------------------------------------
+# Served form: Poisson arrivals of compress / decompress requests
+# ---------------------------------------------------------------------------
+
+def _percentile(v, q):
+    import numpy as np
+    return float(np.percentile(np.asarray(v), q)) if len(v) else None
+
+
+def make_requests(rng, rate, seconds, pools, streams, log2_lo=18.0, log2_hi=27.0):
+    """Open-loop request list: (arrival_s, op, tensor, n, in_bytes).  Sizes are
+    2^U[log2_lo, log2_hi] floats sliced (16-byte aligned) from the device
+    pools; decompress requests take one of the pre-compressed streams."""
+    t, out = 0.0, []
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t >= seconds:
+            return out
+        if rng.random() < 0.5:
+            n = int(round(2.0 ** rng.uniform(log2_lo, log2_hi)))
+            fits = [p for p in pools if p.numel() >= n]
+            src = fits[int(rng.integers(len(fits)))]
+            off = int(rng.integers(0, (src.numel() - n) // 4 + 1)) * 4
+            out.append((t, "c", src[off: off + n], n, 0))
+        else:
+            st, n, nb = streams[int(rng.integers(len(streams)))]
+            out.append((t, "d", st, n, nb))
+
+
+def run_served(sz, ctx, reqs, eb):
+    """Submit at the arrival times (producer), wait and release in ticket order
+    (consumer thread).  Returns per-request latencies and the makespan."""
+    import ctypes as C
+    tickets = [None] * len(reqs)
+    lat = [0.0] * len(reqs)
+    bad = []
+    ready = threading.Semaphore(0)
+
+    def consumer():
+        for i in range(len(reqs)):
+            ready.acquire()
+            r = sz.sz_serve_wait(ctx, tickets[i], 600.0)
+            if r.status != sz.SZ_OK:
+                bad.append((i, r.status))
+            lat[i] = r.latency_s
+            if r.out:
+                sz.sz_serve_release(ctx, r.out)
+
+    th = threading.Thread(target=consumer)
+    # the producer sleeps between arrivals (releasing the GIL) and spins only
+    # for the last 0.2 ms, so the consumer releases outputs promptly
+    old_sw = sys.getswitchinterval()
+    sys.setswitchinterval(1e-4)
+    th.start()
+    t0 = time.perf_counter()
+    for i, (ta, op, x, n, nb) in enumerate(reqs):
+        while True:
+            d = ta - (time.perf_counter() - t0)
+            if d <= 0:
+                break
+            if d > 3e-4:
+                time.sleep(d - 2e-4)
+        if op == "c":
+            req = sz.request(sz.SZ_OP_COMPRESS, x, n, eb=eb, kind=sz.SZ_EB_REL)
+        else:
+            req = sz.request(sz.SZ_OP_DECOMPRESS, x, n, in_bytes=nb)
+        tickets[i] = sz.sz_serve_submit(ctx, req)
+        ready.release()
+    th.join()
+    span = time.perf_counter() - t0
+    sys.setswitchinterval(old_sw)
+    if bad:
+        raise RuntimeError(f"served requests failed: {bad[:5]}")
+    return lat, span
+
+
+def run_serial_plain(sz, ctx, reqs, eb, out_c, out_d):
+    """The same requests back to back through sz_compress / sz_decompress on
+    one stream; per-request device time from CUDA events.  Latency under the
+    same arrivals follows the single-server queue: c_i = max(a_i, c_{i-1}) + s_i."""
+    import torch
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in reqs]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for e, (ta, op, x, n, nb) in zip(ev, reqs):
+        e[0].record(stream)
+        if op == "c":
+            sz.sz_compress(ctx, x, eb, sz.SZ_EB_REL, None, out_c)
+        else:
+            sz.sz_decompress(ctx, x, nb, out_d, n)
+        e[1].record(stream)
+    sz.sz_sync(ctx)
+    torch.cuda.synchronize()
+    span = time.perf_counter() - t0
+    svc = [a.elapsed_time(b) / 1e3 for a, b in ev]
+    c, lat = 0.0, []
+    for (ta, *_), s in zip(reqs, svc):
+        c = max(ta, c) + s
+        lat.append(c - ta)
+    return lat, sum(svc), span
+
+
+def served_bench(sz, snap, eb, rate, seconds, stress, stress_seconds, slots, budget_gb, device):
+    """Config-4 style serving run; returns the "served" object of the JSON line."""
+    import numpy as np
+    import torch
+    import synth
+    rng = np.random.default_rng(5)
+    md = synth.md_fcc(device="cuda")
+    pools = [snap[f] for f in FIELDS] + [md[f] for f in ("xx", "yy", "zz")]
+    plain = sz.Context(device)
+    # pre-compressed streams for the decompress requests
+    streams = []
+    for i in range(32):
+        n = int(round(2.0 ** rng.uniform(18.0, 27.0)))
+        fits = [p for p in pools if p.numel() >= n]
+        src = fits[int(rng.integers(len(fits)))]
+        off = int(rng.integers(0, (src.numel() - n) // 4 + 1)) * 4
+        out, nb = sz.sz_compress(plain, src[off: off + n], eb, sz.SZ_EB_REL)
+        sz.sz_sync(plain)
+        streams.append((out[: nb.value].clone(), n, nb.value))
+        del out
+    nmax = max(p.numel() for p in pools)
+    out_c = torch.empty(sz.sz_max_compressed_bytes(nmax), dtype=torch.uint8, device="cuda")
+    out_d = torch.empty(nmax, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+
+    ctx = sz.Context(device, budget=int(budget_gb * (1 << 30)))
+    sz.sz_serve_start(ctx, slots)
+    # warm-up: every slot's workspace grows to the largest request size once
+    big = pools[0][: nmax // 4 * 4]
+    warm = [(0.0, "c", big, big.numel(), 0)] * slots + [(0.0, "d", st, n, nb) for st, n, nb in streams[:slots]]
+    run_served(sz, ctx, warm, eb)
+
+    res = {"workload": f"Poisson arrivals, {rate:g} req/s for {seconds:g} s; compress or decompress (p=1/2); "
+                       f"2^U[18,27] float32 per request sliced from the cosmology snapshot and the MD crystal; "
+                       f"rel eb {eb:g}",
+           "slots": slots, "budget_gb": budget_gb}
+    for tag, lam, secs in (("nominal", rate, seconds), ("stress", rate * stress, stress_seconds)):
+        reqs = make_requests(rng, lam, secs, pools, streams)
+        nbytes = sum(4 * r[3] for r in reqs)
+        lat, span = run_served(sz, ctx, reqs, eb)
+        lat_p, busy_p, span_p = run_serial_plain(sz, plain, reqs, eb, out_c, out_d)
+        res[tag] = {
+            "rate_per_s": lam, "requests": len(reqs), "gbytes": nbytes / 1e9,
+            "p50_ms": 1e3 * _percentile(lat, 50), "p99_ms": 1e3 * _percentile(lat, 99),
+            "gbs": nbytes / span / 1e9,
+            "serial_plain": {"p50_ms": 1e3 * _percentile(lat_p, 50), "p99_ms": 1e3 * _percentile(lat_p, 99),
+                             "gbs_device_busy": nbytes / busy_p / 1e9, "gbs_wall": nbytes / span_p / 1e9},
+        }
+    res["counters"] = sz.sz_serve_stats(ctx)
+    sz.sz_serve_stop(ctx)
+    ctx.close()
+    plain.close()
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -201,6 +359,13 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-log2n", type=int, default=24)
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-rate", type=float, default=2000.0)
+    ap.add_argument("--serve-seconds", type=float, default=1.0)
+    ap.add_argument("--serve-stress", type=float, default=10.0)
+    ap.add_argument("--serve-stress-seconds", type=float, default=0.25)
+    ap.add_argument("--serve-slots", type=int, default=16)
+    ap.add_argument("--serve-budget-gb", type=float, default=48.0)
     args = ap.parse_args()
 
     ws, rank, local = _dist()
@@ -411,6 +576,12 @@ def main():
                "ms_per_step": 1e3 * te}
         del hx, hs, hy, dx, ds
 
+    # ---- served form (rank 0): Poisson arrivals vs the same requests serially --
+    served = None
+    if rank == 0 and not args.no_serve:
+        served = served_bench(sz, snap, args.eb, args.serve_rate, args.serve_seconds, args.serve_stress,
+                              args.serve_stress_seconds, args.serve_slots, args.serve_budget_gb, local)
+
     # ---- CPU oracle on a bounded sample (rank 0) -------------------------------
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -429,7 +600,7 @@ def main():
             "compress_gbs": comp_gbs, "decompress_gbs": decomp_gbs,
             "compress_frac_hbm": comp_gbs / peak, "decompress_frac_hbm": decomp_gbs / peak,
             "ratio": ratio, "roofline": roofline, "kernels": kernels, "gpu_launches": launches,
-            "plain_path": plain,
+            "plain_path": plain, "served": served,
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "wall_s_timed": t_wall,
         }
         print(json.dumps(line))

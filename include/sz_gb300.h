@@ -197,14 +197,28 @@ sz_status sz_profile_enable(sz_ctx* ctx, int on);
  * milliseconds (host arrays of nphases entries).  Clears the counters. */
 sz_status sz_profile_read(sz_ctx* ctx, uint64_t* launches, double* ms, int nphases);
 
-/* ---- serving: continuous batching of compress / decompress requests ---- */
+/* ---- serving: continuous batching of compress / decompress requests ----
+ *
+ * The paper's in-situ setting (Sec. I, Sec. III): every simulation rank
+ * compresses the snapshot data it holds in memory.  Here many ranks' requests
+ * share one GPU.  A host thread owned by the context admits queued requests in
+ * arrival order whenever one of `slots` is free and the request's device bytes
+ * fit the context's budget (hbm_budget_bytes of sz_ctx_create), launches its
+ * kernels on the slot's own stream, so that admitted requests overlap on the
+ * device, and retires it when its completion event fires.  Each request runs
+ * the same kernels as sz_compress / sz_decompress on a private workspace, so
+ * its result is byte-identical to the plain call's. */
 
 typedef enum { SZ_OP_COMPRESS = 0, SZ_OP_DECOMPRESS = 1 } sz_op;
 
-/* One request.  Buffers are device pointers owned by the caller and must stay
- * valid until the request completes.  For SZ_OP_COMPRESS: in = float data of
- * n elements, out = stream buffer of out_cap bytes.  For SZ_OP_DECOMPRESS:
- * in = stream of in_bytes, out = float buffer of n (capacity) elements. */
+/* One request.  Input buffers are device pointers owned by the caller and must
+ * stay valid until the request completes.  For SZ_OP_COMPRESS: in = float data
+ * of n elements, out = stream buffer of out_cap bytes.  For SZ_OP_DECOMPRESS:
+ * in = stream of in_bytes, out = float buffer of n (capacity) elements.
+ * out = NULL asks the service for the output buffer: it is taken from a device
+ * arena of hbm_budget_bytes (compress: sz_max_compressed_bytes(n) bytes;
+ * decompress: 4*n bytes), returned in sz_result.out and held against the
+ * budget until sz_serve_release.  That needs a nonzero budget. */
 typedef struct {
     sz_op op;
     const void* in;
@@ -219,21 +233,45 @@ typedef struct {
 typedef struct {
     sz_status status;     /* SZ_OK once done; SZ_ERR_BUSY while pending */
     size_t out_size;      /* stream bytes (compress) or elements (decompress) */
-    double latency_s;     /* completion time - submit time */
+    double latency_s;     /* completion seen on the host - submit time */
+    void* out;            /* the output buffer (the caller's or the service's) */
 } sz_result;
 
-/* Start the serving loop on a context: up to `slots` requests in flight, at
- * most hbm_budget_bytes (from sz_ctx_create) of workspace admitted at once. */
+typedef struct {
+    uint64_t submitted, completed;
+    uint32_t peak_inflight;   /* most requests on the device at once */
+    uint32_t peak_queue;      /* longest wait queue */
+    size_t peak_bytes;        /* most budget bytes held at once */
+    uint64_t budget_waits;    /* admissions that waited for budget bytes */
+} sz_serve_counters;
+
+/* Start the serving loop: up to `slots` (1..64) requests in flight.  A request
+ * holds in_bytes-or-4n input bytes, its output bytes and 2n bytes of code
+ * workspace against the budget while it runs; a service-owned output stays
+ * held until released.  Errors: SZ_ERR_ARG (bad slots, loop already running),
+ * SZ_ERR_NOMEM (arena), SZ_ERR_CUDA. */
 sz_status sz_serve_start(sz_ctx* ctx, int slots);
 
 /* Queue a request; *ticket identifies it.  Returns SZ_ERR_ARG for a bad
  * request, SZ_ERR_BUSY if it could never fit the memory budget. */
 sz_status sz_serve_submit(sz_ctx* ctx, const sz_request* req, uint64_t* ticket);
 
-/* Non-blocking: fills *res; res->status is SZ_ERR_BUSY while pending. */
+/* Non-blocking: fills *res and forgets the ticket once done; res->status is
+ * SZ_ERR_BUSY while pending.  SZ_ERR_ARG for an unknown ticket. */
 sz_status sz_serve_poll(sz_ctx* ctx, uint64_t ticket, sz_result* res);
 
-/* Drain all queued requests and stop the loop. */
+/* As sz_serve_poll, but waits up to timeout_s seconds for completion. */
+sz_status sz_serve_wait(sz_ctx* ctx, uint64_t ticket, double timeout_s, sz_result* res);
+
+/* Return a service-owned output buffer (sz_result.out of an out = NULL
+ * request) to the arena.  SZ_ERR_ARG if `out` is not such a buffer. */
+sz_status sz_serve_release(sz_ctx* ctx, void* out);
+
+/* Counters since sz_serve_start. */
+sz_status sz_serve_stats(sz_ctx* ctx, sz_serve_counters* out);
+
+/* Drain all queued requests, stop the loop and free the arena (service-owned
+ * outputs not yet released become invalid). */
 sz_status sz_serve_stop(sz_ctx* ctx);
 
 #ifdef __cplusplus

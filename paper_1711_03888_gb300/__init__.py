@@ -34,7 +34,8 @@ HEADER_BYTES = 160
 EXPORTS = ("sz_ctx_create", "sz_ctx_destroy", "sz_max_compressed_bytes", "sz_compress", "sz_decompress",
            "sz_compress_batch", "sz_decompress_batch", "sz_compress_snapshot", "sz_sync", "sz_status_string",
            "sz_profile_enable", "sz_profile_read", "sz_compress_noalloc",
-           "sz_serve_start", "sz_serve_submit", "sz_serve_poll", "sz_serve_stop")
+           "sz_serve_start", "sz_serve_submit", "sz_serve_poll", "sz_serve_wait", "sz_serve_release",
+           "sz_serve_stats", "sz_serve_stop")
 PHASES = ("range", "quant", "codebook", "encode", "decode_setup", "decode", "reorder", "batch")
 
 
@@ -49,7 +50,12 @@ class sz_request(C.Structure):
 
 
 class sz_result(C.Structure):
-    _fields_ = [("status", C.c_int), ("out_size", C.c_size_t), ("latency_s", C.c_double)]
+    _fields_ = [("status", C.c_int), ("out_size", C.c_size_t), ("latency_s", C.c_double), ("out", C.c_void_p)]
+
+
+class sz_serve_counters(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("peak_inflight", C.c_uint32),
+                ("peak_queue", C.c_uint32), ("peak_bytes", C.c_size_t), ("budget_waits", C.c_uint64)]
 
 
 _vp, _sz, _st = C.c_void_p, C.c_size_t, C.c_int
@@ -75,6 +81,9 @@ _sig = {
     "sz_serve_start": (_st, [_vp, C.c_int]),
     "sz_serve_submit": (_st, [_vp, C.POINTER(sz_request), C.POINTER(C.c_uint64)]),
     "sz_serve_poll": (_st, [_vp, C.c_uint64, C.POINTER(sz_result)]),
+    "sz_serve_wait": (_st, [_vp, C.c_uint64, C.c_double, C.POINTER(sz_result)]),
+    "sz_serve_release": (_st, [_vp, _vp]),
+    "sz_serve_stats": (_st, [_vp, C.POINTER(sz_serve_counters)]),
     "sz_serve_stop": (_st, [_vp]),
 }
 for _name, (_res, _args) in _sig.items():
@@ -272,8 +281,47 @@ def sz_serve_submit(ctx: Context, req: sz_request) -> int:
 
 def sz_serve_poll(ctx: Context, ticket: int) -> sz_result:
     r = sz_result()
-    _lib.sz_serve_poll(ctx.handle, ticket, C.byref(r))
+    _check(_lib.sz_serve_poll(ctx.handle, ticket, C.byref(r)), "sz_serve_poll")
     return r
+
+
+def sz_serve_wait(ctx: Context, ticket: int, timeout_s: float = 60.0) -> sz_result:
+    r = sz_result()
+    _check(_lib.sz_serve_wait(ctx.handle, ticket, float(timeout_s), C.byref(r)), "sz_serve_wait")
+    return r
+
+
+def sz_serve_release(ctx: Context, out: int):
+    _check(_lib.sz_serve_release(ctx.handle, C.c_void_p(out)), "sz_serve_release")
+
+
+def sz_serve_stats(ctx: Context) -> dict:
+    c = sz_serve_counters()
+    _check(_lib.sz_serve_stats(ctx.handle, C.byref(c)), "sz_serve_stats")
+    return {f: getattr(c, f) for f, _ in sz_serve_counters._fields_}
+
+
+def request(op: int, inp, n: int, out=None, out_cap: int = 0, in_bytes: int = 0, eb: float = 0.0,
+            kind: int = SZ_EB_REL) -> sz_request:
+    """Build an sz_request from CUDA tensors or raw device addresses (out=None:
+    the service allocates the output)."""
+    def addr(t):
+        return None if t is None else (t if isinstance(t, int) else t.data_ptr())
+    return sz_request(op, addr(inp), n, in_bytes, addr(out), out_cap, eb, kind)
+
+
+class _DevBuf:
+    """Exposes a raw device range through __cuda_array_interface__ (for torch.as_tensor)."""
+
+    def __init__(self, ptr: int, nbytes: int):
+        self.__cuda_array_interface__ = {"shape": (nbytes,), "typestr": "|u1", "data": (ptr, False),
+                                         "version": 3, "strides": None}
+
+
+def device_bytes(ptr: int, nbytes: int):
+    """A uint8 CUDA tensor viewing nbytes at device address ptr (no copy)."""
+    import torch
+    return torch.as_tensor(_DevBuf(ptr, nbytes), device="cuda")
 
 
 def sz_serve_stop(ctx: Context):

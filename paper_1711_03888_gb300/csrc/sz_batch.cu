@@ -1,14 +1,18 @@
 // sz_batch.cu -- many arrays per call (a15).
 //
-// Compression: one persistent launch (k_batch.cu) over every array's range,
-// quantize, codebook and encode items.  The context keeps a batch pool with
-// each array's own state, histogram, codeword table, codebook scratch and
-// per-chunk tables, sliced by that array's size.  Each stream is
-// byte-identical to sz_compress on the same array.  Arrays whose chunk size
-// is above 4096 (set explicitly through params) go through the per-array
-// path instead.
+// Compression: one CUDA graph per batch shape, replayed on every call.  Its
+// nodes: the plan copy and a counter reset, then two parallel branches --
+//   small arrays (< 2^22 elements): one persistent launch (k_batch.cu) over
+//     every array's range, quantize, codebook and encode items;
+//   large arrays: one launch per phase over all of them (k_multi.cu).
+// The context keeps a batch pool with each array's own state, histogram,
+// codeword table, codebook scratch and per-chunk tables, sliced by that
+// array's size.  Each stream is byte-identical to sz_compress on the same
+// array.  Arrays whose chunk size is above 4096 (set explicitly through
+// params) go through the per-array path instead.
 // Decompression: the setup and decode kernels per stream, enqueued back to
 // back (each decode launch already spans the whole GPU).
+#include <algorithm>
 #include <string.h>
 #include <vector>
 #include "sz_ctx.h"
@@ -56,16 +60,34 @@ sz_status batch_compress(sz_ctx* ctx, int k, const float* const* d_in, const siz
     }
     const uint32_t kb = (uint32_t)batched.size();
     if (kb == 0) return SZ_OK;
+    // small arrays first (the persistent kernel's), then large ones grouped by C
+    {
+        std::vector<int> small, large;
+        for (int i : batched) (n[i] < kBatchLargeElems ? small : large).push_back(i);
+        std::stable_sort(large.begin(), large.end(), [&](int x, int y) { return Cs[x] < Cs[y]; });
+        batched = small;
+        batched.insert(batched.end(), large.begin(), large.end());
+    }
+    uint32_t ks = 0;
+    while (ks < kb && n[batched[ks]] < kBatchLargeElems) ++ks;
+    std::vector<MultiGroup> groups;
+    for (uint32_t j = ks; j < kb; ++j) {
+        const int i = batched[j];
+        const uint32_t nc = (uint32_t)((n[i] + Cs[i] - 1) / Cs[i]);
+        if (groups.empty() || groups.back().C != Cs[i]) groups.push_back(MultiGroup{j, 0u, Cs[i], 0u});
+        groups.back().count++;
+        if (nc > groups.back().max_chunks) groups.back().max_chunks = nc;
+    }
 
     // ---- pool layout: plan | counters | states | per-array buffers ------------------
     size_t bytes = 0;
     auto take = [&](size_t b) { size_t o = bytes; bytes += align256(b); return o; };
     const size_t o_args = take(sizeof(CompressArgs) * kb);
-    const size_t o_tiles = take(sizeof(uint32_t) * kb);
-    const size_t o_groups = take(sizeof(uint32_t) * kb);
-    const size_t o_off = take(sizeof(uint32_t) * 4 * (kb + 1));
+    const size_t o_tiles = take(sizeof(uint32_t) * (ks + 1));
+    const size_t o_groups = take(sizeof(uint32_t) * (ks + 1));
+    const size_t o_off = take(sizeof(uint32_t) * 4 * (ks + 1));
     const size_t plan_bytes = bytes;
-    const size_t cnt_bytes = sizeof(BatchCounters) * kb + 256;
+    const size_t cnt_bytes = sizeof(BatchCounters) * ks + 256;
     const size_t o_cnt = take(cnt_bytes);
     const size_t o_state = take(sizeof(ArrayState) * kb);
     std::vector<size_t> o_hist(kb), o_enc(kb), o_cb(kb), o_cesc(kb), o_cst(kb), o_codes(kb);
@@ -85,21 +107,21 @@ sz_status batch_compress(sz_ctx* ctx, int k, const float* const* d_in, const siz
 
     // ---- plan -------------------------------------------------------------------
     std::vector<CompressArgs> args(kb);
-    std::vector<uint32_t> tiles(kb), groups(kb), off(4 * (kb + 1));
+    std::vector<uint32_t> tiles(ks + 1), qgroups(ks + 1), off(4 * (ks + 1));
     uint32_t item = 0;
     for (int ph = 0; ph < 4; ++ph) {
-        for (uint32_t j = 0; j < kb; ++j) {
+        for (uint32_t j = 0; j < ks; ++j) {
             const int i = batched[j];
             const uint64_t nc = (n[i] + Cs[i] - 1) / Cs[i];
-            off[ph * (kb + 1) + j] = item;
+            off[ph * (ks + 1) + j] = item;
             uint32_t cnt;
             if (ph == 0) cnt = tiles[j] = (uint32_t)((n[i] + kRangeTile - 1) / kRangeTile) + (n[i] == 0 ? 1u : 0u);
-            else if (ph == 1) cnt = groups[j] = (uint32_t)((nc + kQuantGroup - 1) / kQuantGroup);
+            else if (ph == 1) cnt = qgroups[j] = (uint32_t)((nc + kQuantGroup - 1) / kQuantGroup);
             else if (ph == 2) cnt = 1;
             else cnt = (uint32_t)nc;
             item += cnt;
         }
-        off[ph * (kb + 1) + kb] = item;
+        off[ph * (ks + 1) + ks] = item;
     }
     uint64_t key = 1469598103934665603ull;      // FNV-1a over everything the graph bakes in
     auto mix = [&](const void* p, size_t b) {
@@ -150,8 +172,8 @@ sz_status batch_compress(sz_ctx* ctx, int k, const float* const* d_in, const siz
         }
         uint8_t* hp = ctx->batch_host;
         memcpy(hp + o_args, args.data(), sizeof(CompressArgs) * kb);
-        memcpy(hp + o_tiles, tiles.data(), sizeof(uint32_t) * kb);
-        memcpy(hp + o_groups, groups.data(), sizeof(uint32_t) * kb);
+        memcpy(hp + o_tiles, tiles.data(), sizeof(uint32_t) * (ks + 1));
+        memcpy(hp + o_groups, qgroups.data(), sizeof(uint32_t) * (ks + 1));
         memcpy(hp + o_off, off.data(), sizeof(uint32_t) * off.size());
         // arm the per-array range accumulators of a new layout
         if (ctx->batch_layout_bytes != bytes || ctx->batch_k != kb || !ctx->batch_states_armed) {
@@ -172,10 +194,11 @@ sz_status batch_compress(sz_ctx* ctx, int k, const float* const* d_in, const siz
         plan.range_tiles = (const uint32_t*)(base + o_tiles);
         plan.quant_groups = (const uint32_t*)(base + o_groups);
         plan.item_off = (const uint32_t*)(base + o_off);
-        plan.k = kb;
-        plan.next = (uint32_t*)(base + o_cnt + sizeof(BatchCounters) * kb);
+        plan.k = ks;
+        plan.next = (uint32_t*)(base + o_cnt + sizeof(BatchCounters) * ks);
         plan.err = ctx->d_err;
-        // graph: plan copy and counter reset, then the persistent kernel
+        // graph: plan copy and counter reset, then the persistent kernel (small
+        // arrays) beside the per-phase launches (large arrays)
         if (ctx->bg_exec) cudaGraphExecDestroy(ctx->bg_exec);
         if (ctx->bg_graph) cudaGraphDestroy(ctx->bg_graph);
         ctx->bg_exec = nullptr;
@@ -212,7 +235,8 @@ sz_status batch_compress(sz_ctx* ctx, int k, const float* const* d_in, const siz
         }
         deps[0] = n_copy;
         deps[1] = n_reset;
-        if (cudaGraphAddKernelNode(&n_kern, g, deps, 2, &kp) != cudaSuccess ||
+        if ((ks && cudaGraphAddKernelNode(&n_kern, g, deps, 2, &kp) != cudaSuccess) ||
+            add_multi_compress_nodes(g, n_copy, plan.args, groups.data(), (int)groups.size()) != 0 ||
             cudaGraphInstantiate(&ctx->bg_exec, g, 0) != cudaSuccess) {
             cudaGetLastError();
             cudaGraphDestroy(g);

@@ -139,6 +139,19 @@ struct BatchPlan {
     uint32_t* err;
 };
 void launch_batch_compress(const BatchPlan& plan, void* stream);
+
+// Large arrays of a batch: one launch per phase over args[first .. first+count)
+// of every group (the groups are contiguous; a group's arrays share C).
+constexpr uint64_t kBatchLargeElems = 1ull << 22;
+struct MultiGroup {
+    uint32_t first, count;      // arrays args[first .. first+count)
+    uint32_t C;                 // their chunk size (2048 or 4096)
+    uint32_t max_chunks;        // largest chunk count among them
+};
+// Adds the four phase nodes to the CUDA graph `graph` after node `dep` (may be
+// null); returns 0 or a CUDA error code.
+int add_multi_compress_nodes(void* graph, void* dep, const CompressArgs* d_args, const MultiGroup* groups,
+                             int ngroups);
 void batch_compress_config(void** func, unsigned* grid, unsigned* block, size_t* smem);
 
 // MD reordering (Sec. IV-B)

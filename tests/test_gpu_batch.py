@@ -89,3 +89,37 @@ def test_batch_full_config_many_ranks(sz, ctx, oracle):
     for i in rng.choice(768, 6, replace=False):
         h = oracle.parse_header(got[i])
         assert got[i] == oracle.compress(xs[i].cpu().numpy(), ebs[i], 1, h["chunk"], h["sub"])
+
+
+def _plain_p(sz, ctx, x, eb, kind, chunk):
+    out, nb = sz.sz_compress(ctx, x, eb, kind, sz._params(chunk))
+    sz.sz_sync(ctx)
+    return out[: nb.value].cpu().numpy().tobytes()
+
+
+@pytest.mark.parametrize("chunk", [0, 2048, 4096])
+def test_batch_large_arrays_per_phase_path(sz, ctx, chunk):
+    """Arrays of 2^22 elements and more take one launch per phase over all of
+    them, beside the persistent kernel of the small ones; streams still equal
+    the plain path's, including a raw (constant) and a NaN-laden large array."""
+    L = 1 << 22
+    snap = synth.cosmology(L + 777, 64, 21, device="cuda")
+    xs = [snap["xx"][:L], snap["vy"], synth.random_walk_f32(5000, 3).cuda(), snap["zz"][: L + 4],
+          torch.full((L + 1,), -3.5, dtype=torch.float32, device="cuda"), synth.random_walk_f32(70001, 4).cuda()]
+    w = snap["vx"].clone()
+    w[::1001] = float("nan")
+    w[7::5003] = float("inf")
+    xs.append(w)
+    ebs = [1e-4, 1e-3, 1e-4, 1e-5, 1e-4, 1e-3, 1e-4]
+    outs, nb = sz.sz_compress_batch(ctx, xs, ebs, sz.SZ_EB_REL, sz._params(chunk))
+    sz.sz_sync(ctx)
+    got = [outs[i][: nb[i]].cpu().numpy().tobytes() for i in range(len(xs))]
+    for x, e, g in zip(xs, ebs, got):
+        assert g == _plain_p(sz, ctx, x, e, sz.SZ_EB_REL, chunk)
+    # again, replaying the cached graph on new data in the same buffers
+    for x in xs:
+        x.copy_(x.flip(0) * 0.5)
+    outs, nb = sz.sz_compress_batch(ctx, xs, ebs, sz.SZ_EB_REL, sz._params(chunk), outs=outs)
+    sz.sz_sync(ctx)
+    for i, (x, e) in enumerate(zip(xs, ebs)):
+        assert outs[i][: nb[i]].cpu().numpy().tobytes() == _plain_p(sz, ctx, x, e, sz.SZ_EB_REL, chunk)
