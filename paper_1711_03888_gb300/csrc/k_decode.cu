@@ -27,7 +27,7 @@ constexpr int kSetupThreads = 1024;
 constexpr int kDecThreads = kSubPerChunk;    // 64 threads per team
 constexpr int kMaxTeams = 8;
 constexpr int kDecBlock = kMaxTeams * kDecThreads;   // 512
-constexpr size_t kDecDynSmem = 176u * 1024u;         // team regions: delta/value slots + payload stage
+constexpr size_t kDecDynSmem = 208u * 1024u;         // second-level table (32 KB) + team regions
 constexpr uint32_t kEscMark = 0x80000000u;           // delta slot of an escape
 
 struct SetupSmem {
@@ -148,57 +148,66 @@ __global__ void __launch_bounds__(kSetupThreads) decode_setup_kernel(DecompressA
         }
         st->lim[kMaxLen + 1] = 0xffffffffu;
     }
+    __syncthreads();
+    // second level: codes of 13..16 bits by their 16-bit prefix, over the
+    // prefixes [lim[12], lim[16]) >> 8 (those of longer codes read 0)
+    constexpr int kSh = kMaxLen - kLut2Bits;
+    const uint32_t l2_lo = st->lim[kLutBits] >> kSh;
+    const uint32_t l2_hi = st->lim[kLut2Bits] >> kSh;
+    const uint32_t l2_n = (l2_hi > l2_lo && l2_hi - l2_lo <= kLut2Max) ? l2_hi - l2_lo : 0u;
+    uint32_t* lut2 = a.lut + (1u << kLutBits);
     for (uint32_t i = tid; i < (1u << kLutBits); i += kSetupThreads) a.lut[i] = 0u;
+    for (uint32_t i = tid; i < l2_n; i += kSetupThreads) lut2[i] = 0u;
     __syncthreads();
     for (uint32_t p = tid; p < m; p += kSetupThreads) {
         uint32_t l = kl[p], s = vl[p];
         a.by_len[p] = (uint16_t)s;
+        const uint32_t code = st->first[l] + (p - st->base[l]);
         if (l <= (uint32_t)kLutBits) {
-            uint32_t code = st->first[l] + (p - st->base[l]);
             uint32_t lo = code << (kLutBits - l), hi = (code + 1) << (kLutBits - l);
             for (uint32_t e = lo; e < hi; ++e) a.lut[e] = (s << 8) | l;
+        } else if (l2_n && l <= (uint32_t)kLut2Bits) {
+            uint32_t lo = (code << (kLut2Bits - l)) - l2_lo, hi = ((code + 1) << (kLut2Bits - l)) - l2_lo;
+            for (uint32_t e = lo; e < hi && e < l2_n; ++e) lut2[e] = (s << 8) | l;
         }
     }
     __syncthreads();
-    if (tid == 0) st->dec_ok = 1;
+    if (tid == 0) {
+        st->l2_lo = l2_lo;
+        st->l2_n = l2_n;
+        st->dec_ok = 1;
+    }
 }
 
-// Bit reader over a chunk payload in shared or global memory (generic
-// pointer).  Words at or past `end` read as zero, so a bad stream cannot make
-// it read outside the chunk.
+// Bit reader over a chunk payload in shared or global memory.  Two 32-bit
+// words (hi, lo) hold the stream from word pos-2 on; the next codeword starts
+// b bits into hi.  peek() returns the 32 bits from there by one funnel shift;
+// consume() advances and pulls in one word when b passes 32 (predicated, so
+// lanes do not diverge).  Words at or past `end` read as zero, so a bad
+// stream cannot make it read outside the chunk.
 struct BitReader {
     const uint32_t* words;
-    uint32_t pos, end;            // word index of the next refill, end (exclusive)
-    unsigned long long win;       // bits MSB-aligned
-    uint32_t avail;
+    uint32_t pos, end, hi, lo, b;
     __device__ __forceinline__ void init(const uint32_t* w, uint32_t begin_bit, uint32_t end_word) {
         words = w;
         end = end_word;
-        pos = begin_bit >> 5;
-        win = 0;
-        avail = 0;
-        uint32_t skip = begin_bit & 31u;
-        refill();
-        refill();
-        win <<= skip;
-        avail -= skip;
+        const uint32_t p = begin_bit >> 5;
+        hi = p < end ? w[p] : 0u;
+        lo = p + 1 < end ? w[p + 1] : 0u;
+        pos = p + 2;
+        b = begin_bit & 31u;
     }
-    __device__ __forceinline__ void refill() {
-        uint32_t v = (pos < end) ? words[pos] : 0u;
-        ++pos;
-        win |= (unsigned long long)v << (32u - avail);
-        avail += 32;
-    }
-    // branch-free: the refill load is predicated, so lanes do not diverge
-    __device__ __forceinline__ void consume(uint32_t l) {
-        win <<= l;
-        avail -= l;
-        const bool need = avail < 32u;
-        const uint32_t v = (need && pos < end) ? words[pos] : 0u;
-        win |= (unsigned long long)v << ((32u - avail) & 63u);
-        avail += need ? 32u : 0u;
+    __device__ __forceinline__ uint32_t peek() const { return __funnelshift_l(lo, hi, b); }
+    __device__ __forceinline__ void consume(uint32_t len) {
+        b += len;
+        const bool need = b >= 32u;
+        const uint32_t nxt = (need && pos < end) ? words[pos] : 0u;
+        hi = need ? lo : hi;
+        lo = need ? nxt : lo;
         pos += need ? 1u : 0u;
+        b -= need ? 32u : 0u;
     }
+    __device__ __forceinline__ uint32_t bit_pos() const { return (pos - 2u) * 32u + b; }
 };
 
 // Team-level primitives: a team is 64 threads (2 warps) with named barrier
@@ -227,28 +236,59 @@ struct DecSmem {
     long long ws64[kMaxTeams][2];
 };
 
+// dynamic shared memory: the second-level table, then one region per team
+constexpr size_t kLut2Bytes = sizeof(uint32_t) * kLut2Max;
+
 __device__ __forceinline__ int teams_for(uint32_t C) {
     return C <= 4096 ? 8 : (C == 8192 ? 4 : 2);
 }
 
-// One symbol: 12-bit direct lookup, else a walk over the left-justified limits.
-__device__ __forceinline__ uint32_t decode_symbol(BitReader& br, const DecSmem& sm, const uint16_t* by_len,
-                                                  uint32_t& used, bool& bad) {
-    const uint32_t w24 = (uint32_t)(br.win >> 40);
-    const uint32_t ent = sm.lut[w24 >> (kMaxLen - kLutBits)];
-    uint32_t sym, len;
-    if (ent) {
-        sym = ent >> 8;
-        len = ent & 255u;
-    } else {
-        len = kLutBits + 1;
-        while (w24 >= sm.lim[len]) ++len;   // lim[25] = ~0 stops the walk
-        if (len > (uint32_t)kMaxLen) { bad = true; len = 0; sym = 0; }
-        else sym = by_len[sm.base[len] + (w24 >> (kMaxLen - len)) - sm.first[len]];
+// A code longer than the second level covers: walk the left-justified limits.
+__device__ __noinline__ uint32_t decode_long(uint32_t w24, const DecSmem& sm, const uint16_t* by_len, bool& bad) {
+    uint32_t len = kLutBits + 1;
+    while (w24 >= sm.lim[len]) ++len;   // lim[25] = ~0 stops the walk
+    if (len > (uint32_t)kMaxLen) {
+        bad = true;
+        return 0u;
     }
-    br.consume(len);
-    used += len;
-    return sym;
+    return ((uint32_t)by_len[sm.base[len] + (w24 >> (kMaxLen - len)) - sm.first[len]] << 8) | len;
+}
+
+// One symbol: 12-bit direct lookup, then the 16-bit second level, then the walk.
+__device__ __forceinline__ uint32_t decode_symbol(BitReader& br, const DecSmem& sm, const uint32_t* lut2,
+                                                  uint32_t l2_lo, uint32_t l2_n, const uint16_t* by_len, bool& bad) {
+    const uint32_t w = br.peek();
+    uint32_t ent = sm.lut[w >> (32 - kLutBits)];
+    if (ent == 0u) {
+        const uint32_t i2 = (w >> (32 - kLut2Bits)) - l2_lo;   // wraps above l2_n below the range
+        ent = i2 < l2_n ? lut2[i2] : 0u;
+        if (ent == 0u) ent = decode_long(w >> (32 - kMaxLen), sm, by_len, bad);
+    }
+    br.consume(ent & 255u);
+    return ent >> 8;
+}
+
+// Phase 1 of one sub-stream: decode nsym symbols into the team's slots (raw
+// symbols: 0 marks an escape).  Returns the sum of the symbols and counts the
+// escapes; the reader's end position checks the sub-stream length.
+template <bool FULL>
+__device__ __forceinline__ uint32_t decode_run(BitReader& br, const DecSmem& sm, const uint32_t* lut2, uint32_t l2_lo,
+                                               uint32_t l2_n, const uint16_t* by_len, uint32_t* xs, uint32_t e0,
+                                               uint32_t gshift, uint32_t nsym, uint32_t& nesc, bool& bad) {
+    uint32_t ssum = 0;
+    for (uint32_t j4 = 0; j4 < nsym; j4 += 4) {
+        uint32_t s[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            if (FULL || j4 + t < nsym) {
+                s[t] = decode_symbol(br, sm, lut2, l2_lo, l2_n, by_len, bad);
+                ssum += s[t];
+                nesc += (s[t] == 0u);
+            }
+        }
+        *reinterpret_cast<uint4*>(&xs[swz(e0 + j4, gshift)]) = make_uint4(s[0], s[1], s[2], s[3]);
+    }
+    return ssum;
 }
 
 __global__ void __launch_bounds__(kDecBlock, 1) decode_kernel(DecompressArgs a) {
@@ -277,9 +317,12 @@ __global__ void __launch_bounds__(kDecBlock, 1) decode_kernel(DecompressArgs a) 
     const uint8_t* escs = in + st->off[S_ESC];
     const uint32_t* payload = reinterpret_cast<const uint32_t*>(in + st->off[S_PAYLOAD]);
     const uint16_t* by_len = a.by_len;
+    const uint32_t l2_lo = st->l2_lo, l2_n = st->l2_n;
+    uint32_t* lut2 = reinterpret_cast<uint32_t*>(dyn_smem);
 
     for (uint32_t i = tid; i < (1u << kLutBits) / 4; i += kDecBlock)
         reinterpret_cast<uint4*>(sm.lut)[i] = __ldg(reinterpret_cast<const uint4*>(a.lut) + i);
+    for (uint32_t i = tid; i < l2_n; i += kDecBlock) lut2[i] = __ldg(a.lut + (1u << kLutBits) + i);
     if (tid < kMaxLen + 2) {
         sm.first[tid] = st->first[tid];
         sm.base[tid] = st->base[tid];
@@ -290,12 +333,15 @@ __global__ void __launch_bounds__(kDecBlock, 1) decode_kernel(DecompressArgs a) 
     const int teams = teams_for(C);
     const int team = tid / kDecThreads, k = tid % kDecThreads;
     if (team >= teams) return;
-    const uint32_t region_words = (uint32_t)(kDecDynSmem / 4) / teams;
-    uint32_t* xs = reinterpret_cast<uint32_t*>(dyn_smem) + (size_t)team * region_words;
+    const uint32_t region_words = (uint32_t)((kDecDynSmem - kLut2Bytes) / 4) / teams;
+    uint32_t* xs = reinterpret_cast<uint32_t*>(dyn_smem) + kLut2Max + (size_t)team * region_words;
     uint32_t* stage = xs + C;
     const uint32_t stage_words = region_words - C;      // multiple of 4
     const bool vec = ((uintptr_t)a.out & 15u) == 0;
     const uint64_t stride = (uint64_t)gridDim.x * teams;
+    // every partial sum of a sub-stream without escapes stays within
+    // q0 +- G * 32767, so |q0| below this bound keeps all of them within 2^24
+    const long long q_fast = (1ll << 24) - (long long)G * (kRadius - 1);
 
     for (uint64_t c = (uint64_t)blockIdx.x * teams + team; c < nc; c += stride) {
         const uint64_t base = c * C;
@@ -314,8 +360,8 @@ __global__ void __launch_bounds__(kDecBlock, 1) decode_kernel(DecompressArgs a) 
         }
         // ---- stage the chunk payload; prefetch the next chunk into L2 ---------------
         const uint32_t cw_words = (uint32_t)(we - wb);
-        const uint32_t* src;
-        if (cw_words <= stage_words) {
+        const bool staged = cw_words <= stage_words;
+        if (staged) {
             // asynchronous 16-byte copies, all in flight at once
             const uint4* g4 = reinterpret_cast<const uint4*>(payload + wb);
             const uint32_t s_base = (uint32_t)__cvta_generic_to_shared(stage);
@@ -324,9 +370,6 @@ __global__ void __launch_bounds__(kDecBlock, 1) decode_kernel(DecompressArgs a) 
                              "l"(__cvta_generic_to_global(g4 + w4))
                              : "memory");
             asm volatile("cp.async.wait_all;" ::: "memory");
-            src = stage;
-        } else {
-            src = payload + wb;
         }
         if (k == 0 && c + stride < nc) {
             const uint64_t nb = cword[c + stride], ne = cword[c + stride + 1];
@@ -337,28 +380,24 @@ __global__ void __launch_bounds__(kDecBlock, 1) decode_kernel(DecompressArgs a) 
             }
         }
         team_sync(team);
-        // ---- phase 1: decode the sub-stream into deltas -----------------------------
-        BitReader br;
-        br.init(src, start, cw_words);
-        int dsum = 0, dabs = 0;
-        uint32_t nesc = 0, used = 0;
+        // ---- phase 1: decode the sub-stream into symbols ----------------------------
+        // (separate calls for the staged and the global source, so that the
+        // staged reader's loads are shared-memory loads)
+        uint32_t nesc = 0, ssum, end_bit;
         bool bad = false;
-        for (uint32_t j4 = 0; j4 < nsym; j4 += 4) {
-            uint32_t dl[4] = {0u, 0u, 0u, 0u};
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                if (nsym == G || j4 + t < nsym) {
-                    const uint32_t sym = decode_symbol(br, sm, by_len, used, bad);
-                    const int d = (int)sym - kRadius;
-                    dl[t] = sym ? (uint32_t)d : kEscMark;
-                    nesc += (sym == 0u);
-                    dsum += sym ? d : 0;
-                    dabs += sym ? abs(d) : 0;
-                }
-            }
-            *reinterpret_cast<uint4*>(&xs[swz(e0 + j4, gshift)]) = make_uint4(dl[0], dl[1], dl[2], dl[3]);
+        if (staged) {
+            BitReader br;
+            br.init(stage, start, cw_words);
+            ssum = nsym == G ? decode_run<true>(br, sm, lut2, l2_lo, l2_n, by_len, xs, e0, gshift, nsym, nesc, bad)
+                             : decode_run<false>(br, sm, lut2, l2_lo, l2_n, by_len, xs, e0, gshift, nsym, nesc, bad);
+            end_bit = br.bit_pos();
+        } else {
+            BitReader br;
+            br.init(payload + wb, start, cw_words);
+            ssum = decode_run<false>(br, sm, lut2, l2_lo, l2_n, by_len, xs, e0, gshift, nsym, nesc, bad);
+            end_bit = br.bit_pos();
         }
-        bad = bad || used != sl;
+        bad = bad || end_bit - start != sl;
         // ---- escapes and the team-wide prefix ----------------------------------------
         uint32_t tot_esc;
         const uint32_t eoff = team_exclusive_scan<uint32_t>(nesc + (bad ? 0x10000u : 0u), sm.ws32b[team], team, k,
@@ -367,23 +406,24 @@ __global__ void __launch_bounds__(kDecBlock, 1) decode_kernel(DecompressArgs a) 
             if (k == 0) raise_err(a.err, E_CORRUPT);
             return;
         }
-        long long sum = dsum;
+        // sum of deltas: escape symbols are 0, every other one is delta + radius
+        long long sum = (long long)ssum - (long long)kRadius * (long long)(nsym - nesc);
         for (uint32_t t = 0; t < nesc; ++t)
             sum += *reinterpret_cast<const long long*>(escs + (uint64_t)kEscBytes * (eb + eoff + t));
         long long tot_sum;
         const long long pre = team_exclusive_scan<long long>(sum, sm.ws64[team], team, k, &tot_sum);
         // ---- phase 2: reconstruct in place -----------------------------------------
         const long long q0 = anchor[c] + pre;
-        if (nesc == 0 && q0 >= -(1ll << 24) + dabs && q0 <= (1ll << 24) - dabs) {
-            // every partial sum stays within |q| <= 2^24: 32-bit, one fmul each
+        if (nesc == 0 && q0 >= -q_fast && q0 <= q_fast) {
+            // 32-bit: q stays within 2^24, one exact int -> float and one fmul each
             int q = (int)q0;
             for (uint32_t j4 = 0; j4 < nsym; j4 += 4) {
                 uint4* slot = reinterpret_cast<uint4*>(&xs[swz(e0 + j4, gshift)]);
                 uint4 s4 = *slot;
-                q += (int)s4.x; const float v0 = __fmul_rn((float)q, D);
-                q += (int)s4.y; const float v1 = __fmul_rn((float)q, D);
-                q += (int)s4.z; const float v2 = __fmul_rn((float)q, D);
-                q += (int)s4.w; const float v3 = __fmul_rn((float)q, D);
+                q += (int)s4.x - kRadius; const float v0 = __fmul_rn((float)q, D);
+                q += (int)s4.y - kRadius; const float v1 = __fmul_rn((float)q, D);
+                q += (int)s4.z - kRadius; const float v2 = __fmul_rn((float)q, D);
+                q += (int)s4.w - kRadius; const float v3 = __fmul_rn((float)q, D);
                 *slot = make_uint4(__float_as_uint(v0), __float_as_uint(v1), __float_as_uint(v2), __float_as_uint(v3));
             }
         } else {
@@ -392,15 +432,15 @@ __global__ void __launch_bounds__(kDecBlock, 1) decode_kernel(DecompressArgs a) 
             for (uint32_t j4 = 0; j4 < nsym; j4 += 4) {
                 uint4* slot = reinterpret_cast<uint4*>(&xs[swz(e0 + j4, gshift)]);
                 uint4 s4 = *slot;
-                uint32_t dl[4] = {s4.x, s4.y, s4.z, s4.w};
+                uint32_t sy[4] = {s4.x, s4.y, s4.z, s4.w};
                 uint32_t ov[4];
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
                     ov[t] = 0u;
                     if (j4 + t < nsym) {
                         float v;
-                        if (dl[t] != kEscMark) {
-                            q += (int)dl[t];
+                        if (sy[t] != 0u) {
+                            q += (long long)sy[t] - kRadius;
                             v = recon_f(q, D);
                         } else {
                             const uint8_t* r = escs + (uint64_t)kEscBytes * ecur++;

@@ -59,7 +59,7 @@ sz_status ctx_reserve(sz_ctx* ctx, int arrays, uint64_t max_chunks, uint64_t max
     size_t o_cesc = take(sizeof(uint32_t) * nc * na);
     size_t o_cst = take(sizeof(unsigned long long) * nc * na);
     size_t o_cb = take(sizeof(uint32_t) * kCbScratchWords * na);
-    size_t o_lut = take(sizeof(uint32_t) * (1u << kLutBits) * na);
+    size_t o_lut = take(sizeof(uint32_t) * kLutWords * na);
     size_t o_bylen = take(sizeof(uint16_t) * 65536 * na);
     size_t o_codes = take(sizeof(uint16_t) * ncode * na);
     void* base = nullptr;
@@ -125,7 +125,7 @@ DecompressArgs make_decompress_args(sz_ctx* ctx, int slot, const void* in, uint6
     d.out = out;
     d.n_cap = n_cap;
     d.st = ctx->d_state + slot;
-    d.lut = ctx->d_lut + (size_t)(1u << kLutBits) * slot;
+    d.lut = ctx->d_lut + (size_t)kLutWords * slot;
     d.by_len = ctx->d_bylen + (size_t)65536 * slot;
     d.cb_scratch = ctx->d_cb + kCbScratchWords * slot;
     d.err = ctx->d_err;

@@ -23,6 +23,9 @@ constexpr uint32_t kEscBytes = 16;
 constexpr int kSubPerChunk = 64;                  // sub-streams per chunk on the GPU path
 constexpr int kRangeBlocks = 1216;                // 8 x 152 SMs
 constexpr int kLutBits = 12;                      // decoder direct-lookup width
+constexpr int kLut2Bits = 16;                     // second level: codes of 13..16 bits by 16-bit prefix
+constexpr uint32_t kLut2Max = 8192;               // second-level entries (above: limit walk only)
+constexpr uint32_t kLutWords = (1u << kLutBits) + kLut2Max;   // both levels, per array
 
 // header byte offsets
 constexpr int H_MAGIC = 0, H_VERSION = 4, H_HDRBYTES = 6, H_N = 8, H_EB = 16, H_D = 24,
@@ -70,6 +73,8 @@ struct ArrayState {
     uint32_t base[kMaxLen + 2];
     uint32_t lim[kMaxLen + 2];   // left-justified end of each length's codes (24 bits)
     uint32_t dec_ok;
+    uint32_t l2_lo;            // decoder: first 16-bit prefix of the second-level table
+    uint32_t l2_n;             // decoder: its entries (0 = no second level)
     uint32_t pad1;
 };
 
@@ -100,7 +105,8 @@ struct DecompressArgs {
     float* out;
     uint64_t n_cap;
     ArrayState* st;
-    uint32_t* lut;              // 1 << kLutBits entries: sym << 8 | len, 0 = long/invalid
+    uint32_t* lut;              // kLutWords: 1 << kLutBits entries sym << 8 | len (0 = longer code),
+                                //   then kLut2Max second-level entries for 16-bit prefixes l2_lo ..
     uint16_t* by_len;           // 65536: symbols in (length, symbol) order
     uint32_t* cb_scratch;
     uint32_t* err;
