@@ -115,9 +115,13 @@ __device__ void batch_range_tile(const CompressArgs& a, BatchCounters* cnt, uint
         __threadfence();
         if (atomicAdd(&cnt->range_done, 1u) == ntiles - 1) {
             __threadfence();
-            st->min_key = atomicExch(&st->acc_min, 0xffffffffu);
-            st->max_key = atomicExch(&st->acc_max, 0u);
-            st->any_finite = atomicExch(&st->acc_any, 0u);
+            const uint32_t kmin2 = atomicExch(&st->acc_min, 0xffffffffu);
+            const uint32_t kmax2 = atomicExch(&st->acc_max, 0u);
+            const uint32_t any2 = atomicExch(&st->acc_any, 0u);
+            st->min_key = kmin2;
+            st->max_key = kmax2;
+            st->any_finite = any2;
+            st->P = make_params(range_eb_abs(a.eb, a.eb_kind, kmin2, kmax2, any2));
             signal_add(&cnt->range_ready, 1u);
         }
     }
@@ -159,8 +163,7 @@ __global__ void __launch_bounds__(kBatchThreads) batch_compress_kernel(BatchPlan
             batch_range_tile(a, cnt, idx, plan.range_tiles[arr], sm);
         } else if (phase == 1) {
             const ArrayState* st = a.st;
-            const LatticeParams P =
-                make_params(range_eb_abs(a.eb, a.eb_kind, st->min_key, st->max_key, st->any_finite));
+            const LatticeParams P = st->P;
             if (!P.raw && a.n) {
                 hist_window_zero(sm.q.win);
                 __syncthreads();

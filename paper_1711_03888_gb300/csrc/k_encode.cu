@@ -5,35 +5,59 @@
 
 namespace szg {
 
-template <int NT, bool FROM_CODES>
-__global__ void __launch_bounds__(NT, (NT >= 512 ? 1 : 512 / NT)) encode_kernel(CompressArgs a) {
+template <int C, bool FROM_CODES>
+__global__ void __launch_bounds__(EncShape<C>::kThreads, EncShape<C>::kMinBlocks) encode_kernel(CompressArgs a) {
+    constexpr int NT = EncShape<C>::kThreads;
     extern __shared__ uint4 dyn_smem[];
     __shared__ EncSmem<NT> esm;
-    __shared__ uint32_t s_c;
+    __shared__ uint32_t s_c[2];
+    __shared__ float s_prev;
     ArrayState* st = a.st;
     if (st->raw) {
         const uint64_t words = (a.n + 3u) & ~(uint64_t)3u;
         raw_copy_words(a, 0, words, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, (uint64_t)gridDim.x * blockDim.x);
         return;
     }
-    if (threadIdx.x == 0) s_c = atomicAdd(&st->ticket, 1u);
-    __syncthreads();
-    const uint32_t c = s_c;
-    if (c >= a.n_chunks) return;
-    encode_chunk<NT, 32, FROM_CODES>(a, c, reinterpret_cast<uint32_t*>(dyn_smem), esm);
+    uint32_t* smem = reinterpret_cast<uint32_t*>(dyn_smem);
+    if (FROM_CODES) {
+        encode_array_pipelined<C, NT, kEncWindow>(a, smem, esm, s_c, &s_prev);
+        return;
+    }
+    // codes recomputed from the input: one chunk per ticket
+    uint32_t* win = smem + C + C / 2;
+    if (kEncWindow) load_enc_window(a.enc, win, threadIdx.x, NT);
+    for (;;) {
+        if (threadIdx.x == 0) s_c[0] = atomicAdd(&st->ticket, 1u);
+        __syncthreads();          // also: the window is loaded / the last chunk's buffer is free
+        const uint32_t c = s_c[0];
+        __syncthreads();
+        if (c >= a.n_chunks) return;
+        encode_chunk<NT, EncShape<C>::kRun, false, kEncWindow>(a, c, smem, esm, win);
+    }
 }
 
-template <int NT>
+template <int C>
 static void launch_encode_t(const CompressArgs& a, cudaStream_t s) {
-    const size_t smem = (size_t)NT * 32u * 4u;
-    static bool configured = false;
-    if (!configured) {
-        cudaFuncSetAttribute(encode_kernel<NT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(encode_kernel<NT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        configured = true;
+    const size_t smem = enc_smem_bytes(C);
+    constexpr int NT = EncShape<C>::kThreads;
+    static int resident[2] = {0, 0};
+    if (!resident[0]) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaFuncSetAttribute(encode_kernel<C, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(encode_kernel<C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int b0 = 0, b1 = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, encode_kernel<C, false>, NT, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, encode_kernel<C, true>, NT, smem);
+        resident[0] = (b0 > 0 ? b0 : 1) * (sms > 0 ? sms : 148);
+        resident[1] = (b1 > 0 ? b1 : 1) * (sms > 0 ? sms : 148);
     }
-    if (a.codes) encode_kernel<NT, true><<<a.n_chunks, NT, smem, s>>>(a);
-    else encode_kernel<NT, false><<<a.n_chunks, NT, smem, s>>>(a);
+    // persistent: at most the resident blocks, each taking chunks by ticket
+    const int v = a.codes ? 1 : 0;
+    const uint32_t grid = umin32(a.n_chunks, (uint32_t)resident[v]);
+    if (v) encode_kernel<C, true><<<grid, NT, smem, s>>>(a);
+    else encode_kernel<C, false><<<grid, NT, smem, s>>>(a);
 }
 
 void launch_encode(const CompressArgs* a, int k, void* stream) {
@@ -41,10 +65,10 @@ void launch_encode(const CompressArgs* a, int k, void* stream) {
     for (int i = 0; i < k; ++i) {
         if (a[i].n == 0) continue;
         switch (a[i].C) {
-            case 2048: launch_encode_t<64>(a[i], s); break;
-            case 4096: launch_encode_t<128>(a[i], s); break;
-            case 8192: launch_encode_t<256>(a[i], s); break;
-            case 16384: launch_encode_t<512>(a[i], s); break;
+            case 2048: launch_encode_t<2048>(a[i], s); break;
+            case 4096: launch_encode_t<4096>(a[i], s); break;
+            case 8192: launch_encode_t<8192>(a[i], s); break;
+            case 16384: launch_encode_t<16384>(a[i], s); break;
             default: break;
         }
     }

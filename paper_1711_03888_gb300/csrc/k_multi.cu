@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(kQuantThreads, 4) quant_multi_kernel(MultiArgs
     __shared__ CompressArgs sa;
     stage_args(m, sa);
     const ArrayState* st = sa.st;
-    const LatticeParams P = make_params(range_eb_abs(sa.eb, sa.eb_kind, st->min_key, st->max_key, st->any_finite));
+    const LatticeParams P = st->P;
     if (P.raw || sa.n == 0) return;
     hist_window_zero(sh);
     __syncthreads();
@@ -55,11 +55,13 @@ __global__ void __launch_bounds__(kCbBlock) codebook_multi_kernel(MultiArgs m) {
     codebook_body<kCbBlock>(sa, sm);
 }
 
-template <int NT>
-__global__ void __launch_bounds__(NT, (NT >= 512 ? 1 : 512 / NT)) encode_multi_kernel(MultiArgs m) {
+template <int C>
+__global__ void __launch_bounds__(EncShape<C>::kThreads, EncShape<C>::kMinBlocks) encode_multi_kernel(MultiArgs m) {
+    constexpr int NT = EncShape<C>::kThreads;
     extern __shared__ uint4 dyn_smem[];
     __shared__ EncSmem<NT> esm;
-    __shared__ uint32_t s_c;
+    __shared__ uint32_t s_c[2];
+    __shared__ float s_prev;
     __shared__ CompressArgs sa;
     stage_args(m, sa);
     ArrayState* st = sa.st;
@@ -69,12 +71,11 @@ __global__ void __launch_bounds__(NT, (NT >= 512 ? 1 : 512 / NT)) encode_multi_k
         raw_copy_words(sa, 0, words, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, (uint64_t)gridDim.x * blockDim.x);
         return;
     }
-    if (threadIdx.x == 0) s_c = atomicAdd(&st->ticket, 1u);
-    __syncthreads();
-    const uint32_t c = s_c;
-    if (c >= sa.n_chunks) return;
-    encode_chunk<NT, 32, true>(sa, c, reinterpret_cast<uint32_t*>(dyn_smem), esm);
+    encode_array_pipelined<C, NT, kEncWindow>(sa, reinterpret_cast<uint32_t*>(dyn_smem), esm, s_c, &s_prev);
 }
+
+constexpr int kEncSmem2048 = (int)enc_smem_bytes(2048);
+constexpr int kEncSmem4096 = (int)enc_smem_bytes(4096);
 
 int sm_count() {
     static int sms = 0;
@@ -113,13 +114,18 @@ int add_multi_compress_nodes(void* graph, void* dep, const CompressArgs* d_args,
         count += groups[i].count;
         if (groups[i].max_chunks > max_nc) max_nc = groups[i].max_chunks;
     }
-    static int per_sm = 0;
+    static int per_sm = 0, enc_res[2] = {0, 0};
     static bool configured = false;
     if (!configured) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, quant_multi_kernel, kQuantThreads, 0);
         if (per_sm <= 0) per_sm = 1;
-        cudaFuncSetAttribute(encode_multi_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 32 * 4);
-        cudaFuncSetAttribute(encode_multi_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 32 * 4);
+        cudaFuncSetAttribute(encode_multi_kernel<2048>, cudaFuncAttributeMaxDynamicSharedMemorySize, kEncSmem2048);
+        cudaFuncSetAttribute(encode_multi_kernel<4096>, cudaFuncAttributeMaxDynamicSharedMemorySize, kEncSmem4096);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&enc_res[0], encode_multi_kernel<2048>,
+                                                      EncShape<2048>::kThreads, kEncSmem2048);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&enc_res[1], encode_multi_kernel<4096>,
+                                                      EncShape<4096>::kThreads, kEncSmem4096);
+        for (int j = 0; j < 2; ++j) enc_res[j] = (enc_res[j] > 0 ? enc_res[j] : 1) * sm_count();
         configured = true;
     }
     MultiArgs all{d_args, first};
@@ -138,11 +144,17 @@ int add_multi_compress_nodes(void* graph, void* dep, const CompressArgs* d_args,
     for (int i = 0; i < ngroups; ++i) {
         MultiArgs mg{d_args, groups[i].first};
         cudaGraphNode_t n_enc;
-        const dim3 grid(groups[i].max_chunks ? groups[i].max_chunks : 1, groups[i].count);
+        // persistent encoders: the resident blocks shared out over the group's arrays
+        const int j = groups[i].C == 2048 ? 0 : 1;
+        const uint32_t per = umin32(groups[i].max_chunks ? groups[i].max_chunks : 1u,
+                                    (uint32_t)(enc_res[j] / (int)groups[i].count > 0 ? enc_res[j] / (int)groups[i].count : 1));
+        const dim3 grid(per, groups[i].count);
         if (groups[i].C == 2048)
-            e = add_node(g, &n_enc, &n_cb, 1, (void*)encode_multi_kernel<64>, grid, dim3(64), 64 * 32 * 4, &mg);
+            e = add_node(g, &n_enc, &n_cb, 1, (void*)encode_multi_kernel<2048>, grid,
+                         dim3(EncShape<2048>::kThreads), kEncSmem2048, &mg);
         else if (groups[i].C == 4096)
-            e = add_node(g, &n_enc, &n_cb, 1, (void*)encode_multi_kernel<128>, grid, dim3(128), 128 * 32 * 4, &mg);
+            e = add_node(g, &n_enc, &n_cb, 1, (void*)encode_multi_kernel<4096>, grid,
+                         dim3(EncShape<4096>::kThreads), kEncSmem4096, &mg);
         else
             return (int)cudaErrorInvalidValue;
         if (e != cudaSuccess) return (int)e;

@@ -10,7 +10,7 @@ __global__ void __launch_bounds__(kQuantThreads) quant_kernel(CompressArgs a) {
     __shared__ uint32_t sh[kWin];
     __shared__ uint32_t s_esc[kQuantThreads / 32];
     const ArrayState* st = a.st;
-    const LatticeParams P = make_params(range_eb_abs(a.eb, a.eb_kind, st->min_key, st->max_key, st->any_finite));
+    const LatticeParams P = st->P;
     if (P.raw || a.n == 0) return;
     hist_window_zero(sh);
     __syncthreads();

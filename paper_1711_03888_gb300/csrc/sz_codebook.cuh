@@ -108,7 +108,7 @@ __device__ void codebook_body(const CompressArgs& a, CbSmem<NT>& sm) {
     constexpr int kCbThreads = NT;
     const int tid = threadIdx.x;
     ArrayState* st = a.st;
-    const LatticeParams P = make_params(range_eb_abs(a.eb, a.eb_kind, st->min_key, st->max_key, st->any_finite));
+    const LatticeParams P = st->P;
     uint8_t* out = a.out;
     const uint64_t n = a.n;
     const uint32_t flags = a.extra_flags & kFlagReordered;

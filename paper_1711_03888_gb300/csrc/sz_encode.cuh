@@ -23,6 +23,24 @@ namespace szg {
 
 constexpr uint32_t kLookbackSpins = 1u << 22;
 
+// Elements per thread of the stand-alone encode launches (chunks of up to
+// 1024 * kEncRun elements use C / kEncRun threads; larger ones 1024).
+// The launch bounds ask for kEncThreadsPerSM resident threads per SM.
+#ifndef SZ_ENC_RUN
+#define SZ_ENC_RUN 32
+#endif
+#ifndef SZ_ENC_TPSM
+#define SZ_ENC_TPSM 512
+#endif
+constexpr int kEncRun = SZ_ENC_RUN;
+constexpr int kEncThreadsPerSM = SZ_ENC_TPSM;
+template <int C>
+struct EncShape {
+    static constexpr int kRun = (C / kEncRun > 1024) ? C / 1024 : kEncRun;
+    static constexpr int kThreads = C / kRun;
+    static constexpr int kMinBlocks = kThreads >= kEncThreadsPerSM ? 1 : kEncThreadsPerSM / kThreads;
+};
+
 // raw stream: words [wb, we) of the payload are the input bits (zero past n)
 __device__ __forceinline__ void raw_copy_words(const CompressArgs& a, uint64_t wb, uint64_t we, uint64_t t0,
                                                uint64_t tstride) {
@@ -32,118 +50,73 @@ __device__ __forceinline__ void raw_copy_words(const CompressArgs& a, uint64_t w
     for (uint64_t i = wb + t0; i < we; i += tstride) dst[i] = (i < a.n) ? __ldg(src + i) : 0u;
 }
 
+// Codeword-table window held in shared memory by the persistent encoders:
+// codes kEncWinLo .. kEncWinLo + kEncWin - 1 (deltas within +-4096), which
+// carry nearly every element at practical bounds; others read global memory.
+constexpr uint32_t kEncWin = 8192;
+constexpr uint32_t kEncWinLo = kRadius - kEncWin / 2;
+#ifndef SZ_ENC_WIN
+#define SZ_ENC_WIN 0
+#endif
+constexpr bool kEncWindow = SZ_ENC_WIN != 0;
+
+// dynamic shared memory of a persistent encoder for chunks of C elements:
+// payload buffer (C words), code stage (C / 2 words), window (if used)
+constexpr size_t enc_smem_bytes(int C) {
+    return 4u * ((size_t)C + (size_t)C / 2 + (kEncWindow ? (size_t)kEncWin : 0u));
+}
+
+__device__ __forceinline__ void load_enc_window(const uint32_t* enc, uint32_t* win, int tid, int nt) {
+    const uint4* src = reinterpret_cast<const uint4*>(enc + kEncWinLo);
+    for (int i = tid; i < (int)(kEncWin / 4); i += nt) reinterpret_cast<uint4*>(win)[i] = __ldg(src + i);
+}
+
+template <bool WIN>
+__device__ __forceinline__ uint32_t enc_lookup(const uint32_t* enc, const uint32_t* win, uint32_t code) {
+    if (WIN) {
+        const uint32_t wi = code - kEncWinLo;
+        return wi < kEncWin ? win[wi] : __ldg(enc + code);
+    }
+    return __ldg(enc + code);
+}
+
 template <int NT>
 struct EncSmem {
-    uint32_t ws32[NT / 32 + 1], ws32b[NT / 32 + 1];
+    unsigned long long ws64[NT / 32 + 1];
     unsigned long long prefix;
 };
 
-// Encode chunk c of array a with a block of NT threads, kRun = C / NT
-// consecutive elements per thread.  buf: C words of shared memory.
-template <int NT, int kRun, bool FROM_CODES>
-__device__ void encode_chunk(const CompressArgs& a, const uint32_t c, uint32_t* buf, EncSmem<NT>& esm) {
+// The part of a chunk's encoding after each thread holds its kRun packed
+// entries r[j] = codeword << 6 | length << 1 | escape (0 past the chunk's
+// end): block scan of bit lengths and escape counts, publication of the
+// chunk size, packing, escape records, look-back for the word offset, the
+// chunk tables and the coalesced copy of the payload.  anchor (thread 0): the
+// lattice value before the chunk.
+template <int NT, int kRun>
+__device__ __forceinline__ void encode_chunk_body(const CompressArgs& a, const LatticeParams& P, const uint32_t c,
+                                                  const uint32_t (&r)[kRun], const long long anchor, uint32_t* buf,
+                                                  EncSmem<NT>& esm) {
     constexpr int C = NT * kRun;
-    constexpr int kRunShift = kRun == 8 ? 3 : (kRun == 16 ? 4 : 5);
-    static_assert(kRun == 8 || kRun == 16 || kRun == 32, "run length");
-    uint32_t* ws32 = esm.ws32;
-    uint32_t* ws32b = esm.ws32b;
     unsigned long long& s_prefix = esm.prefix;
     ArrayState* st = a.st;
-    const int tid = threadIdx.x, lane = tid & 31;
-
-    const LatticeParams P = make_params(range_eb_abs(a.eb, a.eb_kind, st->min_key, st->max_key, st->any_finite));
+    const int tid = threadIdx.x;
     const uint64_t n = a.n, base = (uint64_t)c * C;
     const uint32_t cnt = (uint32_t)umin64(C, n - base);
     const float* in = a.in;
-    const bool vec = ((uintptr_t)in & 15u) == 0;
-    const uint32_t* enc = a.enc;
     const uint32_t e0 = tid * kRun;
-    uint32_t r[kRun];
-    long long anchor = 0;
-
-    if (FROM_CODES) {
-        // ---- pass 1+2: the quantizer's codes for elements e0 .. e0+31 ----------------
-        const uint16_t* cp = a.codes + base + e0;
-        uint32_t w[kRun / 2];
-        if (e0 + kRun <= cnt) {
-#pragma unroll
-            for (int m = 0; m < kRun / 8; ++m) {
-                uint4 v = __ldg(reinterpret_cast<const uint4*>(cp) + m);
-                w[4 * m] = v.x; w[4 * m + 1] = v.y; w[4 * m + 2] = v.z; w[4 * m + 3] = v.w;
-            }
-        } else {
-#pragma unroll
-            for (int j = 0; j < kRun / 2; ++j) {
-                uint32_t lo = (e0 + 2 * j < cnt) ? __ldg(cp + 2 * j) : 0u;
-                uint32_t hi = (e0 + 2 * j + 1 < cnt) ? __ldg(cp + 2 * j + 1) : 0u;
-                w[j] = lo | (hi << 16);
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < kRun; ++j) {
-            const uint32_t code = (j & 1) ? (w[j >> 1] >> 16) : (w[j >> 1] & 0xffffu);
-            const uint32_t ent = __ldg(enc + code);
-            r[j] = (e0 + j < cnt) ? (((ent >> 5) << 6) | ((ent & 31u) << 1) | (code == 0u ? 1u : 0u)) : 0u;
-        }
-        if (tid == 0 && base > 0) {
-            bool vv;
-            lattice_q(__ldg(in + base - 1), P, anchor, vv);
-        }
-    } else {
-    // ---- pass 1: codes and (codeword, length), coalesced -----------------------
-#pragma unroll 2
-    for (uint32_t e = 4 * tid; e < (uint32_t)C; e += 4 * NT) {
-        float x[4];
-        if (vec && e + 3 < cnt) {
-            float4 v = __ldg(reinterpret_cast<const float4*>(in + base + e));
-            x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
-        } else {
-#pragma unroll
-            for (int j = 0; j < 4; ++j) x[j] = (e + j < cnt) ? __ldg(in + base + e + j) : 0.0f;
-        }
-        long long q[4];
-        bool vb[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) lattice_q(x[j], P, q[j], vb[j]);
-        long long qprev = __shfl_up_sync(0xffffffffu, q[3], 1);
-        if (lane == 0) {
-            qprev = 0;
-            if (base + e > 0 && e < cnt) {
-                bool vv;
-                lattice_q(__ldg(in + base + e - 1), P, qprev, vv);
-            }
-            if (e == 0) anchor = qprev;
-        }
-        uint32_t pk[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            pk[j] = 0u;
-            if (e + j < cnt) {
-                uint32_t code = make_code(q[j], j == 0 ? qprev : q[j - 1], vb[j]);
-                uint32_t ent = __ldg(enc + code);
-                pk[j] = ((ent >> 5) << 6) | ((ent & 31u) << 1) | (code == 0u ? 1u : 0u);
-            }
-        }
-        *reinterpret_cast<uint4*>(&buf[swz(e, kRunShift)]) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-    }
-    __syncthreads();
-
-    // ---- pass 2: this thread's 32 consecutive entries ---------------------------
-#pragma unroll
-    for (int m = 0; m < kRun / 4; ++m) {
-        uint4 v = *reinterpret_cast<const uint4*>(&buf[swz(e0 + 4 * m, kRunShift)]);
-        r[4 * m] = v.x; r[4 * m + 1] = v.y; r[4 * m + 2] = v.z; r[4 * m + 3] = v.w;
-    }
-    }  // !FROM_CODES
+    (void)cnt;
     uint32_t bits = 0, escs = 0;
 #pragma unroll
     for (int j = 0; j < kRun; ++j) {
         bits += (r[j] >> 1) & 31u;
         escs += r[j] & 1u;
     }
-    uint32_t chunk_bits, chunk_escs;
-    const uint32_t start = block_exclusive_scan<NT>(bits, ws32, &chunk_bits);
-    const uint32_t eoff = block_exclusive_scan<NT>(escs, ws32b, &chunk_escs);
+    // one block scan of (escapes << 32 | bits)
+    unsigned long long tot;
+    const unsigned long long ex =
+        block_exclusive_scan<NT>(((unsigned long long)escs << 32) | bits, esm.ws64, &tot);
+    const uint32_t start = (uint32_t)ex, eoff = (uint32_t)(ex >> 32);
+    const uint32_t chunk_bits = (uint32_t)tot;
     const uint32_t chunk_words = ((chunk_bits + 127u) >> 7) << 2;
     // sub-stream bit length: reduce over the G/32 lanes that share sub-stream
     constexpr int kLanesPerSub = C / kSubPerChunk / kRun;   // 1, 2, 4 or 8
@@ -279,6 +252,175 @@ __device__ void encode_chunk(const CompressArgs& a, const uint32_t c, uint32_t* 
         uint4* dst = reinterpret_cast<uint4*>(out + off_payload + 4ull * prefix);
         const uint4* src = reinterpret_cast<const uint4*>(buf);
         for (uint32_t w4 = tid; w4 < chunk_words / 4; w4 += NT) dst[w4] = src[w4];
+    }
+}
+
+// Encode chunk c of array a with a block of NT threads, kRun = C / NT
+// consecutive elements per thread.  buf: C words of shared memory; win: the
+// codeword-table window in shared memory (WIN) or unused.
+template <int NT, int kRun, bool FROM_CODES, bool WIN = false>
+__device__ void encode_chunk(const CompressArgs& a, const uint32_t c, uint32_t* buf, EncSmem<NT>& esm,
+                             const uint32_t* win = nullptr) {
+    constexpr int C = NT * kRun;
+    constexpr int kRunShift = kRun == 8 ? 3 : (kRun == 16 ? 4 : 5);
+    static_assert(kRun == 8 || kRun == 16 || kRun == 32, "run length");
+    ArrayState* st = a.st;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const LatticeParams P = st->P;
+    const uint64_t n = a.n, base = (uint64_t)c * C;
+    const uint32_t cnt = (uint32_t)umin64(C, n - base);
+    const float* in = a.in;
+    const bool vec = ((uintptr_t)in & 15u) == 0;
+    const uint32_t* enc = a.enc;
+    const uint32_t e0 = tid * kRun;
+    uint32_t r[kRun];
+    long long anchor = 0;
+
+    if (FROM_CODES) {
+        // ---- pass 1+2: the quantizer's codes for elements e0 .. e0+31 ----------------
+        const uint16_t* cp = a.codes + base + e0;
+        uint32_t w[kRun / 2];
+        if (e0 + kRun <= cnt) {
+#pragma unroll
+            for (int m = 0; m < kRun / 8; ++m) {
+                uint4 v = __ldg(reinterpret_cast<const uint4*>(cp) + m);
+                w[4 * m] = v.x; w[4 * m + 1] = v.y; w[4 * m + 2] = v.z; w[4 * m + 3] = v.w;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < kRun / 2; ++j) {
+                uint32_t lo = (e0 + 2 * j < cnt) ? __ldg(cp + 2 * j) : 0u;
+                uint32_t hi = (e0 + 2 * j + 1 < cnt) ? __ldg(cp + 2 * j + 1) : 0u;
+                w[j] = lo | (hi << 16);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kRun; ++j) {
+            const uint32_t code = (j & 1) ? (w[j >> 1] >> 16) : (w[j >> 1] & 0xffffu);
+            const uint32_t ent = enc_lookup<WIN>(enc, win, code);
+            r[j] = (e0 + j < cnt) ? (((ent >> 5) << 6) | ((ent & 31u) << 1) | (code == 0u ? 1u : 0u)) : 0u;
+        }
+        if (tid == 0 && base > 0) {
+            bool vv;
+            lattice_q(__ldg(in + base - 1), P, anchor, vv);
+        }
+    } else {
+    // ---- pass 1: codes and (codeword, length), coalesced -----------------------
+#pragma unroll 2
+    for (uint32_t e = 4 * tid; e < (uint32_t)C; e += 4 * NT) {
+        float x[4];
+        if (vec && e + 3 < cnt) {
+            float4 v = __ldg(reinterpret_cast<const float4*>(in + base + e));
+            x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) x[j] = (e + j < cnt) ? __ldg(in + base + e + j) : 0.0f;
+        }
+        long long q[4];
+        bool vb[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) lattice_q(x[j], P, q[j], vb[j]);
+        long long qprev = __shfl_up_sync(0xffffffffu, q[3], 1);
+        if (lane == 0) {
+            qprev = 0;
+            if (base + e > 0 && e < cnt) {
+                bool vv;
+                lattice_q(__ldg(in + base + e - 1), P, qprev, vv);
+            }
+            if (e == 0) anchor = qprev;
+        }
+        uint32_t pk[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            pk[j] = 0u;
+            if (e + j < cnt) {
+                uint32_t code = make_code(q[j], j == 0 ? qprev : q[j - 1], vb[j]);
+                uint32_t ent = enc_lookup<WIN>(enc, win, code);
+                pk[j] = ((ent >> 5) << 6) | ((ent & 31u) << 1) | (code == 0u ? 1u : 0u);
+            }
+        }
+        *reinterpret_cast<uint4*>(&buf[swz(e, kRunShift)]) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    }
+    __syncthreads();
+
+    // ---- pass 2: this thread's 32 consecutive entries ---------------------------
+#pragma unroll
+    for (int m = 0; m < kRun / 4; ++m) {
+        uint4 v = *reinterpret_cast<const uint4*>(&buf[swz(e0 + 4 * m, kRunShift)]);
+        r[4 * m] = v.x; r[4 * m + 1] = v.y; r[4 * m + 2] = v.z; r[4 * m + 3] = v.w;
+    }
+    }  // !FROM_CODES
+    encode_chunk_body<NT, kRun>(a, P, c, r, anchor, buf, esm);
+}
+
+// Persistent, pipelined encoding of one array from the quantizer's codes
+// (block of NT = C / kRun threads).  smem: C words (payload buffer) | C / 2
+// words (code stage) | kEncWin words (codeword window, WIN).  The block takes
+// chunk tickets in order; while it encodes chunk c, the codes and the
+// preceding element of its next ticket are already on their way into the
+// stage (cp.async).  A block holds at most two tickets, and the smallest
+// unfinished ticket is always being encoded, so the look-back still only
+// waits on chunks that make progress.
+template <int C, int NT, bool WIN>
+__device__ __forceinline__ void encode_array_pipelined(const CompressArgs& a, uint32_t* smem, EncSmem<NT>& esm,
+                                                       uint32_t* s_ticket, float* s_prev) {
+    constexpr int kRun = C / NT;
+    ArrayState* st = a.st;
+    const int tid = threadIdx.x;
+    uint32_t* buf = smem;
+    uint16_t* stage = reinterpret_cast<uint16_t*>(smem + C);
+    uint32_t* win = smem + C + C / 2;
+    const LatticeParams P = st->P;
+    if (WIN) load_enc_window(a.enc, win, tid, NT);
+    const uint32_t s_stage = (uint32_t)__cvta_generic_to_shared(stage);
+    const uint32_t s_prevp = (uint32_t)__cvta_generic_to_shared(s_prev);
+    auto issue = [&](uint32_t cc) {
+        // the chunk's C codes (the code buffer holds whole chunks) and, for thread 0,
+        // the element before the chunk
+        const uint16_t* src = a.codes + (uint64_t)cc * C;
+        for (int i = tid; i < C / 8; i += NT)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s_stage + 16u * i),
+                         "l"(__cvta_generic_to_global(src + 8 * i))
+                         : "memory");
+        if (tid == 0 && cc > 0)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s_prevp),
+                         "l"(__cvta_generic_to_global(a.in + (uint64_t)cc * C - 1))
+                         : "memory");
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    if (tid == 0) s_ticket[0] = atomicAdd(&st->ticket, 1u);
+    __syncthreads();
+    uint32_t c = s_ticket[0];
+    if (c < a.n_chunks) issue(c);
+    while (c < a.n_chunks) {
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        __syncthreads();          // stage holds chunk c; the window is loaded; buf is free
+        const uint32_t cnt = (uint32_t)umin64(C, a.n - (uint64_t)c * C);
+        const uint32_t e0 = tid * kRun;
+        uint32_t w[kRun / 2];
+#pragma unroll
+        for (int m = 0; m < kRun / 8; ++m) {
+            const uint4 v = *reinterpret_cast<const uint4*>(stage + e0 + 8 * m);
+            w[4 * m] = v.x; w[4 * m + 1] = v.y; w[4 * m + 2] = v.z; w[4 * m + 3] = v.w;
+        }
+        long long anchor = 0;
+        if (tid == 0 && c > 0) {
+            bool vv;
+            lattice_q(*s_prev, P, anchor, vv);
+        }
+        if (tid == 0) s_ticket[1] = atomicAdd(&st->ticket, 1u);
+        __syncthreads();          // the stage is read; the next ticket is known
+        const uint32_t cn = s_ticket[1];
+        if (cn < a.n_chunks) issue(cn);
+        uint32_t r[kRun];
+#pragma unroll
+        for (int j = 0; j < kRun; ++j) {
+            const uint32_t code = (j & 1) ? (w[j >> 1] >> 16) : (w[j >> 1] & 0xffffu);
+            const uint32_t ent = enc_lookup<WIN>(a.enc, win, code);
+            r[j] = (e0 + j < cnt) ? (((ent >> 5) << 6) | ((ent & 31u) << 1) | (code == 0u ? 1u : 0u)) : 0u;
+        }
+        encode_chunk_body<NT, kRun>(a, P, c, r, anchor, buf, esm);
+        c = cn;
     }
 }
 

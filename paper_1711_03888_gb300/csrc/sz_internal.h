@@ -56,6 +56,7 @@ struct LatticeParams {
 struct ArrayState {
     // range (set by the last range block)
     uint32_t min_key, max_key, any_finite, range_done;
+    LatticeParams P;           // lattice parameters from the range (set with it)
     uint32_t acc_min, acc_max, acc_any, acc_blocks;   // accumulators, self-resetting
     // codebook / layout (set by the codebook kernel)
     uint64_t off[8];

@@ -79,9 +79,13 @@ __device__ __forceinline__ void range_body(const CompressArgs& a, uint32_t bid, 
     __syncthreads();
     if (s_last && tid == 0) {
         __threadfence();
-        st->min_key = atomicExch(&st->acc_min, 0xffffffffu);
-        st->max_key = atomicExch(&st->acc_max, 0u);
-        st->any_finite = atomicExch(&st->acc_any, 0u);
+        const uint32_t kmin2 = atomicExch(&st->acc_min, 0xffffffffu);
+        const uint32_t kmax2 = atomicExch(&st->acc_max, 0u);
+        const uint32_t any2 = atomicExch(&st->acc_any, 0u);
+        st->min_key = kmin2;
+        st->max_key = kmax2;
+        st->any_finite = any2;
+        st->P = make_params(range_eb_abs(a.eb, a.eb_kind, kmin2, kmax2, any2));
         st->acc_blocks = 0u;
         st->range_done = 1u;
     }
