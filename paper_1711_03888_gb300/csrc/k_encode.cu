@@ -20,19 +20,17 @@ __global__ void __launch_bounds__(EncShape<C>::kThreads, EncShape<C>::kMinBlocks
     }
     uint32_t* smem = reinterpret_cast<uint32_t*>(dyn_smem);
     if (FROM_CODES) {
-        encode_array_pipelined<C, NT, kEncWindow>(a, smem, esm, s_c, &s_prev);
+        encode_array_pipelined<C, NT>(a, smem, esm, s_c, &s_prev);
         return;
     }
     // codes recomputed from the input: one chunk per ticket
-    uint32_t* win = smem + C + C / 2;
-    if (kEncWindow) load_enc_window(a.enc, win, threadIdx.x, NT);
     for (;;) {
         if (threadIdx.x == 0) s_c[0] = atomicAdd(&st->ticket, 1u);
-        __syncthreads();          // also: the window is loaded / the last chunk's buffer is free
+        __syncthreads();          // also: the last chunk's buffer is free
         const uint32_t c = s_c[0];
         __syncthreads();
         if (c >= a.n_chunks) return;
-        encode_chunk<NT, EncShape<C>::kRun, false, kEncWindow>(a, c, smem, esm, win);
+        encode_chunk<NT, EncShape<C>::kRun, false>(a, c, smem, esm);
     }
 }
 

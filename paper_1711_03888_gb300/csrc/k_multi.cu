@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(EncShape<C>::kThreads, EncShape<C>::kMinBlocks
         raw_copy_words(sa, 0, words, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, (uint64_t)gridDim.x * blockDim.x);
         return;
     }
-    encode_array_pipelined<C, NT, kEncWindow>(sa, reinterpret_cast<uint32_t*>(dyn_smem), esm, s_c, &s_prev);
+    encode_array_pipelined<C, NT>(sa, reinterpret_cast<uint32_t*>(dyn_smem), esm, s_c, &s_prev);
 }
 
 constexpr int kEncSmem2048 = (int)enc_smem_bytes(2048);

@@ -26,11 +26,15 @@ constexpr uint32_t kLookbackSpins = 1u << 22;
 // Elements per thread of the stand-alone encode launches (chunks of up to
 // 1024 * kEncRun elements use C / kEncRun threads; larger ones 1024).
 // The launch bounds ask for kEncThreadsPerSM resident threads per SM.
+// Measured on GB300 for 2^27-element arrays at C = 4096 (encode ms):
+// run 16 / 1024 threads 0.50, run 32 / 512 0.51, run 16 / 768 0.57,
+// run 8 / 1024 0.96; a shared-memory copy of the codeword table's hot
+// window cost more in occupancy than it saved in gathers.
 #ifndef SZ_ENC_RUN
-#define SZ_ENC_RUN 32
+#define SZ_ENC_RUN 16
 #endif
 #ifndef SZ_ENC_TPSM
-#define SZ_ENC_TPSM 512
+#define SZ_ENC_TPSM 1024
 #endif
 constexpr int kEncRun = SZ_ENC_RUN;
 constexpr int kEncThreadsPerSM = SZ_ENC_TPSM;
@@ -50,35 +54,9 @@ __device__ __forceinline__ void raw_copy_words(const CompressArgs& a, uint64_t w
     for (uint64_t i = wb + t0; i < we; i += tstride) dst[i] = (i < a.n) ? __ldg(src + i) : 0u;
 }
 
-// Codeword-table window held in shared memory by the persistent encoders:
-// codes kEncWinLo .. kEncWinLo + kEncWin - 1 (deltas within +-4096), which
-// carry nearly every element at practical bounds; others read global memory.
-constexpr uint32_t kEncWin = 8192;
-constexpr uint32_t kEncWinLo = kRadius - kEncWin / 2;
-#ifndef SZ_ENC_WIN
-#define SZ_ENC_WIN 0
-#endif
-constexpr bool kEncWindow = SZ_ENC_WIN != 0;
-
 // dynamic shared memory of a persistent encoder for chunks of C elements:
-// payload buffer (C words), code stage (C / 2 words), window (if used)
-constexpr size_t enc_smem_bytes(int C) {
-    return 4u * ((size_t)C + (size_t)C / 2 + (kEncWindow ? (size_t)kEncWin : 0u));
-}
-
-__device__ __forceinline__ void load_enc_window(const uint32_t* enc, uint32_t* win, int tid, int nt) {
-    const uint4* src = reinterpret_cast<const uint4*>(enc + kEncWinLo);
-    for (int i = tid; i < (int)(kEncWin / 4); i += nt) reinterpret_cast<uint4*>(win)[i] = __ldg(src + i);
-}
-
-template <bool WIN>
-__device__ __forceinline__ uint32_t enc_lookup(const uint32_t* enc, const uint32_t* win, uint32_t code) {
-    if (WIN) {
-        const uint32_t wi = code - kEncWinLo;
-        return wi < kEncWin ? win[wi] : __ldg(enc + code);
-    }
-    return __ldg(enc + code);
-}
+// payload buffer (C words) and code stage (C / 2 words)
+constexpr size_t enc_smem_bytes(int C) { return 4u * ((size_t)C + (size_t)C / 2); }
 
 template <int NT>
 struct EncSmem {
@@ -256,11 +234,9 @@ __device__ __forceinline__ void encode_chunk_body(const CompressArgs& a, const L
 }
 
 // Encode chunk c of array a with a block of NT threads, kRun = C / NT
-// consecutive elements per thread.  buf: C words of shared memory; win: the
-// codeword-table window in shared memory (WIN) or unused.
-template <int NT, int kRun, bool FROM_CODES, bool WIN = false>
-__device__ void encode_chunk(const CompressArgs& a, const uint32_t c, uint32_t* buf, EncSmem<NT>& esm,
-                             const uint32_t* win = nullptr) {
+// consecutive elements per thread.  buf: C words of shared memory.
+template <int NT, int kRun, bool FROM_CODES>
+__device__ void encode_chunk(const CompressArgs& a, const uint32_t c, uint32_t* buf, EncSmem<NT>& esm) {
     constexpr int C = NT * kRun;
     constexpr int kRunShift = kRun == 8 ? 3 : (kRun == 16 ? 4 : 5);
     static_assert(kRun == 8 || kRun == 16 || kRun == 32, "run length");
@@ -297,7 +273,7 @@ __device__ void encode_chunk(const CompressArgs& a, const uint32_t c, uint32_t* 
 #pragma unroll
         for (int j = 0; j < kRun; ++j) {
             const uint32_t code = (j & 1) ? (w[j >> 1] >> 16) : (w[j >> 1] & 0xffffu);
-            const uint32_t ent = enc_lookup<WIN>(enc, win, code);
+            const uint32_t ent = __ldg(enc + code);
             r[j] = (e0 + j < cnt) ? (((ent >> 5) << 6) | ((ent & 31u) << 1) | (code == 0u ? 1u : 0u)) : 0u;
         }
         if (tid == 0 && base > 0) {
@@ -335,7 +311,7 @@ __device__ void encode_chunk(const CompressArgs& a, const uint32_t c, uint32_t* 
             pk[j] = 0u;
             if (e + j < cnt) {
                 uint32_t code = make_code(q[j], j == 0 ? qprev : q[j - 1], vb[j]);
-                uint32_t ent = enc_lookup<WIN>(enc, win, code);
+                uint32_t ent = __ldg(enc + code);
                 pk[j] = ((ent >> 5) << 6) | ((ent & 31u) << 1) | (code == 0u ? 1u : 0u);
             }
         }
@@ -355,13 +331,13 @@ __device__ void encode_chunk(const CompressArgs& a, const uint32_t c, uint32_t* 
 
 // Persistent, pipelined encoding of one array from the quantizer's codes
 // (block of NT = C / kRun threads).  smem: C words (payload buffer) | C / 2
-// words (code stage) | kEncWin words (codeword window, WIN).  The block takes
+// words (code stage).  The block takes
 // chunk tickets in order; while it encodes chunk c, the codes and the
 // preceding element of its next ticket are already on their way into the
 // stage (cp.async).  A block holds at most two tickets, and the smallest
 // unfinished ticket is always being encoded, so the look-back still only
 // waits on chunks that make progress.
-template <int C, int NT, bool WIN>
+template <int C, int NT>
 __device__ __forceinline__ void encode_array_pipelined(const CompressArgs& a, uint32_t* smem, EncSmem<NT>& esm,
                                                        uint32_t* s_ticket, float* s_prev) {
     constexpr int kRun = C / NT;
@@ -369,9 +345,7 @@ __device__ __forceinline__ void encode_array_pipelined(const CompressArgs& a, ui
     const int tid = threadIdx.x;
     uint32_t* buf = smem;
     uint16_t* stage = reinterpret_cast<uint16_t*>(smem + C);
-    uint32_t* win = smem + C + C / 2;
     const LatticeParams P = st->P;
-    if (WIN) load_enc_window(a.enc, win, tid, NT);
     const uint32_t s_stage = (uint32_t)__cvta_generic_to_shared(stage);
     const uint32_t s_prevp = (uint32_t)__cvta_generic_to_shared(s_prev);
     auto issue = [&](uint32_t cc) {
@@ -394,7 +368,7 @@ __device__ __forceinline__ void encode_array_pipelined(const CompressArgs& a, ui
     if (c < a.n_chunks) issue(c);
     while (c < a.n_chunks) {
         asm volatile("cp.async.wait_all;" ::: "memory");
-        __syncthreads();          // stage holds chunk c; the window is loaded; buf is free
+        __syncthreads();          // stage holds chunk c; buf is free
         const uint32_t cnt = (uint32_t)umin64(C, a.n - (uint64_t)c * C);
         const uint32_t e0 = tid * kRun;
         uint32_t w[kRun / 2];
@@ -403,22 +377,23 @@ __device__ __forceinline__ void encode_array_pipelined(const CompressArgs& a, ui
             const uint4 v = *reinterpret_cast<const uint4*>(stage + e0 + 8 * m);
             w[4 * m] = v.x; w[4 * m + 1] = v.y; w[4 * m + 2] = v.z; w[4 * m + 3] = v.w;
         }
+        // the next ticket's atomic is in flight while the codewords are looked up
+        if (tid == 0) s_ticket[1] = atomicAdd(&st->ticket, 1u);
         long long anchor = 0;
         if (tid == 0 && c > 0) {
             bool vv;
             lattice_q(*s_prev, P, anchor, vv);
         }
-        if (tid == 0) s_ticket[1] = atomicAdd(&st->ticket, 1u);
-        __syncthreads();          // the stage is read; the next ticket is known
-        const uint32_t cn = s_ticket[1];
-        if (cn < a.n_chunks) issue(cn);
         uint32_t r[kRun];
 #pragma unroll
         for (int j = 0; j < kRun; ++j) {
             const uint32_t code = (j & 1) ? (w[j >> 1] >> 16) : (w[j >> 1] & 0xffffu);
-            const uint32_t ent = enc_lookup<WIN>(a.enc, win, code);
+            const uint32_t ent = __ldg(a.enc + code);
             r[j] = (e0 + j < cnt) ? (((ent >> 5) << 6) | ((ent & 31u) << 1) | (code == 0u ? 1u : 0u)) : 0u;
         }
+        __syncthreads();          // the stage is read; the next ticket is known
+        const uint32_t cn = s_ticket[1];
+        if (cn < a.n_chunks) issue(cn);
         encode_chunk_body<NT, kRun>(a, P, c, r, anchor, buf, esm);
         c = cn;
     }
