@@ -192,6 +192,69 @@ def cpu_sample(snap, n_sample):
 # ---------------------------------------------------------------------------
 
 # ---------------------------------------------------------------------------
+# Batched form: 128 simulated ranks x 6 fields of uneven sizes
+# ---------------------------------------------------------------------------
+
+def batched_bench(sz, device, steps):
+    """768 arrays of 2^U[14,24] float32 (128 ranks x 6 fields, per-array rel eb
+    from {1e-3, 1e-4}): one sz_compress_batch call (one CUDA graph) against
+    768 sz_compress calls on the same stream; then the batched decompression.
+    Device-resident inputs; CUDA events around each variant."""
+    import torch
+    import synth
+    arrays = synth.batch_ranks(device="cuda")
+    xs = [t for _, _, t, _ in arrays]
+    ebs = [e for _, _, _, e in arrays]
+    nbytes = sum(4 * x.numel() for x in xs)
+    ctx = sz.Context(device)
+    outs = [torch.empty(sz.sz_max_compressed_bytes(x.numel()), dtype=torch.uint8, device="cuda") for x in xs]
+    ys = [torch.empty(max(x.numel(), 1), dtype=torch.float32, device="cuda") for x in xs]
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, k):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        for a, b in ev:
+            a.record(stream)
+            fn()
+            b.record(stream)
+        sz.sz_sync(ctx)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in ev) / k / 1e3
+
+    def batch():
+        return sz.sz_compress_batch(ctx, xs, ebs, sz.SZ_EB_REL, outs=outs)[1]
+
+    def plain():
+        for x, e, o in zip(xs, ebs, outs):
+            sz.sz_compress(ctx, x, e, sz.SZ_EB_REL, None, o)
+
+    for _ in range(3):
+        nb = batch()
+        sz.sz_sync(ctx)
+    sizes = [int(nb[i]) for i in range(len(xs))]
+    t_batch = timed(batch, steps)
+    plain()
+    sz.sz_sync(ctx)
+    t_plain = timed(plain, max(1, min(steps, 2)))
+
+    def decomp():
+        sz.sz_decompress_batch(ctx, outs, [o.numel() for o in outs], ys)
+
+    decomp()
+    sz.sz_sync(ctx)
+    t_dec = timed(decomp, steps)
+    res = {"workload": "768 float32 arrays (128 ranks x 6 fields), 2^U[14,24] elements each, per-array rel eb "
+                       "from {1e-3, 1e-4}; cosmology generator per rank sub-box",
+           "arrays": len(xs), "gbytes": nbytes / 1e9, "ratio": nbytes / sum(sizes),
+           "batched_compress_gbs": nbytes / t_batch / 1e9, "batched_compress_ms": 1e3 * t_batch,
+           "plain_compress_gbs": nbytes / t_plain / 1e9, "plain_compress_ms": 1e3 * t_plain,
+           "speedup": t_plain / t_batch,
+           "decompress_gbs": nbytes / t_dec / 1e9, "decompress_ms": 1e3 * t_dec}
+    ctx.close()
+    return res
+
+
+# ---------------------------------------------------------------------------
 # Served form: Poisson arrivals of compress / decompress requests
 # ---------------------------------------------------------------------------
 
@@ -361,6 +424,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-log2n", type=int, default=24)
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--serve-stress", type=float, default=10.0)
@@ -600,6 +664,11 @@ def main():
                "ms_per_step": 1e3 * te}
         del hx, hs, hy, dx, ds
 
+    # ---- batched form (rank 0): 768 uneven arrays, one graph vs 768 calls --------
+    batched = None
+    if rank == 0 and not args.no_batched:
+        batched = batched_bench(sz, local, args.steps)
+
     # ---- served form (rank 0): Poisson arrivals vs the same requests serially --
     served = None
     if rank == 0 and not args.no_serve:
@@ -625,7 +694,7 @@ def main():
             "compress_frac_hbm": comp_gbs / peak, "decompress_frac_hbm": decomp_gbs / peak,
             "ratio": ratio, "roofline": roofline, "kernels": kernels, "kernels_plain_path": kernels_plain,
             "gpu_launches": launches,
-            "plain_path": plain, "served": served,
+            "plain_path": plain, "batched": batched, "served": served,
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "wall_s_timed": t_wall,
         }
         print(json.dumps(line))

@@ -44,8 +44,8 @@ __device__ __forceinline__ bool shape_ok(uint32_t C, uint32_t G) {
     return (C == 2048 || C == 4096 || C == 8192 || C == 16384) && G * kSubPerChunk == C;
 }
 
-__global__ void __launch_bounds__(kSetupThreads) decode_setup_kernel(DecompressArgs a) {
-    __shared__ SetupSmem sm;
+// Validation and tables of one stream, by one block of kSetupThreads threads.
+__device__ __forceinline__ void decode_setup_body(const DecompressArgs& a, SetupSmem& sm) {
     const int tid = threadIdx.x;
     ArrayState* st = a.st;
     const uint8_t* in = a.in;
@@ -179,6 +179,11 @@ __global__ void __launch_bounds__(kSetupThreads) decode_setup_kernel(DecompressA
     }
 }
 
+__global__ void __launch_bounds__(kSetupThreads) decode_setup_kernel(DecompressArgs a) {
+    __shared__ SetupSmem sm;
+    decode_setup_body(a, sm);
+}
+
 // Bit reader over a chunk payload in shared or global memory.  Two 32-bit
 // words (hi, lo) hold the stream from word pos-2 on; the next codeword starts
 // b bits into hi.  peek() returns the 32 bits from there by one funnel shift;
@@ -291,182 +296,333 @@ __device__ __forceinline__ uint32_t decode_run(BitReader& br, const DecSmem& sm,
     return ssum;
 }
 
+// Per-stream decode parameters, read from the validated header and state.
+struct DecArray {
+    const uint64_t* cword;
+    const long long* anchor;
+    const uint64_t* cesc;
+    const uint16_t* sublen;
+    const uint8_t* escs;
+    const uint32_t* payload;
+    const uint16_t* by_len;
+    float* out;
+    uint64_t n, nc, E, pw;
+    uint32_t C, G, gshift, l2_lo, l2_n;
+    float D;
+    bool vec;
+};
+
+__device__ __forceinline__ void dec_array(const DecompressArgs& a, DecArray& d) {
+    const ArrayState* st = a.st;
+    const uint8_t* in = a.in;
+    d.n = st->n_out;
+    d.out = a.out;
+    d.vec = ((uintptr_t)a.out & 15u) == 0;
+    d.payload = reinterpret_cast<const uint32_t*>(in + st->off[S_PAYLOAD]);
+    if (st->raw) return;
+    d.C = rd32(in + H_C);
+    d.G = rd32(in + H_G);
+    d.gshift = 31 - __clz(d.G);
+    d.nc = rd64(in + H_NCHUNKS);
+    d.E = rd64(in + H_NESC);
+    d.pw = rd64(in + H_PWORDS);
+    d.D = __uint_as_float(rd32(in + H_D));
+    d.cword = reinterpret_cast<const uint64_t*>(in + st->off[S_CWORD]);
+    d.anchor = reinterpret_cast<const long long*>(in + st->off[S_ANCHOR]);
+    d.cesc = reinterpret_cast<const uint64_t*>(in + st->off[S_CESC]);
+    d.sublen = reinterpret_cast<const uint16_t*>(in + st->off[S_SUBLEN]);
+    d.escs = in + st->off[S_ESC];
+    d.by_len = a.by_len;
+    d.l2_lo = st->l2_lo;
+    d.l2_n = st->l2_n;
+}
+
+// Block-wide: the stream's first- and second-level tables and limits into
+// shared memory.
+__device__ __forceinline__ void load_dec_tables(const DecompressArgs& a, const DecArray& d, DecSmem& sm,
+                                                uint32_t* lut2) {
+    const int tid = threadIdx.x;
+    const ArrayState* st = a.st;
+    for (uint32_t i = tid; i < (1u << kLutBits) / 4; i += blockDim.x)
+        reinterpret_cast<uint4*>(sm.lut)[i] = __ldg(reinterpret_cast<const uint4*>(a.lut) + i);
+    for (uint32_t i = tid; i < d.l2_n; i += blockDim.x) lut2[i] = __ldg(a.lut + (1u << kLutBits) + i);
+    if (tid < kMaxLen + 2) {
+        sm.first[tid] = st->first[tid];
+        sm.base[tid] = st->base[tid];
+        sm.lim[tid] = st->lim[tid];
+    }
+}
+
+// One chunk by one team of 64 threads (thread k = sub-stream k): stage, decode,
+// escapes and prefix, reconstruct, store.  next: the chunk this team takes next
+// (L2 prefetch), or >= nc.  Returns false (and raises E_CORRUPT) on a bad chunk.
+__device__ __forceinline__ bool decode_chunk_team(const DecArray& d, DecSmem& sm, const uint32_t* lut2,
+                                                  uint32_t* xs, uint32_t* stage, uint32_t stage_words, int team,
+                                                  int k, uint64_t c, uint64_t next, uint32_t* err) {
+    const uint32_t C = d.C, G = d.G, gshift = d.gshift;
+    const uint64_t base = c * C;
+    const uint32_t cnt = (uint32_t)umin64(C, d.n - base);
+    const uint64_t wb = d.cword[c], we = d.cword[c + 1];
+    const uint64_t eb = d.cesc[c], ee = d.cesc[c + 1];
+    const bool hdr_bad = (wb > we || we > d.pw || eb > ee || ee > d.E || (wb & 3u));
+    const uint32_t e0 = k * G;
+    const uint32_t nsym = e0 < cnt ? umin32(G, cnt - e0) : 0u;
+    const uint32_t sl = d.sublen[c * kSubPerChunk + k];
+    uint32_t tot_bits;
+    const uint32_t start = team_exclusive_scan<uint32_t>(sl, sm.ws32[team], team, k, &tot_bits);
+    if (hdr_bad || (uint64_t)tot_bits > 32ull * (we - wb)) {
+        if (k == 0) raise_err(err, E_CORRUPT);
+        return false;
+    }
+    // ---- stage the chunk payload; prefetch the team's next chunk into L2 --------
+    const uint32_t cw_words = (uint32_t)(we - wb);
+    const bool staged = cw_words <= stage_words;
+    if (staged) {
+        // asynchronous 16-byte copies, all in flight at once
+        const uint4* g4 = reinterpret_cast<const uint4*>(d.payload + wb);
+        const uint32_t s_base = (uint32_t)__cvta_generic_to_shared(stage);
+        for (uint32_t w4 = k; w4 < cw_words / 4; w4 += kDecThreads)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s_base + 16u * w4),
+                         "l"(__cvta_generic_to_global(g4 + w4))
+                         : "memory");
+        asm volatile("cp.async.wait_all;" ::: "memory");
+    }
+    if (k == 0 && next < d.nc) {
+        const uint64_t nb = d.cword[next], ne = d.cword[next + 1];
+        if (nb < ne && ne <= d.pw && !(nb & 3u) && !(ne & 3u) && ne - nb < (1u << 24)) {
+            const uint32_t* p = d.payload + nb;
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(__cvta_generic_to_global(p)), "r"((uint32_t)(4 * (ne - nb)))
+                         : "memory");
+        }
+    }
+    team_sync(team);
+    // ---- phase 1: decode the sub-stream into symbols ----------------------------
+    // (separate calls for the staged and the global source, so that the staged
+    // reader's loads are shared-memory loads)
+    uint32_t nesc = 0, ssum, end_bit;
+    bool bad = false;
+    if (staged) {
+        BitReader br;
+        br.init(stage, start, cw_words);
+        ssum = nsym == G ? decode_run<true>(br, sm, lut2, d.l2_lo, d.l2_n, d.by_len, xs, e0, gshift, nsym, nesc, bad)
+                         : decode_run<false>(br, sm, lut2, d.l2_lo, d.l2_n, d.by_len, xs, e0, gshift, nsym, nesc, bad);
+        end_bit = br.bit_pos();
+    } else {
+        BitReader br;
+        br.init(d.payload + wb, start, cw_words);
+        ssum = decode_run<false>(br, sm, lut2, d.l2_lo, d.l2_n, d.by_len, xs, e0, gshift, nsym, nesc, bad);
+        end_bit = br.bit_pos();
+    }
+    bad = bad || end_bit - start != sl;
+    // ---- escapes and the team-wide prefix ----------------------------------------
+    uint32_t tot_esc;
+    const uint32_t eoff =
+        team_exclusive_scan<uint32_t>(nesc + (bad ? 0x10000u : 0u), sm.ws32b[team], team, k, &tot_esc);
+    if ((tot_esc >> 16) || eb + tot_esc != ee) {
+        if (k == 0) raise_err(err, E_CORRUPT);
+        return false;
+    }
+    // sum of deltas: escape symbols are 0, every other one is delta + radius
+    long long sum = (long long)ssum - (long long)kRadius * (long long)(nsym - nesc);
+    for (uint32_t t = 0; t < nesc; ++t)
+        sum += *reinterpret_cast<const long long*>(d.escs + (uint64_t)kEscBytes * (eb + eoff + t));
+    long long tot_sum;
+    const long long pre = team_exclusive_scan<long long>(sum, sm.ws64[team], team, k, &tot_sum);
+    // ---- phase 2: reconstruct in place -----------------------------------------
+    // every partial sum of a sub-stream without escapes stays within
+    // q0 +- G * 32767, so |q0| below this bound keeps all of them within 2^24
+    const long long q_fast = (1ll << 24) - (long long)G * (kRadius - 1);
+    const float D = d.D;
+    const long long q0 = d.anchor[c] + pre;
+    if (nesc == 0 && q0 >= -q_fast && q0 <= q_fast) {
+        // 32-bit: q stays within 2^24, one exact int -> float and one fmul each
+        int q = (int)q0;
+        for (uint32_t j4 = 0; j4 < nsym; j4 += 4) {
+            uint4* slot = reinterpret_cast<uint4*>(&xs[swz(e0 + j4, gshift)]);
+            uint4 s4 = *slot;
+            q += (int)s4.x - kRadius; const float v0 = __fmul_rn((float)q, D);
+            q += (int)s4.y - kRadius; const float v1 = __fmul_rn((float)q, D);
+            q += (int)s4.z - kRadius; const float v2 = __fmul_rn((float)q, D);
+            q += (int)s4.w - kRadius; const float v3 = __fmul_rn((float)q, D);
+            *slot = make_uint4(__float_as_uint(v0), __float_as_uint(v1), __float_as_uint(v2), __float_as_uint(v3));
+        }
+    } else {
+        long long q = q0;
+        uint64_t ecur = eb + eoff;
+        for (uint32_t j4 = 0; j4 < nsym; j4 += 4) {
+            uint4* slot = reinterpret_cast<uint4*>(&xs[swz(e0 + j4, gshift)]);
+            uint4 s4 = *slot;
+            uint32_t sy[4] = {s4.x, s4.y, s4.z, s4.w};
+            uint32_t ov[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                ov[t] = 0u;
+                if (j4 + t < nsym) {
+                    float v;
+                    if (sy[t] != 0u) {
+                        q += (long long)sy[t] - kRadius;
+                        v = recon_f(q, D);
+                    } else {
+                        const uint8_t* r = d.escs + (uint64_t)kEscBytes * ecur++;
+                        q += *reinterpret_cast<const long long*>(r);
+                        v = (rd32(r + 12) & 1u) ? __uint_as_float(rd32(r + 8)) : recon_f(q, D);
+                    }
+                    ov[t] = __float_as_uint(v);
+                }
+            }
+            *slot = make_uint4(ov[0], ov[1], ov[2], ov[3]);
+        }
+    }
+    team_sync(team);
+    // ---- phase 3: coalesced store ---------------------------------------------
+    float* dst = d.out + base;
+    if (d.vec && cnt == C) {
+        for (uint32_t e = 4 * k; e < C; e += 4 * kDecThreads)
+            *reinterpret_cast<uint4*>(dst + e) = *reinterpret_cast<const uint4*>(&xs[swz(e, gshift)]);
+    } else {
+        for (uint32_t e = 4 * k; e < cnt; e += 4 * kDecThreads) {
+            uint4 v = *reinterpret_cast<const uint4*>(&xs[swz(e, gshift)]);
+            uint32_t vv[4] = {v.x, v.y, v.z, v.w};
+            for (int j = 0; j < 4 && e + j < cnt; ++j) dst[e + j] = __uint_as_float(vv[j]);
+        }
+    }
+    team_sync(team);
+    return true;
+}
+
+// team region of a block decoding chunks of C elements: C value slots and the
+// payload stage
+__device__ __forceinline__ uint32_t* team_region(uint4* dyn, int teams, int team, uint32_t* stage_words,
+                                                 uint32_t C) {
+    const uint32_t region_words = (uint32_t)((kDecDynSmem - kLut2Bytes) / 4) / teams;
+    *stage_words = region_words - C;      // multiple of 4
+    return reinterpret_cast<uint32_t*>(dyn) + kLut2Max + (size_t)team * region_words;
+}
+
 __global__ void __launch_bounds__(kDecBlock, 1) decode_kernel(DecompressArgs a) {
     __shared__ DecSmem sm;
     extern __shared__ uint4 dyn_smem[];
     const ArrayState* st = a.st;
     const int tid = threadIdx.x;
     if (!st->dec_ok) return;
-    const uint8_t* in = a.in;
-    const uint64_t n = st->n_out;
-    if (n == 0) return;
+    DecArray d;
+    dec_array(a, d);
+    if (d.n == 0) return;
     if (st->raw) {
-        const uint32_t* src = reinterpret_cast<const uint32_t*>(in + st->off[S_PAYLOAD]);
+        const uint32_t* src = d.payload;
         uint32_t* dst = reinterpret_cast<uint32_t*>(a.out);
-        for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + tid; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + tid; i < d.n; i += (uint64_t)gridDim.x * blockDim.x)
             dst[i] = __ldg(src + i);
         return;
     }
-    const uint32_t C = rd32(in + H_C), G = rd32(in + H_G), gshift = 31 - __clz(G);
-    const uint64_t nc = rd64(in + H_NCHUNKS), E = rd64(in + H_NESC), pw = rd64(in + H_PWORDS);
-    const float D = __uint_as_float(rd32(in + H_D));
-    const uint64_t* cword = reinterpret_cast<const uint64_t*>(in + st->off[S_CWORD]);
-    const long long* anchor = reinterpret_cast<const long long*>(in + st->off[S_ANCHOR]);
-    const uint64_t* cesc = reinterpret_cast<const uint64_t*>(in + st->off[S_CESC]);
-    const uint16_t* sublen = reinterpret_cast<const uint16_t*>(in + st->off[S_SUBLEN]);
-    const uint8_t* escs = in + st->off[S_ESC];
-    const uint32_t* payload = reinterpret_cast<const uint32_t*>(in + st->off[S_PAYLOAD]);
-    const uint16_t* by_len = a.by_len;
-    const uint32_t l2_lo = st->l2_lo, l2_n = st->l2_n;
     uint32_t* lut2 = reinterpret_cast<uint32_t*>(dyn_smem);
-
-    for (uint32_t i = tid; i < (1u << kLutBits) / 4; i += kDecBlock)
-        reinterpret_cast<uint4*>(sm.lut)[i] = __ldg(reinterpret_cast<const uint4*>(a.lut) + i);
-    for (uint32_t i = tid; i < l2_n; i += kDecBlock) lut2[i] = __ldg(a.lut + (1u << kLutBits) + i);
-    if (tid < kMaxLen + 2) {
-        sm.first[tid] = st->first[tid];
-        sm.base[tid] = st->base[tid];
-        sm.lim[tid] = st->lim[tid];
-    }
+    load_dec_tables(a, d, sm, lut2);
     __syncthreads();
-
-    const int teams = teams_for(C);
+    const int teams = teams_for(d.C);
     const int team = tid / kDecThreads, k = tid % kDecThreads;
     if (team >= teams) return;
-    const uint32_t region_words = (uint32_t)((kDecDynSmem - kLut2Bytes) / 4) / teams;
-    uint32_t* xs = reinterpret_cast<uint32_t*>(dyn_smem) + kLut2Max + (size_t)team * region_words;
-    uint32_t* stage = xs + C;
-    const uint32_t stage_words = region_words - C;      // multiple of 4
-    const bool vec = ((uintptr_t)a.out & 15u) == 0;
+    uint32_t stage_words;
+    uint32_t* xs = team_region(dyn_smem, teams, team, &stage_words, d.C);
     const uint64_t stride = (uint64_t)gridDim.x * teams;
-    // every partial sum of a sub-stream without escapes stays within
-    // q0 +- G * 32767, so |q0| below this bound keeps all of them within 2^24
-    const long long q_fast = (1ll << 24) - (long long)G * (kRadius - 1);
+    for (uint64_t c = (uint64_t)blockIdx.x * teams + team; c < d.nc; c += stride)
+        if (!decode_chunk_team(d, sm, lut2, xs, xs + d.C, stage_words, team, k, c, c + stride, a.err)) return;
+}
 
-    for (uint64_t c = (uint64_t)blockIdx.x * teams + team; c < nc; c += stride) {
-        const uint64_t base = c * C;
-        const uint32_t cnt = (uint32_t)umin64(C, n - base);
-        const uint64_t wb = cword[c], we = cword[c + 1];
-        const uint64_t eb = cesc[c], ee = cesc[c + 1];
-        const bool hdr_bad = (wb > we || we > pw || eb > ee || ee > E || (wb & 3u));
-        const uint32_t e0 = k * G;
-        const uint32_t nsym = e0 < cnt ? umin32(G, cnt - e0) : 0u;
-        const uint32_t sl = sublen[c * kSubPerChunk + k];
-        uint32_t tot_bits;
-        const uint32_t start = team_exclusive_scan<uint32_t>(sl, sm.ws32[team], team, k, &tot_bits);
-        if (hdr_bad || (uint64_t)tot_bits > 32ull * (we - wb)) {
-            if (k == 0) raise_err(a.err, E_CORRUPT);
-            return;
-        }
-        // ---- stage the chunk payload; prefetch the next chunk into L2 ---------------
-        const uint32_t cw_words = (uint32_t)(we - wb);
-        const bool staged = cw_words <= stage_words;
-        if (staged) {
-            // asynchronous 16-byte copies, all in flight at once
-            const uint4* g4 = reinterpret_cast<const uint4*>(payload + wb);
-            const uint32_t s_base = (uint32_t)__cvta_generic_to_shared(stage);
-            for (uint32_t w4 = k; w4 < cw_words / 4; w4 += kDecThreads)
-                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s_base + 16u * w4),
-                             "l"(__cvta_generic_to_global(g4 + w4))
-                             : "memory");
-            asm volatile("cp.async.wait_all;" ::: "memory");
-        }
-        if (k == 0 && c + stride < nc) {
-            const uint64_t nb = cword[c + stride], ne = cword[c + stride + 1];
-            if (nb < ne && ne <= pw && !(nb & 3u) && !(ne & 3u) && ne - nb < (1u << 24)) {
-                const uint32_t* p = payload + nb;
-                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(__cvta_generic_to_global(p)), "r"((uint32_t)(4 * (ne - nb)))
-                             : "memory");
+// ---- batched decompression ---------------------------------------------------
+// setup: one block per stream; also writes the stream's decode units (chunks,
+// or 4096-word pieces of a raw stream; 0 for a rejected stream)
+constexpr uint32_t kRawUnit = 4096;
+
+__global__ void __launch_bounds__(kSetupThreads) decode_setup_multi_kernel(const DecompressArgs* args,
+                                                                           uint32_t* units) {
+    __shared__ SetupSmem sm;
+    __shared__ DecompressArgs sa;
+    if (threadIdx.x == 0) sa = args[blockIdx.x];
+    __syncthreads();
+    decode_setup_body(sa, sm);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const ArrayState* st = sa.st;
+        uint64_t u = 0;
+        if (st->dec_ok && st->n_out) u = st->raw ? (st->n_out + kRawUnit - 1) / kRawUnit : rd64(sa.in + H_NCHUNKS);
+        units[blockIdx.x] = (uint32_t)umin64(u, 0xffffffffu);
+    }
+}
+
+// exclusive prefix of the units over the k streams (one block)
+__global__ void __launch_bounds__(1024) decode_units_scan_kernel(const uint32_t* units, uint64_t* uoff, uint32_t k) {
+    __shared__ unsigned long long ws[33];
+    __shared__ unsigned long long carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (uint32_t b = 0; b < k; b += 1024) {
+        const uint32_t i = b + threadIdx.x;
+        const unsigned long long v = i < k ? units[i] : 0ull;
+        unsigned long long tot;
+        const unsigned long long ex = block_exclusive_scan<1024>(v, ws, &tot);
+        if (i < k) uoff[i] = carry + ex;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) uoff[k] = carry;
+}
+
+// last index i < k with uoff[i] <= x (uoff non-decreasing)
+__device__ __forceinline__ uint32_t find_stream(const uint64_t* uoff, uint32_t k, uint64_t x) {
+    uint32_t lo = 0, hi = k;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (uoff[mid] <= x) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// All streams' units in one launch: block b takes the contiguous units
+// [F b / B, F (b+1) / B) of the flattened list and walks the streams they
+// belong to, loading each stream's tables once; its teams share out the
+// stream's chunks.  A bad chunk stops its team on that stream only.
+__global__ void __launch_bounds__(kDecBlock, 1) decode_multi_kernel(const DecompressArgs* args, const uint64_t* uoff,
+                                                                    uint32_t k) {
+    __shared__ DecSmem sm;
+    __shared__ DecompressArgs sa;
+    extern __shared__ uint4 dyn_smem[];
+    const int tid = threadIdx.x;
+    const uint64_t F = uoff[k];
+    const uint64_t lo = F * blockIdx.x / gridDim.x, hi = F * (blockIdx.x + 1) / gridDim.x;
+    if (lo >= hi) return;
+    uint32_t* lut2 = reinterpret_cast<uint32_t*>(dyn_smem);
+    const int team = tid / kDecThreads, kk = tid % kDecThreads;
+    uint64_t pos = lo;
+    for (uint32_t i = find_stream(uoff, k, lo); pos < hi && i < k; ++i) {
+        const uint64_t u0 = uoff[i], u1 = uoff[i + 1];
+        if (u1 <= pos) continue;
+        const uint64_t s0 = pos - u0, s1 = umin64(hi, u1) - u0;     // this block's units of stream i
+        pos = u0 + s1;
+        __syncthreads();          // the previous stream's teams are done with the tables
+        if (tid == 0) sa = args[i];
+        __syncthreads();
+        DecArray d;
+        dec_array(sa, d);
+        if (sa.st->raw) {
+            // 4096-word pieces, one per team
+            uint32_t* dst = reinterpret_cast<uint32_t*>(sa.out);
+            for (uint64_t u = s0 + team; u < s1; u += kMaxTeams) {
+                const uint64_t e1 = umin64(d.n, (u + 1) * kRawUnit);
+                for (uint64_t e = u * kRawUnit + kk; e < e1; e += kDecThreads) dst[e] = __ldg(d.payload + e);
             }
+            continue;
         }
-        team_sync(team);
-        // ---- phase 1: decode the sub-stream into symbols ----------------------------
-        // (separate calls for the staged and the global source, so that the
-        // staged reader's loads are shared-memory loads)
-        uint32_t nesc = 0, ssum, end_bit;
-        bool bad = false;
-        if (staged) {
-            BitReader br;
-            br.init(stage, start, cw_words);
-            ssum = nsym == G ? decode_run<true>(br, sm, lut2, l2_lo, l2_n, by_len, xs, e0, gshift, nsym, nesc, bad)
-                             : decode_run<false>(br, sm, lut2, l2_lo, l2_n, by_len, xs, e0, gshift, nsym, nesc, bad);
-            end_bit = br.bit_pos();
-        } else {
-            BitReader br;
-            br.init(payload + wb, start, cw_words);
-            ssum = decode_run<false>(br, sm, lut2, l2_lo, l2_n, by_len, xs, e0, gshift, nsym, nesc, bad);
-            end_bit = br.bit_pos();
+        load_dec_tables(sa, d, sm, lut2);
+        __syncthreads();
+        const int teams = teams_for(d.C);
+        if (team >= teams) continue;
+        uint32_t stage_words;
+        uint32_t* xs = team_region(dyn_smem, teams, team, &stage_words, d.C);
+        for (uint64_t c = s0 + team; c < s1; c += teams) {
+            const uint64_t nx = c + teams < s1 ? c + teams : d.nc;
+            if (!decode_chunk_team(d, sm, lut2, xs, xs + d.C, stage_words, team, kk, c, nx, sa.err)) break;
         }
-        bad = bad || end_bit - start != sl;
-        // ---- escapes and the team-wide prefix ----------------------------------------
-        uint32_t tot_esc;
-        const uint32_t eoff = team_exclusive_scan<uint32_t>(nesc + (bad ? 0x10000u : 0u), sm.ws32b[team], team, k,
-                                                             &tot_esc);
-        if ((tot_esc >> 16) || eb + tot_esc != ee) {
-            if (k == 0) raise_err(a.err, E_CORRUPT);
-            return;
-        }
-        // sum of deltas: escape symbols are 0, every other one is delta + radius
-        long long sum = (long long)ssum - (long long)kRadius * (long long)(nsym - nesc);
-        for (uint32_t t = 0; t < nesc; ++t)
-            sum += *reinterpret_cast<const long long*>(escs + (uint64_t)kEscBytes * (eb + eoff + t));
-        long long tot_sum;
-        const long long pre = team_exclusive_scan<long long>(sum, sm.ws64[team], team, k, &tot_sum);
-        // ---- phase 2: reconstruct in place -----------------------------------------
-        const long long q0 = anchor[c] + pre;
-        if (nesc == 0 && q0 >= -q_fast && q0 <= q_fast) {
-            // 32-bit: q stays within 2^24, one exact int -> float and one fmul each
-            int q = (int)q0;
-            for (uint32_t j4 = 0; j4 < nsym; j4 += 4) {
-                uint4* slot = reinterpret_cast<uint4*>(&xs[swz(e0 + j4, gshift)]);
-                uint4 s4 = *slot;
-                q += (int)s4.x - kRadius; const float v0 = __fmul_rn((float)q, D);
-                q += (int)s4.y - kRadius; const float v1 = __fmul_rn((float)q, D);
-                q += (int)s4.z - kRadius; const float v2 = __fmul_rn((float)q, D);
-                q += (int)s4.w - kRadius; const float v3 = __fmul_rn((float)q, D);
-                *slot = make_uint4(__float_as_uint(v0), __float_as_uint(v1), __float_as_uint(v2), __float_as_uint(v3));
-            }
-        } else {
-            long long q = q0;
-            uint64_t ecur = eb + eoff;
-            for (uint32_t j4 = 0; j4 < nsym; j4 += 4) {
-                uint4* slot = reinterpret_cast<uint4*>(&xs[swz(e0 + j4, gshift)]);
-                uint4 s4 = *slot;
-                uint32_t sy[4] = {s4.x, s4.y, s4.z, s4.w};
-                uint32_t ov[4];
-#pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    ov[t] = 0u;
-                    if (j4 + t < nsym) {
-                        float v;
-                        if (sy[t] != 0u) {
-                            q += (long long)sy[t] - kRadius;
-                            v = recon_f(q, D);
-                        } else {
-                            const uint8_t* r = escs + (uint64_t)kEscBytes * ecur++;
-                            q += *reinterpret_cast<const long long*>(r);
-                            v = (rd32(r + 12) & 1u) ? __uint_as_float(rd32(r + 8)) : recon_f(q, D);
-                        }
-                        ov[t] = __float_as_uint(v);
-                    }
-                }
-                *slot = make_uint4(ov[0], ov[1], ov[2], ov[3]);
-            }
-        }
-        team_sync(team);
-        // ---- phase 3: coalesced store ---------------------------------------------
-        float* dst = a.out + base;
-        if (vec && cnt == C) {
-            for (uint32_t e = 4 * k; e < C; e += 4 * kDecThreads)
-                *reinterpret_cast<uint4*>(dst + e) = *reinterpret_cast<const uint4*>(&xs[swz(e, gshift)]);
-        } else {
-            for (uint32_t e = 4 * k; e < cnt; e += 4 * kDecThreads) {
-                uint4 v = *reinterpret_cast<const uint4*>(&xs[swz(e, gshift)]);
-                uint32_t vv[4] = {v.x, v.y, v.z, v.w};
-                for (int j = 0; j < 4 && e + j < cnt; ++j) dst[e + j] = __uint_as_float(vv[j]);
-            }
-        }
-        team_sync(team);
     }
 }
 
@@ -474,20 +630,32 @@ void launch_decode_setup(const DecompressArgs* a, int k, void* stream) {
     for (int i = 0; i < k; ++i) decode_setup_kernel<<<1, kSetupThreads, 0, (cudaStream_t)stream>>>(a[i]);
 }
 
-void launch_decode(const DecompressArgs* a, int k, void* stream) {
+static int decode_grid() {
     static int sms = 0;
     if (!sms) {
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (sms <= 0) sms = 148;
-    }
-    static bool configured = false;
-    if (!configured) {
         cudaFuncSetAttribute(decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDecDynSmem);
-        configured = true;
+        cudaFuncSetAttribute(decode_multi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDecDynSmem);
     }
+    return sms;
+}
+
+void launch_decode(const DecompressArgs* a, int k, void* stream) {
+    const int sms = decode_grid();
     for (int i = 0; i < k; ++i) decode_kernel<<<sms, kDecBlock, kDecDynSmem, (cudaStream_t)stream>>>(a[i]);
+}
+
+void launch_decode_multi(const DecompressArgs* d_args, uint32_t k, uint32_t* d_units, uint64_t* d_uoff,
+                         void* stream) {
+    if (k == 0) return;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int sms = decode_grid();
+    decode_setup_multi_kernel<<<k, kSetupThreads, 0, s>>>(d_args, d_units);
+    decode_units_scan_kernel<<<1, 1024, 0, s>>>(d_units, d_uoff, k);
+    decode_multi_kernel<<<sms, kDecBlock, kDecDynSmem, s>>>(d_args, d_uoff, k);
 }
 
 }  // namespace szg

@@ -10,8 +10,9 @@
 // array's size.  Each stream is byte-identical to sz_compress on the same
 // array.  Arrays whose chunk size is above 4096 (set explicitly through
 // params) go through the per-array path instead.
-// Decompression: the setup and decode kernels per stream, enqueued back to
-// back (each decode launch already spans the whole GPU).
+// Decompression (k > 1): one setup launch (a block per stream), a scan of the
+// streams' decode units, and one decode launch whose blocks take contiguous
+// ranges of all streams' chunks (k_decode.cu).
 #include <algorithm>
 #include <string.h>
 #include <vector>
@@ -260,12 +261,83 @@ sz_status batch_compress(sz_ctx* ctx, int k, const float* const* d_in, const siz
 sz_status batch_decompress(sz_ctx* ctx, int k, const void* const* d_in, const size_t* in_bytes, float* const* d_out,
                            const size_t* n_cap, size_t* n_out, cudaStream_t s) {
     cudaSetDevice(ctx->device);
-    for (int i = 0; i < k; ++i) {
-        if (!d_in[i] || ((uintptr_t)d_in[i] & 15u) || (n_cap[i] && !d_out[i])) return SZ_ERR_ARG;
-        DecompressArgs d = make_decompress_args(ctx, 0, d_in[i], in_bytes[i], d_out[i], n_cap[i]);
-        sz_status st = enqueue_decompress(ctx, d, n_out ? &n_out[i] : nullptr, s);
-        if (st != SZ_OK) return st;
+    for (int i = 0; i < k; ++i)
+        if (!d_in[i] || ((uintptr_t)d_in[i] & 15u) || (n_cap[i] && !d_out[i]) || ((uintptr_t)d_out[i] & 3u))
+            return SZ_ERR_ARG;
+    if (k == 0) return SZ_OK;
+    if (k == 1) {
+        DecompressArgs d = make_decompress_args(ctx, 0, d_in[0], in_bytes[0], d_out[0], n_cap[0]);
+        return enqueue_decompress(ctx, d, n_out ? &n_out[0] : nullptr, s);
     }
+    // ---- pool: args | units | unit offsets | per-stream state, tables, scratch ----------
+    size_t bytes = 0;
+    auto take = [&](size_t b) { size_t o = bytes; bytes += align256(b); return o; };
+    const size_t o_args = take(sizeof(DecompressArgs) * k);
+    const size_t plan_bytes = bytes;
+    const size_t o_units = take(sizeof(uint32_t) * k);
+    const size_t o_uoff = take(sizeof(uint64_t) * (k + 1));
+    const size_t o_state = take(sizeof(ArrayState) * k);
+    const size_t per = align256(sizeof(uint32_t) * kLutWords) + align256(sizeof(uint16_t) * 65536) +
+                       align256(sizeof(uint32_t) * 4 * 65536);
+    const size_t o_tab = take(per * k);
+    if (bytes > ctx->dbatch_bytes) {
+        if (cudaStreamSynchronize(s) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) return SZ_ERR_CUDA;
+        if (ctx->dbatch_pool) cudaFree(ctx->dbatch_pool);
+        ctx->dbatch_pool = nullptr;
+        ctx->dbatch_bytes = 0;
+        void* p = nullptr;
+        if (cudaMalloc(&p, bytes) != cudaSuccess) { cudaGetLastError(); return SZ_ERR_NOMEM; }
+        ctx->dbatch_pool = (uint8_t*)p;
+        ctx->dbatch_bytes = bytes;
+    }
+    // the previous call's plan copy must be done before the staging is reused
+    if (ctx->dbatch_done && cudaEventSynchronize(ctx->dbatch_done) != cudaSuccess) { cudaGetLastError(); return SZ_ERR_CUDA; }
+    if (!ctx->dbatch_done && cudaEventCreateWithFlags(&ctx->dbatch_done, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return SZ_ERR_CUDA;
+    }
+    if (plan_bytes > ctx->dbatch_host_bytes) {
+        if (ctx->dbatch_host) cudaFreeHost(ctx->dbatch_host);
+        ctx->dbatch_host = nullptr;
+        ctx->dbatch_host_bytes = 0;
+        void* h = nullptr;
+        if (cudaMallocHost(&h, plan_bytes) != cudaSuccess) { cudaGetLastError(); return SZ_ERR_NOMEM; }
+        ctx->dbatch_host = (uint8_t*)h;
+        ctx->dbatch_host_bytes = plan_bytes;
+    }
+    uint8_t* base = ctx->dbatch_pool;
+    DecompressArgs* h_args = reinterpret_cast<DecompressArgs*>(ctx->dbatch_host + o_args);
+    for (int i = 0; i < k; ++i) {
+        DecompressArgs& d = h_args[i];
+        memset(&d, 0, sizeof(d));
+        uint8_t* t = base + o_tab + per * (size_t)i;
+        d.in = (const uint8_t*)d_in[i];
+        d.in_bytes = in_bytes[i];
+        d.out = d_out[i];
+        d.n_cap = n_cap[i];
+        d.st = reinterpret_cast<ArrayState*>(base + o_state) + i;
+        d.lut = reinterpret_cast<uint32_t*>(t);
+        d.by_len = reinterpret_cast<uint16_t*>(t + align256(sizeof(uint32_t) * kLutWords));
+        d.cb_scratch = reinterpret_cast<uint32_t*>(t + align256(sizeof(uint32_t) * kLutWords) +
+                                                   align256(sizeof(uint16_t) * 65536));
+        d.err = ctx->d_err;
+    }
+    if (cudaMemcpyAsync(base + o_args, h_args, sizeof(DecompressArgs) * k, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaEventRecord(ctx->dbatch_done, s) != cudaSuccess) {
+        cudaGetLastError();
+        return SZ_ERR_CUDA;
+    }
+    {
+        ProfScope pr(ctx, SZ_PHASE_DECODE, s);
+        launch_decode_multi(reinterpret_cast<const DecompressArgs*>(base + o_args), (uint32_t)k,
+                            reinterpret_cast<uint32_t*>(base + o_units), reinterpret_cast<uint64_t*>(base + o_uoff), s);
+    }
+    if (cudaPeekAtLastError() != cudaSuccess) { cudaGetLastError(); return SZ_ERR_CUDA; }
+    if (n_out)
+        for (int i = 0; i < k; ++i) {
+            sz_status st = queue_result(ctx, &h_args[i].st->n_out, &n_out[i], s);
+            if (st != SZ_OK) return st;
+        }
     return SZ_OK;
 }
 

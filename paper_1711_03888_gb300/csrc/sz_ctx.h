@@ -48,6 +48,12 @@ struct sz_ctx {
     cudaEvent_t bg_done = nullptr;
     uint8_t* batch_host = nullptr;      // pinned plan staging
     size_t batch_host_bytes = 0;
+    // batched decompression: per-stream state and tables, and the plan staging
+    uint8_t* dbatch_pool = nullptr;
+    size_t dbatch_bytes = 0;
+    uint8_t* dbatch_host = nullptr;
+    size_t dbatch_host_bytes = 0;
+    cudaEvent_t dbatch_done = nullptr;
     // serving loop
     sz_serve_state* serve = nullptr;
     // tracing: event pairs around launches

@@ -123,6 +123,11 @@ void launch_codebook(const CompressArgs* a, int k, void* stream);
 void launch_encode(const CompressArgs* a, int k, void* stream);
 void launch_decode_setup(const DecompressArgs* a, int k, void* stream);
 void launch_decode(const DecompressArgs* a, int k, void* stream);
+// Batched decompression: setup of all k streams (one block each), the prefix
+// of their decode units, then one launch over every unit.  d_args: k device
+// entries; d_units: k words; d_uoff: k + 1 words of scratch.
+void launch_decode_multi(const DecompressArgs* d_args, uint32_t k, uint32_t* d_units, uint64_t* d_uoff,
+                         void* stream);
 
 // Batched form: one persistent launch over every array's work items.
 constexpr uint32_t kRangeTile = 1u << 16;   // elements per range item

@@ -28,6 +28,14 @@ void sz_ctx::free_extra() {
     batch_host = nullptr;
     batch_host_bytes = 0;
     bg_key = 0;
+    if (dbatch_pool) cudaFree(dbatch_pool);
+    if (dbatch_host) cudaFreeHost(dbatch_host);
+    if (dbatch_done) cudaEventDestroy(dbatch_done);
+    dbatch_pool = nullptr;
+    dbatch_bytes = 0;
+    dbatch_host = nullptr;
+    dbatch_host_bytes = 0;
+    dbatch_done = nullptr;
 }
 
 namespace {

@@ -89,6 +89,14 @@ def test_batch_full_config_many_ranks(sz, ctx, oracle):
     for i in rng.choice(768, 6, replace=False):
         h = oracle.parse_header(got[i])
         assert got[i] == oracle.compress(xs[i].cpu().numpy(), ebs[i], 1, h["chunk"], h["sub"])
+    # batched decompression of all 768 streams equals the per-stream decoder
+    bufs = [torch.frombuffer(bytearray(g), dtype=torch.uint8).cuda() for g in got]
+    ys = [torch.empty(max(x.numel(), 1), dtype=torch.float32, device="cuda") for x in xs]
+    no = sz.sz_decompress_batch(ctx, bufs, [len(g) for g in got], ys)
+    assert sz.sz_sync(ctx) == sz.SZ_OK
+    for i, x in enumerate(xs):
+        assert no[i] == x.numel()
+        assert ys[i][: x.numel()].cpu().numpy().tobytes() == _plain_decode(sz, ctx, bufs[i], x.numel())
 
 
 def _plain_p(sz, ctx, x, eb, kind, chunk):
@@ -123,3 +131,58 @@ def test_batch_large_arrays_per_phase_path(sz, ctx, chunk):
     sz.sz_sync(ctx)
     for i, (x, e) in enumerate(zip(xs, ebs)):
         assert outs[i][: nb[i]].cpu().numpy().tobytes() == _plain_p(sz, ctx, x, e, sz.SZ_EB_REL, chunk)
+
+
+def _plain_decode(sz, ctx, buf, n):
+    y = torch.empty(max(n, 1), dtype=torch.float32, device="cuda")
+    no = sz.sz_decompress(ctx, buf, buf.numel(), y, n)
+    sz.sz_sync(ctx)
+    return y[: no.value].cpu().numpy().tobytes()
+
+
+def test_batch_decompress_mixed_streams(sz, ctx, oracle):
+    """One batched decompression over streams of every chunk size, raw, empty,
+    NaN-laden and escape-heavy streams equals the per-stream decoder, and a
+    corrupt stream among them fails alone (its neighbours still decode)."""
+    snap = synth.cosmology(300000, 32, 5, device="cuda")
+    xs, chunks = [], []
+    for i, C in enumerate([2048, 4096, 8192, 16384, 0, 0]):
+        xs.append(snap[["xx", "yy", "zz", "vx", "vy", "vz"][i]][: 250000 - 7 * i].contiguous())
+        chunks.append(C)
+    xs.append(torch.full((70001,), 2.5, dtype=torch.float32, device="cuda"))        # raw
+    xs.append(torch.empty(0, dtype=torch.float32, device="cuda"))                   # empty
+    w = synth.uniform_f32(40000, 7, -1e30, 1e30).numpy().copy()
+    w[::97] = np.nan
+    xs.append(torch.from_numpy(w).cuda())                                             # NaN / huge range
+    s = synth.random_walk_f32(60000, 8, 1e-3).numpy().copy()
+    s[::301] = 1e6
+    xs.append(torch.from_numpy(s).cuda())                                             # escapes
+    chunks += [0, 0, 0, 0]
+    streams = []
+    for x, C in zip(xs, chunks):
+        out, nb = sz.sz_compress(ctx, x, 1e-4, sz.SZ_EB_REL, sz._params(C))
+        sz.sz_sync(ctx)
+        streams.append(out[: nb.value].clone())
+    expect = [_plain_decode(sz, ctx, st, x.numel()) for st, x in zip(streams, xs)]
+    ys = [torch.empty(max(x.numel(), 1), dtype=torch.float32, device="cuda") for x in xs]
+    no = sz.sz_decompress_batch(ctx, streams, [st.numel() for st in streams], ys)
+    assert sz.sz_sync(ctx) == sz.SZ_OK
+    for i, x in enumerate(xs):
+        assert no[i] == x.numel()
+        assert ys[i][: x.numel()].cpu().numpy().tobytes() == expect[i], i
+    # sample against the oracle
+    for i in (0, 3, 6, 9):
+        yr = oracle.decompress(streams[i].cpu().numpy().tobytes())
+        assert ys[i][: xs[i].numel()].cpu().numpy().tobytes() == yr.tobytes()
+    # a corrupt stream in the middle
+    bad = streams[2].clone()
+    bad[0] ^= 1
+    s2 = streams[:2] + [bad] + streams[3:]
+    ys2 = [torch.zeros_like(y) for y in ys]
+    no2 = sz.sz_decompress_batch(ctx, s2, [st.numel() for st in s2], ys2)
+    assert sz.sz_sync(ctx, check=False) == sz.SZ_ERR_CORRUPT
+    for i, x in enumerate(xs):
+        if i == 2:
+            continue
+        assert no2[i] == x.numel()
+        assert ys2[i][: x.numel()].cpu().numpy().tobytes() == expect[i], i
