@@ -534,7 +534,7 @@ __global__ void __launch_bounds__(kDecBlock, 1) decode_kernel(DecompressArgs a) 
 constexpr uint32_t kRawUnit = 4096;
 
 __global__ void __launch_bounds__(kSetupThreads) decode_setup_multi_kernel(const DecompressArgs* args,
-                                                                           uint32_t* units) {
+                                                                           uint32_t* units, uint32_t* ctr) {
     __shared__ SetupSmem sm;
     __shared__ DecompressArgs sa;
     if (threadIdx.x == 0) sa = args[blockIdx.x];
@@ -546,6 +546,7 @@ __global__ void __launch_bounds__(kSetupThreads) decode_setup_multi_kernel(const
         uint64_t u = 0;
         if (st->dec_ok && st->n_out) u = st->raw ? (st->n_out + kRawUnit - 1) / kRawUnit : rd64(sa.in + H_NCHUNKS);
         units[blockIdx.x] = (uint32_t)umin64(u, 0xffffffffu);
+        ctr[blockIdx.x] = 0u;
     }
 }
 
@@ -578,50 +579,63 @@ __device__ __forceinline__ uint32_t find_stream(const uint64_t* uoff, uint32_t k
     return lo;
 }
 
-// All streams' units in one launch: block b takes the contiguous units
-// [F b / B, F (b+1) / B) of the flattened list and walks the streams they
-// belong to, loading each stream's tables once; its teams share out the
-// stream's chunks.  A bad chunk stops its team on that stream only.
+// All streams' units in one launch, shared out dynamically: every stream has
+// a unit counter (zeroed by the setup launch) from which teams take one chunk
+// (or one raw piece) at a time.  Block b starts at the stream holding unit
+// F b / B of the flattened list -- so blocks start spread in proportion to
+// the work -- and sweeps the streams cyclically from there, visiting each
+// once: it loads a stream's tables, its teams drain the stream's counter, and
+// the block moves on.  Streams with fast and slow chunks thus end together.
+// A bad chunk stops its team on that stream only.
 __global__ void __launch_bounds__(kDecBlock, 1) decode_multi_kernel(const DecompressArgs* args, const uint64_t* uoff,
-                                                                    uint32_t k) {
+                                                                    uint32_t* ctr, uint32_t k) {
     __shared__ DecSmem sm;
     __shared__ DecompressArgs sa;
+    __shared__ uint32_t s_go;
+    __shared__ uint32_t s_unit[kMaxTeams];
     extern __shared__ uint4 dyn_smem[];
     const int tid = threadIdx.x;
     const uint64_t F = uoff[k];
-    const uint64_t lo = F * blockIdx.x / gridDim.x, hi = F * (blockIdx.x + 1) / gridDim.x;
-    if (lo >= hi) return;
+    if (F == 0) return;
     uint32_t* lut2 = reinterpret_cast<uint32_t*>(dyn_smem);
     const int team = tid / kDecThreads, kk = tid % kDecThreads;
-    uint64_t pos = lo;
-    for (uint32_t i = find_stream(uoff, k, lo); pos < hi && i < k; ++i) {
-        const uint64_t u0 = uoff[i], u1 = uoff[i + 1];
-        if (u1 <= pos) continue;
-        const uint64_t s0 = pos - u0, s1 = umin64(hi, u1) - u0;     // this block's units of stream i
-        pos = u0 + s1;
+    const uint64_t ahead = (uint64_t)gridDim.x * kMaxTeams;     // units in flight across the GPU
+    uint32_t i = find_stream(uoff, k, F * blockIdx.x / gridDim.x);
+    for (uint32_t v = 0; v < k; ++v, i = (i + 1 == k) ? 0 : i + 1) {
+        const uint32_t nu = (uint32_t)(uoff[i + 1] - uoff[i]);
+        if (nu == 0) continue;
         __syncthreads();          // the previous stream's teams are done with the tables
-        if (tid == 0) sa = args[i];
+        if (tid == 0) {
+            s_go = *reinterpret_cast<volatile const uint32_t*>(ctr + i) < nu;
+            if (s_go) sa = args[i];
+        }
         __syncthreads();
+        if (!s_go) continue;
         DecArray d;
         dec_array(sa, d);
-        if (sa.st->raw) {
-            // 4096-word pieces, one per team
-            uint32_t* dst = reinterpret_cast<uint32_t*>(sa.out);
-            for (uint64_t u = s0 + team; u < s1; u += kMaxTeams) {
-                const uint64_t e1 = umin64(d.n, (u + 1) * kRawUnit);
-                for (uint64_t e = u * kRawUnit + kk; e < e1; e += kDecThreads) dst[e] = __ldg(d.payload + e);
-            }
-            continue;
+        const bool raw = sa.st->raw != 0;
+        if (!raw) {
+            load_dec_tables(sa, d, sm, lut2);
+            __syncthreads();
         }
-        load_dec_tables(sa, d, sm, lut2);
-        __syncthreads();
-        const int teams = teams_for(d.C);
+        const int teams = raw ? kMaxTeams : teams_for(d.C);
         if (team >= teams) continue;
-        uint32_t stage_words;
-        uint32_t* xs = team_region(dyn_smem, teams, team, &stage_words, d.C);
-        for (uint64_t c = s0 + team; c < s1; c += teams) {
-            const uint64_t nx = c + teams < s1 ? c + teams : d.nc;
-            if (!decode_chunk_team(d, sm, lut2, xs, xs + d.C, stage_words, team, kk, c, nx, sa.err)) break;
+        uint32_t stage_words = 0;
+        uint32_t* xs = raw ? nullptr : team_region(dyn_smem, teams, team, &stage_words, d.C);
+        for (;;) {
+            if (kk == 0) s_unit[team] = atomicAdd(ctr + i, 1u);
+            team_sync(team);
+            const uint32_t u = s_unit[team];
+            team_sync(team);
+            if (u >= nu) break;
+            if (raw) {
+                // a 4096-word piece
+                uint32_t* dst = reinterpret_cast<uint32_t*>(sa.out);
+                const uint64_t e1 = umin64(d.n, ((uint64_t)u + 1) * kRawUnit);
+                for (uint64_t e = (uint64_t)u * kRawUnit + kk; e < e1; e += kDecThreads) dst[e] = __ldg(d.payload + e);
+            } else if (!decode_chunk_team(d, sm, lut2, xs, xs + d.C, stage_words, team, kk, u, u + ahead, sa.err)) {
+                break;
+            }
         }
     }
 }
@@ -645,17 +659,27 @@ static int decode_grid() {
 
 void launch_decode(const DecompressArgs* a, int k, void* stream) {
     const int sms = decode_grid();
-    for (int i = 0; i < k; ++i) decode_kernel<<<sms, kDecBlock, kDecDynSmem, (cudaStream_t)stream>>>(a[i]);
+    for (int i = 0; i < k; ++i) {
+        const int div = a[i].grid_div > 1 ? (int)a[i].grid_div : 1;
+        const int grid = sms / div > 0 ? sms / div : 1;
+        decode_kernel<<<grid, kDecBlock, kDecDynSmem, (cudaStream_t)stream>>>(a[i]);
+    }
 }
 
-void launch_decode_multi(const DecompressArgs* d_args, uint32_t k, uint32_t* d_units, uint64_t* d_uoff,
-                         void* stream) {
+void launch_decode_multi_setup(const DecompressArgs* d_args, uint32_t k, uint32_t* d_units, uint64_t* d_uoff,
+                               void* stream) {
     if (k == 0) return;
     cudaStream_t s = (cudaStream_t)stream;
-    const int sms = decode_grid();
-    decode_setup_multi_kernel<<<k, kSetupThreads, 0, s>>>(d_args, d_units);
+    // the units words double as the per-stream unit counters after the scan
+    decode_setup_multi_kernel<<<k, kSetupThreads, 0, s>>>(d_args, d_units, d_units + k);
     decode_units_scan_kernel<<<1, 1024, 0, s>>>(d_units, d_uoff, k);
-    decode_multi_kernel<<<sms, kDecBlock, kDecDynSmem, s>>>(d_args, d_uoff, k);
+}
+
+void launch_decode_multi(const DecompressArgs* d_args, uint32_t k, uint32_t* d_units, const uint64_t* d_uoff,
+                         void* stream) {
+    if (k == 0) return;
+    const int sms = decode_grid();
+    decode_multi_kernel<<<sms, kDecBlock, kDecDynSmem, (cudaStream_t)stream>>>(d_args, d_uoff, d_units + k, k);
 }
 
 }  // namespace szg

@@ -53,7 +53,9 @@ static void launch_encode_t(const CompressArgs& a, cudaStream_t s) {
     }
     // persistent: at most the resident blocks, each taking chunks by ticket
     const int v = a.codes ? 1 : 0;
-    const uint32_t grid = umin32(a.n_chunks, (uint32_t)resident[v]);
+    const uint32_t div = a.grid_div > 1 ? a.grid_div : 1u;
+    uint32_t grid = umin32(a.n_chunks, (uint32_t)resident[v] / div);
+    if (grid == 0) grid = 1;
     if (v) encode_kernel<C, true><<<grid, NT, smem, s>>>(a);
     else encode_kernel<C, false><<<grid, NT, smem, s>>>(a);
 }

@@ -35,7 +35,8 @@ void launch_quant(const CompressArgs* a, int k, void* stream) {
     }
     for (int i = 0; i < k; ++i) {
         const int v = a[i].codes ? 1 : 0;
-        uint32_t grid = umin32(a[i].n_chunks, (uint32_t)(sms * per_sm[v]));
+        const uint32_t div = a[i].grid_div > 1 ? a[i].grid_div : 1u;
+        uint32_t grid = umin32(a[i].n_chunks, umin32((uint32_t)(sms * per_sm[v]) / div, (uint32_t)(sms * per_sm[v])));
         if (grid == 0) grid = 1;
         if (v)
             quant_kernel<true><<<grid, kQuantThreads, 0, (cudaStream_t)stream>>>(a[i]);

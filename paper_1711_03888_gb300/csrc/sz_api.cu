@@ -113,6 +113,7 @@ CompressArgs make_compress_args(sz_ctx* ctx, int slot, const float* in, uint64_t
     a.cb_scratch = ctx->d_cb + kCbScratchWords * slot;
     a.err = ctx->d_err;
     a.codes = ctx->d_codes + ctx->cap_codes * slot;
+    a.grid_div = ctx->grid_div;
     return a;
 }
 
@@ -129,6 +130,7 @@ DecompressArgs make_decompress_args(sz_ctx* ctx, int slot, const void* in, uint6
     d.by_len = ctx->d_bylen + (size_t)65536 * slot;
     d.cb_scratch = ctx->d_cb + kCbScratchWords * slot;
     d.err = ctx->d_err;
+    d.grid_div = ctx->grid_div;
     return d;
 }
 

@@ -274,7 +274,7 @@ sz_status batch_decompress(sz_ctx* ctx, int k, const void* const* d_in, const si
     auto take = [&](size_t b) { size_t o = bytes; bytes += align256(b); return o; };
     const size_t o_args = take(sizeof(DecompressArgs) * k);
     const size_t plan_bytes = bytes;
-    const size_t o_units = take(sizeof(uint32_t) * k);
+    const size_t o_units = take(sizeof(uint32_t) * 2 * k);
     const size_t o_uoff = take(sizeof(uint64_t) * (k + 1));
     const size_t o_state = take(sizeof(ArrayState) * k);
     const size_t per = align256(sizeof(uint32_t) * kLutWords) + align256(sizeof(uint16_t) * 65536) +
@@ -327,10 +327,15 @@ sz_status batch_decompress(sz_ctx* ctx, int k, const void* const* d_in, const si
         cudaGetLastError();
         return SZ_ERR_CUDA;
     }
+    const DecompressArgs* d_args = reinterpret_cast<const DecompressArgs*>(base + o_args);
+    uint64_t* d_uoff = reinterpret_cast<uint64_t*>(base + o_uoff);
+    {
+        ProfScope pr(ctx, SZ_PHASE_DECODE_SETUP, s);
+        launch_decode_multi_setup(d_args, (uint32_t)k, reinterpret_cast<uint32_t*>(base + o_units), d_uoff, s);
+    }
     {
         ProfScope pr(ctx, SZ_PHASE_DECODE, s);
-        launch_decode_multi(reinterpret_cast<const DecompressArgs*>(base + o_args), (uint32_t)k,
-                            reinterpret_cast<uint32_t*>(base + o_units), reinterpret_cast<uint64_t*>(base + o_uoff), s);
+        launch_decode_multi(d_args, (uint32_t)k, reinterpret_cast<uint32_t*>(base + o_units), d_uoff, s);
     }
     if (cudaPeekAtLastError() != cudaSuccess) { cudaGetLastError(); return SZ_ERR_CUDA; }
     if (n_out)

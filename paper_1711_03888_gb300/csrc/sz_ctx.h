@@ -11,6 +11,7 @@ struct sz_serve_state;
 struct sz_ctx {
     int device = 0;
     size_t budget = 0;
+    uint32_t grid_div = 1;              // share of the GPU the persistent launches take (1/grid_div)
     // workspace (one block of device memory, grown on demand)
     uint8_t* ws = nullptr;
     size_t ws_bytes = 0;

@@ -98,6 +98,7 @@ struct CompressArgs {
     uint32_t* cb_scratch;       // codebook scratch (kCbScratchWords words)
     uint32_t* err;              // context error word
     uint16_t* codes;            // n_chunks*C u16 codes written by the quantizer, or null (encoder recomputes)
+    uint32_t grid_div;          // persistent launches use 1/grid_div of the resident blocks (0, 1: all)
 };
 
 struct DecompressArgs {
@@ -111,6 +112,7 @@ struct DecompressArgs {
     uint16_t* by_len;           // 65536: symbols in (length, symbol) order
     uint32_t* cb_scratch;
     uint32_t* err;
+    uint32_t grid_div;          // the decode launch uses 1/grid_div of the SMs (0, 1: all)
 };
 
 // codebook scratch: 9 arrays of 65536 words and 5 of 131072 (see k_codebook.cu)
@@ -123,10 +125,13 @@ void launch_codebook(const CompressArgs* a, int k, void* stream);
 void launch_encode(const CompressArgs* a, int k, void* stream);
 void launch_decode_setup(const DecompressArgs* a, int k, void* stream);
 void launch_decode(const DecompressArgs* a, int k, void* stream);
-// Batched decompression: setup of all k streams (one block each), the prefix
-// of their decode units, then one launch over every unit.  d_args: k device
-// entries; d_units: k words; d_uoff: k + 1 words of scratch.
-void launch_decode_multi(const DecompressArgs* d_args, uint32_t k, uint32_t* d_units, uint64_t* d_uoff,
+// Batched decompression: setup of all k streams (one block each) and the
+// prefix of their decode units, then one launch over every unit.  d_args: k
+// device entries; d_units: 2k words (units, then per-stream unit counters);
+// d_uoff: k + 1 words.
+void launch_decode_multi_setup(const DecompressArgs* d_args, uint32_t k, uint32_t* d_units, uint64_t* d_uoff,
+                               void* stream);
+void launch_decode_multi(const DecompressArgs* d_args, uint32_t k, uint32_t* d_units, const uint64_t* d_uoff,
                          void* stream);
 
 // Batched form: one persistent launch over every array's work items.

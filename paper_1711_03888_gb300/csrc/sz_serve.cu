@@ -167,10 +167,13 @@ void CUDART_CB on_done(void* p) {
     s->owner->wake.notify_one();
 }
 
-// enqueue one request on a slot: the plain call's kernels, then the result copies
-sz_status launch_request(Slot& s, const sz_request& r, void* out) {
+// enqueue one request on a slot: the plain call's kernels, then the result copies.
+// share: the request's persistent launches take 1/share of the GPU, so that
+// requests in flight together split it instead of queueing behind each other.
+sz_status launch_request(Slot& s, const sz_request& r, void* out, uint32_t share) {
     sz_ctx* w = s.ws;
     cudaSetDevice(w->device);
+    w->grid_div = share;
     sz_status st;
     if (r.op == SZ_OP_COMPRESS) {
         uint32_t C, G;
@@ -267,7 +270,7 @@ void serve_loop(sz_serve_state* S) {
             S->queue.pop_front();
             if ((uint32_t)S->active > S->c.peak_inflight) S->c.peak_inflight = (uint32_t)S->active;
             if (S->held > S->c.peak_bytes) S->c.peak_bytes = S->held;
-            const sz_status st = launch_request(s, r, out);
+            const sz_status st = launch_request(s, r, out, (uint32_t)(S->active < 8 ? S->active : 8));
             if (st != SZ_OK) finish(S, s, st, 0);
             admitted = true;
         }
