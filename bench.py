@@ -110,24 +110,39 @@ def _barrier(ws):
         dist.barrier()
 
 
-def _max_over_ranks(v: float, ws: int) -> float:
+def _reduce_over_ranks(v: float, ws: int, op: str) -> float:
+    """All-reduce of one host scalar (timing bookkeeping only; the data path
+    has no collective).  NCCL reduces a CUDA tensor, gloo a CPU one."""
     if ws == 1:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
     return float(t.item())
+
+
+def _max_over_ranks(v: float, ws: int) -> float:
+    return _reduce_over_ranks(v, ws, "max")
 
 
 def _sum_over_ranks(v: float, ws: int) -> float:
-    if ws == 1:
-        return v
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    return _reduce_over_ranks(v, ws, "sum")
+
+
+def rank_snapshot_seed(rank: int) -> int:
+    """Weak scaling: rank r compresses its own snapshot, generated with seed
+    3 + r (independent data, the same size on every rank)."""
+    return 3 + rank
+
+
+def weak_scaling_value(bytes_per_rank: float, seconds_per_step: float, ws: int):
+    """Whole-job throughput: all ranks' bytes over the slowest rank's step
+    time.  Returns (GB/s, max step seconds, total bytes)."""
+    t = _max_over_ranks(seconds_per_step, ws)
+    b = _sum_over_ranks(bytes_per_rank, ws)
+    return b / t / 1e9, t, b
 
 
 def _traffic(kernel: str):
@@ -475,7 +490,7 @@ def main():
     import synth
     import paper_1711_03888_gb300 as sz
 
-    snap = synth.cosmology(n, halos, 3 + rank, device="cuda")
+    snap = synth.cosmology(n, halos, rank_snapshot_seed(rank), device="cuda")
     xs = [snap[f] for f in FIELDS]
     raw_bytes = 4 * n * len(xs)
     ctx = sz.Context(local)
@@ -541,9 +556,7 @@ def main():
     t_c = sum(e[0].elapsed_time(e[1]) for e in ev) / 1e3
     t_d = sum(e[1].elapsed_time(e[2]) for e in ev) / 1e3
     t_step = (t_c + t_d) / args.steps
-    t_step_max = _max_over_ranks(t_step, ws)
-    total_bytes = _sum_over_ranks(raw_bytes, ws)
-    value = total_bytes / t_step_max / 1e9
+    value, t_step_max, total_bytes = weak_scaling_value(raw_bytes, t_step, ws)
     comp_gbs = raw_bytes / (t_c / args.steps) / 1e9
     decomp_gbs = raw_bytes / (t_d / args.steps) / 1e9
 

@@ -1,0 +1,83 @@
+"""The N>1 host path on CPU: two gloo ranks run bench.py's bookkeeping (max
+step time and summed bytes over ranks, the barrier) and its weak-scaling
+sharding (every rank compresses its own snapshot, so the ranks' inputs are
+independent and no collective touches the data).  The oracle stands in for
+the GPU path, so the per-rank results can be checked end to end."""
+import os
+import socket
+
+import numpy as np
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, ws, port, q):
+    import sys
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(ws),
+                      LOCAL_RANK=str(rank))
+    import torch.distributed as dist
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    import bench
+    import oracle
+    import synth
+    got_ws, got_rank, _ = bench._dist()
+    # each rank: its own snapshot (seed 3 + rank), compressed by the oracle
+    n = 1 << 12
+    snap = synth.cosmology(n, 4, bench.rank_snapshot_seed(got_rank))
+    x = snap["vx"].numpy()
+    stream = oracle.compress(x, 1e-4, 1, 2048, 32)
+    y = oracle.decompress(stream)
+    bench._barrier(got_ws)
+    # rank r pretends its step took (r + 1) ms over 4n bytes
+    value, tmax, total = bench.weak_scaling_value(4.0 * n, (got_rank + 1) * 1e-3, got_ws)
+    R = float(x.max()) - float(x.min())
+    q.put((got_rank, got_ws, float(np.abs(x.astype(np.float64) - y).max()) / R, float(x[0]), len(stream),
+           value, tmax, total))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_weak_scaling():
+    import oracle
+    oracle.build()
+    ws, port = 2, _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_rank_main, args=(r, ws, port, q)) for r in range(ws)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=240) for _ in range(ws))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    n = 1 << 12
+    for rank, got_ws, rel_err, x0, nbytes, value, tmax, total in res:
+        assert got_ws == ws
+        assert tmax == pytest.approx(ws * 1e-3)             # the slowest rank's step
+        assert total == pytest.approx(ws * 4.0 * n)         # every rank's bytes
+        assert value == pytest.approx(total / tmax / 1e9)
+        assert nbytes > 160
+        assert rel_err <= 1e-4                               # |x - x'| <= eb_rel * R on every element
+    # independent shards: different seeds give different data
+    assert res[0][3] != res[1][3]
+
+
+def test_reference_arm_runs_on_rank_zero_only(tmp_path):
+    """Under torchrun the reference arm prints from rank 0 and the other ranks
+    exit without work (checked here without a launcher: RANK=1 returns)."""
+    import subprocess
+    import sys
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2",
+                        "--steps", "1", "--warmup", "0"], env=env, capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0
+    assert r.stdout.strip() == ""
