@@ -66,7 +66,7 @@ def test_two_gloo_ranks_weak_scaling():
         assert total == pytest.approx(ws * 4.0 * n)         # every rank's bytes
         assert value == pytest.approx(total / tmax / 1e9)
         assert nbytes > 160
-        assert rel_err <= 1e-4                               # |x - x'| <= eb_rel * R on every element
+        assert rel_err <= 1e-4 * (1 + 1e-12)                 # |x - x'| <= eb_rel * R on every element
     # independent shards: different seeds give different data
     assert res[0][3] != res[1][3]
 
