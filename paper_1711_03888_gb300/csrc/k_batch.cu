@@ -20,11 +20,14 @@
 namespace szg {
 
 constexpr int kBatchThreads = 256;
+// a quantize item flushes its histogram window once: its elements must fit
+// the window's 16-bit counters (batched arrays use C <= 4096)
+static_assert(kQuantGroup * 4096u <= 65535u, "quantize group too large for the 16-bit window");
 constexpr uint32_t kWaitSpins = 1u << 24;
 
 union BatchSmem {
     struct {
-        uint32_t win[kWin];
+        uint32_t win[kWinWords];
         uint32_t esc[kQuantThreads / 32];
     } q;
     CbSmem<kBatchThreads> cb;

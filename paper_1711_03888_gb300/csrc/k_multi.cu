@@ -34,17 +34,21 @@ __global__ void __launch_bounds__(256) range_multi_kernel(MultiArgs m) {
     range_body<256>(sa, blockIdx.x, gridDim.x);
 }
 
-__global__ void __launch_bounds__(kQuantThreads, 4) quant_multi_kernel(MultiArgs m) {
-    __shared__ uint32_t sh[kWin];
+__global__ void __launch_bounds__(kQuantThreads) quant_multi_kernel(MultiArgs m) {
+    __shared__ uint32_t sh[kWinWords];
     __shared__ uint32_t s_esc[kQuantThreads / 32];
     __shared__ CompressArgs sa;
+    extern __shared__ float4 stage4[];
     stage_args(m, sa);
     const ArrayState* st = sa.st;
     const LatticeParams P = st->P;
     if (P.raw || sa.n == 0) return;
     hist_window_zero(sh);
     __syncthreads();
-    for (uint32_t c = blockIdx.x; c < sa.n_chunks; c += gridDim.x) quant_chunk<true>(sa, P, c, sh, s_esc);
+    if (((uintptr_t)sa.in & 15u) == 0)
+        quant_array_staged<true>(sa, P, blockIdx.x, gridDim.x, reinterpret_cast<float*>(stage4), sh, s_esc);
+    else
+        quant_array_global<true>(sa, P, blockIdx.x, gridDim.x, sh, s_esc);
     hist_window_flush(sh, sa.hist);
 }
 
@@ -117,7 +121,10 @@ int add_multi_compress_nodes(void* graph, void* dep, const CompressArgs* d_args,
     static int per_sm = 0, enc_res[2] = {0, 0};
     static bool configured = false;
     if (!configured) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, quant_multi_kernel, kQuantThreads, 0);
+        cudaFuncSetAttribute(quant_multi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)quant_stage_bytes(4096));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, quant_multi_kernel, kQuantThreads,
+                                                      quant_stage_bytes(4096));
         if (per_sm <= 0) per_sm = 1;
         cudaFuncSetAttribute(encode_multi_kernel<2048>, cudaFuncAttributeMaxDynamicSharedMemorySize, kEncSmem2048);
         cudaFuncSetAttribute(encode_multi_kernel<4096>, cudaFuncAttributeMaxDynamicSharedMemorySize, kEncSmem4096);
@@ -135,8 +142,10 @@ int add_multi_compress_nodes(void* graph, void* dep, const CompressArgs* d_args,
                       &all)) != cudaSuccess)
         return (int)e;
     const uint32_t qgrid = umin32(max_nc, (uint32_t)(sm_count() * per_sm));
-    if ((e = add_node(g, &n_quant, &n_range, 1, (void*)quant_multi_kernel, dim3(qgrid, count), dim3(kQuantThreads), 0,
-                      &all)) != cudaSuccess)
+    uint32_t maxC = 2048;
+    for (int i = 0; i < ngroups; ++i) maxC = groups[i].C > maxC ? groups[i].C : maxC;
+    if ((e = add_node(g, &n_quant, &n_range, 1, (void*)quant_multi_kernel, dim3(qgrid, count), dim3(kQuantThreads),
+                      quant_stage_bytes(maxC), &all)) != cudaSuccess)
         return (int)e;
     if ((e = add_node(g, &n_cb, &n_quant, 1, (void*)codebook_multi_kernel, dim3(1, count), dim3(kCbBlock), 0, &all)) !=
         cudaSuccess)

@@ -1,20 +1,25 @@
 // k_quant.cu -- stand-alone launch of the quantize + histogram phase (a2-a4;
 // body in sz_quant.cuh): persistent 256-thread blocks walk the chunks of one
-// array with a block-private window of the histogram, flushed once at exit.
+// array with a block-private window of the histogram, flushed once at exit,
+// the next chunk's input staged into shared memory while one is quantized.
 #include "sz_quant.cuh"
 
 namespace szg {
 
 template <bool STORE>
 __global__ void __launch_bounds__(kQuantThreads) quant_kernel(CompressArgs a) {
-    __shared__ uint32_t sh[kWin];
+    __shared__ uint32_t sh[kWinWords];
     __shared__ uint32_t s_esc[kQuantThreads / 32];
+    extern __shared__ float4 stage4[];
     const ArrayState* st = a.st;
     const LatticeParams P = st->P;
     if (P.raw || a.n == 0) return;
     hist_window_zero(sh);
     __syncthreads();
-    for (uint32_t c = blockIdx.x; c < a.n_chunks; c += gridDim.x) quant_chunk<STORE>(a, P, c, sh, s_esc);
+    if (((uintptr_t)a.in & 15u) == 0)
+        quant_array_staged<STORE>(a, P, blockIdx.x, gridDim.x, reinterpret_cast<float*>(stage4), sh, s_esc);
+    else
+        quant_array_global<STORE>(a, P, blockIdx.x, gridDim.x, sh, s_esc);
     hist_window_flush(sh, a.hist);
 }
 
@@ -26,22 +31,31 @@ void launch_quant(const CompressArgs* a, int k, void* stream) {
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (sms <= 0) sms = 148;
     }
-    // persistent grid: exactly the blocks that fit at once
-    static int per_sm[2] = {0, 0};
-    if (!per_sm[0]) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[0], quant_kernel<false>, kQuantThreads, 0);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[1], quant_kernel<true>, kQuantThreads, 0);
-        for (int j = 0; j < 2; ++j) if (per_sm[j] <= 0) per_sm[j] = 1;
+    // persistent grid: exactly the blocks that fit at once, for the stage of
+    // the array's chunk size (two stages of C + 4 floats)
+    static int per_sm[2][4] = {};
+    static const uint32_t kCs[4] = {2048u, 4096u, 8192u, 16384u};
+    if (!per_sm[0][0]) {
+        for (int j = 0; j < 4; ++j) {
+            const size_t sm = quant_stage_bytes(kCs[j]);
+            cudaFuncSetAttribute(quant_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)quant_stage_bytes(16384));
+            cudaFuncSetAttribute(quant_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)quant_stage_bytes(16384));
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[0][j], quant_kernel<false>, kQuantThreads, sm);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[1][j], quant_kernel<true>, kQuantThreads, sm);
+            for (int v = 0; v < 2; ++v) if (per_sm[v][j] <= 0) per_sm[v][j] = 1;
+        }
     }
     for (int i = 0; i < k; ++i) {
         const int v = a[i].codes ? 1 : 0;
+        const int j = a[i].C == 2048 ? 0 : a[i].C == 4096 ? 1 : a[i].C == 8192 ? 2 : 3;
+        const size_t smem = quant_stage_bytes(a[i].C);
         const uint32_t div = a[i].grid_div > 1 ? a[i].grid_div : 1u;
-        uint32_t grid = umin32(a[i].n_chunks, umin32((uint32_t)(sms * per_sm[v]) / div, (uint32_t)(sms * per_sm[v])));
+        uint32_t grid = umin32(a[i].n_chunks, (uint32_t)(sms * per_sm[v][j]) / div);
         if (grid == 0) grid = 1;
         if (v)
-            quant_kernel<true><<<grid, kQuantThreads, 0, (cudaStream_t)stream>>>(a[i]);
+            quant_kernel<true><<<grid, kQuantThreads, smem, (cudaStream_t)stream>>>(a[i]);
         else
-            quant_kernel<false><<<grid, kQuantThreads, 0, (cudaStream_t)stream>>>(a[i]);
+            quant_kernel<false><<<grid, kQuantThreads, smem, (cudaStream_t)stream>>>(a[i]);
     }
 }
 

@@ -13,19 +13,34 @@
 // for that step.  Codes near the centre go to a shared-memory window of the
 // histogram, the rest to global atomics.  When `codes` is set the u16 codes
 // are stored for the encoder.  The chunk's escape count is recorded and the
-// encoder's look-back word re-armed.
+// encoder's look-back word re-armed.  quant_chunk reads the input from global
+// memory; quant_chunk_staged from a shared-memory stage that the persistent
+// loop (quant_array_staged) fills for the next chunk while this one runs.
 #pragma once
 #include "sz_device.cuh"
 
 namespace szg {
 
 constexpr int kQuantThreads = 256;
-constexpr int kWin = 8192;                 // shared histogram window (codes 28672..36863)
+// Shared histogram window: codes kWinLo .. kWinLo + kWin - 1 (deltas within
+// +-8192), two 16-bit counters per word (kWinWords words, 32 KB).  A block
+// flushes it into the global histogram before a counter can wrap: after at
+// most 65535 elements (quant_flush_every chunks).  Measured on GB300 (2^27
+// elements, quantize ms, positions / velocities): 32-bit counters over 8192
+// codes 0.50 / 0.29; 16-bit counters over 16384 codes 0.33 / 0.32 -- position
+// data puts ~3 % of its codes beyond +-4096, and every one of those costs a
+// divergent global atomic.
+constexpr int kWin = 16384;
+constexpr int kWinWords = kWin / 2;
 constexpr uint32_t kWinLo = kRadius - kWin / 2;
+__host__ __device__ constexpr uint32_t quant_flush_every(uint32_t C) { return 65535u / C; }
+
+// dynamic shared memory of the staged quantize loop: two stages of C + 4 floats
+constexpr size_t quant_stage_bytes(uint32_t C) { return 2u * 4u * ((size_t)C + 4u); }
 
 __device__ __forceinline__ void hist_add(uint32_t code, uint32_t* sh, uint32_t* gh) {
-    uint32_t w = code - kWinLo;
-    if (w < (uint32_t)kWin) atomicAdd(&sh[w], 1u);
+    const uint32_t w = code - kWinLo;
+    if (w < (uint32_t)kWin) atomicAdd(&sh[w >> 1], 1u << ((w & 1u) << 4));
     else atomicAdd(&gh[code], 1u);
 }
 
@@ -48,13 +63,17 @@ __device__ __forceinline__ uint32_t code32(int q, int qprev, bool verb) {
 }
 
 __device__ __forceinline__ void hist_window_zero(uint32_t* sh) {
-    for (int i = threadIdx.x; i < kWin; i += kQuantThreads) sh[i] = 0u;
+    for (int i = threadIdx.x; i < kWinWords; i += kQuantThreads) sh[i] = 0u;
 }
 
+// adds the window into the global histogram and clears it (callers
+// synchronize the block before and after)
 __device__ __forceinline__ void hist_window_flush(uint32_t* sh, uint32_t* gh) {
-    for (int i = threadIdx.x; i < kWin; i += kQuantThreads) {
-        uint32_t v = sh[i];
-        if (v) atomicAdd(&gh[kWinLo + i], v);
+    for (int i = threadIdx.x; i < kWinWords; i += kQuantThreads) {
+        const uint32_t v = sh[i];
+        if (v & 0xffffu) atomicAdd(&gh[kWinLo + 2 * i], v & 0xffffu);
+        if (v >> 16) atomicAdd(&gh[kWinLo + 2 * i + 1], v >> 16);
+        sh[i] = 0u;
     }
 }
 
@@ -156,6 +175,166 @@ __device__ void quant_chunk(const CompressArgs& a, const LatticeParams& P, uint3
         a.chunk_status[c] = 0ull;
     }
     __syncthreads();
+}
+
+template <bool STORE>
+__device__ void quant_chunk_staged(const CompressArgs& a, const LatticeParams& P, uint32_t c, const float* stage,
+                                   uint32_t* sh, uint32_t* s_esc) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint64_t cbase = (uint64_t)c * a.C;
+    const float* sx = stage + 4;           // sx[e - cbase] = x[e]; sx[-4 .. -1] = the elements before the chunk
+    const bool fast_ok = P.fast != 0;
+    const uint64_t n = a.n;
+    const uint32_t span = a.C / 8;
+    uint16_t* codes = a.codes;
+    const uint64_t s0 = (uint64_t)c * a.C + (uint64_t)warp * span;
+    const uint64_t s1 = umin64(n, s0 + span);
+    uint32_t esc = 0;
+    long long carry = 0;
+    if (s0 < s1 && s0 > 0 && lane == 0) {
+        bool vv;
+        lattice_q(sx[s0 - 1 - cbase], P, carry, vv);
+    }
+    carry = __shfl_sync(0xffffffffu, carry, 0);
+    for (uint64_t ib = s0; ib < s1; ib += 256) {
+        float xg[2][4];
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {
+            const uint64_t i = ib + 128 * g + 4 * (uint64_t)lane;
+            if (ib + 128 * g + 128 <= s1) {
+                float4 v = *reinterpret_cast<const float4*>(sx + (i - cbase));
+                xg[g][0] = v.x; xg[g][1] = v.y; xg[g][2] = v.z; xg[g][3] = v.w;
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) xg[g][j] = (i + j < s1) ? sx[i + j - cbase] : 0.0f;
+            }
+        }
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {
+            const uint64_t i0 = ib + 128 * g;
+            if (i0 >= s1) break;
+            const uint64_t i = i0 + 4 * (uint64_t)lane;
+            const bool full = (i0 + 128 <= s1);
+            float x[4] = {xg[g][0], xg[g][1], xg[g][2], xg[g][3]};
+            uint32_t cd[4];
+            int q32[4];
+            bool vb[4];
+            bool ok = fast_ok;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) ok &= lattice_fast32(x[j], P, q32[j], vb[j]);
+            if (__all_sync(0xffffffffu, ok) && carry >= -(1ll << 30) && carry <= (1ll << 30)) {
+                int qp = __shfl_up_sync(0xffffffffu, q32[3], 1);
+                if (lane == 0) qp = (int)carry;
+                cd[0] = code32(q32[0], qp, vb[0]);
+                cd[1] = code32(q32[1], q32[0], vb[1]);
+                cd[2] = code32(q32[2], q32[1], vb[2]);
+                cd[3] = code32(q32[3], q32[2], vb[3]);
+                carry = __shfl_sync(0xffffffffu, q32[3], 31);
+            } else {
+                long long q[4];
+                bool v2[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) lattice_q(x[j], P, q[j], v2[j]);
+                long long qp = __shfl_up_sync(0xffffffffu, q[3], 1);
+                if (lane == 0) qp = carry;
+                cd[0] = make_code(q[0], qp, v2[0]);
+                cd[1] = make_code(q[1], q[0], v2[1]);
+                cd[2] = make_code(q[2], q[1], v2[2]);
+                cd[3] = make_code(q[3], q[2], v2[3]);
+                // only full groups continue, so lane 31's q[3] is the last element
+                carry = __shfl_sync(0xffffffffu, q[3], 31);
+            }
+            if (full) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    esc += (cd[j] == 0u);
+                    hist_add(cd[j], sh, a.hist);
+                }
+                if (STORE) {
+                    uint2 pk = make_uint2(cd[0] | (cd[1] << 16), cd[2] | (cd[3] << 16));
+                    *reinterpret_cast<uint2*>(codes + i) = pk;
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (i + j < s1) {
+                        esc += (cd[j] == 0u);
+                        hist_add(cd[j], sh, a.hist);
+                        if (STORE) codes[i + j] = (uint16_t)cd[j];
+                    }
+            }
+        }
+    }
+    esc = warp_reduce_sum(esc);
+    if (lane == 0) s_esc[warp] = esc;
+    __syncthreads();
+    if (tid == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < kQuantThreads / 32; ++w) t += s_esc[w];
+        a.chunk_esc[c] = t;
+        a.chunk_status[c] = 0ull;
+    }
+    __syncthreads();
+}
+
+
+// Staged input: the chunk's elements and the four before it, in shared memory
+// (C + 4 floats).  quant_issue starts the asynchronous copies of chunk cc into
+// `stage` (16-byte cp.async pieces, the last < 4 elements by plain loads) and
+// commits them as one group; the caller waits and synchronizes the block
+// before quant_chunk_staged reads the stage.  Needs a 16-byte aligned input.
+__device__ __forceinline__ void quant_issue(const CompressArgs& a, uint32_t cc, float* stage) {
+    const uint64_t cb = (uint64_t)cc * a.C;
+    const uint64_t e0 = cc ? cb - 4 : 0, e1 = umin64(a.n, cb + a.C);
+    float* sx = stage + 4;
+    const uint32_t nvec = (uint32_t)((e1 - e0) / 4);
+    const uint32_t s_base = (uint32_t)__cvta_generic_to_shared(sx + (e0 - cb));   // e0 - cb is 0 or -4
+    for (uint32_t i = threadIdx.x; i < nvec; i += kQuantThreads)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s_base + 16u * i),
+                     "l"(__cvta_generic_to_global(a.in + e0 + 4 * (uint64_t)i))
+                     : "memory");
+    for (uint64_t e = e0 + 4 * (uint64_t)nvec + threadIdx.x; e < e1; e += kQuantThreads) sx[e - cb] = __ldg(a.in + e);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// The same loop reading the input from global memory (unaligned input).
+template <bool STORE>
+__device__ __forceinline__ void quant_array_global(const CompressArgs& a, const LatticeParams& P, uint32_t first,
+                                                   uint32_t step, uint32_t* sh, uint32_t* s_esc) {
+    uint32_t since = 0;
+    for (uint32_t c = first; c < a.n_chunks; c += step) {
+        quant_chunk<STORE>(a, P, c, sh, s_esc);
+        if (++since == quant_flush_every(a.C)) {
+            hist_window_flush(sh, a.hist);
+            __syncthreads();
+            since = 0;
+        }
+    }
+}
+
+// The persistent quantize loop of one array over chunks first, first + step,
+// ...: chunk c + step is copied into one stage while chunk c is quantized from
+// the other.  stage: 2 (C + 4) floats, 16-byte aligned.
+template <bool STORE>
+__device__ __forceinline__ void quant_array_staged(const CompressArgs& a, const LatticeParams& P, uint32_t first,
+                                                   uint32_t step, float* stage, uint32_t* sh, uint32_t* s_esc) {
+    float* buf[2] = {stage, stage + a.C + 4};
+    uint32_t c = first, since = 0;
+    if (c < a.n_chunks) quant_issue(a, c, buf[0]);
+    for (int b = 0; c < a.n_chunks; b ^= 1) {
+        const uint32_t cn = c + step;
+        if (cn < a.n_chunks) quant_issue(a, cn, buf[b ^ 1]);
+        else asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
+        __syncthreads();          // chunk c is staged (every thread's pieces)
+        quant_chunk_staged<STORE>(a, P, c, buf[b], sh, s_esc);   // ends with a block barrier
+        if (++since == quant_flush_every(a.C)) {
+            hist_window_flush(sh, a.hist);
+            __syncthreads();
+            since = 0;
+        }
+        c = cn;
+    }
 }
 
 }  // namespace szg
