@@ -5,11 +5,17 @@ namespace szg {
 
 __global__ void __launch_bounds__(kCbBlock) codebook_kernel(CompressArgs a) {
     __shared__ CbSmem<kCbBlock> sm;
-    codebook_body<kCbBlock>(a, sm);
+    extern __shared__ uint32_t fast[];
+    codebook_body<kCbBlock>(a, sm, fast, kCbFastSyms);
 }
 
 void launch_codebook(const CompressArgs* a, int k, void* stream) {
-    for (int i = 0; i < k; ++i) codebook_kernel<<<1, kCbBlock, 0, (cudaStream_t)stream>>>(a[i]);
+    static bool configured = false;
+    if (!configured) {
+        cudaFuncSetAttribute(codebook_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCbFastBytes);
+        configured = true;
+    }
+    for (int i = 0; i < k; ++i) codebook_kernel<<<1, kCbBlock, kCbFastBytes, (cudaStream_t)stream>>>(a[i]);
 }
 
 }  // namespace szg

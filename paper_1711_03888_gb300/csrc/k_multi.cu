@@ -55,8 +55,9 @@ __global__ void __launch_bounds__(kQuantThreads) quant_multi_kernel(MultiArgs m)
 __global__ void __launch_bounds__(kCbBlock) codebook_multi_kernel(MultiArgs m) {
     __shared__ CbSmem<kCbBlock> sm;
     __shared__ CompressArgs sa;
+    extern __shared__ uint32_t fast[];
     stage_args(m, sa);
-    codebook_body<kCbBlock>(sa, sm);
+    codebook_body<kCbBlock>(sa, sm, fast, kCbFastSyms);
 }
 
 template <int C>
@@ -121,6 +122,7 @@ int add_multi_compress_nodes(void* graph, void* dep, const CompressArgs* d_args,
     static int per_sm = 0, enc_res[2] = {0, 0};
     static bool configured = false;
     if (!configured) {
+        cudaFuncSetAttribute(codebook_multi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCbFastBytes);
         cudaFuncSetAttribute(quant_multi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)quant_stage_bytes(4096));
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, quant_multi_kernel, kQuantThreads,
@@ -147,8 +149,8 @@ int add_multi_compress_nodes(void* graph, void* dep, const CompressArgs* d_args,
     if ((e = add_node(g, &n_quant, &n_range, 1, (void*)quant_multi_kernel, dim3(qgrid, count), dim3(kQuantThreads),
                       quant_stage_bytes(maxC), &all)) != cudaSuccess)
         return (int)e;
-    if ((e = add_node(g, &n_cb, &n_quant, 1, (void*)codebook_multi_kernel, dim3(1, count), dim3(kCbBlock), 0, &all)) !=
-        cudaSuccess)
+    if ((e = add_node(g, &n_cb, &n_quant, 1, (void*)codebook_multi_kernel, dim3(1, count), dim3(kCbBlock),
+                      kCbFastBytes, &all)) != cudaSuccess)
         return (int)e;
     for (int i = 0; i < ngroups; ++i) {
         MultiArgs mg{d_args, groups[i].first};

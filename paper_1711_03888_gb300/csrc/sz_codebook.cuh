@@ -21,6 +21,11 @@
 namespace szg {
 
 constexpr int kCbBlock = 1024;      // threads of the stand-alone codebook launch
+// Alphabets up to this many used symbols sort, merge and take depths in
+// shared memory (4 * kCbFastSyms words of dynamic shared memory).
+constexpr uint32_t kCbFastSyms = 11264;
+constexpr size_t kCbFastBytes = 4u * 4u * kCbFastSyms;
+constexpr uint32_t kCbMaxRounds = 256;   // merge rounds recorded for the depth sweep
 
 // scratch layout (u32 words)
 constexpr size_t SC_SYM = 0;
@@ -45,7 +50,8 @@ struct CbSmem {
     RadixSmem rs;
     uint32_t ws32[NT / 32 + 1];
     unsigned long long ws64[NT / 32 + 1];
-    uint32_t m, lf, ifr, iend, a, b, done, left_leaf, changed, maxd;
+    uint32_t m, lf, ifr, iend, a, b, done, left_leaf[2], changed, maxd;
+    uint32_t r_lo[kCbMaxRounds], r_n[kCbMaxRounds];   // merge rounds: first new node, new nodes
     unsigned long long s;
     uint32_t cnt_len[kMaxLen + 2];
     uint32_t first[kMaxLen + 2];
@@ -103,8 +109,11 @@ __device__ __forceinline__ uint32_t count_le(const uint32_t* p, uint32_t len, ui
 
 // The codebook and layout of one array, computed by one block of NT threads
 // (NT = 1024 for the stand-alone launch, 256 inside the batched kernel).
+// fast: optional shared-memory space (4 * fast_cap words); alphabets of at
+// most fast_cap used symbols run the sort, the merge and the depths there.
 template <int NT>
-__device__ void codebook_body(const CompressArgs& a, CbSmem<NT>& sm) {
+__device__ void codebook_body(const CompressArgs& a, CbSmem<NT>& sm, uint32_t* fast = nullptr,
+                              uint32_t fast_cap = 0) {
     constexpr int kCbThreads = NT;
     const int tid = threadIdx.x;
     ArrayState* st = a.st;
@@ -172,14 +181,22 @@ __device__ void codebook_body(const CompressArgs& a, CbSmem<NT>& sm) {
         if (tid == 0) lenA[0] = 1u;
         __syncthreads();
     } else {
-        uint32_t* wi = scr + SC_WI;
+        // Working arrays: four of fast_cap words in shared memory when the
+        // alphabet fits, else the global scratch.  The sort ping-pongs keys
+        // between KA / KB and values between VA / VB; the merge keeps the
+        // internal-node weights in the key buffer the sort did not end in.
+        const bool in_smem = fast != nullptr && m <= fast_cap;
+        uint32_t* KA = in_smem ? fast : scr + SC_KA;
+        uint32_t* VA = in_smem ? fast + fast_cap : scr + SC_VA;
+        uint32_t* KB = in_smem ? fast + 2 * fast_cap : scr + SC_KB;
+        uint32_t* VB = in_smem ? fast + 3 * fast_cap : scr + SC_VB;
         uint32_t* par = scr + SC_PAR;
         for (;;) {
             // keys: working weights; values: ascending-symbol index
             uint32_t wmax = 0;
             for (uint32_t k = tid; k < m; k += kCbThreads) {
-                scr[SC_KA + k] = wrk[k];
-                scr[SC_VA + k] = k;
+                KA[k] = wrk[k];
+                VA[k] = k;
                 wmax = max(wmax, wrk[k]);
             }
 #pragma unroll
@@ -193,102 +210,128 @@ __device__ void codebook_body(const CompressArgs& a, CbSmem<NT>& sm) {
             }
             __syncthreads();
             uint32_t *wl, *vl;
-            radix_sort<kCbThreads>(scr + SC_KA, scr + SC_VA, scr + SC_KB, scr + SC_VB, m, (int)sm.maxd, sm.rs, &wl, &vl);
+            radix_sort<kCbThreads>(KA, VA, KB, VB, m, (int)sm.maxd, sm.rs, &wl, &vl);
+            uint32_t* wi = (wl == KA) ? KB : KA;
 
-            // round-parallel two-queue merge
+            // Round-parallel two-queue merge.  Every thread follows the queue
+            // state (lf, ifr, iend) itself, so a round needs one barrier; each
+            // round's new nodes [iend, iend + pairs) are recorded for the depths.
             for (uint32_t k = tid; k < m; k += kCbThreads) wi[k] = 0u;
-            if (tid == 0) { sm.lf = 0; sm.ifr = m; sm.iend = m; }
             __syncthreads();
+            uint32_t lf = 0, ifr = m, iend = m, nr = 0;
             for (;;) {
-                if (tid == 0) {
-                    uint32_t lf = sm.lf, ifr = sm.ifr, iend = sm.iend;
-                    uint32_t rem = (m - lf) + (iend - ifr);
-                    if (rem <= 1) {
-                        sm.done = 1;
-                    } else {
-                        uint32_t l = lf, i = ifr;
-                        unsigned long long s = 0;
-                        for (int t = 0; t < 2; ++t) {
-                            if (l < m && (i == iend || wl[l] <= wi[i - m])) s += wl[l++];
-                            else s += wi[(i++) - m];
-                        }
-                        sm.s = s;
-                        sm.a = count_le(wl + lf, m - lf, s);
-                        sm.b = iend - ifr;
-                        sm.done = 0;
-                    }
+                if ((m - lf) + (iend - ifr) <= 1) break;
+                uint32_t l = lf, i = ifr;
+                unsigned long long sw = 0;
+                for (int t = 0; t < 2; ++t) {
+                    if (l < m && (i == iend || wl[l] <= wi[i - m])) sw += wl[l++];
+                    else sw += wi[(i++) - m];
                 }
-                __syncthreads();
-                if (sm.done) break;
-                const uint32_t lf = sm.lf, ifr = sm.ifr, iend = sm.iend, na = sm.a, nb = sm.b;
+                const uint32_t na = count_le(wl + lf, m - lf, sw), nb = iend - ifr;
                 const uint32_t c = na + nb, pairs = c >> 1;
-                for (uint32_t j = tid; j < na; j += kCbThreads) {
-                    uint32_t w = wl[lf + j];
-                    uint32_t r = j + count_less(wi + (ifr - m), nb, w);
-                    if (r < 2 * pairs) {
-                        uint32_t p = iend + (r >> 1);
-                        par[lf + j] = p;
-                        atomicAdd(&wi[p - m], w);
-                    } else {
-                        sm.left_leaf = 1;
-                    }
+                if (tid == 0 && nr < kCbMaxRounds) {
+                    sm.r_lo[nr] = iend;
+                    sm.r_n[nr] = pairs;
                 }
-                for (uint32_t i = tid; i < nb; i += kCbThreads) {
-                    uint32_t w = wi[ifr - m + i];
-                    uint32_t r = i + count_le(wl + lf, na, w);
-                    if (r < 2 * pairs) {
-                        uint32_t p = iend + (r >> 1);
-                        par[ifr + i] = p;
-                        atomicAdd(&wi[p - m], w);
-                    } else {
-                        sm.left_leaf = 0;
+                uint32_t* left_leaf = &sm.left_leaf[nr & 1];
+                {
+                    // Merged order of the round's na leaves and nb internal nodes
+                    // (a leaf first at equal weight); positions 2k and 2k+1 become
+                    // the children of node iend + k.  Thread t takes positions
+                    // [d0, d1): one merge-path search finds how many leaves precede
+                    // d0, then a sequential merge of its slice.
+                    const uint32_t* L = wl + lf;
+                    const uint32_t* I = wi + (ifr - m);
+                    const uint32_t per = (c + kCbThreads - 1) / kCbThreads;
+                    const uint32_t d0 = umin32(c, tid * per), d1 = umin32(c, d0 + per);
+                    if (d0 < d1) {
+                        // smallest li in [max(0, d0 - nb), min(d0, na)] with the leaf li
+                        // not before internal d0 - li - 1 in the merged order
+                        uint32_t lo = d0 > nb ? d0 - nb : 0u, hi = umin32(d0, na);
+                        while (lo < hi) {
+                            const uint32_t mid = (lo + hi) >> 1;
+                            if (L[mid] <= I[d0 - mid - 1]) lo = mid + 1; else hi = mid;
+                        }
+                        uint32_t li = lo, ii = d0 - lo;
+                        for (uint32_t r = d0; r < d1; ++r) {
+                            const bool leaf = li < na && (ii >= nb || L[li] <= I[ii]);
+                            const uint32_t node = leaf ? lf + li : ifr + ii;
+                            const uint32_t w = leaf ? L[li] : I[ii];
+                            li += leaf ? 1u : 0u;
+                            ii += leaf ? 0u : 1u;
+                            if (r < 2 * pairs) {
+                                const uint32_t p = iend + (r >> 1);
+                                par[node] = p;
+                                atomicAdd(&wi[p - m], w);
+                            } else {
+                                *left_leaf = leaf ? 1u : 0u;
+                            }
+                        }
                     }
                 }
                 __syncthreads();
-                if (tid == 0) {
-                    if (c & 1u) {
-                        if (sm.left_leaf) { sm.lf = lf + na - 1; sm.ifr = iend; }
-                        else { sm.lf = lf + na; sm.ifr = iend - 1; }
-                    } else {
-                        sm.lf = lf + na;
-                        sm.ifr = iend;
-                    }
-                    sm.iend = iend + pairs;
+                if (c & 1u) {
+                    if (*left_leaf) { lf = lf + na - 1; ifr = iend; }
+                    else { lf = lf + na; ifr = iend - 1; }
+                } else {
+                    lf = lf + na;
+                    ifr = iend;
                 }
-                __syncthreads();
+                iend += pairs;
+                ++nr;
             }
-            // depths by pointer jumping (root = 2m-2)
+            // Depths.  A node's parent is created in a later round than the
+            // node, so one sweep over the rounds from the last (the root)
+            // back to the first fixes every internal depth, and one more step
+            // the leaves'.  Beyond kCbMaxRounds rounds: pointer jumping.
             const uint32_t nodes = 2 * m - 1, root = 2 * m - 2;
-            uint32_t *DA = scr + SC_DA, *JA = scr + SC_JA, *DB = scr + SC_DB, *JB = scr + SC_JB;
-            for (uint32_t v = tid; v < nodes; v += kCbThreads) {
-                DA[v] = (v == root) ? 0u : 1u;
-                JA[v] = (v == root) ? root : par[v];
-            }
-            __syncthreads();
-            for (int it = 0; it < 40; ++it) {
-                if (tid == 0) sm.changed = 0;
+            uint32_t* dep;
+            if (nr <= kCbMaxRounds) {
+                // 2m words: the two key buffers and the values buffer the sort did not end in are free
+                dep = !in_smem ? scr + SC_DA : (vl == VA ? KB : KA);
+                if (tid == 0) dep[root] = 0u;
                 __syncthreads();
-                uint32_t ch = 0;
-                for (uint32_t v = tid; v < nodes; v += kCbThreads) {
-                    uint32_t j = JA[v];
-                    if (j != root) {
-                        DB[v] = DA[v] + DA[j];
-                        JB[v] = JA[j];
-                        ch = 1;
-                    } else {
-                        DB[v] = DA[v];
-                        JB[v] = j;
-                    }
+                for (int r = (int)nr - 1; r >= 0; --r) {
+                    const uint32_t lo = sm.r_lo[r], hi = lo + sm.r_n[r];
+                    for (uint32_t v = lo + tid; v < hi; v += kCbThreads)
+                        if (v != root) dep[v] = dep[par[v]] + 1u;
+                    __syncthreads();
                 }
-                if (ch) sm.changed = 1;
+                for (uint32_t v = tid; v < m; v += kCbThreads) dep[v] = dep[par[v]] + 1u;
                 __syncthreads();
-                uint32_t* t = DA; DA = DB; DB = t;
-                t = JA; JA = JB; JB = t;
-                if (!sm.changed) break;
+            } else {
+                uint32_t *DA = scr + SC_DA, *JA = scr + SC_JA, *DB = scr + SC_DB, *JB = scr + SC_JB;
+                for (uint32_t v = tid; v < nodes; v += kCbThreads) {
+                    DA[v] = (v == root) ? 0u : 1u;
+                    JA[v] = (v == root) ? root : par[v];
+                }
                 __syncthreads();
+                for (int it = 0; it < 40; ++it) {
+                    if (tid == 0) sm.changed = 0;
+                    __syncthreads();
+                    uint32_t ch = 0;
+                    for (uint32_t v = tid; v < nodes; v += kCbThreads) {
+                        uint32_t j = JA[v];
+                        if (j != root) {
+                            DB[v] = DA[v] + DA[j];
+                            JB[v] = JA[j];
+                            ch = 1;
+                        } else {
+                            DB[v] = DA[v];
+                            JB[v] = j;
+                        }
+                    }
+                    if (ch) sm.changed = 1;
+                    __syncthreads();
+                    uint32_t* t = DA; DA = DB; DB = t;
+                    t = JA; JA = JB; JB = t;
+                    if (!sm.changed) break;
+                    __syncthreads();
+                }
+                dep = DA;
             }
             uint32_t md = 0;
-            for (uint32_t j = tid; j < m; j += kCbThreads) md = max(md, DA[j]);
+            for (uint32_t j = tid; j < m; j += kCbThreads) md = max(md, dep[j]);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) md = max(md, __shfl_xor_sync(0xffffffffu, md, o));
             if ((tid & 31) == 0) sm.ws32[tid >> 5] = md;
@@ -300,7 +343,7 @@ __device__ void codebook_body(const CompressArgs& a, CbSmem<NT>& sm) {
             }
             __syncthreads();
             if (sm.maxd <= (uint32_t)kMaxLen) {
-                for (uint32_t j = tid; j < m; j += kCbThreads) lenA[vl[j]] = DA[j];
+                for (uint32_t j = tid; j < m; j += kCbThreads) lenA[vl[j]] = dep[j];
                 __syncthreads();
                 break;
             }
