@@ -259,16 +259,17 @@ __device__ __noinline__ uint32_t decode_long(uint32_t w24, const DecSmem& sm, co
     return ((uint32_t)by_len[sm.base[len] + (w24 >> (kMaxLen - len)) - sm.first[len]] << 8) | len;
 }
 
-// One symbol: 12-bit direct lookup, then the 16-bit second level, then the walk.
+// One symbol: the 12-bit direct lookup and the 16-bit second level are read
+// together (independent loads, no divergent branch for the tenth of symbols
+// with longer codes); the walk takes codes beyond 16 bits.
 __device__ __forceinline__ uint32_t decode_symbol(BitReader& br, const DecSmem& sm, const uint32_t* lut2,
                                                   uint32_t l2_lo, uint32_t l2_n, const uint16_t* by_len, bool& bad) {
     const uint32_t w = br.peek();
-    uint32_t ent = sm.lut[w >> (32 - kLutBits)];
-    if (ent == 0u) {
-        const uint32_t i2 = (w >> (32 - kLut2Bits)) - l2_lo;   // wraps above l2_n below the range
-        ent = i2 < l2_n ? lut2[i2] : 0u;
-        if (ent == 0u) ent = decode_long(w >> (32 - kMaxLen), sm, by_len, bad);
-    }
+    const uint32_t e1 = sm.lut[w >> (32 - kLutBits)];
+    const uint32_t i2 = (w >> (32 - kLut2Bits)) - l2_lo;   // wraps above l2_n below the range
+    const uint32_t e2 = i2 < l2_n ? lut2[i2] : 0u;
+    uint32_t ent = e1 ? e1 : e2;
+    if (ent == 0u) ent = decode_long(w >> (32 - kMaxLen), sm, by_len, bad);
     br.consume(ent & 255u);
     return ent >> 8;
 }
