@@ -592,9 +592,14 @@ def main():
     # reads the stream and writes 4n.  The batch graph covers all six arrays.
     per_stream = stream_bytes / len(xs)
     # Per launch: the plain path's kernels cover one array; the batched step's
-    # graph and decoder (decode_multi_kernel) cover all six.
+    # per-phase kernels (range_multi, quant_multi, encode_multi, decode_multi)
+    # cover all six.
+    k6 = len(xs)
     algo_plain = {"range": 4 * n, "quant": 6 * n, "encode": 2 * n + per_stream, "decode": per_stream + 4 * n}
-    algo_batched = {"batch": 12 * n * len(xs) + stream_bytes, "decode": stream_bytes + 4 * n * len(xs)}
+    algo_batched = {"range": 4 * n * k6, "quant": 6 * n * k6, "encode": 2 * n * k6 + stream_bytes,
+                    "decode": stream_bytes + 4 * n * k6}
+    kernel_multi = {"range": "range_multi_kernel", "quant": "quant_multi_kernel", "encode": "encode_multi_kernel",
+                    "decode": "decode_multi_kernel"}
     kernel_of = {"encode": "encode_kernel", "decode": "decode_kernel", "quant": "quant_kernel",
                  "range": "range_kernel", "codebook": "codebook_kernel", "decode_setup": "decode_setup_kernel"}
 
@@ -614,21 +619,14 @@ def main():
 
     kernels = kernel_table(prof, args.steps, algo_batched)
     kernels_plain = kernel_table(prof_plain, args.steps, algo_plain)
-    # The dominant single kernel by device time per step.  The batched step
-    # runs decode_multi_kernel (one launch over the six streams) and the batch
-    # graph, whose per-phase launches run the stand-alone kernels' bodies; their
-    # per-kernel times are read from the plain path, one launch per array.  (The
-    # codebook kernel works on the 2^16-entry histogram whatever n is: a fixed
-    # latency, not a bandwidth-bound pass, so it is not a candidate.)
-    cands = {"decode_multi": kernels["decode"]["ms_per_step"]}
-    for ph in ("range", "quant", "encode"):
-        if ph in kernels_plain:
-            cands[ph] = kernels_plain[ph]["ms_per_step"]
+    # The dominant single kernel of the batched step by device time per step.
+    # While tracing is on, the batch's graph work runs as direct launches of the
+    # same per-phase kernels, each between two events on the step's stream.
+    # (The codebook kernel works on the 2^16-entry histogram whatever n is: a
+    # fixed latency, not a bandwidth-bound pass, so it is not a candidate.)
+    cands = {ph: kernels[ph]["ms_per_step"] for ph in ("range", "quant", "encode", "decode") if ph in kernels}
     dom = max(cands, key=cands.get)
-    if dom == "decode_multi":
-        dk, kname, abytes = kernels["decode"], "decode_multi_kernel", algo_batched["decode"]
-    else:
-        dk, kname, abytes = kernels_plain[dom], kernel_of[dom], algo_plain[dom]
+    dk, kname, abytes = kernels[dom], kernel_multi[dom], algo_batched[dom]
     roofline = {"bound": "hbm", "kernel": kname, "achieved": dk["achieved_gbs"], "peak": peak,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": dk["frac"],
                 "traffic": _traffic(kname),

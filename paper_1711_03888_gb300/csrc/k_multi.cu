@@ -4,10 +4,11 @@
 // bodies are the stand-alone kernels' (sz_range.cuh, sz_quant.cuh,
 // sz_codebook.cuh, sz_encode.cuh), so every stream is byte-identical to
 // sz_compress; the gain is that the arrays' single-block codebooks run side by
-// side instead of one after another.  The four launches are kernel nodes of
-// the batch's CUDA graph, on a branch parallel to the persistent kernel that
-// takes the small arrays.
+// side instead of one after another.  multi_compress_launches describes the
+// launches; the batch's CUDA graph takes them as kernel nodes on a branch
+// parallel to the persistent kernel of the small arrays.
 #include <cuda_runtime.h>
+#include "../../include/sz_gb300.h"
 #include "sz_codebook.cuh"
 #include "sz_encode.cuh"
 #include "sz_quant.cuh"
@@ -16,11 +17,6 @@
 namespace szg {
 
 namespace {
-
-struct MultiArgs {
-    const CompressArgs* args;   // device
-    uint32_t first;             // array of blockIdx.y == 0
-};
 
 // the block's array, staged once in shared memory
 __device__ __forceinline__ void stage_args(const MultiArgs& m, CompressArgs& sa) {
@@ -93,31 +89,18 @@ int sm_count() {
     return sms;
 }
 
-cudaError_t add_node(cudaGraph_t g, cudaGraphNode_t* node, const cudaGraphNode_t* deps, size_t ndeps, void* func,
-                     dim3 grid, dim3 block, size_t smem, MultiArgs* m) {
-    cudaKernelNodeParams kp;
-    memset(&kp, 0, sizeof(kp));
-    void* kargs[] = {m};
-    kp.func = func;
-    kp.gridDim = grid;
-    kp.blockDim = block;
-    kp.sharedMemBytes = (unsigned)smem;
-    kp.kernelParams = kargs;
-    return cudaGraphAddKernelNode(node, g, deps, ndeps, &kp);
-}
-
 }  // namespace
 
-int add_multi_compress_nodes(void* graph, void* dep, const CompressArgs* d_args, const MultiGroup* groups,
-                             int ngroups) {
+int multi_compress_launches(const CompressArgs* d_args, const MultiGroup* groups, int ngroups, KernelLaunch* out,
+                            int max_out) {
     if (ngroups <= 0) return 0;
-    cudaGraph_t g = (cudaGraph_t)graph;
-    cudaGraphNode_t d0 = (cudaGraphNode_t)dep;
+    if (max_out < 3 + ngroups) return -1;
     const uint32_t first = groups[0].first;
-    uint32_t count = 0, max_nc = 1;
+    uint32_t count = 0, max_nc = 1, maxC = 2048;
     for (int i = 0; i < ngroups; ++i) {
         count += groups[i].count;
         if (groups[i].max_chunks > max_nc) max_nc = groups[i].max_chunks;
+        if (groups[i].C > maxC) maxC = groups[i].C;
     }
     static int per_sm = 0, enc_res[2] = {0, 0};
     static bool configured = false;
@@ -137,40 +120,36 @@ int add_multi_compress_nodes(void* graph, void* dep, const CompressArgs* d_args,
         for (int j = 0; j < 2; ++j) enc_res[j] = (enc_res[j] > 0 ? enc_res[j] : 1) * sm_count();
         configured = true;
     }
-    MultiArgs all{d_args, first};
-    cudaGraphNode_t n_range, n_quant, n_cb;
-    cudaError_t e;
-    if ((e = add_node(g, &n_range, &d0, d0 ? 1 : 0, (void*)range_multi_kernel, dim3(kRangeBlocks, count), dim3(256), 0,
-                      &all)) != cudaSuccess)
-        return (int)e;
-    const uint32_t qgrid = umin32(max_nc, (uint32_t)(sm_count() * per_sm));
-    uint32_t maxC = 2048;
-    for (int i = 0; i < ngroups; ++i) maxC = groups[i].C > maxC ? groups[i].C : maxC;
-    if ((e = add_node(g, &n_quant, &n_range, 1, (void*)quant_multi_kernel, dim3(qgrid, count), dim3(kQuantThreads),
-                      quant_stage_bytes(maxC), &all)) != cudaSuccess)
-        return (int)e;
-    if ((e = add_node(g, &n_cb, &n_quant, 1, (void*)codebook_multi_kernel, dim3(1, count), dim3(kCbBlock),
-                      kCbFastBytes, &all)) != cudaSuccess)
-        return (int)e;
+    auto set = [](KernelLaunch& L, const void* f, uint32_t gx, uint32_t gy, uint32_t bx, size_t smem, int phase,
+                  const CompressArgs* args, uint32_t first) {
+        L.func = f;
+        L.grid[0] = gx; L.grid[1] = gy; L.grid[2] = 1;
+        L.block[0] = bx; L.block[1] = 1; L.block[2] = 1;
+        L.smem = smem;
+        L.phase = phase;
+        L.args = MultiArgs{args, first};
+    };
+    int k = 0;
+    set(out[k++], (const void*)range_multi_kernel, kRangeBlocks, count, 256, 0, SZ_PHASE_RANGE, d_args, first);
+    set(out[k++], (const void*)quant_multi_kernel, umin32(max_nc, (uint32_t)(sm_count() * per_sm)), count,
+        kQuantThreads, quant_stage_bytes(maxC), SZ_PHASE_QUANT, d_args, first);
+    set(out[k++], (const void*)codebook_multi_kernel, 1, count, kCbBlock, kCbFastBytes, SZ_PHASE_CODEBOOK, d_args,
+        first);
     for (int i = 0; i < ngroups; ++i) {
-        MultiArgs mg{d_args, groups[i].first};
-        cudaGraphNode_t n_enc;
         // persistent encoders: the resident blocks shared out over the group's arrays
         const int j = groups[i].C == 2048 ? 0 : 1;
-        const uint32_t per = umin32(groups[i].max_chunks ? groups[i].max_chunks : 1u,
-                                    (uint32_t)(enc_res[j] / (int)groups[i].count > 0 ? enc_res[j] / (int)groups[i].count : 1));
-        const dim3 grid(per, groups[i].count);
+        const int share = enc_res[j] / (int)groups[i].count;
+        const uint32_t per = umin32(groups[i].max_chunks ? groups[i].max_chunks : 1u, (uint32_t)(share > 0 ? share : 1));
         if (groups[i].C == 2048)
-            e = add_node(g, &n_enc, &n_cb, 1, (void*)encode_multi_kernel<2048>, grid,
-                         dim3(EncShape<2048>::kThreads), kEncSmem2048, &mg);
+            set(out[k++], (const void*)encode_multi_kernel<2048>, per, groups[i].count, EncShape<2048>::kThreads,
+                kEncSmem2048, SZ_PHASE_ENCODE, d_args, groups[i].first);
         else if (groups[i].C == 4096)
-            e = add_node(g, &n_enc, &n_cb, 1, (void*)encode_multi_kernel<4096>, grid,
-                         dim3(EncShape<4096>::kThreads), kEncSmem4096, &mg);
+            set(out[k++], (const void*)encode_multi_kernel<4096>, per, groups[i].count, EncShape<4096>::kThreads,
+                kEncSmem4096, SZ_PHASE_ENCODE, d_args, groups[i].first);
         else
-            return (int)cudaErrorInvalidValue;
-        if (e != cudaSuccess) return (int)e;
+            return -1;
     }
-    return 0;
+    return k;
 }
 
 }  // namespace szg

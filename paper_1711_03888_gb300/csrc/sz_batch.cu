@@ -236,8 +236,25 @@ sz_status batch_compress(sz_ctx* ctx, int k, const float* const* d_in, const siz
         }
         deps[0] = n_copy;
         deps[1] = n_reset;
-        if ((ks && cudaGraphAddKernelNode(&n_kern, g, deps, 2, &kp) != cudaSuccess) ||
-            add_multi_compress_nodes(g, n_copy, plan.args, groups.data(), (int)groups.size()) != 0 ||
+        KernelLaunch ml[8];
+        const int nml = multi_compress_launches(plan.args, groups.data(), (int)groups.size(), ml, 8);
+        bool nodes_ok = nml >= 0;
+        cudaGraphNode_t prev = n_copy;
+        for (int i = 0; nodes_ok && i < nml; ++i) {
+            // range -> quantize -> codebook in a chain; the encoders after the codebook
+            cudaKernelNodeParams mp;
+            memset(&mp, 0, sizeof(mp));
+            void* margs[] = {&ml[i].args};
+            mp.func = const_cast<void*>(ml[i].func);
+            mp.gridDim = dim3(ml[i].grid[0], ml[i].grid[1], ml[i].grid[2]);
+            mp.blockDim = dim3(ml[i].block[0], ml[i].block[1], ml[i].block[2]);
+            mp.sharedMemBytes = (unsigned)ml[i].smem;
+            mp.kernelParams = margs;
+            cudaGraphNode_t node;
+            nodes_ok = cudaGraphAddKernelNode(&node, g, &prev, 1, &mp) == cudaSuccess;
+            if (i < 3) prev = node;
+        }
+        if (!nodes_ok || (ks && cudaGraphAddKernelNode(&n_kern, g, deps, 2, &kp) != cudaSuccess) ||
             cudaGraphInstantiate(&ctx->bg_exec, g, 0) != cudaSuccess) {
             cudaGetLastError();
             cudaGraphDestroy(g);
@@ -247,9 +264,44 @@ sz_status batch_compress(sz_ctx* ctx, int k, const float* const* d_in, const siz
         ctx->bg_graph = g;
         ctx->bg_key = key;
     }
-    {
-        ProfScope pr(ctx, SZ_PHASE_BATCH, s);
+    if (!ctx->prof_on) {
         if (cudaGraphLaunch(ctx->bg_exec, s) != cudaSuccess) { cudaGetLastError(); return SZ_ERR_CUDA; }
+    } else {
+        // tracing: the graph's work as direct launches (same kernels, same
+        // order) with an event pair around each, so each kernel is timed
+        uint8_t* hp = ctx->batch_host;
+        if (cudaMemcpyAsync(base, hp, plan_bytes, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemsetAsync(base + o_cnt, 0, cnt_bytes, s) != cudaSuccess) {
+            cudaGetLastError();
+            return SZ_ERR_CUDA;
+        }
+        if (ks) {
+            BatchPlan plan;
+            plan.args = (const CompressArgs*)(base + o_args);
+            plan.cnt = (BatchCounters*)(base + o_cnt);
+            plan.range_tiles = (const uint32_t*)(base + o_tiles);
+            plan.quant_groups = (const uint32_t*)(base + o_groups);
+            plan.item_off = (const uint32_t*)(base + o_off);
+            plan.k = ks;
+            plan.next = (uint32_t*)(base + o_cnt + sizeof(BatchCounters) * ks);
+            plan.err = ctx->d_err;
+            ProfScope pr(ctx, SZ_PHASE_BATCH, s);
+            launch_batch_compress(plan, s);
+        }
+        KernelLaunch ml[8];
+        const int nml = multi_compress_launches((const CompressArgs*)(base + o_args), groups.data(), (int)groups.size(),
+                                                ml, 8);
+        if (nml < 0) return SZ_ERR_ARG;
+        for (int i = 0; i < nml; ++i) {
+            ProfScope pr(ctx, ml[i].phase, s);
+            void* margs[] = {&ml[i].args};
+            if (cudaLaunchKernel(ml[i].func, dim3(ml[i].grid[0], ml[i].grid[1], ml[i].grid[2]),
+                                 dim3(ml[i].block[0], ml[i].block[1], ml[i].block[2]), margs, ml[i].smem,
+                                 s) != cudaSuccess) {
+                cudaGetLastError();
+                return SZ_ERR_CUDA;
+            }
+        }
     }
     if (cudaEventRecord(ctx->bg_done, s) != cudaSuccess) { cudaGetLastError(); return SZ_ERR_CUDA; }
     if (out_bytes)

@@ -156,6 +156,7 @@ struct BatchPlan {
     uint32_t* err;
 };
 void launch_batch_compress(const BatchPlan& plan, void* stream);
+void batch_compress_config(void** func, unsigned* grid, unsigned* block, size_t* smem);
 
 // Large arrays of a batch: one launch per phase over args[first .. first+count)
 // of every group (the groups are contiguous; a group's arrays share C).
@@ -165,11 +166,21 @@ struct MultiGroup {
     uint32_t C;                 // their chunk size (2048 or 4096)
     uint32_t max_chunks;        // largest chunk count among them
 };
-// Adds the four phase nodes to the CUDA graph `graph` after node `dep` (may be
-// null); returns 0 or a CUDA error code.
-int add_multi_compress_nodes(void* graph, void* dep, const CompressArgs* d_args, const MultiGroup* groups,
-                             int ngroups);
-void batch_compress_config(void** func, unsigned* grid, unsigned* block, size_t* smem);
+struct MultiArgs {              // parameter of the per-phase kernels
+    const CompressArgs* args;   // device
+    uint32_t first;             // array of blockIdx.y == 0
+};
+struct KernelLaunch {           // one launch, for a graph node or a direct launch
+    const void* func;
+    unsigned grid[3], block[3];
+    size_t smem;
+    int phase;                  // tracing phase (sz_phase)
+    MultiArgs args;
+};
+// Fills out[] with the per-phase launches (range, quantize, codebook, one
+// encode per group), in dependency order; returns their count or -1.
+int multi_compress_launches(const CompressArgs* d_args, const MultiGroup* groups, int ngroups, KernelLaunch* out,
+                            int max_out);
 
 // MD reordering (Sec. IV-B)
 struct ReorderArgs {
