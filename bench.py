@@ -64,8 +64,13 @@ class ClockSampler:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
+            # wait (up to 5 s) for the first sample, so the sampler is live
+            # before the region it is meant to cover
+            t0 = time.time()
+            while time.time() - t0 < 5.0 and os.path.getsize(self.path) == 0:
+                time.sleep(0.02)
         except Exception:
             self.proc = None
 
@@ -270,6 +275,53 @@ def batched_bench(sz, device, steps):
 
 
 # ---------------------------------------------------------------------------
+# Molecular-dynamics snapshot: the three position arrays, with and without the
+# R-index reordering (Sec. IV-B; Tables 4-5)
+# ---------------------------------------------------------------------------
+
+def md_bench(sz, device, steps):
+    """FCC crystal of 100^3 cells (3.92 M atoms after 2 % vacancies, 10 %
+    swapped), xx/yy/zz: best_speed (SZ-LV in stored order) against best_tradeoff
+    (SZ-LV-PRX: segment 16384, p = 6 ignored digits, and p = 0 = full radix
+    sort), at rel eb 1e-4 and 1e-3.  Compression GB/s of the three arrays
+    (reordering included) and the ratio; CUDA events on the stream."""
+    import torch
+    import synth
+    md = synth.md_fcc(device="cuda")
+    xs = [md[f] for f in ("xx", "yy", "zz")]
+    n = xs[0].numel()
+    nbytes = 4 * n * len(xs)
+    ctx = sz.Context(device)
+    fields = [sz.SZ_FIELD_XX, sz.SZ_FIELD_YY, sz.SZ_FIELD_ZZ]
+    stream = torch.cuda.current_stream()
+    out = {"workload": f"MD snapshot: FCC crystal 100^3 cells, {n} atoms, 3 float32 position arrays",
+           "atoms": n, "modes": {}}
+    for eb in (1e-4, 1e-3):
+        for name, mode, p in (("best_speed LV", sz.SZ_MODE_LV, None), ("best_tradeoff LV-PRX p=6", sz.SZ_MODE_LV_PRX, 6),
+                              ("LV-RX (p=0)", sz.SZ_MODE_LV_PRX, 0)):
+            params = sz._params(0, 0, 16384, p) if p is not None else None
+
+            def run():
+                return sz.sz_compress_snapshot(ctx, fields, xs, n, [eb] * 3, sz.SZ_EB_REL, mode, params)
+
+            for _ in range(2):
+                outs, nb = run()
+                sz.sz_sync(ctx)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            for a, b in ev:
+                a.record(stream)
+                outs, nb = run()
+                b.record(stream)
+            sz.sz_sync(ctx)
+            torch.cuda.synchronize()
+            t = sum(a.elapsed_time(b) for a, b in ev) / steps / 1e3
+            out["modes"][f"{name} @ {eb:g}"] = {"compress_gbs": nbytes / t / 1e9, "ms": 1e3 * t,
+                                               "ratio": nbytes / sum(int(nb[i]) for i in range(3))}
+    ctx.close()
+    return out
+
+
+# ---------------------------------------------------------------------------
 # Served form: Poisson arrivals of compress / decompress requests
 # ---------------------------------------------------------------------------
 
@@ -430,7 +482,7 @@ def served_bench(sz, snap, eb, rate, seconds, stress, stress_seconds, slots, bud
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--log2n", type=int, default=27)
@@ -440,6 +492,7 @@ def main():
     ap.add_argument("--cpu-log2n", type=int, default=24)
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-md", action="store_true")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--serve-stress", type=float, default=10.0)
@@ -528,13 +581,13 @@ def main():
         assert err <= args.eb * R * (1 + 1e-12), f"error bound violated: {err} > {args.eb * R}"
     ratio = raw_bytes / sum(sizes)
 
+    clocks = ClockSampler(local)
+    clocks.start()            # sampling from the warm-up through the timed region
     for _ in range(args.warmup):
         step()
         sz.sz_sync(ctx)
     torch.cuda.synchronize()
     _barrier(ws)
-    clocks = ClockSampler(local)
-    clocks.start()
     sz.sz_profile_enable(ctx, True)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
            torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -690,6 +743,11 @@ def main():
     if rank == 0 and not args.no_batched:
         batched = batched_bench(sz, local, args.steps)
 
+    # ---- MD snapshot (rank 0): reordering modes ---------------------------------
+    md = None
+    if rank == 0 and not args.no_md:
+        md = md_bench(sz, local, args.steps)
+
     # ---- served form (rank 0): Poisson arrivals vs the same requests serially --
     served = None
     if rank == 0 and not args.no_serve:
@@ -715,7 +773,7 @@ def main():
             "compress_frac_hbm": comp_gbs / peak, "decompress_frac_hbm": decomp_gbs / peak,
             "ratio": ratio, "roofline": roofline, "kernels": kernels, "kernels_plain_path": kernels_plain,
             "gpu_launches": launches,
-            "plain_path": plain, "batched": batched, "served": served,
+            "plain_path": plain, "batched": batched, "md": md, "served": served,
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "wall_s_timed": t_wall,
         }
         print(json.dumps(line))
