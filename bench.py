@@ -48,33 +48,78 @@ def _peaks():
 
 
 class ClockSampler:
-    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    """SM clock and clock-event reasons during a region, read (never set)
+    through NVML by a sampling thread every 5 ms; nvidia-smi if NVML cannot be
+    loaded."""
 
+    # nvmlClocksEventReasons bits
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+               0x80: "hw_power_brake_slowdown"}
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index: int):
         self.index = index
+        self.samples = []
+        self.reasons = set()
+        self.max_mhz = None
+        self.stop_flag = threading.Event()
+        self.thread = None
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def _nvml(self):
+        import ctypes as C
+        lib = C.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit")
+        h = C.c_void_p()
+        if lib.nvmlDeviceGetHandleByIndex_v2(self.index, C.byref(h)) != 0:
+            raise OSError("nvml handle")
+        mx = C.c_uint(0)
+        if lib.nvmlDeviceGetMaxClockInfo(h, 1, C.byref(mx)) == 0:     # NVML_CLOCK_SM
+            self.max_mhz = float(mx.value)
+        get_reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        return lib, h, get_reasons
+
+    def _loop(self, lib, h, get_reasons):
+        import ctypes as C
+        clk, rs = C.c_uint(0), C.c_ulonglong(0)
+        while not self.stop_flag.is_set():
+            if lib.nvmlDeviceGetClockInfo(h, 1, C.byref(clk)) == 0:
+                self.samples.append(float(clk.value))
+            if get_reasons(h, C.byref(rs)) == 0:
+                for bit, name in self.REASONS.items():
+                    if rs.value & bit:
+                        self.reasons.add(name)
+            time.sleep(0.005)
 
     def start(self):
         try:
+            lib, h, get_reasons = self._nvml()
+            self.thread = threading.Thread(target=self._loop, args=(lib, h, get_reasons), daemon=True)
+            self.thread.start()
+            return
+        except Exception:
+            self.thread = None
+        try:
+            self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
                                           "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
-            # wait (up to 5 s) for the first sample, so the sampler is live
-            # before the region it is meant to cover
-            t0 = time.time()
-            while time.time() - t0 < 5.0 and os.path.getsize(self.path) == 0:
-                time.sleep(0.02)
         except Exception:
             self.proc = None
 
     def stop(self):
+        if self.thread is not None:
+            self.stop_flag.set()
+            self.thread.join(timeout=5)
+            sm = sorted(self.samples)
+            return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": self.max_mhz,
+                    "reasons": sorted(self.reasons), "samples": len(sm), "source": "nvml"}
         if not self.proc:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
         self.proc.terminate()
@@ -99,7 +144,8 @@ class ClockSampler:
                     reasons.add(nm)
         sm.sort()
         med = sm[len(sm) // 2] if sm else None
-        return {"sm_mhz": med, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+        return {"sm_mhz": med, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm),
+                "source": "nvidia-smi"}
 
 
 def _dist():

@@ -61,16 +61,24 @@ sz_status batch_compress(sz_ctx* ctx, int k, const float* const* d_in, const siz
     }
     const uint32_t kb = (uint32_t)batched.size();
     if (kb == 0) return SZ_OK;
-    // small arrays first (the persistent kernel's), then large ones grouped by C
+    // Small arrays first (the persistent kernel's), then the others grouped by
+    // C (the per-phase launches').  A few small arrays are latency-bound by
+    // their codebooks, so they take the per-phase launches too (1024-thread
+    // codebooks side by side); many small arrays keep the persistent kernel,
+    // where their codebook items overlap the other arrays' work.
+    uint32_t ks = 0;
     {
         std::vector<int> small, large;
         for (int i : batched) (n[i] < kBatchLargeElems ? small : large).push_back(i);
+        if (small.size() <= kBatchFewSmall) {
+            large.insert(large.begin(), small.begin(), small.end());
+            small.clear();
+        }
         std::stable_sort(large.begin(), large.end(), [&](int x, int y) { return Cs[x] < Cs[y]; });
+        ks = (uint32_t)small.size();
         batched = small;
         batched.insert(batched.end(), large.begin(), large.end());
     }
-    uint32_t ks = 0;
-    while (ks < kb && n[batched[ks]] < kBatchLargeElems) ++ks;
     std::vector<MultiGroup> groups;
     for (uint32_t j = ks; j < kb; ++j) {
         const int i = batched[j];

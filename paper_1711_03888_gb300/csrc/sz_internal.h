@@ -161,6 +161,7 @@ void batch_compress_config(void** func, unsigned* grid, unsigned* block, size_t*
 // Large arrays of a batch: one launch per phase over args[first .. first+count)
 // of every group (the groups are contiguous; a group's arrays share C).
 constexpr uint64_t kBatchLargeElems = 1ull << 22;
+constexpr uint32_t kBatchFewSmall = 304;   // at most this many small arrays: per-phase launches for all
 struct MultiGroup {
     uint32_t first, count;      // arrays args[first .. first+count)
     uint32_t C;                 // their chunk size (2048 or 4096)
