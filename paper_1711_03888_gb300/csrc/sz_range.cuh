@@ -1,6 +1,6 @@
 // sz_range.cuh -- a1 body: value range of the finite elements of one array
 // (Sec. III, "value-range-based relative error bound": eb_abs = eb_rel *
-// (max - min)).  Block `bid` of `nblocks` takes a grid-stride share with two
+// (max - min)).  Block `bid` of `nblocks` takes a grid-stride share with four
 // float4 loads in flight per thread; per-block min/max keys go to device
 // atomics and the array's last block publishes the result and re-arms the
 // accumulators.  The same blocks zero the array's code histogram.
@@ -27,19 +27,23 @@ __device__ __forceinline__ void range_body(const CompressArgs& a, uint32_t bid, 
         if (((uintptr_t)in & 15u) == 0) {
             const float4* v4 = reinterpret_cast<const float4*>(in);
             const uint64_t n4 = n >> 2;
-            // two 16-byte loads in flight per thread
-            for (uint64_t i = gtid; i < n4; i += 2 * gstride) {
-                float4 va = __ldg(v4 + i);
-                float4 vb = (i + gstride < n4) ? __ldg(v4 + i + gstride) : va;
-                float e[8] = {va.x, va.y, va.z, va.w, vb.x, vb.y, vb.z, vb.w};
+            // four 16-byte loads in flight per thread
+            for (uint64_t i = gtid; i < n4; i += 4 * gstride) {
+                float4 v[4];
 #pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    if (finite_f(e[j])) {
-                        uint32_t k = float_key(e[j]);
-                        kmin = min(kmin, k);
-                        kmax = max(kmax, k);
-                        any = 1u;
-                    }
+                for (int u = 0; u < 4; ++u) v[u] = (i + u * gstride < n4) ? __ldg(v4 + i + u * gstride) : __ldg(v4 + i);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const float e[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (finite_f(e[j])) {
+                            uint32_t k = float_key(e[j]);
+                            kmin = min(kmin, k);
+                            kmax = max(kmax, k);
+                            any = 1u;
+                        }
+                }
             }
             head = n4 << 2;
         }

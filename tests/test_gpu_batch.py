@@ -186,3 +186,25 @@ def test_batch_decompress_mixed_streams(sz, ctx, oracle):
             continue
         assert no2[i] == x.numel()
         assert ys2[i][: x.numel()].cpu().numpy().tobytes() == expect[i], i
+
+
+def test_batch_traced_direct_launches_equal_graph(sz, ctx):
+    """With tracing on, the batched form launches its graph's kernels directly
+    (for per-kernel timing); streams and results equal the graph replay's."""
+    snap = synth.cosmology((1 << 22) + 3, 64, 31, device="cuda")
+    xs = [snap["xx"], snap["vy"], synth.random_walk_f32(5000, 3).cuda(), snap["zz"][: 1 << 20].contiguous()]
+    ebs = [1e-4, 1e-3, 1e-4, 1e-4]
+    outs, nb = sz.sz_compress_batch(ctx, xs, ebs, sz.SZ_EB_REL)
+    sz.sz_sync(ctx)
+    ref = [outs[i][: nb[i]].cpu().numpy().tobytes() for i in range(len(xs))]
+    sz.sz_profile_enable(ctx, True)
+    try:
+        outs2, nb2 = sz.sz_compress_batch(ctx, xs, ebs, sz.SZ_EB_REL)
+        sz.sz_sync(ctx)
+        prof = sz.sz_profile_read(ctx)
+    finally:
+        sz.sz_profile_enable(ctx, False)
+    got = [outs2[i][: nb2[i]].cpu().numpy().tobytes() for i in range(len(xs))]
+    assert got == ref
+    assert prof["range"][0] >= 1 and prof["encode"][0] >= 1      # per-phase launches were timed
+    assert ref[2] == _plain(sz, ctx, xs[2], ebs[2], sz.SZ_EB_REL)
