@@ -175,6 +175,19 @@ __device__ void codebook_body(const CompressArgs& a, CbSmem<NT>& sm, uint32_t* f
         __syncthreads();
     }
     const uint32_t m = sm.m;
+    // A non-raw array of n > 0 elements always has a used symbol.  An empty
+    // histogram would leave the tree without a root: report it and write
+    // nothing (the encoder then finds no layout to fill).
+    if (m == 0) {
+        if (tid == 0) {
+            raise_err(a.err, E_INTERNAL);
+            st->raw = 1u;                        // the encoders' raw copy then finds no room and writes nothing
+            st->total_bytes = a.out_cap + 1;
+            st->ticket = 0u;
+            for (int s2 = 0; s2 < 8; ++s2) st->off[s2] = a.out_cap + 1;
+        }
+        return;
+    }
 
     // -------- 2-4. Huffman lengths with the length limit ------------------------
     if (m == 1) {
