@@ -736,7 +736,9 @@ def main():
                 "traffic": _traffic(kname),
                 "algorithmic_bytes_per_launch": abytes,
                 "timing": "CUDA events around each launch on its stream, inside the timed region"}
-    launches = sum(c for c, _ in prof.values())
+    # kernels launched in the timed region: one per traced launch, plus the
+    # batched decoder's unit scan, which shares the setup phase's event pair
+    launches = sum(c for c, _ in prof.values()) + prof.get("decode_setup", (0, 0.0))[0]
 
     # ---- end to end through host buffers ------------------------------------
     e2e = None
