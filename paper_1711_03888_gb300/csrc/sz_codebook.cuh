@@ -35,8 +35,7 @@ constexpr size_t SC_KA = SC_WRK + 65536;
 constexpr size_t SC_VA = SC_KA + 65536;
 constexpr size_t SC_KB = SC_VA + 65536;
 constexpr size_t SC_VB = SC_KB + 65536;
-constexpr size_t SC_WI = SC_VB + 65536;
-constexpr size_t SC_LEN = SC_WI + 65536;
+constexpr size_t SC_LEN = SC_VB + 65536;
 constexpr size_t SC_PAR = SC_LEN + 65536;
 constexpr size_t SC_DA = SC_PAR + 131072;
 constexpr size_t SC_JA = SC_DA + 131072;
