@@ -115,7 +115,8 @@ struct DecompressArgs {
     uint32_t grid_div;          // the decode launch uses 1/grid_div of the SMs (0, 1: all)
 };
 
-// codebook scratch: 9 arrays of 65536 words and 5 of 131072 (see k_codebook.cu)
+// codebook scratch: 8 arrays of 65536 words and 5 of 131072 (layout in
+// sz_codebook.cuh), rounded up; the decoder's setup uses the first 4 x 65536
 constexpr size_t kCbScratchWords = 65536u * 20u;
 
 // ---- host-side launchers (defined in the kernel files) ----
