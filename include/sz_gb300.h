@@ -129,6 +129,36 @@ sz_status sz_compress_batch(sz_ctx* ctx, int k, const float* const* d_in, const 
 sz_status sz_decompress_batch(sz_ctx* ctx, int k, const void* const* d_in, const size_t* in_bytes,
                               float* const* d_out, const size_t* n_cap, size_t* n_out, void* stream);
 
+/* Host-memory forms (Sec. I / Sec. III: in-situ compression of the arrays a
+ * simulation holds in its own memory).  Same arguments as the batch calls,
+ * but every data pointer (h_in, h_out) is HOST memory that the caller owns;
+ * page-locked memory (cudaHostAlloc / cudaHostRegister) lets the copies run
+ * asynchronously, pageable memory works but serializes them with the host.
+ * The library stages the arrays through device memory of its own (two slots
+ * of groups of consecutive arrays, each group at least 64 MiB of input):
+ * copy-in of one group, the kernels of the previous one and the copy-out of
+ * the one before run concurrently on two internal copy streams and `stream`.
+ * Each stream (compress) and each array (decompress) is byte-identical to
+ * sz_compress / sz_decompress of the same data.
+ *
+ * Both calls are SYNCHRONOUS: they return when every output is in host
+ * memory, ending with sz_sync(ctx, stream) (which also delivers results of
+ * earlier calls on `stream`) and returning its status.
+ *
+ * sz_compress_host: out_bytes[i] = stream size; when it exceeds out_cap[i]
+ *   nothing is written to h_out[i] and the call returns SZ_ERR_CAPACITY.
+ * sz_decompress_host: n_out[i] = element count from the stream's header;
+ *   a stream of more than n_cap[i] elements writes nothing to h_out[i] and
+ *   the call returns SZ_ERR_CAPACITY; a malformed stream returns
+ *   SZ_ERR_CORRUPT (outputs of the call then undefined).
+ * Errors: SZ_ERR_ARG (NULL arrays, bad bound, n >= 2^32), SZ_ERR_NOMEM
+ * (staging), SZ_ERR_CUDA, and the device errors of sz_sync. */
+sz_status sz_compress_host(sz_ctx* ctx, int k, const float* const* h_in, const size_t* n, const double* eb,
+                           sz_eb_kind kind, const sz_params* params, void* const* h_out,
+                           const size_t* out_cap, size_t* out_bytes, void* stream);
+sz_status sz_decompress_host(sz_ctx* ctx, int k, const void* const* h_in, const size_t* in_bytes,
+                             float* const* h_out, const size_t* n_cap, size_t* n_out, void* stream);
+
 /* Molecular-dynamics snapshot (Sec. IV-B).  fields[0..2] must be XX, YY, ZZ;
  * further fields (velocities) follow the same reordering.  mode SZ_MODE_LV
  * compresses each field in stored order; SZ_MODE_LV_PRX first reorders every

@@ -32,7 +32,7 @@ SZ_OP_COMPRESS, SZ_OP_DECOMPRESS = 0, 1
 HEADER_BYTES = 160
 
 EXPORTS = ("sz_ctx_create", "sz_ctx_destroy", "sz_max_compressed_bytes", "sz_compress", "sz_decompress",
-           "sz_compress_batch", "sz_decompress_batch", "sz_compress_snapshot", "sz_sync", "sz_status_string",
+           "sz_compress_batch", "sz_decompress_batch", "sz_compress_host", "sz_decompress_host", "sz_compress_snapshot", "sz_sync", "sz_status_string",
            "sz_profile_enable", "sz_profile_read", "sz_compress_noalloc",
            "sz_serve_start", "sz_serve_submit", "sz_serve_poll", "sz_serve_wait", "sz_serve_release",
            "sz_serve_stats", "sz_serve_stop")
@@ -70,6 +70,10 @@ _sig = {
                                 C.POINTER(sz_params), C.POINTER(_vp), C.POINTER(_sz), C.POINTER(_sz), _vp]),
     "sz_decompress_batch": (_st, [_vp, C.c_int, C.POINTER(_vp), C.POINTER(_sz), C.POINTER(_vp), C.POINTER(_sz),
                                   C.POINTER(_sz), _vp]),
+    "sz_compress_host": (_st, [_vp, C.c_int, C.POINTER(_vp), C.POINTER(_sz), C.POINTER(C.c_double), C.c_int,
+                               C.POINTER(sz_params), C.POINTER(_vp), C.POINTER(_sz), C.POINTER(_sz), _vp]),
+    "sz_decompress_host": (_st, [_vp, C.c_int, C.POINTER(_vp), C.POINTER(_sz), C.POINTER(_vp), C.POINTER(_sz),
+                                 C.POINTER(_sz), _vp]),
     "sz_compress_snapshot": (_st, [_vp, C.c_int, C.POINTER(C.c_int), C.POINTER(_vp), _sz, C.POINTER(C.c_double),
                                    C.c_int, C.c_int, C.POINTER(sz_params), C.POINTER(_vp), C.POINTER(_sz),
                                    C.POINTER(_sz), _vp, _vp]),
@@ -210,6 +214,42 @@ def sz_decompress_batch(ctx: Context, streams, in_bytes, outs, stream=None):
     no = ctx.hold((C.c_size_t * k)())
     _check(_lib.sz_decompress_batch(ctx.handle, k, ins, ib, o, caps, no, _stream(stream)), "sz_decompress_batch")
     return no
+
+
+def sz_compress_host(ctx: Context, xs, ebs, kind: int = SZ_EB_REL, params=None, outs=None, stream=None,
+                     check: bool = True):
+    """Host tensors in, host streams out (synchronous).  Returns (status,
+    outs, sizes); raises on failure when `check`."""
+    import torch
+    k = len(xs)
+    if outs is None:
+        outs = [torch.empty(sz_max_compressed_bytes(x.numel()), dtype=torch.uint8).pin_memory() for x in xs]
+    ins = (C.c_void_p * k)(*[_ptr(x) for x in xs])
+    ns = (C.c_size_t * k)(*[x.numel() for x in xs])
+    e = (C.c_double * k)(*ebs)
+    o = (C.c_void_p * k)(*[_ptr(t) for t in outs])
+    caps = (C.c_size_t * k)(*[t.numel() for t in outs])
+    nb = (C.c_size_t * k)()
+    p = params if params is not None else _params()
+    st = _lib.sz_compress_host(ctx.handle, k, ins, ns, e, kind, C.byref(p), o, caps, nb, _stream(stream))
+    if check:
+        _check(st, "sz_compress_host")
+    return st, outs, [int(v) for v in nb]
+
+
+def sz_decompress_host(ctx: Context, streams, in_bytes, outs, stream=None, check: bool = True):
+    """Host streams in, host float32 tensors out (synchronous).  Returns
+    (status, element counts); raises on failure when `check`."""
+    k = len(streams)
+    ins = (C.c_void_p * k)(*[_ptr(s) for s in streams])
+    ib = (C.c_size_t * k)(*in_bytes)
+    o = (C.c_void_p * k)(*[_ptr(t) for t in outs])
+    caps = (C.c_size_t * k)(*[t.numel() for t in outs])
+    no = (C.c_size_t * k)()
+    st = _lib.sz_decompress_host(ctx.handle, k, ins, ib, o, caps, no, _stream(stream))
+    if check:
+        _check(st, "sz_decompress_host")
+    return st, [int(v) for v in no]
 
 
 def sz_compress_snapshot(ctx: Context, fields, xs, n: int, ebs, kind: int = SZ_EB_REL, mode: int = SZ_MODE_LV_PRX,

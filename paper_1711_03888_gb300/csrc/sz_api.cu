@@ -231,6 +231,7 @@ sz_status sz_ctx_destroy(sz_ctx* ctx) {
     cudaDeviceSynchronize();
     ctx->free_workspace();
     ctx->free_extra();
+    ctx->free_host();
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
     if (ctx->d_err) cudaFree(ctx->d_err);
     if (ctx->h_res) cudaFreeHost(ctx->h_res);

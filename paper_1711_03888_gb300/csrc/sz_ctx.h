@@ -55,6 +55,14 @@ struct sz_ctx {
     uint8_t* dbatch_host = nullptr;
     size_t dbatch_host_bytes = 0;
     cudaEvent_t dbatch_done = nullptr;
+    // host-memory calls: copy streams, per-slot events (copy-in done, kernels
+    // done, copy-out done), device staging and pinned per-array results
+    cudaStream_t host_h2d = nullptr, host_d2h = nullptr;
+    cudaEvent_t host_ev[2][3] = {};
+    uint8_t* host_pool = nullptr;
+    size_t host_pool_bytes = 0;
+    uint64_t* host_pin = nullptr;
+    size_t host_pin_cap = 0;
     // serving loop
     sz_serve_state* serve = nullptr;
     // tracing: event pairs around launches
@@ -66,6 +74,7 @@ struct sz_ctx {
 
     void free_workspace();
     void free_extra();
+    void free_host();
 };
 
 namespace szg {
