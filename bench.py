@@ -198,6 +198,39 @@ def weak_scaling_value(bytes_per_rank: float, seconds_per_step: float, ws: int):
     return b / t / 1e9, t, b
 
 
+def link_rates(hx, hy):
+    """Host<->device copy rates of the pinned buffers the end-to-end leg uses
+    (plain copies, one direction at a time and both at once): the ceiling of
+    that leg.  GB/s."""
+    import torch
+    d = [torch.empty_like(x, device="cuda") for x in hx]
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    nb = sum(4 * x.numel() for x in hx)
+
+    def h2d():
+        with torch.cuda.stream(s1):
+            for a, b in zip(hx, d):
+                b.copy_(a, non_blocking=True)
+
+    def d2h():
+        with torch.cuda.stream(s2):
+            for a, b in zip(d, hy):
+                b.copy_(a, non_blocking=True)
+
+    def timed(f):
+        f()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        f()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0
+
+    t_in, t_out = timed(h2d), timed(d2h)
+    t_both = timed(lambda: (h2d(), d2h()))
+    del d
+    return {"h2d_gbs": nb / t_in / 1e9, "d2h_gbs": nb / t_out / 1e9, "both_gbs": 2 * nb / t_both / 1e9}
+
+
 def _traffic(kernel: str):
     """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if the
     kernel source is unchanged since the capture; else None."""
@@ -769,7 +802,7 @@ def main():
         te = _max_over_ranks((time.perf_counter() - t0) / k2, ws)
         assert np.array_equal(hy[0][: 1 << 16].numpy().view(np.uint32), ys[0][: 1 << 16].cpu().numpy().view(np.uint32))
         e2e = {"value": total_bytes / te / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-               "ms_per_step": 1e3 * te}
+               "ms_per_step": 1e3 * te, "link": link_rates(hx, hy)}
         del hx, hs, hy
 
     # ---- batched form (rank 0): 768 uneven arrays, one graph vs 768 calls --------
