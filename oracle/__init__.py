@@ -31,6 +31,7 @@ _lib = None
 OK, ERR_ARG, ERR_NOMEM, ERR_CAPACITY, ERR_CORRUPT = 0, 1, 2, 3, 4
 HEADER_BYTES = 160
 FLAG_RAW, FLAG_REORDERED = 1, 2
+PRED_LV, PRED_LCF = 1, 2          # header byte 43
 
 
 def build(force: bool = False) -> str:
@@ -68,8 +69,13 @@ def lib():
         L.szo_canonical_codes.argtypes = [vp, C.c_uint32, vp]
         L.szo_max_bytes.restype = u64
         L.szo_max_bytes.argtypes = [u64]
+        L.szo_codes_lcf.restype = None
+        L.szo_codes_lcf.argtypes = [vp, vp, u64, vp, vp]
         L.szo_compress.restype = i32
         L.szo_compress.argtypes = [vp, u64, dbl, i32, C.c_uint32, C.c_uint32, C.c_uint32, vp, u64, vp]
+        L.szo_compress_pred.restype = i32
+        L.szo_compress_pred.argtypes = [vp, u64, dbl, i32, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32,
+                                        vp, u64, vp]
         L.szo_stream_n.restype = i32
         L.szo_stream_n.argtypes = [vp, u64, vp]
         L.szo_decompress.restype = i32
@@ -145,6 +151,16 @@ def codes(q, verbatim):
     return c, d
 
 
+def codes_lcf(q, verbatim):
+    """Second-difference (LCF) codes on the lattice: delta_i = q_i - 2 q_{i-1} + q_{i-2}."""
+    q = np.ascontiguousarray(q, np.int64)
+    v = np.ascontiguousarray(verbatim, np.uint8)
+    c = np.zeros(q.size, np.uint16)
+    d = np.zeros(q.size, np.int64)
+    lib().szo_codes_lcf(_p(q), _p(v), q.size, _p(c), _p(d))
+    return c, d
+
+
 def huffman_lengths(freq, sym=None) -> np.ndarray:
     """Code lengths for used symbols (ascending symbol order) with their counts."""
     f = np.ascontiguousarray(freq, np.uint64)
@@ -167,14 +183,16 @@ def max_bytes(n: int) -> int:
     return int(lib().szo_max_bytes(n))
 
 
-def compress(x, eb: float, kind: int = 1, chunk: int = 8192, sub: int = 128, reordered: bool = False) -> bytes:
-    """Compress one float32 array; returns the stream bytes."""
+def compress(x, eb: float, kind: int = 1, chunk: int = 8192, sub: int = 128, reordered: bool = False,
+             pred: int = PRED_LV) -> bytes:
+    """Compress one float32 array; returns the stream bytes.  pred: PRED_LV
+    (Sec. IV-A last value) or PRED_LCF (the original SZ's curve fitting)."""
     x = _f32(x)
     cap = max_bytes(x.size)
     out = np.zeros(cap, np.uint8)
     nb = C.c_uint64()
-    rc = lib().szo_compress(_p(x), x.size, eb, kind, chunk, sub, FLAG_REORDERED if reordered else 0,
-                            _p(out), cap, C.byref(nb))
+    rc = lib().szo_compress_pred(_p(x), x.size, eb, kind, chunk, sub, FLAG_REORDERED if reordered else 0,
+                                 pred, _p(out), cap, C.byref(nb))
     if rc:
         raise OracleError(rc, "compress")
     return out[: nb.value].tobytes()

@@ -19,7 +19,9 @@
  *                         dividing by the error bound); the lattice step is
  *                         2*eb so the rounding error stays within eb.
  *   prediction .......... Sec. IV-A, last-value (LV) model: pred_i = x_{i-1},
- *                         applied on the integer lattice.
+ *                         applied on the integer lattice; and the original
+ *                         SZ's linear-curve-fitting (LCF) model,
+ *                         pred_i = 2 x_{i-1} - x_{i-2}, on the same lattice.
  *   quantization ........ Sec. IV-A: linear-scaling quantization with a very
  *                         large number of intervals (2^16 here, radius 32768);
  *                         values outside are stored aside (escapes).
@@ -45,6 +47,8 @@
 #define O_FLAG_RAW        1u
 #define O_FLAG_REORDERED  2u
 #define O_ESC_BYTES    16u
+#define O_PRED_LV      1u            /* header byte 43: predictor */
+#define O_PRED_LCF     2u
 
 /* return codes (mirrors the meaning of the C-ABI status values) */
 #define SZO_OK       0
@@ -144,6 +148,22 @@ void szo_codes(const int64_t* q, const uint8_t* verbatim, uint64_t n, uint16_t* 
         if (verbatim[i] || d < -(O_RADIUS - 1) || d > (O_RADIUS - 1)) code[i] = 0;
         else code[i] = (uint16_t)(d + O_RADIUS);
         prev = q[i];
+    }
+}
+
+/* LCF prediction on the lattice (Sec. IV-A, the original SZ's linear curve
+ * fitting: pred_i = 2 x_{i-1} - x_{i-2}), with q_{-1} = q_{-2} = 0:
+ * delta_i = q_i - 2 q_{i-1} + q_{i-2}; codes as for LV. */
+void szo_codes_lcf(const int64_t* q, const uint8_t* verbatim, uint64_t n, uint16_t* code, int64_t* delta)
+{
+    int64_t p1 = 0, p2 = 0;
+    for (uint64_t i = 0; i < n; ++i) {
+        int64_t d = q[i] - 2 * p1 + p2;
+        delta[i] = d;
+        if (verbatim[i] || d < -(O_RADIUS - 1) || d > (O_RADIUS - 1)) code[i] = 0;
+        else code[i] = (uint16_t)(d + O_RADIUS);
+        p2 = p1;
+        p1 = q[i];
     }
 }
 
@@ -259,8 +279,8 @@ static void put_bits(uint8_t* payload, uint64_t* bitpos, uint32_t cw, int len)
 }
 
 static void write_header(uint8_t* out, uint64_t n, double eb_abs, float D, uint32_t flags,
-                         uint32_t C, uint32_t G, uint64_t n_chunks, uint64_t n_sym, uint64_t n_esc,
-                         uint64_t payload_words, const uint64_t off[8], uint64_t total)
+                         uint32_t C, uint32_t G, uint32_t pred, uint64_t n_chunks, uint64_t n_sym,
+                         uint64_t n_esc, uint64_t payload_words, const uint64_t off[8], uint64_t total)
 {
     memset(out, 0, O_HEADER_BYTES);
     put_u32(out + 0, O_MAGIC);
@@ -274,7 +294,7 @@ static void write_header(uint8_t* out, uint64_t n, double eb_abs, float D, uint3
     put_u32(out + 36, G);
     put_u16(out + 40, (uint16_t)O_M_BITS);
     out[42] = (uint8_t)O_MAX_LEN;
-    out[43] = 1;                       /* predictor: last value */
+    out[43] = (uint8_t)pred;           /* predictor: 1 last value, 2 linear curve fitting */
     put_u64(out + 48, n_chunks);
     put_u64(out + 56, n_sym);
     put_u64(out + 64, n_esc);
@@ -284,7 +304,7 @@ static void write_header(uint8_t* out, uint64_t n, double eb_abs, float D, uint3
 }
 
 static int write_raw(const float* x, uint64_t n, double eb_abs, float D, uint32_t flags,
-                     uint32_t C, uint32_t G, uint8_t* out, uint64_t cap, uint64_t* out_bytes)
+                     uint32_t C, uint32_t G, uint32_t pred, uint8_t* out, uint64_t cap, uint64_t* out_bytes)
 {
     uint64_t words = (n + 3u) & ~(uint64_t)3u;
     uint64_t total = O_HEADER_BYTES + 4u * words;
@@ -292,7 +312,7 @@ static int write_raw(const float* x, uint64_t n, double eb_abs, float D, uint32_
     if (cap < total) return SZO_ERR_CAPACITY;
     uint64_t off[8];
     for (int s = 0; s < 8; ++s) off[s] = O_HEADER_BYTES;
-    write_header(out, n, eb_abs, D, flags | O_FLAG_RAW, C, G, 0, 0, 0, words, off, total);
+    write_header(out, n, eb_abs, D, flags | O_FLAG_RAW, C, G, pred, 0, 0, 0, words, off, total);
     memset(out + O_HEADER_BYTES, 0, 4u * words);
     for (uint64_t i = 0; i < n; ++i) put_u32(out + O_HEADER_BYTES + 4 * i, f2u(x[i]));
     return SZO_OK;
@@ -300,12 +320,13 @@ static int write_raw(const float* x, uint64_t n, double eb_abs, float D, uint32_
 
 /* Compress one float32 array.  kind: 0 = absolute eb, 1 = value-range relative.
  * C = elements per chunk, G = elements per sub-stream (powers of two).
- * extra_flags: O_FLAG_REORDERED when the caller reordered the array. */
-int szo_compress(const float* x, uint64_t n, double eb, int kind, uint32_t C, uint32_t G,
-                 uint32_t extra_flags, uint8_t* out, uint64_t cap, uint64_t* out_bytes)
+ * extra_flags: O_FLAG_REORDERED when the caller reordered the array.
+ * pred: O_PRED_LV or O_PRED_LCF (the LCF chunk anchors are q_{b-1}, q_{b-2}). */
+int szo_compress_pred(const float* x, uint64_t n, double eb, int kind, uint32_t C, uint32_t G,
+                      uint32_t extra_flags, uint32_t pred, uint8_t* out, uint64_t cap, uint64_t* out_bytes)
 {
     *out_bytes = 0;
-    if (!valid_params(n, C, G)) return SZO_ERR_ARG;
+    if (!valid_params(n, C, G) || (pred != O_PRED_LV && pred != O_PRED_LCF)) return SZO_ERR_ARG;
     double eb_abs; float D;
     int rc = szo_error_bound(x, n, eb, kind, &eb_abs, &D);
     if (rc) return rc;
@@ -315,10 +336,10 @@ int szo_compress(const float* x, uint64_t n, double eb, int kind, uint32_t C, ui
         for (int s = 0; s < 8; ++s) off[s] = O_HEADER_BYTES;
         *out_bytes = O_HEADER_BYTES;
         if (cap < O_HEADER_BYTES) return SZO_ERR_CAPACITY;
-        write_header(out, 0, eb_abs, D, flags, C, G, 0, 0, 0, 0, off, O_HEADER_BYTES);
+        write_header(out, 0, eb_abs, D, flags, C, G, pred, 0, 0, 0, 0, off, O_HEADER_BYTES);
         return SZO_OK;
     }
-    if (D == 0.0f) return write_raw(x, n, eb_abs, D, flags, C, G, out, cap, out_bytes);
+    if (D == 0.0f) return write_raw(x, n, eb_abs, D, flags, C, G, pred, out, cap, out_bytes);
 
     int64_t* q = (int64_t*)malloc(8 * n);
     int64_t* delta = (int64_t*)malloc(8 * n);
@@ -330,7 +351,8 @@ int szo_compress(const float* x, uint64_t n, double eb, int kind, uint32_t C, ui
         return SZO_ERR_NOMEM;
     }
     szo_lattice(x, n, D, eb_abs, q, verb);
-    szo_codes(q, verb, n, code, delta);
+    if (pred == O_PRED_LCF) szo_codes_lcf(q, verb, n, code, delta);
+    else szo_codes(q, verb, n, code, delta);
     uint64_t n_esc = 0;
     for (uint64_t i = 0; i < n; ++i) { hist[code[i]]++; if (code[i] == 0) n_esc++; }
 
@@ -364,7 +386,8 @@ int szo_compress(const float* x, uint64_t n, double eb, int kind, uint32_t C, ui
     off[0] = o; o = pad16(o + 2 * (uint64_t)m);              /* symbols u16 */
     off[1] = o; o = pad16(o + (uint64_t)m);                  /* lengths u8 */
     off[2] = o; o = pad16(o + 8 * (n_chunks + 1));           /* chunk word offsets u64 */
-    off[3] = o; o = pad16(o + 8 * n_chunks);                 /* chunk anchors i64 */
+    const uint64_t n_anchor = pred == O_PRED_LCF ? 2 : 1;
+    off[3] = o; o = pad16(o + 8 * n_anchor * n_chunks);      /* chunk anchors i64 (LCF: two each) */
     off[4] = o; o = pad16(o + 8 * (n_chunks + 1));           /* chunk escape bases u64 */
     off[5] = o; o = pad16(o + 2 * n_chunks * S);             /* sub-stream bit lengths u16 */
     off[6] = o; o = pad16(o + (uint64_t)O_ESC_BYTES * n_esc); /* escape records */
@@ -373,7 +396,7 @@ int szo_compress(const float* x, uint64_t n, double eb, int kind, uint32_t C, ui
     uint64_t raw_total = O_HEADER_BYTES + 4u * ((n + 3u) & ~(uint64_t)3u);
     uint64_t bound = off[7] + (B + 128u * n_chunks + 7u) / 8u;
     if (bound >= raw_total) {
-        rc = write_raw(x, n, eb_abs, D, flags, C, G, out, cap, out_bytes);
+        rc = write_raw(x, n, eb_abs, D, flags, C, G, pred, out, cap, out_bytes);
         goto done;
     }
 
@@ -389,7 +412,7 @@ int szo_compress(const float* x, uint64_t n, double eb, int kind, uint32_t C, ui
     *out_bytes = total;
     if (cap < total) { rc = SZO_ERR_CAPACITY; goto done; }
     memset(out, 0, total);
-    write_header(out, n, eb_abs, D, flags, C, G, n_chunks, m, n_esc, words, off, total);
+    write_header(out, n, eb_abs, D, flags, C, G, pred, n_chunks, m, n_esc, words, off, total);
     for (uint32_t k = 0; k < m; ++k) {
         put_u16(out + off[0] + 2 * k, (uint16_t)sym[k]);
         out[off[1] + k] = len[k];
@@ -401,7 +424,8 @@ int szo_compress(const float* x, uint64_t n, double eb, int kind, uint32_t C, ui
             uint64_t b0 = c * C;
             uint64_t e = b0 + C < n ? b0 + C : n;
             put_u64(out + off[2] + 8 * c, wpos);
-            put_u64(out + off[3] + 8 * c, (uint64_t)(c == 0 ? 0 : q[b0 - 1]));
+            put_u64(out + off[3] + 8 * n_anchor * c, (uint64_t)(b0 >= 1 ? q[b0 - 1] : 0));
+            if (pred == O_PRED_LCF) put_u64(out + off[3] + 8 * (2 * c + 1), (uint64_t)(b0 >= 2 ? q[b0 - 2] : 0));
             put_u64(out + off[4] + 8 * c, esc);
             uint64_t bitpos = 32 * wpos;
             for (uint64_t k = 0; k < S; ++k) {
@@ -430,6 +454,12 @@ done:
     free(q); free(delta); free(verb); free(code); free(hist);
     free(sym); free(fr); free(len); free(cw); free(sym_len); free(sym_cw);
     return rc;
+}
+
+int szo_compress(const float* x, uint64_t n, double eb, int kind, uint32_t C, uint32_t G,
+                 uint32_t extra_flags, uint8_t* out, uint64_t cap, uint64_t* out_bytes)
+{
+    return szo_compress_pred(x, n, eb, kind, C, G, extra_flags, O_PRED_LV, out, cap, out_bytes);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -462,9 +492,11 @@ int szo_decompress(const uint8_t* in, uint64_t in_bytes, float* out, uint64_t n_
     uint32_t C = get_u32(in + 32), G = get_u32(in + 36);
     uint64_t n_chunks = get_u64(in + 48), m = get_u64(in + 56), n_esc = get_u64(in + 64);
     uint64_t words = get_u64(in + 72), total = get_u64(in + 144);
+    uint32_t pred = in[43];
     uint64_t off[8];
     for (int s = 0; s < 8; ++s) off[s] = get_u64(in + 80 + 8 * s);
     if (total > in_bytes || off[7] + 4 * words > total || !valid_params(n, C, G)) return SZO_ERR_CORRUPT;
+    if (pred != O_PRED_LV && pred != O_PRED_LCF) return SZO_ERR_CORRUPT;
     *n_out = n;
     if (n > n_cap) return SZO_ERR_CAPACITY;
     if (n == 0) return SZO_OK;
@@ -476,6 +508,9 @@ int szo_decompress(const uint8_t* in, uint64_t in_bytes, float* out, uint64_t n_
     if (n_chunks != (n + C - 1) / C || m == 0 || m > 65536) return SZO_ERR_CORRUPT;
     uint64_t S = C / G;
     if (off[6] + O_ESC_BYTES * n_esc > off[7] || off[5] + 2 * n_chunks * S > off[6]) return SZO_ERR_CORRUPT;
+    if (off[2] + 8 * (n_chunks + 1) > off[3] || off[3] + 8 * (pred == O_PRED_LCF ? 2 : 1) * n_chunks > off[4] ||
+        off[4] + 8 * (n_chunks + 1) > off[5])
+        return SZO_ERR_CORRUPT;
 
     /* canonical decode tables: count per length, first code, symbols by (len, sym) */
     uint32_t count[O_MAX_LEN + 2] = {0}, first[O_MAX_LEN + 2] = {0}, base[O_MAX_LEN + 2] = {0};
@@ -505,7 +540,11 @@ int szo_decompress(const uint8_t* in, uint64_t in_bytes, float* out, uint64_t n_
         uint64_t e = b0 + C < n ? b0 + C : n;
         uint64_t wpos = get_u64(in + off[2] + 8 * c);
         uint64_t wend = get_u64(in + off[2] + 8 * (c + 1));
-        int64_t qv = (int64_t)get_u64(in + off[3] + 8 * c);
+        /* LV: q_i = q_{i-1} + delta_i.  LCF: q_i = 2 q_{i-1} - q_{i-2} + delta_i
+         * (two's-complement wrap on corrupt input) */
+        const uint64_t n_anchor = pred == O_PRED_LCF ? 2 : 1;
+        int64_t qv = (int64_t)get_u64(in + off[3] + 8 * n_anchor * c);
+        int64_t qv2 = pred == O_PRED_LCF ? (int64_t)get_u64(in + off[3] + 8 * (2 * c + 1)) : 0;
         uint64_t esc = get_u64(in + off[4] + 8 * c);
         if (wend > words || wpos > wend) { rc = SZO_ERR_CORRUPT; break; }
         uint64_t bitpos = 32 * wpos;
@@ -534,7 +573,13 @@ int szo_decompress(const uint8_t* in, uint64_t in_bytes, float* out, uint64_t n_
                 } else {
                     d = (int64_t)sv - O_RADIUS;
                 }
-                qv = (int64_t)((uint64_t)qv + (uint64_t)d);
+                if (pred == O_PRED_LCF) {
+                    int64_t qn = (int64_t)(2 * (uint64_t)qv - (uint64_t)qv2 + (uint64_t)d);
+                    qv2 = qv;
+                    qv = qn;
+                } else {
+                    qv = (int64_t)((uint64_t)qv + (uint64_t)d);
+                }
                 out[i] = verbatim ? u2f(raw) : szo_recon(qv, D);
             }
         }

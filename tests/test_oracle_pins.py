@@ -527,3 +527,116 @@ def test_prx_trend_on_md(oracle):
     prx = raw / sum(len(s) for s in oracle.compress_snapshot(f, 1e-4, 1, 8192, 128, 16384, 6)[0])
     assert rx > lv * 1.03 and prx > lv * 1.03
     assert abs(prx / rx - 1) < 0.05
+
+
+# --------------------------------------------------------------------------
+# LCF predictor (Sec. IV-A: the original SZ's linear curve fitting,
+# pred_i = 2 x_{i-1} - x_{i-2}; Table 3, Fig. 4)
+# --------------------------------------------------------------------------
+
+def _sequential_sz_lcf(x, D: Fraction):
+    """Textbook sequential SZ with the linear-curve-fitting predictor, in exact
+    rational arithmetic: the prediction extrapolates the two previous
+    *reconstructed* values (both 0 before the array)."""
+    r1 = r2 = Fraction(0)
+    codes, recon = [], []
+    for xi in x:
+        pred = 2 * r1 - r2
+        k = _rne((Fraction(float(xi)) - pred) / D)
+        r2, r1 = r1, pred + k * D
+        codes.append(k + 32768 if -32767 <= k <= 32767 else 0)
+        recon.append(np.float32(float(r1)))
+    return codes, recon
+
+
+@pytest.mark.parametrize("eb_abs", [2.0 ** -5, 0.0123, 3.7e-3])
+def test_bruteforce_sequential_lcf(oracle, eb_abs):
+    rng = np.random.default_rng(12)
+    n = 400
+    D = float(oracle.step(eb_abs))
+    # a smooth trajectory: accelerations of a few lattice steps, one jump that escapes
+    acc = rng.normal(0, 20, n) * D
+    x = np.cumsum(np.cumsum(acc) * 0.05).astype(np.float32)
+    x[200:] += np.float32(70000 * D)
+    t = np.asarray([Fraction(float(v)) / Fraction(D) for v in x])
+    frac = np.asarray([float(ti - math.floor(ti)) for ti in t])
+    # away from half-steps: no ties, and |x| reaches ~600 here, where the float32
+    # rounding of q*D could push an element within ulp/2 of D/2 past eb (verbatim)
+    x = x[np.abs(frac - 0.5) > 0.02]
+    codes_bf, recon_bf = _sequential_sz_lcf(x, Fraction(D))
+    assert 0 in codes_bf                                      # the jump is an escape
+    ea, Dd = oracle.error_bound(x, eb_abs, 0)
+    q, v = oracle.lattice(x, Dd, ea)
+    c, _ = oracle.codes_lcf(q, v)
+    assert c.tolist() == codes_bf
+    s = oracle.compress(x, eb_abs, kind=0, chunk=256, sub=16, pred=oracle.PRED_LCF)
+    assert (_f32bits(oracle.decompress(s)) == _f32bits(recon_bf)).all()
+
+
+def test_lcf_closed_forms(oracle):
+    """Second differences: a line on the lattice predicts exactly from its
+    third element on, a parabola c i^2 leaves the constant 2c, and a single
+    spike J leaves +J, -2J, +J (the sign and index pattern of the formula)."""
+    z = np.zeros(12, bool)
+    i = np.arange(12, dtype=np.int64)
+    _, d = oracle.codes_lcf(7 + 5 * i, z)
+    assert d.tolist() == [7, 5 - 7] + [0] * 10
+    _, d = oracle.codes_lcf(3 * i * i, z)
+    assert d.tolist() == [0, 3] + [6] * 10
+    q = np.zeros(12, np.int64)
+    q[5] = 40000
+    c, d = oracle.codes_lcf(q, z)
+    assert d.tolist() == [0] * 5 + [40000, -80000, 40000] + [0] * 4
+    assert c.tolist() == [32768] * 5 + [0, 0, 0] + [32768] * 4  # |delta| >= 32768 escapes
+
+
+@pytest.mark.parametrize("n,chunk,sub", [(1, 256, 16), (2, 256, 16), (3, 256, 16), (257, 256, 16),
+                                         (5000, 1024, 16), (70001, 4096, 64)])
+def test_lcf_round_trip_equals_lv(oracle, n, chunk, sub):
+    """Both predictors code the same lattice losslessly, so their streams
+    decode to the same floats bit for bit (verbatim values, escapes and chunk
+    anchors included); the LCF stream carries predictor 2 and two anchors
+    (q_{b-1}, q_{b-2}) per chunk."""
+    x = synth.random_walk_f32(n, n + 17, 0.3).numpy().copy()
+    if n > 100:
+        x[::53] = np.nan
+        x[7::101] = np.inf
+        x[30::97] += 5e3
+    lv = oracle.compress(x, 1e-4, 1, chunk, sub)
+    lcf = oracle.compress(x, 1e-4, 1, chunk, sub, pred=oracle.PRED_LCF)
+    assert (_f32bits(oracle.decompress(lcf)) == _f32bits(oracle.decompress(lv))).all()
+    h = oracle.parse_header(lcf)
+    assert h["predictor"] == 2 and oracle.parse_header(lv)["predictor"] == 1
+    if h["flags"] & 1:
+        return
+    nc = h["n_chunks"]
+    anchors = np.frombuffer(lcf, np.int64, 2 * nc, h["off_chunk_anchor"])
+    ea, D = oracle.error_bound(x, 1e-4, 1)
+    q, _ = oracle.lattice(x, D, ea)
+    for c in range(nc):
+        b = c * chunk
+        assert anchors[2 * c] == (q[b - 1] if b >= 1 else 0)
+        assert anchors[2 * c + 1] == (q[b - 2] if b >= 2 else 0)
+
+
+def test_lcf_rejects_unknown_predictor(oracle):
+    s = bytearray(oracle.compress(synth.random_walk_f32(3000, 5).numpy(), 1e-4, 1, 1024, 16))
+    s[43] = 3
+    with pytest.raises(oracle.OracleError):
+        oracle.decompress(bytes(s))
+
+
+def test_lv_beats_lcf_on_particle_data(oracle):
+    """Table 3 / Fig. 4 trend: on particle fields (no smoothness along the
+    stored order) the last-value predictor has the smaller prediction error
+    and the higher compression ratio than linear curve fitting."""
+    snap = synth.cosmology(1 << 16, 16, 1)
+    for f in synth.FIELDS:
+        x = snap[f].numpy()
+        xd = x.astype(np.float64)
+        e_lv = np.sqrt(np.mean((xd[1:] - xd[:-1]) ** 2))
+        e_lcf = np.sqrt(np.mean((xd[2:] - 2 * xd[1:-1] + xd[:-2]) ** 2))
+        assert e_lv < e_lcf
+        lv = len(oracle.compress(x, 1e-4, 1, 4096, 64))
+        lcf = len(oracle.compress(x, 1e-4, 1, 4096, 64, pred=oracle.PRED_LCF))
+        assert lv < lcf
