@@ -198,6 +198,41 @@ def weak_scaling_value(bytes_per_rank: float, seconds_per_step: float, ws: int):
     return b / t / 1e9, t, b
 
 
+def lcf_bench(sz, ctx, stream, step, xs, ys, outs, args, raw_bytes, ratio_lv):
+    """The per-array path with the LCF predictor on the benchmark arrays:
+    compress / decompress GB/s from CUDA events, the ratio against LV's, and
+    each kernel phase's device time.  Checks the error bound first."""
+    import torch
+    holders = step(plain=True, lcf=True)
+    sz.sz_sync(ctx)
+    sizes = [h.value for h in holders]
+    for x, y in zip(xs, ys):
+        fin = torch.isfinite(x)
+        R = (x[fin].max().double() - x[fin].min().double()).item()
+        assert (x.double() - y.double()).abs().max().item() <= args.eb * R * (1 + 1e-12)
+    step(plain=True, lcf=True)
+    sz.sz_sync(ctx)
+    k = max(1, min(args.steps, 3))
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+    torch.cuda.synchronize()
+    sz.sz_profile_enable(ctx, True)
+    for i in range(k):
+        ev[i][0].record(stream)
+        step(ev[i][1], plain=True, lcf=True)
+        ev[i][2].record(stream)
+    sz.sz_sync(ctx)
+    torch.cuda.synchronize()
+    prof = sz.sz_profile_read(ctx)
+    sz.sz_profile_enable(ctx, False)
+    tc = sum(e[0].elapsed_time(e[1]) for e in ev) / 1e3 / k
+    td = sum(e[1].elapsed_time(e[2]) for e in ev) / 1e3 / k
+    return {"compress_gbs": raw_bytes / tc / 1e9, "decompress_gbs": raw_bytes / td / 1e9,
+            "round_trip_gbs": raw_bytes / (tc + td) / 1e9, "ratio": raw_bytes / sum(sizes), "ratio_lv": ratio_lv,
+            "ms_per_step": {ph: round(ms / k, 4) for ph, (c, ms) in prof.items() if c},
+            "note": "per field: sz_compress / sz_decompress with predictor SZ_PRED_LCF (second differences)"}
+
+
 def link_rates(hx, hy):
     """Host<->device copy rates of the pinned buffers the end-to-end leg uses
     (plain copies, one direction at a time and both at once): the ceiling of
@@ -569,6 +604,7 @@ def main():
     ap.add_argument("--log2n", type=int, default=27)
     ap.add_argument("--eb", type=float, default=1e-4)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-lcf", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-log2n", type=int, default=24)
     ap.add_argument("--no-serve", action="store_true")
@@ -632,13 +668,17 @@ def main():
     ys = [torch.empty(n, dtype=torch.float32, device="cuda") for _ in xs]
     stream = torch.cuda.current_stream()
 
-    def step(ev_mid=None, plain=False):
+    lcf_params = sz._params(predictor=sz.SZ_PRED_LCF)
+
+    def step(ev_mid=None, plain=False, lcf=False):
         # fully asynchronous: the decoder reads each stream's size from its
         # header, so in_bytes is the buffer capacity and no host sync is needed.
         # The snapshot's six fields go through the batched form (one persistent
-        # launch replayed as a CUDA graph); plain=True uses one sz_compress per field.
+        # launch replayed as a CUDA graph); plain=True uses one sz_compress per
+        # field; lcf=True the same with the LCF predictor.
         if plain:
-            holders = [sz.sz_compress(ctx, x, args.eb, sz.SZ_EB_REL, None, o)[1] for x, o in zip(xs, outs)]
+            prm = lcf_params if lcf else None
+            holders = [sz.sz_compress(ctx, x, args.eb, sz.SZ_EB_REL, prm, o)[1] for x, o in zip(xs, outs)]
         else:
             _, nb = sz.sz_compress_batch(ctx, xs, [args.eb] * len(xs), sz.SZ_EB_REL, outs=outs)
             holders = [_Holder(nb, i) for i in range(len(xs))]
@@ -716,6 +756,11 @@ def main():
              "round_trip_gbs": raw_bytes / (tp_c + tp_d) / 1e9,
              "note": "per field: sz_compress (4 launches) and sz_decompress (2 launches), instead of the "
                      "batched graph and the batched decoder"}
+
+    # ---- the LCF predictor (Sec. IV-A, original SZ) on the same arrays ---------
+    lcf = None
+    if not args.no_lcf:
+        lcf = lcf_bench(sz, ctx, stream, step, xs, ys, outs, args, raw_bytes, ratio)
 
     # ---- roofline of the dominant kernel -----------------------------------
     peak, peak_kind = _peaks()
@@ -840,7 +885,7 @@ def main():
             "compress_frac_hbm": comp_gbs / peak, "decompress_frac_hbm": decomp_gbs / peak,
             "ratio": ratio, "roofline": roofline, "kernels": kernels, "kernels_plain_path": kernels_plain,
             "gpu_launches": launches,
-            "plain_path": plain, "batched": batched, "md": md, "served": served,
+            "plain_path": plain, "lcf": lcf, "batched": batched, "md": md, "served": served,
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "wall_s_timed": t_wall,
         }
         print(json.dumps(line))

@@ -68,6 +68,12 @@ typedef enum {
     SZ_FIELD_VX = 3, SZ_FIELD_VY = 4, SZ_FIELD_VZ = 5, SZ_FIELD_OTHER = 6
 } sz_field;
 
+/* Sec. IV-A: the predictor on the lattice.  SZ_PRED_LV = last value
+ * (SZ-LV, delta = q_i - q_{i-1}); SZ_PRED_LCF = the original SZ's linear
+ * curve fitting (delta = q_i - 2 q_{i-1} + q_{i-2}).  The stream records it
+ * (header byte 43: 1 or 2); decoders accept both. */
+typedef enum { SZ_PRED_DEFAULT = 0, SZ_PRED_LV = 1, SZ_PRED_LCF = 2 } sz_predictor;
+
 /* Tuning parameters; a NULL pointer or a zero field selects the default.
  *   chunk_elems    elements per chunk: 2048, 4096, 8192 or 16384
  *                  (0 = chosen from n by the built-in tuner).
@@ -76,12 +82,16 @@ typedef enum {
  *                  (0 = 16384).
  *   ignored_digits MD mode: 3-bit R-index digits ignored by the sort
  *                  (Table 5), 0..21 (the default 6 applies when segment is 0
- *                  too; set segment explicitly to request 0). */
+ *                  too; set segment explicitly to request 0).
+ *   predictor      an sz_predictor (0 = SZ_PRED_LV).  SZ_PRED_LCF runs the
+ *                  per-array kernels: sz_compress_batch takes those arrays
+ *                  one by one. */
 typedef struct {
     uint32_t chunk_elems;
     uint32_t sub_elems;
     uint32_t segment;
     uint32_t ignored_digits;
+    uint32_t predictor;
 } sz_params;
 
 /* Create a context on CUDA device `device`.  hbm_budget_bytes caps the device

@@ -18,7 +18,9 @@
 // 32-bit integers when no escape occurs and |q| provably stays within 2^24 --
 // and the chunk leaves with 128-bit coalesced stores.  Every table entry and
 // payload word is bounds-checked against in_bytes; a bad stream sets
-// E_CORRUPT.
+// E_CORRUPT.  Streams with the LCF predictor (second differences, two anchors
+// per chunk) take a second team scan for the entry state of each sub-stream
+// and 64-bit reconstruction, in non-inlined functions of their own.
 #include "sz_blocksort.cuh"
 
 namespace szg {
@@ -63,10 +65,15 @@ __device__ __forceinline__ void decode_setup_body(const DecompressArgs& a, Setup
         } else {
             const uint64_t n = rd64(in + H_N), total = rd64(in + H_TOTAL), pw = rd64(in + H_PWORDS);
             const uint32_t flags = rd32(in + H_FLAGS), C = rd32(in + H_C), G = rd32(in + H_G);
+            const uint32_t pred = in[H_PRED];
+            const uint64_t na = pred == kPredLCF ? 2 : 1;     // chunk anchors per chunk
             const uint64_t nc = rd64(in + H_NCHUNKS), m = rd64(in + H_NSYM), E = rd64(in + H_NESC);
             uint64_t off[8];
             for (int s = 0; s < 8; ++s) off[s] = rd64(in + H_OFF + 8 * s);
-            if (total > a.in_bytes || total < kHeaderBytes || n >= (1ull << 32)) status = E_CORRUPT;
+            if (total > a.in_bytes || total < kHeaderBytes || n >= (1ull << 32) ||
+                (pred != kPredLV && pred != kPredLCF))
+                status = E_CORRUPT;
+            st->pred = pred;
             for (int s = 0; !status && s < 8; ++s)
                 if (off[s] < kHeaderBytes || off[s] > total || (off[s] & 15u) || (s && off[s] < off[s - 1]))
                     status = E_CORRUPT;
@@ -79,7 +86,7 @@ __device__ __forceinline__ void decode_setup_body(const DecompressArgs& a, Setup
                     if (!shape_ok(C, G)) status = E_UNSUPPORTED;
                     else if (nc != (n + C - 1) / C || m == 0 || m > 65536 ||
                              off[S_LENS] - off[S_SYMS] < 2 * m || off[S_CWORD] - off[S_LENS] < m ||
-                             off[S_ANCHOR] - off[S_CWORD] < 8 * (nc + 1) || off[S_CESC] - off[S_ANCHOR] < 8 * nc ||
+                             off[S_ANCHOR] - off[S_CWORD] < 8 * (nc + 1) || off[S_CESC] - off[S_ANCHOR] < 8 * na * nc ||
                              off[S_SUBLEN] - off[S_CESC] < 8 * (nc + 1) ||
                              off[S_ESC] - off[S_SUBLEN] < 2 * nc * kSubPerChunk ||
                              off[S_PAYLOAD] - off[S_ESC] < (uint64_t)kEscBytes * E)
@@ -311,6 +318,7 @@ struct DecArray {
     uint32_t C, G, gshift, l2_lo, l2_n;
     float D;
     bool vec;
+    bool lcf;          // second-difference (LCF) stream: two anchors per chunk
 };
 
 __device__ __forceinline__ void dec_array(const DecompressArgs& a, DecArray& d) {
@@ -336,6 +344,7 @@ __device__ __forceinline__ void dec_array(const DecompressArgs& a, DecArray& d) 
     d.by_len = a.by_len;
     d.l2_lo = st->l2_lo;
     d.l2_n = st->l2_n;
+    d.lcf = st->pred == kPredLCF;
 }
 
 // Block-wide: the stream's first- and second-level tables and limits into
@@ -357,6 +366,8 @@ __device__ __forceinline__ void load_dec_tables(const DecompressArgs& a, const D
 // One chunk by one team of 64 threads (thread k = sub-stream k): stage, decode,
 // escapes and prefix, reconstruct, store.  next: the chunk this team takes next
 // (L2 prefetch), or >= nc.  Returns false (and raises E_CORRUPT) on a bad chunk.
+// LCF: the symbols are second differences; see the reconstruction below.
+template <bool LCF>
 __device__ __forceinline__ bool decode_chunk_team(const DecArray& d, DecSmem& sm, const uint32_t* lut2,
                                                   uint32_t* xs, uint32_t* stage, uint32_t stage_words, int team,
                                                   int k, uint64_t c, uint64_t next, uint32_t* err) {
@@ -429,11 +440,62 @@ __device__ __forceinline__ bool decode_chunk_team(const DecArray& d, DecSmem& sm
         sum += *reinterpret_cast<const long long*>(d.escs + (uint64_t)kEscBytes * (eb + eoff + t));
     long long tot_sum;
     const long long pre = team_exclusive_scan<long long>(sum, sm.ws64[team], team, k, &tot_sum);
+    const float D = d.D;
+    if constexpr (LCF) {
+        // ---- phase 2 (LCF): q_i = 2 q_{i-1} - q_{i-2} + delta_i ------------------
+        // With the first difference f_i = q_i - q_{i-1}: f_i = f_{i-1} + delta_i and
+        // q_i = q_{i-1} + f_i.  A sub-stream of L deltas maps (f, q) to
+        // (f + S, q + L f + T), S = sum of its deltas (`sum`, scanned above into
+        // `pre`), T = sum of its running sums of deltas.  A second team scan of
+        // L * pre + T gives each sub-stream its entry state; unsigned arithmetic
+        // wraps like the two's-complement recurrence.
+        uint64_t run = 0, T = 0;
+        uint64_t ecur = eb + eoff;
+        for (uint32_t j = 0; j < nsym; ++j) {
+            const uint32_t sy = xs[swz(e0 + j, gshift)];
+            const uint64_t dl = sy ? (uint64_t)((long long)sy - kRadius)
+                                   : *reinterpret_cast<const uint64_t*>(d.escs + (uint64_t)kEscBytes * ecur++);
+            run += dl;
+            T += run;
+        }
+        long long tot_t;
+        const long long preT = team_exclusive_scan<long long>((long long)((uint64_t)nsym * (uint64_t)pre + T),
+                                                              sm.ws64[team], team, k, &tot_t);
+        const uint64_t qm1 = (uint64_t)d.anchor[2 * c], qm2 = (uint64_t)d.anchor[2 * c + 1];
+        const uint64_t f0 = qm1 - qm2;
+        uint64_t f = f0 + (uint64_t)pre;
+        uint64_t q = qm1 + (uint64_t)e0 * f0 + (uint64_t)preT;
+        ecur = eb + eoff;
+        for (uint32_t j4 = 0; j4 < nsym; j4 += 4) {
+            uint4* slot = reinterpret_cast<uint4*>(&xs[swz(e0 + j4, gshift)]);
+            uint4 s4 = *slot;
+            uint32_t sy[4] = {s4.x, s4.y, s4.z, s4.w};
+            uint32_t ov[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                ov[t] = 0u;
+                if (j4 + t < nsym) {
+                    float v;
+                    if (sy[t] != 0u) {
+                        f += (uint64_t)((long long)sy[t] - kRadius);
+                        q += f;
+                        v = recon_f((long long)q, D);
+                    } else {
+                        const uint8_t* r = d.escs + (uint64_t)kEscBytes * ecur++;
+                        f += *reinterpret_cast<const uint64_t*>(r);
+                        q += f;
+                        v = (rd32(r + 12) & 1u) ? __uint_as_float(rd32(r + 8)) : recon_f((long long)q, D);
+                    }
+                    ov[t] = __float_as_uint(v);
+                }
+            }
+            *slot = make_uint4(ov[0], ov[1], ov[2], ov[3]);
+        }
+    } else {
     // ---- phase 2: reconstruct in place -----------------------------------------
     // every partial sum of a sub-stream without escapes stays within
     // q0 +- G * 32767, so |q0| below this bound keeps all of them within 2^24
     const long long q_fast = (1ll << 24) - (long long)G * (kRadius - 1);
-    const float D = d.D;
     const long long q0 = d.anchor[c] + pre;
     if (nesc == 0 && q0 >= -q_fast && q0 <= q_fast) {
         // 32-bit: q stays within 2^24, one exact int -> float and one fmul each
@@ -474,6 +536,7 @@ __device__ __forceinline__ bool decode_chunk_team(const DecArray& d, DecSmem& sm
             *slot = make_uint4(ov[0], ov[1], ov[2], ov[3]);
         }
     }
+    }  // LV
     team_sync(team);
     // ---- phase 3: coalesced store ---------------------------------------------
     float* dst = d.out + base;
@@ -489,6 +552,32 @@ __device__ __forceinline__ bool decode_chunk_team(const DecArray& d, DecSmem& sm
     }
     team_sync(team);
     return true;
+}
+
+// LCF streams run their team loops in separate, non-inlined functions, so the
+// LV path the kernels inline keeps its own code and registers (the stream
+// parameters are passed by value: a reference would pin the caller's copy in
+// local memory).  Strided chunks (decode_kernel) and counted units
+// (decode_multi_kernel, s_unit: the block's per-team unit slots).
+__device__ __noinline__ void decode_team_lcf_strided(const DecArray d, DecSmem& sm, const uint32_t* lut2,
+                                                     uint32_t* xs, uint32_t stage_words, int team, int k,
+                                                     uint64_t c0, uint64_t stride, uint32_t* err) {
+    for (uint64_t c = c0; c < d.nc; c += stride)
+        if (!decode_chunk_team<true>(d, sm, lut2, xs, xs + d.C, stage_words, team, k, c, c + stride, err)) return;
+}
+
+__device__ __noinline__ void decode_team_lcf_counted(const DecArray d, DecSmem& sm, const uint32_t* lut2,
+                                                     uint32_t* xs, uint32_t stage_words, int team, int k,
+                                                     uint32_t* ctr, uint32_t nu, uint64_t ahead, uint32_t* s_unit,
+                                                     uint32_t* err) {
+    for (;;) {
+        if (k == 0) s_unit[team] = atomicAdd(ctr, 1u);
+        team_sync(team);
+        const uint32_t u = s_unit[team];
+        team_sync(team);
+        if (u >= nu) return;
+        if (!decode_chunk_team<true>(d, sm, lut2, xs, xs + d.C, stage_words, team, k, u, u + ahead, err)) return;
+    }
 }
 
 // team region of a block decoding chunks of C elements: C value slots and the
@@ -525,8 +614,14 @@ __global__ void __launch_bounds__(kDecBlock, 1) decode_kernel(DecompressArgs a) 
     uint32_t stage_words;
     uint32_t* xs = team_region(dyn_smem, teams, team, &stage_words, d.C);
     const uint64_t stride = (uint64_t)gridDim.x * teams;
+    if (d.lcf) {
+        decode_team_lcf_strided(d, sm, lut2, xs, stage_words, team, k, (uint64_t)blockIdx.x * teams + team, stride,
+                                a.err);
+        return;
+    }
     for (uint64_t c = (uint64_t)blockIdx.x * teams + team; c < d.nc; c += stride)
-        if (!decode_chunk_team(d, sm, lut2, xs, xs + d.C, stage_words, team, k, c, c + stride, a.err)) return;
+        if (!decode_chunk_team<false>(d, sm, lut2, xs, xs + d.C, stage_words, team, k, c, c + stride, a.err))
+            return;
 }
 
 // ---- batched decompression ---------------------------------------------------
@@ -623,6 +718,10 @@ __global__ void __launch_bounds__(kDecBlock, 1) decode_multi_kernel(const Decomp
         if (team >= teams) continue;
         uint32_t stage_words = 0;
         uint32_t* xs = raw ? nullptr : team_region(dyn_smem, teams, team, &stage_words, d.C);
+        if (!raw && d.lcf) {
+            decode_team_lcf_counted(d, sm, lut2, xs, stage_words, team, kk, ctr + i, nu, ahead, s_unit, sa.err);
+            continue;
+        }
         for (;;) {
             if (kk == 0) s_unit[team] = atomicAdd(ctr + i, 1u);
             team_sync(team);
@@ -634,7 +733,8 @@ __global__ void __launch_bounds__(kDecBlock, 1) decode_multi_kernel(const Decomp
                 uint32_t* dst = reinterpret_cast<uint32_t*>(sa.out);
                 const uint64_t e1 = umin64(d.n, ((uint64_t)u + 1) * kRawUnit);
                 for (uint64_t e = (uint64_t)u * kRawUnit + kk; e < e1; e += kDecThreads) dst[e] = __ldg(d.payload + e);
-            } else if (!decode_chunk_team(d, sm, lut2, xs, xs + d.C, stage_words, team, kk, u, u + ahead, sa.err)) {
+            } else if (!decode_chunk_team<false>(d, sm, lut2, xs, xs + d.C, stage_words, team, kk, u, u + ahead,
+                                                 sa.err)) {
                 break;
             }
         }

@@ -5,13 +5,14 @@
 
 namespace szg {
 
-template <int C, bool FROM_CODES>
+template <int C, bool FROM_CODES, bool LCF = false>
 __global__ void __launch_bounds__(EncShape<C>::kThreads, EncShape<C>::kMinBlocks) encode_kernel(CompressArgs a) {
+    static_assert(FROM_CODES || !LCF, "LCF encodes the stored codes");
     constexpr int NT = EncShape<C>::kThreads;
     extern __shared__ uint4 dyn_smem[];
     __shared__ EncSmem<NT> esm;
     __shared__ uint32_t s_c[2];
-    __shared__ float s_prev;
+    __shared__ float s_prev[2];
     ArrayState* st = a.st;
     if (st->raw) {
         const uint64_t words = (a.n + 3u) & ~(uint64_t)3u;
@@ -20,7 +21,7 @@ __global__ void __launch_bounds__(EncShape<C>::kThreads, EncShape<C>::kMinBlocks
     }
     uint32_t* smem = reinterpret_cast<uint32_t*>(dyn_smem);
     if (FROM_CODES) {
-        encode_array_pipelined<C, NT>(a, smem, esm, s_c, &s_prev);
+        encode_array_pipelined<C, NT, LCF>(a, smem, esm, s_c, s_prev);
         return;
     }
     // codes recomputed from the input: one chunk per ticket
@@ -38,25 +39,29 @@ template <int C>
 static void launch_encode_t(const CompressArgs& a, cudaStream_t s) {
     const size_t smem = enc_smem_bytes(C);
     constexpr int NT = EncShape<C>::kThreads;
-    static int resident[2] = {0, 0};
+    // variants: 0 codes recomputed, 1 stored codes, 2 stored codes with LCF
+    static int resident[3] = {0, 0, 0};
     if (!resident[0]) {
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaFuncSetAttribute(encode_kernel<C, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(encode_kernel<C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        int b0 = 0, b1 = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, encode_kernel<C, false>, NT, smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, encode_kernel<C, true>, NT, smem);
-        resident[0] = (b0 > 0 ? b0 : 1) * (sms > 0 ? sms : 148);
-        resident[1] = (b1 > 0 ? b1 : 1) * (sms > 0 ? sms : 148);
+        cudaFuncSetAttribute(encode_kernel<C, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int b[3] = {0, 0, 0};
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b[0], encode_kernel<C, false>, NT, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b[1], encode_kernel<C, true>, NT, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b[2], encode_kernel<C, true, true>, NT, smem);
+        for (int v = 0; v < 3; ++v) resident[v] = (b[v] > 0 ? b[v] : 1) * (sms > 0 ? sms : 148);
     }
     // persistent: at most the resident blocks, each taking chunks by ticket
-    const int v = a.codes ? 1 : 0;
+    // (the quantizer stores the codes whenever the prediction is LCF)
+    const int v = a.codes ? (a.pred == kPredLCF ? 2 : 1) : 0;
     const uint32_t div = a.grid_div > 1 ? a.grid_div : 1u;
     uint32_t grid = umin32(a.n_chunks, (uint32_t)resident[v] / div);
     if (grid == 0) grid = 1;
-    if (v) encode_kernel<C, true><<<grid, NT, smem, s>>>(a);
+    if (v == 2) encode_kernel<C, true, true><<<grid, NT, smem, s>>>(a);
+    else if (v) encode_kernel<C, true><<<grid, NT, smem, s>>>(a);
     else encode_kernel<C, false><<<grid, NT, smem, s>>>(a);
 }
 

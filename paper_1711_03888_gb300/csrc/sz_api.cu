@@ -27,7 +27,10 @@ uint32_t tune_chunk(uint64_t n) {
     return 4096u;
 }
 
+uint32_t params_pred(const sz_params* p) { return (p && p->predictor == SZ_PRED_LCF) ? kPredLCF : kPredLV; }
+
 sz_status resolve_params(const sz_params* p, uint64_t n, uint32_t* C, uint32_t* G) {
+    if (p && p->predictor > (uint32_t)SZ_PRED_LCF) return SZ_ERR_ARG;
     uint32_t c = (p && p->chunk_elems) ? p->chunk_elems : tune_chunk(n);
     bool ok = false;
     for (uint32_t v : kChunkChoices) ok |= (v == c);
@@ -251,6 +254,7 @@ sz_status sz_compress(sz_ctx* ctx, const float* d_in, size_t n, double eb, sz_eb
     cudaSetDevice(ctx->device);
     if ((s = ctx_reserve(ctx, 1, (n + C - 1) / C, (uint64_t)((n + C - 1) / C) * C)) != SZ_OK) return s;
     CompressArgs a = make_compress_args(ctx, 0, d_in, n, eb, (int)kind, C, G, 0u, d_out, out_cap);
+    a.pred = params_pred(params);
     return enqueue_compress(ctx, a, out_bytes, (cudaStream_t)stream);
 }
 

@@ -46,15 +46,16 @@ sz_status batch_compress(sz_ctx* ctx, int k, const float* const* d_in, const siz
     cudaSetDevice(ctx->device);
     std::vector<uint32_t> Cs(k), Gs(k);
     std::vector<int> batched;
+    const bool lcf = params_pred(params) == kPredLCF;
     for (int i = 0; i < k; ++i) {
         sz_status st = validate_compress(d_in[i], n[i], eb[i], kind, d_out[i]);
         if (st != SZ_OK) return st;
         if ((st = resolve_params(params, n[i], &Cs[i], &Gs[i])) != SZ_OK) return st;
-        if (Cs[i] <= 4096) batched.push_back(i);
+        if (Cs[i] <= 4096 && !lcf) batched.push_back(i);
     }
-    // arrays with large explicit chunks: the per-array path
+    // arrays with large explicit chunks or LCF prediction: the per-array path
     for (int i = 0; i < k; ++i) {
-        if (Cs[i] <= 4096) continue;
+        if (Cs[i] <= 4096 && !lcf) continue;
         sz_status st = sz_compress(ctx, d_in[i], n[i], eb[i], kind, params, d_out[i], out_cap[i],
                                    out_bytes ? &out_bytes[i] : nullptr, s);
         if (st != SZ_OK) return st;

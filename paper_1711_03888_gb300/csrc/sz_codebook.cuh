@@ -61,9 +61,14 @@ struct CbSmem {
 
 __device__ __forceinline__ uint64_t pad16(uint64_t b) { return (b + 15u) & ~(uint64_t)15u; }
 
+// header byte H_PRED and chunk anchors per chunk: LV 1 / one (q before the
+// chunk); LCF 2 / two (the two q before it)
+__device__ __forceinline__ uint32_t pred_byte(const CompressArgs& a) { return a.pred == kPredLCF ? kPredLCF : kPredLV; }
+__device__ __forceinline__ uint64_t anchors_per_chunk(const CompressArgs& a) { return a.pred == kPredLCF ? 2u : 1u; }
+
 // header writer (thread 0); payload_words / total may be patched later
 static __device__ void write_header(uint8_t* out, uint64_t n, double eb_abs, float D, uint32_t flags, uint32_t C,
-                             uint32_t G, uint64_t nc, uint64_t nsym, uint64_t nesc, uint64_t pwords,
+                             uint32_t G, uint32_t pred, uint64_t nc, uint64_t nsym, uint64_t nesc, uint64_t pwords,
                              const unsigned long long* off, uint64_t total) {
     uint32_t* w32 = reinterpret_cast<uint32_t*>(out);
     for (int i = 0; i < (int)(kHeaderBytes / 4); ++i) w32[i] = 0u;
@@ -78,7 +83,7 @@ static __device__ void write_header(uint8_t* out, uint64_t n, double eb_abs, flo
     *reinterpret_cast<uint32_t*>(out + H_G) = G;
     *reinterpret_cast<uint16_t*>(out + H_M) = 16;
     out[H_MAXLEN] = (uint8_t)kMaxLen;
-    out[H_PRED] = 1;
+    out[H_PRED] = (uint8_t)pred;
     *reinterpret_cast<uint64_t*>(out + H_NCHUNKS) = nc;
     *reinterpret_cast<uint64_t*>(out + H_NSYM) = nsym;
     *reinterpret_cast<uint64_t*>(out + H_NESC) = nesc;
@@ -129,7 +134,8 @@ __device__ void codebook_body(const CompressArgs& a, CbSmem<NT>& sm, uint32_t* f
             for (int s = 0; s < 8; ++s) off[s] = kHeaderBytes;
             uint64_t total = kHeaderBytes + 4u * words;
             if (a.out_cap >= total)
-                write_header(out, n, P.eb_abs, P.D, flags | (n ? kFlagRaw : 0u), a.C, a.G, 0, 0, 0, words, off, total);
+                write_header(out, n, P.eb_abs, P.D, flags | (n ? kFlagRaw : 0u), a.C, a.G, pred_byte(a), 0, 0, 0, words,
+                             off, total);
             else
                 raise_err(a.err, E_CAPACITY);
             st->raw = n ? 1u : 0u;
@@ -430,7 +436,7 @@ __device__ void codebook_body(const CompressArgs& a, CbSmem<NT>& sm, uint32_t* f
         off[S_SYMS] = o;   o = pad16(o + 2ull * m);
         off[S_LENS] = o;   o = pad16(o + m);
         off[S_CWORD] = o;  o = pad16(o + 8ull * (nc + 1));
-        off[S_ANCHOR] = o; o = pad16(o + 8ull * nc);
+        off[S_ANCHOR] = o; o = pad16(o + 8ull * nc * anchors_per_chunk(a));
         off[S_CESC] = o;   o = pad16(o + 8ull * (nc + 1));
         off[S_SUBLEN] = o; o = pad16(o + 2ull * nc * (a.C / a.G));
         off[S_ESC] = o;    o = pad16(o + (uint64_t)kEscBytes * E);
@@ -442,7 +448,8 @@ __device__ void codebook_body(const CompressArgs& a, CbSmem<NT>& sm, uint32_t* f
             for (int s = 0; s < 8; ++s) off[s] = kHeaderBytes;
             uint64_t words = (n + 3u) & ~(uint64_t)3u;
             if (a.out_cap >= raw_total)
-                write_header(out, n, P.eb_abs, P.D, flags | kFlagRaw, a.C, a.G, 0, 0, 0, words, off, raw_total);
+                write_header(out, n, P.eb_abs, P.D, flags | kFlagRaw, a.C, a.G, pred_byte(a), 0, 0, 0, words, off,
+                             raw_total);
             else
                 raise_err(a.err, E_CAPACITY);
             st->total_bytes = raw_total;
@@ -450,7 +457,7 @@ __device__ void codebook_body(const CompressArgs& a, CbSmem<NT>& sm, uint32_t* f
         } else {
             sm.tables_ok = off[S_PAYLOAD] <= a.out_cap;
             if (a.out_cap >= kHeaderBytes)
-                write_header(out, n, P.eb_abs, P.D, flags, a.C, a.G, nc, m, E, 0, off, 0);
+                write_header(out, n, P.eb_abs, P.D, flags, a.C, a.G, pred_byte(a), nc, m, E, 0, off, 0);
         }
         for (int s = 0; s < 8; ++s) st->off[s] = off[s];
         st->raw = sm.raw;
@@ -478,7 +485,7 @@ __device__ void codebook_body(const CompressArgs& a, CbSmem<NT>& sm, uint32_t* f
         for (uint64_t b = off[S_SYMS] + 2ull * m; b < off[S_LENS]; ++b) out[b] = 0;
         for (uint64_t b = off[S_LENS] + m; b < off[S_CWORD]; ++b) out[b] = 0;
         for (uint64_t b = off[S_CWORD] + 8ull * (nc + 1); b < off[S_ANCHOR]; ++b) out[b] = 0;
-        for (uint64_t b = off[S_ANCHOR] + 8ull * nc; b < off[S_CESC]; ++b) out[b] = 0;
+        for (uint64_t b = off[S_ANCHOR] + 8ull * nc * anchors_per_chunk(a); b < off[S_CESC]; ++b) out[b] = 0;
         for (uint64_t b = off[S_CESC] + 8ull * (nc + 1); b < off[S_SUBLEN]; ++b) out[b] = 0;
     }
 }

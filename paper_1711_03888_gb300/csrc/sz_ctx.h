@@ -89,6 +89,7 @@ struct ProfScope {
 };
 uint32_t tune_chunk(uint64_t n);
 sz_status resolve_params(const sz_params* p, uint64_t n, uint32_t* C, uint32_t* G);
+uint32_t params_pred(const sz_params* p);     // kPredLV or kPredLCF
 sz_status ctx_reserve(sz_ctx* ctx, int arrays, uint64_t max_chunks, uint64_t max_code_elems);
 CompressArgs make_compress_args(sz_ctx* ctx, int slot, const float* in, uint64_t n, double eb, int kind,
                                 uint32_t C, uint32_t G, uint32_t extra_flags, void* out, uint64_t cap);

@@ -69,11 +69,12 @@ struct EncSmem {
 // end): block scan of bit lengths and escape counts, publication of the
 // chunk size, packing, escape records, look-back for the word offset, the
 // chunk tables and the coalesced copy of the payload.  anchor (thread 0): the
-// lattice value before the chunk.
-template <int NT, int kRun>
+// lattice value before the chunk; with LCF, anchor2 is the one before that
+// and escapes carry the second difference.
+template <int NT, int kRun, bool LCF = false>
 __device__ __forceinline__ void encode_chunk_body(const CompressArgs& a, const LatticeParams& P, const uint32_t c,
                                                   const uint32_t (&r)[kRun], const long long anchor, uint32_t* buf,
-                                                  EncSmem<NT>& esm) {
+                                                  EncSmem<NT>& esm, const long long anchor2 = 0) {
     constexpr int C = NT * kRun;
     unsigned long long& s_prefix = esm.prefix;
     ArrayState* st = a.st;
@@ -148,12 +149,13 @@ __device__ __forceinline__ void encode_chunk_body(const CompressArgs& a, const L
             if (r[j] & 1u) {
                 uint64_t i = base + e0 + j;
                 float x = __ldg(in + i);
-                long long q, qp = 0;
+                long long q, qp = 0, qpp = 0;
                 bool vb, vv;
                 lattice_q(x, P, q, vb);
                 if (i > 0) lattice_q(__ldg(in + i - 1), P, qp, vv);
+                if (LCF && i > 1) lattice_q(__ldg(in + i - 2), P, qpp, vv);
                 uint8_t* rec = esc_base + (uint64_t)kEscBytes * idx++;
-                *reinterpret_cast<long long*>(rec) = q - qp;
+                *reinterpret_cast<long long*>(rec) = LCF ? (q - qp) - (qp - qpp) : q - qp;
                 *reinterpret_cast<uint32_t*>(rec + 8) = vb ? __float_as_uint(x) : 0u;
                 *reinterpret_cast<uint32_t*>(rec + 12) = vb ? 1u : 0u;
             }
@@ -214,7 +216,13 @@ __device__ __forceinline__ void encode_chunk_body(const CompressArgs& a, const L
         }
         if (tid == 0) {
             reinterpret_cast<uint64_t*>(out + st->off[S_CWORD])[c] = prefix;
-            reinterpret_cast<long long*>(out + st->off[S_ANCHOR])[c] = anchor;
+            long long* anchors = reinterpret_cast<long long*>(out + st->off[S_ANCHOR]);
+            if (LCF) {
+                anchors[2 * (uint64_t)c] = anchor;
+                anchors[2 * (uint64_t)c + 1] = anchor2;
+            } else {
+                anchors[c] = anchor;
+            }
             if (c == a.n_chunks - 1) reinterpret_cast<uint64_t*>(out + st->off[S_CWORD])[c + 1] = prefix + chunk_words;
         }
     }
@@ -336,8 +344,9 @@ __device__ void encode_chunk(const CompressArgs& a, const uint32_t c, uint32_t* 
 // preceding element of its next ticket are already on their way into the
 // stage (cp.async).  A block holds at most two tickets, and the smallest
 // unfinished ticket is always being encoded, so the look-back still only
-// waits on chunks that make progress.
-template <int C, int NT>
+// waits on chunks that make progress.  s_prev: the element before the chunk
+// (and, with LCF, the one before that in s_prev[1]).
+template <int C, int NT, bool LCF = false>
 __device__ __forceinline__ void encode_array_pipelined(const CompressArgs& a, uint32_t* smem, EncSmem<NT>& esm,
                                                        uint32_t* s_ticket, float* s_prev) {
     constexpr int kRun = C / NT;
@@ -360,6 +369,10 @@ __device__ __forceinline__ void encode_array_pipelined(const CompressArgs& a, ui
             asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s_prevp),
                          "l"(__cvta_generic_to_global(a.in + (uint64_t)cc * C - 1))
                          : "memory");
+        if (LCF && tid == 0 && cc > 0)     // cc * C >= 2048, so the element two back exists
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s_prevp + 4u),
+                         "l"(__cvta_generic_to_global(a.in + (uint64_t)cc * C - 2))
+                         : "memory");
         asm volatile("cp.async.commit_group;" ::: "memory");
     };
     if (tid == 0) s_ticket[0] = atomicAdd(&st->ticket, 1u);
@@ -379,10 +392,11 @@ __device__ __forceinline__ void encode_array_pipelined(const CompressArgs& a, ui
         }
         // the next ticket's atomic is in flight while the codewords are looked up
         if (tid == 0) s_ticket[1] = atomicAdd(&st->ticket, 1u);
-        long long anchor = 0;
+        long long anchor = 0, anchor2 = 0;
         if (tid == 0 && c > 0) {
             bool vv;
-            lattice_q(*s_prev, P, anchor, vv);
+            lattice_q(s_prev[0], P, anchor, vv);
+            if (LCF) lattice_q(s_prev[1], P, anchor2, vv);
         }
         uint32_t r[kRun];
 #pragma unroll
@@ -394,7 +408,7 @@ __device__ __forceinline__ void encode_array_pipelined(const CompressArgs& a, ui
         __syncthreads();          // the stage is read; the next ticket is known
         const uint32_t cn = s_ticket[1];
         if (cn < a.n_chunks) issue(cn);
-        encode_chunk_body<NT, kRun>(a, P, c, r, anchor, buf, esm);
+        encode_chunk_body<NT, kRun, LCF>(a, P, c, r, anchor, buf, esm, anchor2);
         c = cn;
     }
 }

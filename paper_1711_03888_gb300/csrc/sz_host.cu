@@ -240,6 +240,7 @@ sz_status sz_compress_host(sz_ctx* ctx, int k, const float* const* h_in, const s
         for (int i = groups[g].first; i < groups[g].last && st == SZ_OK; ++i) {
             CompressArgs a = make_compress_args(ctx, 0, (const float*)(din[s] + ioff[i]), n[i], eb[i], (int)kind,
                                                 Cs[i], Gs[i], 0u, dout[s] + ooff[i], ob[i]);
+            a.pred = params_pred(params);
             if ((st = enqueue_compress(ctx, a, nullptr, cs)) != SZ_OK) break;
             st = cuda_ok(cudaMemcpyAsync(&sizes[i], &a.st->total_bytes, sizeof(uint64_t), cudaMemcpyDeviceToHost, cs));
         }

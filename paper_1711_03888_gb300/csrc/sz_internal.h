@@ -20,6 +20,8 @@ constexpr int kNumCodes = 65536;
 constexpr uint32_t kFlagRaw = 1u;
 constexpr uint32_t kFlagReordered = 2u;
 constexpr uint32_t kEscBytes = 16;
+constexpr uint32_t kPredLV = 1;                   // header byte H_PRED: last value (Sec. IV-A)
+constexpr uint32_t kPredLCF = 2;                  // linear curve fitting (Sec. IV-A, original SZ)
 constexpr int kSubPerChunk = 64;                  // sub-streams per chunk on the GPU path
 constexpr int kRangeBlocks = 1216;                // 8 x 152 SMs
 constexpr int kLutBits = 12;                      // decoder direct-lookup width
@@ -65,7 +67,7 @@ struct ArrayState {
     uint32_t n_used;
     uint32_t raw;
     uint32_t ticket;           // encoder chunk ticket (reset by the codebook kernel)
-    uint32_t pad0;
+    uint32_t pred;             // decoder: predictor from the header (kPredLV / kPredLCF)
     uint64_t total_bytes;      // final stream size (set by the encoder)
     uint64_t n_out;            // decoder: element count from the header
     // decoder tables
@@ -99,6 +101,7 @@ struct CompressArgs {
     uint32_t* err;              // context error word
     uint16_t* codes;            // n_chunks*C u16 codes written by the quantizer, or null (encoder recomputes)
     uint32_t grid_div;          // persistent launches use 1/grid_div of the resident blocks (0, 1: all)
+    uint32_t pred;              // kPredLCF: second-difference prediction (per-array path only); else LV
 };
 
 struct DecompressArgs {

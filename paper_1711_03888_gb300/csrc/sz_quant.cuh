@@ -16,6 +16,9 @@
 // encoder's look-back word re-armed.  quant_chunk reads the input from global
 // memory; quant_chunk_staged from a shared-memory stage that the persistent
 // loop (quant_array_staged) fills for the next chunk while this one runs.
+// With LCF = true the prediction is the original SZ's linear curve fitting
+// (Sec. IV-A): the code carries the second difference q_i - 2 q_{i-1} +
+// q_{i-2}, so each warp also carries q_{i-2} from group to group.
 #pragma once
 #include "sz_device.cuh"
 
@@ -77,7 +80,7 @@ __device__ __forceinline__ void hist_window_flush(uint32_t* sh, uint32_t* gh) {
     }
 }
 
-template <bool STORE>
+template <bool STORE, bool LCF = false>
 __device__ void quant_chunk(const CompressArgs& a, const LatticeParams& P, uint32_t c, uint32_t* sh,
                             uint32_t* s_esc) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -90,12 +93,14 @@ __device__ void quant_chunk(const CompressArgs& a, const LatticeParams& P, uint3
     const uint64_t s0 = (uint64_t)c * a.C + (uint64_t)warp * span;
     const uint64_t s1 = umin64(n, s0 + span);
     uint32_t esc = 0;
-    long long carry = 0;
+    long long carry = 0, carry2 = 0;     // q_{s0-1}, and q_{s0-2} for LCF
     if (s0 < s1 && s0 > 0 && lane == 0) {
         bool vv;
         lattice_q(__ldg(in + s0 - 1), P, carry, vv);
+        if (LCF && s0 > 1) lattice_q(__ldg(in + s0 - 2), P, carry2, vv);
     }
     carry = __shfl_sync(0xffffffffu, carry, 0);
+    if (LCF) carry2 = __shfl_sync(0xffffffffu, carry2, 0);
     for (uint64_t ib = s0; ib < s1; ib += 256) {
         float xg[2][4];
 #pragma unroll
@@ -122,7 +127,36 @@ __device__ void quant_chunk(const CompressArgs& a, const LatticeParams& P, uint3
             bool ok = fast_ok;
 #pragma unroll
             for (int j = 0; j < 4; ++j) ok &= lattice_fast32(x[j], P, q32[j], vb[j]);
-            if (__all_sync(0xffffffffu, ok) && carry >= -(1ll << 30) && carry <= (1ll << 30)) {
+            if (LCF) {
+                // second differences: delta = (q - q1) - (q1 - q2), so the LV code
+                // builders apply to the first differences
+                if (__all_sync(0xffffffffu, ok) && carry >= -(1ll << 28) && carry <= (1ll << 28) &&
+                    carry2 >= -(1ll << 28) && carry2 <= (1ll << 28)) {
+                    int qp = __shfl_up_sync(0xffffffffu, q32[3], 1);
+                    int qpp = __shfl_up_sync(0xffffffffu, q32[2], 1);
+                    if (lane == 0) { qp = (int)carry; qpp = (int)carry2; }
+                    cd[0] = code32(q32[0] - qp, qp - qpp, vb[0]);
+                    cd[1] = code32(q32[1] - q32[0], q32[0] - qp, vb[1]);
+                    cd[2] = code32(q32[2] - q32[1], q32[1] - q32[0], vb[2]);
+                    cd[3] = code32(q32[3] - q32[2], q32[2] - q32[1], vb[3]);
+                    carry = __shfl_sync(0xffffffffu, q32[3], 31);
+                    carry2 = __shfl_sync(0xffffffffu, q32[2], 31);
+                } else {
+                    long long q[4];
+                    bool v2[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) lattice_q(x[j], P, q[j], v2[j]);
+                    long long qp = __shfl_up_sync(0xffffffffu, q[3], 1);
+                    long long qpp = __shfl_up_sync(0xffffffffu, q[2], 1);
+                    if (lane == 0) { qp = carry; qpp = carry2; }
+                    cd[0] = make_code(q[0] - qp, qp - qpp, v2[0]);
+                    cd[1] = make_code(q[1] - q[0], q[0] - qp, v2[1]);
+                    cd[2] = make_code(q[2] - q[1], q[1] - q[0], v2[2]);
+                    cd[3] = make_code(q[3] - q[2], q[2] - q[1], v2[3]);
+                    carry = __shfl_sync(0xffffffffu, q[3], 31);
+                    carry2 = __shfl_sync(0xffffffffu, q[2], 31);
+                }
+            } else if (__all_sync(0xffffffffu, ok) && carry >= -(1ll << 30) && carry <= (1ll << 30)) {
                 int qp = __shfl_up_sync(0xffffffffu, q32[3], 1);
                 if (lane == 0) qp = (int)carry;
                 cd[0] = code32(q32[0], qp, vb[0]);
@@ -177,7 +211,7 @@ __device__ void quant_chunk(const CompressArgs& a, const LatticeParams& P, uint3
     __syncthreads();
 }
 
-template <bool STORE>
+template <bool STORE, bool LCF = false>
 __device__ void quant_chunk_staged(const CompressArgs& a, const LatticeParams& P, uint32_t c, const float* stage,
                                    uint32_t* sh, uint32_t* s_esc) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -190,12 +224,14 @@ __device__ void quant_chunk_staged(const CompressArgs& a, const LatticeParams& P
     const uint64_t s0 = (uint64_t)c * a.C + (uint64_t)warp * span;
     const uint64_t s1 = umin64(n, s0 + span);
     uint32_t esc = 0;
-    long long carry = 0;
+    long long carry = 0, carry2 = 0;     // q_{s0-1}, and q_{s0-2} for LCF
     if (s0 < s1 && s0 > 0 && lane == 0) {
         bool vv;
         lattice_q(sx[s0 - 1 - cbase], P, carry, vv);
+        if (LCF && s0 > 1) lattice_q(sx[s0 - 2 - cbase], P, carry2, vv);   // the stage holds 4 before the chunk
     }
     carry = __shfl_sync(0xffffffffu, carry, 0);
+    if (LCF) carry2 = __shfl_sync(0xffffffffu, carry2, 0);
     for (uint64_t ib = s0; ib < s1; ib += 256) {
         float xg[2][4];
 #pragma unroll
@@ -222,7 +258,36 @@ __device__ void quant_chunk_staged(const CompressArgs& a, const LatticeParams& P
             bool ok = fast_ok;
 #pragma unroll
             for (int j = 0; j < 4; ++j) ok &= lattice_fast32(x[j], P, q32[j], vb[j]);
-            if (__all_sync(0xffffffffu, ok) && carry >= -(1ll << 30) && carry <= (1ll << 30)) {
+            if (LCF) {
+                // second differences: delta = (q - q1) - (q1 - q2), so the LV code
+                // builders apply to the first differences
+                if (__all_sync(0xffffffffu, ok) && carry >= -(1ll << 28) && carry <= (1ll << 28) &&
+                    carry2 >= -(1ll << 28) && carry2 <= (1ll << 28)) {
+                    int qp = __shfl_up_sync(0xffffffffu, q32[3], 1);
+                    int qpp = __shfl_up_sync(0xffffffffu, q32[2], 1);
+                    if (lane == 0) { qp = (int)carry; qpp = (int)carry2; }
+                    cd[0] = code32(q32[0] - qp, qp - qpp, vb[0]);
+                    cd[1] = code32(q32[1] - q32[0], q32[0] - qp, vb[1]);
+                    cd[2] = code32(q32[2] - q32[1], q32[1] - q32[0], vb[2]);
+                    cd[3] = code32(q32[3] - q32[2], q32[2] - q32[1], vb[3]);
+                    carry = __shfl_sync(0xffffffffu, q32[3], 31);
+                    carry2 = __shfl_sync(0xffffffffu, q32[2], 31);
+                } else {
+                    long long q[4];
+                    bool v2[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) lattice_q(x[j], P, q[j], v2[j]);
+                    long long qp = __shfl_up_sync(0xffffffffu, q[3], 1);
+                    long long qpp = __shfl_up_sync(0xffffffffu, q[2], 1);
+                    if (lane == 0) { qp = carry; qpp = carry2; }
+                    cd[0] = make_code(q[0] - qp, qp - qpp, v2[0]);
+                    cd[1] = make_code(q[1] - q[0], q[0] - qp, v2[1]);
+                    cd[2] = make_code(q[2] - q[1], q[1] - q[0], v2[2]);
+                    cd[3] = make_code(q[3] - q[2], q[2] - q[1], v2[3]);
+                    carry = __shfl_sync(0xffffffffu, q[3], 31);
+                    carry2 = __shfl_sync(0xffffffffu, q[2], 31);
+                }
+            } else if (__all_sync(0xffffffffu, ok) && carry >= -(1ll << 30) && carry <= (1ll << 30)) {
                 int qp = __shfl_up_sync(0xffffffffu, q32[3], 1);
                 if (lane == 0) qp = (int)carry;
                 cd[0] = code32(q32[0], qp, vb[0]);
@@ -298,12 +363,12 @@ __device__ __forceinline__ void quant_issue(const CompressArgs& a, uint32_t cc, 
 }
 
 // The same loop reading the input from global memory (unaligned input).
-template <bool STORE>
+template <bool STORE, bool LCF = false>
 __device__ __forceinline__ void quant_array_global(const CompressArgs& a, const LatticeParams& P, uint32_t first,
                                                    uint32_t step, uint32_t* sh, uint32_t* s_esc) {
     uint32_t since = 0;
     for (uint32_t c = first; c < a.n_chunks; c += step) {
-        quant_chunk<STORE>(a, P, c, sh, s_esc);
+        quant_chunk<STORE, LCF>(a, P, c, sh, s_esc);
         if (++since == quant_flush_every(a.C)) {
             hist_window_flush(sh, a.hist);
             __syncthreads();
@@ -315,7 +380,7 @@ __device__ __forceinline__ void quant_array_global(const CompressArgs& a, const 
 // The persistent quantize loop of one array over chunks first, first + step,
 // ...: chunk c + step is copied into one stage while chunk c is quantized from
 // the other.  stage: 2 (C + 4) floats, 16-byte aligned.
-template <bool STORE>
+template <bool STORE, bool LCF = false>
 __device__ __forceinline__ void quant_array_staged(const CompressArgs& a, const LatticeParams& P, uint32_t first,
                                                    uint32_t step, float* stage, uint32_t* sh, uint32_t* s_esc) {
     float* buf[2] = {stage, stage + a.C + 4};
@@ -327,7 +392,7 @@ __device__ __forceinline__ void quant_array_staged(const CompressArgs& a, const 
         else asm volatile("cp.async.commit_group;" ::: "memory");
         asm volatile("cp.async.wait_group 1;" ::: "memory");
         __syncthreads();          // chunk c is staged (every thread's pieces)
-        quant_chunk_staged<STORE>(a, P, c, buf[b], sh, s_esc);   // ends with a block barrier
+        quant_chunk_staged<STORE, LCF>(a, P, c, buf[b], sh, s_esc);   // ends with a block barrier
         if (++since == quant_flush_every(a.C)) {
             hist_window_flush(sh, a.hist);
             __syncthreads();

@@ -141,6 +141,7 @@ extern "C" sz_status sz_compress_snapshot(sz_ctx* ctx, int nfields, const sz_fie
     for (int f = 0; f < nfields; ++f) {
         CompressArgs a = make_compress_args(ctx, 0, permuted + (size_t)f * n, n, eb[f], (int)kind, C, G,
                                             kFlagReordered, d_out[f], out_cap[f]);
+        a.pred = params_pred(params);
         if ((st = enqueue_compress(ctx, a, out_bytes ? &out_bytes[f] : nullptr, s)) != SZ_OK) return st;
     }
     if (cudaPeekAtLastError() != cudaSuccess) { cudaGetLastError(); return SZ_ERR_CUDA; }
