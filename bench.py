@@ -198,6 +198,72 @@ def weak_scaling_value(bytes_per_rank: float, seconds_per_step: float, ws: int):
     return b / t / 1e9, t, b
 
 
+RD_EBS = (1e-2, 1e-3, 1e-4, 1e-5, 1e-6)
+
+
+def rd_points(sz, ctx, xs, ebs=RD_EBS, params=None, md_mode=None):
+    """Rate-distortion points (Fig. 9) of one snapshot's fields xs (float32
+    CUDA tensors) at value-range-relative bounds `ebs`: bits per value (all
+    fields' stream bits over all values) and PSNR (mean over fields of
+    20 log10(R / RMSE), R = the field's value range; None when lossless).
+    md_mode = SZ_MODE_LV_PRX compresses xs (xx, yy, zz) as one reordered MD
+    snapshot and compares each decoded field with the reordered original.
+    Also the closed form -20 log10(eb / sqrt 3) of uniform quantization noise
+    and the worst |x - x'| / (eb R) over the fields."""
+    import torch
+    pts = []
+    n_tot = sum(x.numel() for x in xs)
+    for eb in ebs:
+        if md_mode is None:
+            outs, nb = sz.sz_compress_batch(ctx, xs, [eb] * len(xs), sz.SZ_EB_REL, params=params)
+            refs = xs
+        else:
+            n = xs[0].numel()
+            perm = torch.empty(n, dtype=torch.int32, device=xs[0].device)
+            outs, nb = sz.sz_compress_snapshot(ctx, [sz.SZ_FIELD_XX, sz.SZ_FIELD_YY, sz.SZ_FIELD_ZZ], xs, n,
+                                               [eb] * 3, sz.SZ_EB_REL, md_mode, params, perm=perm)
+        sz.sz_sync(ctx)
+        sizes = [int(nb[i]) for i in range(len(xs))]
+        if md_mode is not None:
+            refs = [x[perm.long()] for x in xs]
+        ys = [torch.empty_like(x) for x in xs]
+        sz.sz_decompress_batch(ctx, outs, sizes, ys)
+        sz.sz_sync(ctx)
+        psnr, worst, lossless = [], 0.0, True
+        for x, y in zip(refs, ys):
+            fin = torch.isfinite(x)
+            R = (x[fin].max().double() - x[fin].min().double()).item()
+            e = x[fin].double() - y[fin].double()
+            mse = e.square().mean().item()
+            if mse > 0:
+                lossless = False
+                psnr.append(20 * math.log10(R / math.sqrt(mse)))
+            if R > 0:
+                worst = max(worst, e.abs().max().item() / (eb * R))
+        pts.append({"eb": eb, "bits_per_value": 8 * sum(sizes) / n_tot,
+                    "psnr_db": None if lossless else sum(psnr) / len(psnr),
+                    "psnr_closed_form_db": -20 * math.log10(eb / math.sqrt(3)), "max_err_over_eb": worst})
+    return pts
+
+
+def rd_bench(sz, device, xs):
+    """Fig. 9 sweep: the large cosmology snapshot under LV and LCF, and the
+    MD snapshot under best_speed (LV) and best_tradeoff (LV-PRX, p = 6)."""
+    import synth
+    ctx = sz.Context(device)
+    out = {"ebs": list(RD_EBS),
+           "cosmology_lv": rd_points(sz, ctx, xs),
+           "cosmology_lcf": rd_points(sz, ctx, xs, params=sz._params(predictor=sz.SZ_PRED_LCF))}
+    md = synth.md_fcc(device="cuda")
+    ms = [md[f] for f in ("xx", "yy", "zz")]
+    out["md_lv"] = rd_points(sz, ctx, ms)
+    out["md_lv_prx"] = rd_points(sz, ctx, ms, params=sz._params(0, 0, 16384, 6), md_mode=sz.SZ_MODE_LV_PRX)
+    out["note"] = ("bits/value = 8 x stream bytes / values; PSNR averaged over fields; None = lossless "
+                   "(the raw fallback)")
+    ctx.close()
+    return out
+
+
 def lcf_bench(sz, ctx, stream, step, xs, ys, outs, args, raw_bytes, ratio_lv):
     """The per-array path with the LCF predictor on the benchmark arrays:
     compress / decompress GB/s from CUDA events, the ratio against LV's, and
@@ -605,6 +671,7 @@ def main():
     ap.add_argument("--eb", type=float, default=1e-4)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-lcf", action="store_true")
+    ap.add_argument("--no-rd", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-log2n", type=int, default=24)
     ap.add_argument("--no-serve", action="store_true")
@@ -860,6 +927,11 @@ def main():
     if rank == 0 and not args.no_md:
         md = md_bench(sz, local, args.steps)
 
+    # ---- rate-distortion sweep (rank 0; Fig. 9) ----------------------------------
+    rd = None
+    if rank == 0 and not args.no_rd:
+        rd = rd_bench(sz, local, xs)
+
     # ---- served form (rank 0): Poisson arrivals vs the same requests serially --
     served = None
     if rank == 0 and not args.no_serve:
@@ -885,7 +957,7 @@ def main():
             "compress_frac_hbm": comp_gbs / peak, "decompress_frac_hbm": decomp_gbs / peak,
             "ratio": ratio, "roofline": roofline, "kernels": kernels, "kernels_plain_path": kernels_plain,
             "gpu_launches": launches,
-            "plain_path": plain, "lcf": lcf, "batched": batched, "md": md, "served": served,
+            "plain_path": plain, "lcf": lcf, "batched": batched, "md": md, "rd": rd, "served": served,
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "wall_s_timed": t_wall,
         }
         print(json.dumps(line))

@@ -640,3 +640,35 @@ def test_lv_beats_lcf_on_particle_data(oracle):
         lv = len(oracle.compress(x, 1e-4, 1, 4096, 64))
         lcf = len(oracle.compress(x, 1e-4, 1, 4096, 64, pred=oracle.PRED_LCF))
         assert lv < lcf
+
+
+# --------------------------------------------------------------------------
+# Rate-distortion (Fig. 9): PSNR of uniform quantization and the rate slope
+# --------------------------------------------------------------------------
+
+def _rd_point(oracle, x, eb):
+    s = oracle.compress(x, eb, 1, 4096, 64)
+    y = oracle.decompress(s).astype(np.float64)
+    xd = x.astype(np.float64)
+    R = xd.max() - xd.min()
+    mse = np.mean((xd - y) ** 2)
+    return 8 * len(s) / x.size, (20 * math.log10(R / math.sqrt(mse)) if mse > 0 else None)
+
+
+def test_rate_distortion_closed_forms(oracle):
+    """Lattice step D = 2 eb R with errors spread uniformly over a step: RMSE
+    = D / sqrt(12), so PSNR = -20 log10(eb / sqrt 3) (84.77 dB at 1e-4).  At
+    high rate each decade of eb costs log2(10) bits, i.e. about 6.02 dB per
+    bit.  A bound below the data's resolution falls back to the raw stream:
+    32 bits per value, no error."""
+    snap = synth.cosmology(1 << 16, 16, 1)
+    for f in ("xx", "vx"):
+        x = snap[f].numpy()
+        pts = {eb: _rd_point(oracle, x, eb) for eb in (1e-2, 1e-3, 1e-4, 1e-5, 1e-8)}
+        for eb in (1e-2, 1e-3, 1e-4, 1e-5):
+            assert abs(pts[eb][1] - (-20 * math.log10(eb / math.sqrt(3)))) < 0.1
+        bits = [pts[eb][0] for eb in (1e-2, 1e-3, 1e-4, 1e-5)]
+        assert bits == sorted(bits)
+        slope = (pts[1e-3][1] - pts[1e-2][1]) / (pts[1e-3][0] - pts[1e-2][0])
+        assert 5.0 < slope < 6.6
+        assert pts[1e-8] == (8 * (160 + 4 * x.size) / x.size, None)
