@@ -1,0 +1,107 @@
+"""The largest array the C ABI accepts: n = 2^32 - 5 float32 (16 GiB, a ragged
+last chunk), so every global index in every kernel passes 2^31 and 2^32 - 1
+elements' worth of histogram counts, escape bases and payload offsets are in
+play.  Checked at full size:
+  * the error bound on every element (device reductions, in slices);
+  * sampled elements bit-exact against the oracle's one-by-one reconstruction
+    (with an absolute bound each element's decoded value is RN32(q D) or the
+    verbatim original, a function of that element alone);
+  * the batched path's stream byte-identical to the plain path's, and the
+    batched decoder's output identical to the plain decoder's.
+The input is a seeded smooth signal plus counter-hash noise, generated on the
+device in slices to bound memory."""
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+N = (1 << 32) - 5
+SLICE = 1 << 28
+EB = 1e-3                       # absolute
+
+
+@pytest.fixture(scope="module")
+def sz():
+    import __graft_entry__ as g
+    g.build()
+    import paper_1711_03888_gb300 as m
+    return m
+
+
+def _fill(x):
+    # x_i = 300 sin(i / 2^20) + 0.05 u_i, u_i in [-1, 1) from a 64-bit mix of i
+    for s in range(0, N, SLICE):
+        e = min(N, s + SLICE)
+        i = torch.arange(s, e, dtype=torch.int64, device="cuda")
+        h = i * 0x2545F4914F6CDD1D                  # int64 products wrap; shifts are arithmetic
+        h = h ^ (h >> 31)
+        h = h * 0x5851F42D4C957F2D
+        h = h ^ (h >> 29)
+        u = (h & ((1 << 24) - 1)).to(torch.float64) / float(1 << 23) - 1.0
+        x[s:e] = (300.0 * torch.sin(i.to(torch.float64) / float(1 << 20)) + 0.05 * u).to(torch.float32)
+        del i, h, u
+
+
+def _sample_idx():
+    rng = np.random.default_rng(7)
+    edges = [0, 1, 2, 4095, 4096, (1 << 31) - 1, 1 << 31, (1 << 31) + 1, (1 << 32) - 4096 * 3, N - 2, N - 1]
+    return np.unique(np.concatenate([np.asarray(edges, np.int64), rng.integers(0, N, 20000)]))
+
+
+@pytest.fixture(scope="module")
+def big(sz):
+    free, total = torch.cuda.mem_get_info()
+    if free < (120 << 30):
+        pytest.skip("needs about 120 GB of free device memory")
+    x = torch.empty(N, dtype=torch.float32, device="cuda")
+    _fill(x)
+    torch.cuda.synchronize()
+    return x
+
+
+def test_max_size_round_trip(sz, big, oracle):
+    x = big
+    ctx = sz.Context(0)
+    try:
+        out, nb = sz.sz_compress(ctx, x, EB, sz.SZ_EB_ABS)
+        sz.sz_sync(ctx)
+        nbytes = nb.value
+        h = oracle.parse_header(out[:160].cpu().numpy().tobytes())
+        assert h["n"] == N and h["flags"] & 1 == 0
+        assert h["n_chunks"] == (N + h["chunk"] - 1) // h["chunk"] and h["total_bytes"] == nbytes
+        y = torch.empty(N, dtype=torch.float32, device="cuda")
+        no = sz.sz_decompress(ctx, out, nbytes, y)
+        sz.sz_sync(ctx)
+        assert no.value == N
+        D = h["D"]
+        worst = 0.0
+        for s in range(0, N, SLICE):
+            e = min(N, s + SLICE)
+            worst = max(worst, (x[s:e].double() - y[s:e].double()).abs().max().item())
+        assert worst <= EB
+        idx = torch.from_numpy(_sample_idx()).cuda()
+        xs = x[idx].cpu().numpy()
+        ys = y[idx].cpu().numpy()
+        q, v = oracle.lattice(xs, np.float32(D), h["eb_abs"])
+        want = np.where(v.astype(bool), xs, np.array([oracle.recon(int(k), D) for k in q], np.float32))
+        assert np.array_equal(ys.view(np.uint32), want.view(np.uint32))
+
+        # the batched path: the big array beside two small ones
+        smalls = [x[:5000].clone(), x[-70001:].clone()]
+        outs, bnb = sz.sz_compress_batch(ctx, [x] + smalls, [EB] * 3, sz.SZ_EB_ABS)
+        sz.sz_sync(ctx)
+        assert bnb[0] == nbytes
+        assert torch.equal(outs[0][:nbytes], out[:nbytes])
+        del out
+        for t, o, k in zip(smalls, outs[1:], (1, 2)):
+            o2, n2 = sz.sz_compress(ctx, t, EB, sz.SZ_EB_ABS)
+            sz.sz_sync(ctx)
+            assert bnb[k] == n2.value and torch.equal(o[: bnb[k]], o2[: n2.value])
+        y2 = torch.empty(N, dtype=torch.float32, device="cuda")
+        ys2 = [y2] + [torch.empty_like(t) for t in smalls]
+        sz.sz_decompress_batch(ctx, outs, [bnb[i] for i in range(3)], ys2)
+        sz.sz_sync(ctx)
+        assert torch.equal(y2.view(torch.int32), y.view(torch.int32))
+    finally:
+        ctx.close()
