@@ -28,7 +28,7 @@ _LIB = os.path.join(_HERE, "libsz_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-OK, ERR_ARG, ERR_NOMEM, ERR_CAPACITY, ERR_CORRUPT = 0, 1, 2, 3, 4
+OK, ERR_ARG, ERR_NOMEM, ERR_CAPACITY, ERR_CORRUPT, ERR_UNSUPPORTED = 0, 1, 2, 3, 4, 5
 HEADER_BYTES = 160
 FLAG_RAW, FLAG_REORDERED = 1, 2
 PRED_LV, PRED_LCF = 1, 2          # header byte 43
@@ -88,6 +88,16 @@ def lib():
         L.szo_segment_sort.argtypes = [vp, u64, C.c_uint32, C.c_uint32, vp]
         L.szo_rindex_perm.restype = i32
         L.szo_rindex_perm.argtypes = [vp, vp, vp, u64, vp, vp, C.c_uint32, C.c_uint32, vp, vp]
+        L.szo_cpc_rice_bits.restype = u64
+        L.szo_cpc_rice_bits.argtypes = [u64, i32]
+        L.szo_cpc_choose_k.restype = i32
+        L.szo_cpc_choose_k.argtypes = [vp, u64]
+        L.szo_cpc_max_bytes.restype = i32
+        L.szo_cpc_max_bytes.argtypes = [u64, vp]
+        L.szo_compress_cpc.restype = i32
+        L.szo_compress_cpc.argtypes = [vp, vp, vp, u64, vp, i32, vp, u64, vp, vp]
+        L.szo_decompress_cpc.restype = i32
+        L.szo_decompress_cpc.argtypes = [vp, u64, vp, vp, vp, u64, vp]
         L.szo_compress_snapshot.restype = i32
         L.szo_compress_snapshot.argtypes = [i32, vp, u64, vp, i32, C.c_uint32, C.c_uint32,
                                             C.c_uint32, C.c_uint32, vp, vp, vp, vp]
@@ -270,6 +280,57 @@ def compress_snapshot(fields, eb, kind: int = 1, chunk: int = 8192, sub: int = 1
     if rc:
         raise OracleError(rc, "compress_snapshot")
     return [outs[f][: int(nbytes[f])].tobytes() for f in range(nf)], perm[:n]
+
+
+def cpc_rice_bits(d: int, k: int) -> int:
+    return int(lib().szo_cpc_rice_bits(d, k))
+
+
+def cpc_choose_k(deltas) -> int:
+    d = np.ascontiguousarray(deltas, np.uint64)
+    return int(lib().szo_cpc_choose_k(_p(d), d.size))
+
+
+def compress_cpc(x, y, z, eb, kind: int = 1):
+    """SZ-CPC2000 coordinates (Sec. II CPC2000 steps 1-4): one stream for the
+    three coordinate arrays; returns (stream, perm), perm[j] = the original
+    index of the particle at sorted position j."""
+    f = [_f32(a) for a in (x, y, z)]
+    n = f[0].size
+    ebs = np.asarray(eb if np.ndim(eb) else [eb] * 3, np.float64)
+    cap = C.c_uint64()
+    lib().szo_cpc_max_bytes(n, C.byref(cap))
+    out = np.zeros(cap.value, np.uint8)
+    nb = C.c_uint64()
+    perm = np.zeros(max(n, 1), np.uint32)
+    rc = lib().szo_compress_cpc(_p(f[0]), _p(f[1]), _p(f[2]), n, _p(ebs), kind, _p(out), cap.value, C.byref(nb),
+                                _p(perm))
+    if rc:
+        raise OracleError(rc, "compress_cpc")
+    return out[: nb.value].tobytes(), perm[:n]
+
+
+def decompress_cpc(stream: bytes):
+    buf = np.frombuffer(stream, np.uint8).copy()
+    n = struct.unpack_from("<Q", buf, 8)[0] if buf.size >= 16 else 0
+    outs = [np.zeros(max(n, 1), np.float32) for _ in range(3)]
+    no = C.c_uint64()
+    rc = lib().szo_decompress_cpc(_p(buf), buf.size, _p(outs[0]), _p(outs[1]), _p(outs[2]), n, C.byref(no))
+    if rc:
+        raise OracleError(rc, "decompress_cpc")
+    return [o[: no.value] for o in outs]
+
+
+def compress_snapshot_cpc(fields, eb, kind: int = 1, chunk: int = 8192, sub: int = 128):
+    """SZ-CPC2000 (Sec. IV-B, best_compression): the coordinates (fields 0-2)
+    by CPC2000, every further field reordered by the same permutation and
+    compressed with SZ-LV.  Returns ([coordinate stream, further streams...],
+    perm)."""
+    nf = len(fields)
+    ebs = list(eb) if np.ndim(eb) else [eb] * nf
+    s, perm = compress_cpc(fields[0], fields[1], fields[2], ebs[:3], kind)
+    rest = [compress(_f32(fields[f])[perm], ebs[f], kind, chunk, sub, reordered=True) for f in range(3, nf)]
+    return [s] + rest, perm
 
 
 _HDR = struct.Struct("<IHHQdIIIIHBBIQQQQ8QQQ")

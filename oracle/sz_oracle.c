@@ -712,3 +712,266 @@ int szo_compress_snapshot(int nfields, const float* const* in, uint64_t n, const
     free(perm); free(tmp);
     return rc;
 }
+
+/* ------------------------------------------------------------------------ */
+/* SZ-CPC2000 coordinates (Sec. II CPC2000 steps 1-4; Sec. IV-B SZ-CPC2000)  */
+/* ------------------------------------------------------------------------ */
+/*
+ * Step 1: each coordinate onto its own lattice (the SZ-LV lattice and
+ * verbatim rule).  Step 2: the lossless R-index key of every particle (bit
+ * 3k+2 = x_k, 3k+1 = y_k, 3k = z_k of u = q - min q; 3b <= 63 or the bound
+ * is too fine for the key).  Step 3: all particles stably sorted by key and
+ * the differences of adjacent keys taken.  Step 4: the differences coded
+ * with a Rice code whose parameter k is chosen per block of 4096 particles
+ * (the paper's "adaptive variable-length code" is not given; this is the
+ * reading): d >> k zero bits, a one bit, then the low k bits of d, MSB-first.
+ * Each block restarts from its first key (stored raw), so blocks decode
+ * independently; 32 sub-streams of 128 particles per block carry their bit
+ * offsets.  Verbatim coordinates are exception records.
+ *
+ * Stream ("SZCP", version 1, little-endian), sections on 16-byte boundaries:
+ *   0 u32 magic 0x50435A53 | 4 u16 version | 6 u16 header bytes (160)
+ *   8 u64 n | 16 f64 eb_abs[3] | 40 u32 D[3] (float bits) | 52 u32 b
+ *   56 i64 qmin[3] | 80 u32 block (4096) | 84 u32 sub-streams per block (32)
+ *   88 u64 n_blocks | 96 u64 n_exceptions | 104 u64 payload words
+ *   112 u64 offsets: first keys u64[nb] | 120 block word offsets u64[nb+1]
+ *   128 Rice parameters u8[nb] | 136 sub-stream bit offsets u32[nb*32]
+ *   144 exceptions {u64 position, u32 axis, u32 raw bits}[ne] | 152 payload
+ */
+#define O_CPC_MAGIC   0x50435A53u
+#define O_CPC_BLOCK   4096u
+#define O_CPC_SUBS    32u
+#define O_CPC_SUBLEN  (O_CPC_BLOCK / O_CPC_SUBS)
+#define SZO_ERR_UNSUPPORTED 5
+
+uint64_t szo_cpc_rice_bits(uint64_t d, int k) { return (d >> k) + 1u + (uint64_t)k; }
+
+/* k in [0, 63] minimising the Rice bits of d[0..L) (the smallest on ties) */
+int szo_cpc_choose_k(const uint64_t* d, uint64_t L)
+{
+    int best_k = 0;
+    uint64_t best = UINT64_MAX;
+    for (int k = 0; k < 64; ++k) {
+        uint64_t t = 0;
+        for (uint64_t i = 0; i < L; ++i) t += szo_cpc_rice_bits(d[i], k);
+        if (t < best) { best = t; best_k = k; }
+    }
+    return best_k;
+}
+
+static void put_bits64(uint8_t* payload, uint64_t* bitpos, uint64_t v, int len)
+{
+    for (int i = len - 1; i >= 0; --i) {
+        if ((v >> i) & 1u) {
+            uint64_t word = *bitpos >> 5;
+            uint32_t bit = 31u - (uint32_t)(*bitpos & 31u);
+            payload[4 * word + bit / 8] |= (uint8_t)(1u << (bit % 8));
+        }
+        (*bitpos)++;
+    }
+}
+
+/* max(1, ...) allocations */
+static void* zalloc(size_t b) { return calloc(b ? b : 1, 1); }
+
+int szo_cpc_max_bytes(uint64_t n, uint64_t* bytes)
+{
+    uint64_t nb = (n + O_CPC_BLOCK - 1) / O_CPC_BLOCK;
+    /* header + tables + 3 exceptions per particle + 65 bits per particle + padding */
+    *bytes = O_HEADER_BYTES + 16 * 6 + 8 * nb + 8 * (nb + 1) + nb + 4 * O_CPC_SUBS * nb + 48 * n + 9 * n + 4 * nb + 64;
+    return SZO_OK;
+}
+
+int szo_compress_cpc(const float* x, const float* y, const float* z, uint64_t n, const double eb[3], int kind,
+                     uint8_t* out, uint64_t cap, uint64_t* out_bytes, uint32_t* perm_out)
+{
+    *out_bytes = 0;
+    const float* f[3] = {x, y, z};
+    double ea[3];
+    float D[3];
+    for (int a = 0; a < 3; ++a) {
+        int rc = szo_error_bound(f[a], n, eb[a], kind, &ea[a], &D[a]);
+        if (rc) return rc;
+    }
+    int64_t* q[3] = {NULL, NULL, NULL};
+    uint8_t* vb[3] = {NULL, NULL, NULL};
+    uint64_t* key = (uint64_t*)zalloc(8 * n);
+    ki_t* kv = (ki_t*)zalloc(sizeof(ki_t) * n);
+    uint64_t* d = (uint64_t*)zalloc(8 * O_CPC_BLOCK);
+    int rc = SZO_OK;
+    for (int a = 0; a < 3; ++a) { q[a] = (int64_t*)zalloc(8 * n); vb[a] = (uint8_t*)zalloc(n); }
+    if (!key || !kv || !d || !q[0] || !q[1] || !q[2] || !vb[0] || !vb[1] || !vb[2]) { rc = SZO_ERR_NOMEM; goto out; }
+    /* step 1 */
+    for (int a = 0; a < 3; ++a) szo_lattice(f[a], n, D[a], ea[a], q[a], vb[a]);
+    int64_t qmin[3] = {0, 0, 0};
+    uint64_t umax = 0;
+    for (int a = 0; a < 3 && n; ++a) {
+        qmin[a] = q[a][0];
+        for (uint64_t i = 1; i < n; ++i) if (q[a][i] < qmin[a]) qmin[a] = q[a][i];
+        for (uint64_t i = 0; i < n; ++i) {
+            uint64_t u = (uint64_t)(q[a][i] - qmin[a]);
+            if (u > umax) umax = u;
+        }
+    }
+    int b = 0;
+    while (b < 64 && (umax >> b) != 0) ++b;
+    if (b > 21) { rc = SZO_ERR_UNSUPPORTED; goto out; }
+    /* step 2 */
+    for (uint64_t i = 0; i < n; ++i)
+        key[i] = szo_morton3((uint64_t)(q[0][i] - qmin[0]), (uint64_t)(q[1][i] - qmin[1]),
+                             (uint64_t)(q[2][i] - qmin[2]), b);
+    /* step 3: stable sort by key */
+    for (uint64_t i = 0; i < n; ++i) { kv[i].k = key[i]; kv[i].i = i; }
+    qsort(kv, n, sizeof(ki_t), ki_cmp);
+    /* layout */
+    uint64_t nb = (n + O_CPC_BLOCK - 1) / O_CPC_BLOCK;
+    uint64_t ne = 0;
+    for (uint64_t j = 0; j < n; ++j)
+        for (int a = 0; a < 3; ++a) ne += vb[a][kv[j].i];
+    uint8_t* ks = (uint8_t*)zalloc(nb);
+    uint64_t* bwords = (uint64_t*)zalloc(8 * (nb + 1));
+    uint32_t* subs = (uint32_t*)zalloc(4 * O_CPC_SUBS * nb);
+    if (!ks || !bwords || !subs) { free(ks); free(bwords); free(subs); rc = SZO_ERR_NOMEM; goto out; }
+    uint64_t words = 0;
+    for (uint64_t blk = 0; blk < nb; ++blk) {
+        uint64_t j0 = blk * O_CPC_BLOCK, L = n - j0 < O_CPC_BLOCK ? n - j0 : O_CPC_BLOCK;
+        for (uint64_t i = 0; i < L; ++i) d[i] = i ? kv[j0 + i].k - kv[j0 + i - 1].k : 0;
+        int k = szo_cpc_choose_k(d, L);
+        ks[blk] = (uint8_t)k;
+        uint64_t bits = 0;
+        for (uint32_t s = 0; s < O_CPC_SUBS; ++s) {
+            subs[blk * O_CPC_SUBS + s] = (uint32_t)bits;
+            for (uint64_t i = (uint64_t)s * O_CPC_SUBLEN; i < (uint64_t)(s + 1) * O_CPC_SUBLEN && i < L; ++i)
+                bits += szo_cpc_rice_bits(d[i], k);
+        }
+        bwords[blk] = words;
+        words += (bits + 31) / 32;
+    }
+    bwords[nb] = words;
+    uint64_t off[6], o = O_HEADER_BYTES;
+    off[0] = o; o = pad16(o + 8 * nb);
+    off[1] = o; o = pad16(o + 8 * (nb + 1));
+    off[2] = o; o = pad16(o + nb);
+    off[3] = o; o = pad16(o + 4 * O_CPC_SUBS * nb);
+    off[4] = o; o = pad16(o + 16 * ne);
+    off[5] = o;
+    uint64_t total = o + 4 * words;
+    *out_bytes = total;
+    if (cap < total) { rc = SZO_ERR_CAPACITY; free(ks); free(bwords); free(subs); goto out; }
+    memset(out, 0, total);
+    put_u32(out + 0, O_CPC_MAGIC);
+    put_u16(out + 4, 1);
+    put_u16(out + 6, (uint16_t)O_HEADER_BYTES);
+    put_u64(out + 8, n);
+    for (int a = 0; a < 3; ++a) {
+        put_u64(out + 16 + 8 * a, d2u(ea[a]));
+        put_u32(out + 40 + 4 * a, f2u(D[a]));
+        put_u64(out + 56 + 8 * a, (uint64_t)qmin[a]);
+    }
+    put_u32(out + 52, (uint32_t)b);
+    put_u32(out + 80, O_CPC_BLOCK);
+    put_u32(out + 84, O_CPC_SUBS);
+    put_u64(out + 88, nb);
+    put_u64(out + 96, ne);
+    put_u64(out + 104, words);
+    for (int s = 0; s < 6; ++s) put_u64(out + 112 + 8 * s, off[s]);
+    for (uint64_t blk = 0; blk < nb; ++blk) {
+        uint64_t j0 = blk * O_CPC_BLOCK, L = n - j0 < O_CPC_BLOCK ? n - j0 : O_CPC_BLOCK;
+        put_u64(out + off[0] + 8 * blk, kv[j0].k);
+        out[off[2] + blk] = ks[blk];
+        for (uint32_t s = 0; s < O_CPC_SUBS; ++s) put_u32(out + off[3] + 4 * (blk * O_CPC_SUBS + s), subs[blk * O_CPC_SUBS + s]);
+        uint64_t bitpos = 32 * bwords[blk];
+        for (uint64_t i = 0; i < L; ++i) {
+            uint64_t dd = i ? kv[j0 + i].k - kv[j0 + i - 1].k : 0;
+            int k = ks[blk];
+            bitpos += dd >> k;                       /* zero bits */
+            put_bits64(out + off[5], &bitpos, 1u, 1);
+            if (k) put_bits64(out + off[5], &bitpos, dd & ((k == 64) ? ~0ull : ((1ull << k) - 1)), k);
+        }
+    }
+    for (uint64_t blk = 0; blk <= nb; ++blk) put_u64(out + off[1] + 8 * blk, bwords[blk]);
+    {
+        uint64_t e = 0;
+        for (uint64_t j = 0; j < n; ++j)
+            for (int a = 0; a < 3; ++a)
+                if (vb[a][kv[j].i]) {
+                    uint8_t* r = out + off[4] + 16 * e++;
+                    put_u64(r, j);
+                    put_u32(r + 8, (uint32_t)a);
+                    put_u32(r + 12, f2u(f[a][kv[j].i]));
+                }
+    }
+    if (perm_out) for (uint64_t j = 0; j < n; ++j) perm_out[j] = (uint32_t)kv[j].i;
+    free(ks); free(bwords); free(subs);
+out:
+    free(key); free(kv); free(d);
+    for (int a = 0; a < 3; ++a) { free(q[a]); free(vb[a]); }
+    return rc;
+}
+
+/* Inverse of the Morton interleave: u_axis from key (axis 0 = x leads). */
+static uint64_t demorton(uint64_t key, int axis, int b)
+{
+    uint64_t u = 0;
+    for (int k = 0; k < b; ++k) u |= ((key >> (3 * k + (2 - axis))) & 1u) << k;
+    return u;
+}
+
+/* Decode an SZCP stream into the sorted coordinates (x, y, z hold n_cap). */
+int szo_decompress_cpc(const uint8_t* in, uint64_t in_bytes, float* x, float* y, float* z, uint64_t n_cap,
+                       uint64_t* n_out)
+{
+    *n_out = 0;
+    if (in_bytes < O_HEADER_BYTES || get_u32(in) != O_CPC_MAGIC || get_u16(in + 4) != 1) return SZO_ERR_CORRUPT;
+    uint64_t n = get_u64(in + 8), nb = get_u64(in + 88), ne = get_u64(in + 96), words = get_u64(in + 104);
+    int b = (int)get_u32(in + 52);
+    if (get_u32(in + 80) != O_CPC_BLOCK || get_u32(in + 84) != O_CPC_SUBS || b > 21) return SZO_ERR_CORRUPT;
+    if (nb != (n + O_CPC_BLOCK - 1) / O_CPC_BLOCK) return SZO_ERR_CORRUPT;
+    float D[3];
+    int64_t qmin[3];
+    uint64_t off[6];
+    for (int a = 0; a < 3; ++a) { D[a] = u2f(get_u32(in + 40 + 4 * a)); qmin[a] = (int64_t)get_u64(in + 56 + 8 * a); }
+    for (int s = 0; s < 6; ++s) off[s] = get_u64(in + 112 + 8 * s);
+    if (off[0] < O_HEADER_BYTES || off[0] + 8 * nb > off[1] || off[1] + 8 * (nb + 1) > off[2] || off[2] + nb > off[3] ||
+        off[3] + 4 * O_CPC_SUBS * nb > off[4] || off[4] + 16 * ne > off[5] || off[5] + 4 * words > in_bytes)
+        return SZO_ERR_CORRUPT;
+    *n_out = n;
+    if (n > n_cap) return SZO_ERR_CAPACITY;
+    float* o[3] = {x, y, z};
+    const uint8_t* payload = in + off[5];
+    for (uint64_t blk = 0; blk < nb; ++blk) {
+        uint64_t j0 = blk * O_CPC_BLOCK, L = n - j0 < O_CPC_BLOCK ? n - j0 : O_CPC_BLOCK;
+        uint64_t key = get_u64(in + off[0] + 8 * blk);
+        uint64_t wb = get_u64(in + off[1] + 8 * blk), we = get_u64(in + off[1] + 8 * (blk + 1));
+        int k = in[off[2] + blk];
+        if (wb > we || we > words || k > 63) return SZO_ERR_CORRUPT;
+        uint64_t bitpos = 32 * wb, end = 32 * we;
+        for (uint64_t i = 0; i < L; ++i) {
+            uint64_t zeros = 0;
+            while (1) {
+                if (bitpos >= end) return SZO_ERR_CORRUPT;
+                if (get_bit(payload, bitpos++)) break;
+                zeros++;
+            }
+            uint64_t r = 0;
+            for (int t = 0; t < k; ++t) {
+                if (bitpos >= end) return SZO_ERR_CORRUPT;
+                r = (r << 1) | (uint64_t)get_bit(payload, bitpos++);
+            }
+            uint64_t dd = (zeros << k) | r;
+            if (i) key += dd;
+            for (int a = 0; a < 3; ++a) {
+                int64_t qa = (int64_t)demorton(key, a, b) + qmin[a];
+                o[a][j0 + i] = szo_recon(qa, D[a]);
+            }
+        }
+    }
+    for (uint64_t e = 0; e < ne; ++e) {
+        const uint8_t* r = in + off[4] + 16 * e;
+        uint64_t j = get_u64(r);
+        uint32_t a = get_u32(r + 8);
+        if (j >= n || a > 2) return SZO_ERR_CORRUPT;
+        o[a][j] = u2f(get_u32(r + 12));
+    }
+    return SZO_OK;
+}

@@ -672,3 +672,104 @@ def test_rate_distortion_closed_forms(oracle):
         slope = (pts[1e-3][1] - pts[1e-2][1]) / (pts[1e-3][0] - pts[1e-2][0])
         assert 5.0 < slope < 6.6
         assert pts[1e-8] == (8 * (160 + 4 * x.size) / x.size, None)
+
+
+# --------------------------------------------------------------------------
+# SZ-CPC2000 coordinates (Sec. II CPC2000 steps 1-4; Sec. IV-B; Fig. 2)
+# --------------------------------------------------------------------------
+
+def _cpc_fields(s):
+    h = struct.unpack_from("<IHHQ3d3IIqqqIIQQQ6Q", s, 0)
+    return {"n": h[3], "D": h[7:10], "b": h[10], "qmin": h[11:14], "block": h[14], "subs": h[15], "nb": h[16],
+            "ne": h[17], "words": h[18], "off": h[19:25]}
+
+
+def test_cpc_golden_examples(oracle):
+    for case in _load("cpc_examples.json")["cases"]:
+        xyz = np.asarray(case["xyz"], np.float32)
+        s, perm = oracle.compress_cpc(xyz[:, 0], xyz[:, 1], xyz[:, 2], 0.5, kind=0)
+        h = _cpc_fields(s)
+        assert list(h["qmin"]) == case["qmin"] and h["b"] == case["b"] and h["ne"] == 0
+        assert perm.tolist() == case["perm"]
+        assert struct.unpack_from("<Q", s, h["off"][0])[0] == case["first_key"]
+        assert s[h["off"][2]] == case["k"]
+        subs = struct.unpack_from("<32I", s, h["off"][3])
+        assert subs[0] == 0 and all(v == case["bits"] for v in subs[1:])
+        assert h["words"] == 1 and struct.unpack_from("<I", s, h["off"][5])[0] == case["word0"]
+        back = oracle.decompress_cpc(s)
+        for a in range(3):
+            assert back[a].tolist() == xyz[perm, a].tolist()
+
+
+def test_cpc_rice_parameter_is_the_cheapest(oracle):
+    """The per-block k gives the fewest bits (smallest k on ties), and for
+    geometric differences of mean m it sits near log2(m) (Golomb-Rice)."""
+    rng = np.random.default_rng(8)
+    for mean in (0.3, 5.0, 300.0, 70000.0):
+        d = rng.geometric(1.0 / (mean + 1.0), 4096).astype(np.uint64) - 1
+        k = oracle.cpc_choose_k(d)
+        cost = [int(np.sum(d >> np.uint64(j))) + d.size * (1 + j) for j in range(64)]
+        assert cost[k] == min(cost) and cost.index(min(cost)) == k
+        assert abs(k - max(0.0, math.log2(mean))) <= 1.5
+    assert oracle.cpc_rice_bits(9, 2) == 5 and oracle.cpc_rice_bits(0, 0) == 1
+
+
+def _md_xyz(cells, seed=2):
+    md = synth.md_fcc(cells=cells, seed=seed)
+    return [md[k].numpy() for k in ("xx", "yy", "zz")]
+
+
+@pytest.mark.parametrize("eb,kind", [(1e-3, 1), (1e-4, 1), (0.01, 0)])
+def test_cpc_round_trip_is_the_sorted_lattice(oracle, eb, kind):
+    """Decoding gives, at every sorted position j, the lattice reconstruction
+    RN32(q D) of particle perm[j] (its verbatim value where the lattice
+    misses the bound), and perm is the stable full R-index sort (the segment
+    sort with one segment and no ignored digits)."""
+    f = _md_xyz(12)
+    f[1][::997] = np.nan
+    f[2][5::1301] = np.inf
+    s, perm = oracle.compress_cpc(*f, eb, kind)
+    back = oracle.decompress_cpc(s)
+    qs = []
+    for a in range(3):
+        ea, D = oracle.error_bound(f[a], eb, kind)
+        q, v = oracle.lattice(f[a], D, ea)
+        qs.append(q)
+        want = np.where(v.astype(bool), f[a], np.array([oracle.recon(int(k), D) for k in q], np.float32))
+        assert (_f32bits(back[a]) == _f32bits(want[perm])).all()
+        fin = np.isfinite(f[a])
+        assert (np.abs(f[a][perm][fin[perm]].astype(np.float64) - back[a][fin[perm]]) <= ea).all()
+    keys, b = oracle.rindex_keys(*qs)
+    assert b <= 21
+    assert (perm == oracle.segment_sort(keys, f[0].size, 0)).all()
+    assert _cpc_fields(s)["ne"] >= (~np.isfinite(f[1])).sum() + (~np.isfinite(f[2])).sum()
+
+
+def test_cpc_block_edges_and_limits(oracle):
+    for n in (0, 1, 2, 4095, 4096, 4097, 12289):
+        f = [synth.uniform_f32(n, 30 + a, 0.0, 100.0).numpy() for a in range(3)]
+        s, perm = oracle.compress_cpc(*f, 1e-3)
+        h = _cpc_fields(s)
+        assert h["n"] == n and h["nb"] == (n + 4095) // 4096
+        back = oracle.decompress_cpc(s)
+        for a in range(3):
+            assert back[a].size == n
+    # a bound so fine that a key would need more than 63 bits
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.compress_cpc(*_md_xyz(5), 1e-8)
+    assert e.value.rc == oracle.ERR_UNSUPPORTED
+
+
+def test_cpc_trend_on_md(oracle):
+    """Fig. 2 / Sec. IV-B trend: on disordered MD coordinates CPC2000 beats
+    SZ-LV in stored order at both bounds and the segment-sorted SZ-LV-PRX
+    at 1e-3."""
+    f = _md_xyz(25)
+    raw = 12 * f[0].size
+    for eb in (1e-3, 1e-4):
+        lv = raw / sum(len(oracle.compress(a, eb)) for a in f)
+        cpc = raw / len(oracle.compress_cpc(*f, eb)[0])
+        assert cpc > lv * 1.1
+        if eb == 1e-3:
+            prx = raw / sum(len(s) for s in oracle.compress_snapshot(f, eb, 1, 8192, 128, 16384, 6)[0])
+            assert cpc > prx
