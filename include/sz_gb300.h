@@ -58,8 +58,9 @@ typedef enum {
 typedef enum { SZ_EB_ABS = 0, SZ_EB_REL = 1 } sz_eb_kind;
 
 /* Sec. V: the three molecular-dynamics modes.  SZ_MODE_LV = best_speed (SZ-LV),
- * SZ_MODE_LV_PRX = best_tradeoff (SZ-LV-PRX), SZ_MODE_CPC2000 = best_compression
- * (SZ-CPC2000, not built: returns SZ_ERR_UNSUPPORTED). */
+ * SZ_MODE_LV_PRX = best_tradeoff (SZ-LV-PRX), SZ_MODE_CPC2000 =
+ * best_compression (SZ-CPC2000: CPC2000 on the coordinates, SZ-LV on the
+ * other fields in the same order; see sz_compress_snapshot). */
 typedef enum { SZ_MODE_LV = 0, SZ_MODE_LV_PRX = 1, SZ_MODE_CPC2000 = 2 } sz_mode;
 
 /* Sec. III: the six particle fields. */
@@ -176,12 +177,33 @@ sz_status sz_decompress_host(sz_ctx* ctx, int k, const void* const* h_in, const 
  * three positions (Fig. 3a), stably sorted by key >> 3p within consecutive
  * segments (Tables 4-5).  No index array is stored (Sec. IV-B), so the
  * streams decode to the reordered arrays.  d_perm (device, n uint32, may be
- * NULL) receives the permutation: position j holds original index perm[j]. */
+ * NULL) receives the permutation: position j holds original index perm[j].
+ * SZ_MODE_CPC2000 (Sec. II CPC2000 steps 1-4, Sec. IV-B SZ-CPC2000): all n
+ * particles are stably sorted by the full R-index key (lossless: the lattice
+ * coordinates must fit 21 bits per axis, else SZ_ERR_UNSUPPORTED at
+ * sz_sync); d_out[0] (out_cap[0] >= sz_cpc_max_bytes(n)) receives ONE stream
+ * holding all three coordinates -- key differences in Rice code, per block of
+ * 4096 particles -- and d_out[1], d_out[2] are not written (out_bytes 0, may
+ * be NULL); fields 3.. get SZ-LV streams in the sorted order.  Decode the
+ * coordinate stream with sz_decompress_cpc, the others with sz_decompress. */
 sz_status sz_compress_snapshot(sz_ctx* ctx, int nfields, const sz_field* fields,
                                const float* const* d_in, size_t n, const double* eb, sz_eb_kind kind,
                                sz_mode mode, const sz_params* params, void* const* d_out,
                                const size_t* out_cap, size_t* out_bytes, uint32_t* d_perm,
                                void* stream);
+
+/* Largest SZ-CPC2000 coordinate stream for n particles. */
+size_t sz_cpc_max_bytes(size_t n);
+
+/* Decode an SZ-CPC2000 coordinate stream (device, in_bytes, 16-byte aligned)
+ * into d_out[0..2] (device x, y, z arrays with room for n_cap floats each),
+ * in the stream's sorted particle order.  Every coordinate is within its
+ * axis's eb_abs of the original (non-finite and verbatim values come back
+ * bit-exact).  On sz_sync(), *n_out holds the particle count.  Errors at
+ * sz_sync(): SZ_ERR_CORRUPT (malformed stream; no read leaves in_bytes),
+ * SZ_ERR_CAPACITY (n_cap too small). */
+sz_status sz_decompress_cpc(sz_ctx* ctx, const void* d_in, size_t in_bytes, float* const* d_out, size_t n_cap,
+                            size_t* n_out, void* stream);
 
 /* Wait for the context's work on `stream`, fill the pending host results
  * (out_bytes, n_out) and return the first device error since the last sync

@@ -33,7 +33,8 @@ SZ_OP_COMPRESS, SZ_OP_DECOMPRESS = 0, 1
 HEADER_BYTES = 160
 
 EXPORTS = ("sz_ctx_create", "sz_ctx_destroy", "sz_max_compressed_bytes", "sz_compress", "sz_decompress",
-           "sz_compress_batch", "sz_decompress_batch", "sz_compress_host", "sz_decompress_host", "sz_compress_snapshot", "sz_sync", "sz_status_string",
+           "sz_compress_batch", "sz_decompress_batch", "sz_compress_host", "sz_decompress_host", "sz_compress_snapshot",
+           "sz_cpc_max_bytes", "sz_decompress_cpc", "sz_sync", "sz_status_string",
            "sz_profile_enable", "sz_profile_read", "sz_compress_noalloc",
            "sz_serve_start", "sz_serve_submit", "sz_serve_poll", "sz_serve_wait", "sz_serve_release",
            "sz_serve_stats", "sz_serve_stop")
@@ -78,6 +79,8 @@ _sig = {
     "sz_compress_snapshot": (_st, [_vp, C.c_int, C.POINTER(C.c_int), C.POINTER(_vp), _sz, C.POINTER(C.c_double),
                                    C.c_int, C.c_int, C.POINTER(sz_params), C.POINTER(_vp), C.POINTER(_sz),
                                    C.POINTER(_sz), _vp, _vp]),
+    "sz_cpc_max_bytes": (_sz, [_sz]),
+    "sz_decompress_cpc": (_st, [_vp, _vp, _sz, C.POINTER(_vp), _sz, C.POINTER(_sz), _vp]),
     "sz_sync": (_st, [_vp, _vp]),
     "sz_status_string": (C.c_char_p, [C.c_int]),
     "sz_compress_noalloc": (_st, [_vp, _sz, C.c_double, C.c_int, _vp, _sz, C.POINTER(_sz), _vp]),
@@ -259,6 +262,8 @@ def sz_compress_snapshot(ctx: Context, fields, xs, n: int, ebs, kind: int = SZ_E
     k = len(xs)
     if outs is None:
         outs = [torch.empty(sz_max_compressed_bytes(n), dtype=torch.uint8, device=xs[0].device) for _ in xs]
+        if mode == SZ_MODE_CPC2000:
+            outs[0] = torch.empty(sz_cpc_max_bytes(n), dtype=torch.uint8, device=xs[0].device)
     f = (C.c_int * k)(*fields)
     ins = (C.c_void_p * k)(*[_ptr(x) for x in xs])
     e = (C.c_double * k)(*ebs)
@@ -269,6 +274,21 @@ def sz_compress_snapshot(ctx: Context, fields, xs, n: int, ebs, kind: int = SZ_E
     _check(_lib.sz_compress_snapshot(ctx.handle, k, f, ins, n, e, kind, mode, C.byref(p), o, caps, nb,
                                      _ptr(perm), _stream(stream)), "sz_compress_snapshot")
     return outs, nb
+
+
+def sz_cpc_max_bytes(n: int) -> int:
+    return int(_lib.sz_cpc_max_bytes(n))
+
+
+def sz_decompress_cpc(ctx: Context, stream_buf, in_bytes: int, outs, n_cap=None, stream=None):
+    """Enqueue decoding of an SZ-CPC2000 coordinate stream into three float32
+    CUDA tensors (x, y, z).  Returns a holder whose .value is n after sz_sync."""
+    no = ctx.hold(C.c_size_t(0))
+    o = ctx.hold((C.c_void_p * 3)(*[_ptr(t) for t in outs]))
+    cap = min(t.numel() for t in outs) if n_cap is None else n_cap
+    _check(_lib.sz_decompress_cpc(ctx.handle, _ptr(stream_buf), in_bytes, o, cap, C.byref(no), _stream(stream)),
+           "sz_decompress_cpc")
+    return no
 
 
 def sz_sync(ctx: Context, stream=None, check: bool = True) -> int:

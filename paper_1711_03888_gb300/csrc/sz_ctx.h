@@ -63,6 +63,9 @@ struct sz_ctx {
     size_t host_pool_bytes = 0;
     uint64_t* host_pin = nullptr;
     size_t host_pin_cap = 0;
+    // SZ-CPC2000: sort buffers and per-block tables
+    uint8_t* cpc = nullptr;
+    size_t cpc_bytes = 0;
     // serving loop
     sz_serve_state* serve = nullptr;
     // tracing: event pairs around launches
@@ -90,6 +93,9 @@ struct ProfScope {
 uint32_t tune_chunk(uint64_t n);
 sz_status resolve_params(const sz_params* p, uint64_t n, uint32_t* C, uint32_t* G);
 uint32_t params_pred(const sz_params* p);     // kPredLV or kPredLCF
+size_t cpc_max_bytes(uint64_t n);
+sz_status cpc_compress_coords(sz_ctx* ctx, const ReorderArgs& r, uint64_t n, void* d_out, size_t out_cap,
+                              size_t* out_bytes, uint32_t* perm_out, cudaStream_t s);
 sz_status ctx_reserve(sz_ctx* ctx, int arrays, uint64_t max_chunks, uint64_t max_code_elems);
 CompressArgs make_compress_args(sz_ctx* ctx, int slot, const float* in, uint64_t n, double eb, int kind,
                                 uint32_t C, uint32_t G, uint32_t extra_flags, void* out, uint64_t cap);

@@ -157,6 +157,9 @@ sz_status host_finish(sz_ctx* ctx, cudaStream_t cs, sz_status st) {
 }  // namespace
 
 void sz_ctx::free_host() {
+    if (cpc) cudaFree(cpc);
+    cpc = nullptr;
+    cpc_bytes = 0;
     if (host_pool) cudaFree(host_pool);
     host_pool = nullptr;
     host_pool_bytes = 0;

@@ -62,12 +62,13 @@ extern "C" sz_status sz_compress_snapshot(sz_ctx* ctx, int nfields, const sz_fie
                                           const sz_params* params, void* const* d_out, const size_t* out_cap,
                                           size_t* out_bytes, uint32_t* d_perm, void* stream) {
     if (!ctx || nfields < 1 || !d_in || !eb || !d_out || !out_cap) return SZ_ERR_ARG;
-    if (mode == SZ_MODE_CPC2000) return SZ_ERR_UNSUPPORTED;
-    if (mode != SZ_MODE_LV && mode != SZ_MODE_LV_PRX) return SZ_ERR_ARG;
+    if (mode != SZ_MODE_LV && mode != SZ_MODE_LV_PRX && mode != SZ_MODE_CPC2000) return SZ_ERR_ARG;
+    const bool cpc = mode == SZ_MODE_CPC2000;
     cudaStream_t s = (cudaStream_t)stream;
     cudaSetDevice(ctx->device);
     for (int f = 0; f < nfields; ++f) {
-        sz_status st = validate_compress(d_in[f], n, eb[f], kind, d_out[f]);
+        // best_compression writes all three coordinates to d_out[0]
+        sz_status st = validate_compress(d_in[f], n, eb[f], kind, (cpc && (f == 1 || f == 2)) ? d_out[0] : d_out[f]);
         if (st != SZ_OK) return st;
     }
     uint32_t C, G;
@@ -82,12 +83,13 @@ extern "C" sz_status sz_compress_snapshot(sz_ctx* ctx, int nfields, const sz_fie
         }
         return SZ_OK;
     }
-    // ---- best_tradeoff: SZ-LV-PRX ----------------------------------------------
+    // ---- best_tradeoff (SZ-LV-PRX) and best_compression (SZ-CPC2000) -----------
     if (nfields < 3 || !fields || fields[0] != SZ_FIELD_XX || fields[1] != SZ_FIELD_YY || fields[2] != SZ_FIELD_ZZ)
         return SZ_ERR_ARG;
-    const uint32_t S = (params && params->segment) ? params->segment : 16384u;
-    const uint32_t p = (params && (params->segment || params->ignored_digits)) ? params->ignored_digits : 6u;
-    if (S > 65536u || p > 21u) return SZ_ERR_ARG;
+    // best_compression: keys of one segment with no ignored digits (a full sort follows)
+    const uint32_t S = cpc ? (uint32_t)(n ? n : 1) : (params && params->segment) ? params->segment : 16384u;
+    const uint32_t p = cpc ? 0u : (params && (params->segment || params->ignored_digits)) ? params->ignored_digits : 6u;
+    if ((!cpc && S > 65536u) || p > 21u) return SZ_ERR_ARG;
     if ((st = ctx_reserve(ctx, 3, (n + C - 1) / C, (uint64_t)((n + C - 1) / C) * C)) != SZ_OK) return st;
     uint8_t* md = nullptr;
     if ((st = md_reserve(ctx, n, nfields, &md)) != SZ_OK) return st;
@@ -126,7 +128,16 @@ extern "C" sz_status sz_compress_snapshot(sz_ctx* ctx, int nfields, const sz_fie
         cudaGetLastError();
         return SZ_ERR_CUDA;
     }
-    {
+    if (cpc) {
+        // the coordinates: one SZ-CPC2000 stream in d_out[0]; the permutation into r.perm
+        ProfScope pr(ctx, SZ_PHASE_REORDER, s);
+        launch_rindex_keys(r, s);
+        if ((st = cpc_compress_coords(ctx, r, n, d_out[0], out_cap[0], out_bytes ? &out_bytes[0] : nullptr, r.perm,
+                                      s)) != SZ_OK)
+            return st;
+        if (out_bytes) out_bytes[1] = out_bytes[2] = 0;
+        for (int f = 3; f < nfields; ++f) launch_gather(d_in[f], permuted + (size_t)f * n, r.perm, n, s);
+    } else {
         ProfScope pr(ctx, SZ_PHASE_REORDER, s);
         launch_rindex_keys(r, s);
         launch_segment_sort(r, s);
@@ -137,8 +148,9 @@ extern "C" sz_status sz_compress_snapshot(sz_ctx* ctx, int nfields, const sz_fie
         cudaGetLastError();
         return SZ_ERR_CUDA;
     }
-    // SZ-LV on every reordered field; streams carry the reordered flag
-    for (int f = 0; f < nfields; ++f) {
+    // SZ-LV on every reordered field (best_compression: the fields after the
+    // coordinates); streams carry the reordered flag
+    for (int f = cpc ? 3 : 0; f < nfields; ++f) {
         CompressArgs a = make_compress_args(ctx, 0, permuted + (size_t)f * n, n, eb[f], (int)kind, C, G,
                                             kFlagReordered, d_out[f], out_cap[f]);
         a.pred = params_pred(params);
