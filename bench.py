@@ -465,8 +465,10 @@ def md_bench(sz, device, steps):
     """FCC crystal of 100^3 cells (3.92 M atoms after 2 % vacancies, 10 %
     swapped), xx/yy/zz: best_speed (SZ-LV in stored order) against best_tradeoff
     (SZ-LV-PRX: segment 16384, p = 6 ignored digits, and p = 0 = full radix
-    sort), at rel eb 1e-4 and 1e-3.  Compression GB/s of the three arrays
-    (reordering included) and the ratio; CUDA events on the stream."""
+    sort within segments) and best_compression (SZ-CPC2000: full R-index sort,
+    Rice-coded key differences; also its decoding rate), at rel eb 1e-4 and
+    1e-3.  Compression GB/s of the three arrays (reordering included) and the
+    ratio; CUDA events on the stream."""
     import torch
     import synth
     md = synth.md_fcc(device="cuda")
@@ -478,13 +480,17 @@ def md_bench(sz, device, steps):
     stream = torch.cuda.current_stream()
     out = {"workload": f"MD snapshot: FCC crystal 100^3 cells, {n} atoms, 3 float32 position arrays",
            "atoms": n, "modes": {}}
+    cpc_outs = [torch.empty(sz.sz_cpc_max_bytes(n), dtype=torch.uint8, device="cuda")] + \
+        [torch.empty(16, dtype=torch.uint8, device="cuda") for _ in range(2)]
     for eb in (1e-4, 1e-3):
         for name, mode, p in (("best_speed LV", sz.SZ_MODE_LV, None), ("best_tradeoff LV-PRX p=6", sz.SZ_MODE_LV_PRX, 6),
-                              ("LV-RX (p=0)", sz.SZ_MODE_LV_PRX, 0)):
+                              ("LV-RX (p=0)", sz.SZ_MODE_LV_PRX, 0),
+                              ("best_compression SZ-CPC2000", sz.SZ_MODE_CPC2000, None)):
             params = sz._params(0, 0, 16384, p) if p is not None else None
+            outs_m = cpc_outs if mode == sz.SZ_MODE_CPC2000 else None
 
             def run():
-                return sz.sz_compress_snapshot(ctx, fields, xs, n, [eb] * 3, sz.SZ_EB_REL, mode, params)
+                return sz.sz_compress_snapshot(ctx, fields, xs, n, [eb] * 3, sz.SZ_EB_REL, mode, params, outs=outs_m)
 
             for _ in range(2):
                 outs, nb = run()
@@ -497,8 +503,26 @@ def md_bench(sz, device, steps):
             sz.sz_sync(ctx)
             torch.cuda.synchronize()
             t = sum(a.elapsed_time(b) for a, b in ev) / steps / 1e3
-            out["modes"][f"{name} @ {eb:g}"] = {"compress_gbs": nbytes / t / 1e9, "ms": 1e3 * t,
-                                               "ratio": nbytes / sum(int(nb[i]) for i in range(3))}
+            rec = {"compress_gbs": nbytes / t / 1e9, "ms": 1e3 * t,
+                   "ratio": nbytes / sum(int(nb[i]) for i in range(3))}
+            if mode == sz.SZ_MODE_CPC2000:
+                # decoding the coordinate stream (all three arrays)
+                ys = [torch.empty(n, dtype=torch.float32, device="cuda") for _ in range(3)]
+                size = int(nb[0])
+                for _ in range(2):
+                    sz.sz_decompress_cpc(ctx, outs[0], size, ys)
+                    sz.sz_sync(ctx)
+                evd = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                       for _ in range(steps)]
+                for a, b in evd:
+                    a.record(stream)
+                    sz.sz_decompress_cpc(ctx, outs[0], size, ys)
+                    b.record(stream)
+                sz.sz_sync(ctx)
+                torch.cuda.synchronize()
+                td = sum(a.elapsed_time(b) for a, b in evd) / steps / 1e3
+                rec["decompress_gbs"] = nbytes / td / 1e9
+            out["modes"][f"{name} @ {eb:g}"] = rec
     ctx.close()
     return out
 
