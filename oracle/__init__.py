@@ -88,6 +88,10 @@ def lib():
         L.szo_segment_sort.argtypes = [vp, u64, C.c_uint32, C.c_uint32, vp]
         L.szo_rindex_perm.restype = i32
         L.szo_rindex_perm.argtypes = [vp, vp, vp, u64, vp, vp, C.c_uint32, C.c_uint32, vp, vp]
+        L.szo_morton6.restype = u64
+        L.szo_morton6.argtypes = [vp, i32]
+        L.szo_rindex_keys6.restype = None
+        L.szo_rindex_keys6.argtypes = [vp, u64, vp, vp]
         L.szo_cpc_rice_bits.restype = u64
         L.szo_cpc_rice_bits.argtypes = [u64, i32]
         L.szo_cpc_choose_k.restype = i32
@@ -280,6 +284,49 @@ def compress_snapshot(fields, eb, kind: int = 1, chunk: int = 8192, sub: int = 1
     if rc:
         raise OracleError(rc, "compress_snapshot")
     return [outs[f][: int(nbytes[f])].tobytes() for f in range(nf)], perm[:n]
+
+
+def morton6(u, bits: int) -> int:
+    a = np.ascontiguousarray(u, np.uint64)
+    return int(lib().szo_morton6(_p(a), bits))
+
+
+def rindex_keys6(qs):
+    """R-index keys from six lattice arrays (xx, yy, zz, vx, vy, vz); returns
+    (keys, bits per axis)."""
+    arrs = [np.ascontiguousarray(q, np.int64) for q in qs]
+    ptrs = (C.c_void_p * 6)(*[a.ctypes.data for a in arrs])
+    k = np.zeros(max(arrs[0].size, 1), np.uint64)
+    b = C.c_int()
+    lib().szo_rindex_keys6(C.cast(ptrs, C.c_void_p), arrs[0].size, _p(k), C.byref(b))
+    return k[: arrs[0].size], b.value
+
+
+KEY_XYZ, KEY_V, KEY_XYZV = 0, 1, 2
+
+
+def compress_snapshot_keyed(fields, eb, kind: int = 1, chunk: int = 8192, sub: int = 128, segment: int = 16384,
+                            ignored_digits: int = 6, key: int = KEY_XYZ):
+    """best_tradeoff with the R-index built from the coordinates (Fig. 3a),
+    the velocities (fields 3-5) or all six (Fig. 3b; digits of 6 bits):
+    every field reordered by the segment sort of that key, then SZ-LV.
+    Returns (streams, perm)."""
+    fs = [_f32(f) for f in fields]
+    nf = len(fs)
+    ebs = list(eb) if np.ndim(eb) else [eb] * nf
+    axes = {KEY_XYZ: (0, 1, 2), KEY_V: (3, 4, 5), KEY_XYZV: (0, 1, 2, 3, 4, 5)}[key]
+    qs = []
+    for a in axes:
+        ea, D = error_bound(fs[a], ebs[a], kind)
+        q, _ = lattice(fs[a], D, ea) if D != 0 else (np.zeros(fs[a].size, np.int64), None)
+        qs.append(q)
+    if key == KEY_XYZV:
+        keys, _ = rindex_keys6(qs)
+        perm = segment_sort(keys, segment, 2 * ignored_digits)    # 6-bit digits: shift 6p
+    else:
+        keys, _ = rindex_keys(*qs)
+        perm = segment_sort(keys, segment, ignored_digits)
+    return [compress(f[perm], ebs[i], kind, chunk, sub, reordered=True) for i, f in enumerate(fs)], perm
 
 
 def cpc_rice_bits(d: int, k: int) -> int:

@@ -975,3 +975,45 @@ int szo_decompress_cpc(const uint8_t* in, uint64_t in_bytes, float* x, float* y,
     }
     return SZO_OK;
 }
+
+/* ------------------------------------------------------------------------ */
+/* R-index from coordinates and velocities (Sec. IV-C, Fig. 3b, Table 6)     */
+/* ------------------------------------------------------------------------ */
+
+/* Interleave six integers, one bit of each per 6-bit group, axis 0 leading:
+ * bit 6k + (5 - a) = bit k of u[a]. */
+uint64_t szo_morton6(const uint64_t u[6], int b)
+{
+    uint64_t key = 0;
+    for (int k = 0; k < b; ++k)
+        for (int a = 0; a < 6; ++a) key |= ((u[a] >> k) & 1u) << (6 * k + (5 - a));
+    return key;
+}
+
+/* Keys of n particles from six lattice arrays (xx, yy, zz, vx, vy, vz):
+ * u = q - min(q) per axis; b = bit length of the largest u, at most 10 kept
+ * (the lowest bits dropped so that 6b <= 60). */
+void szo_rindex_keys6(const int64_t* const* q, uint64_t n, uint64_t* key, int* bits_out)
+{
+    if (n == 0) { *bits_out = 0; return; }
+    int64_t qmin[6];
+    uint64_t umax = 0;
+    for (int a = 0; a < 6; ++a) {
+        qmin[a] = q[a][0];
+        for (uint64_t i = 1; i < n; ++i) if (q[a][i] < qmin[a]) qmin[a] = q[a][i];
+        for (uint64_t i = 0; i < n; ++i) {
+            uint64_t u = (uint64_t)(q[a][i] - qmin[a]);
+            if (u > umax) umax = u;
+        }
+    }
+    int b = 0;
+    while (b < 64 && (umax >> b) != 0) ++b;
+    int drop = b > 10 ? b - 10 : 0;
+    if (b > 10) b = 10;
+    for (uint64_t i = 0; i < n; ++i) {
+        uint64_t u[6];
+        for (int a = 0; a < 6; ++a) u[a] = (uint64_t)(q[a][i] - qmin[a]) >> drop;
+        key[i] = szo_morton6(u, b);
+    }
+    *bits_out = b;
+}

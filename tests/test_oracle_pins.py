@@ -773,3 +773,59 @@ def test_cpc_trend_on_md(oracle):
         if eb == 1e-3:
             prx = raw / sum(len(s) for s in oracle.compress_snapshot(f, eb, 1, 8192, 128, 16384, 6)[0])
             assert cpc > prx
+
+
+# --------------------------------------------------------------------------
+# R-index from velocities and from coordinates + velocities (Sec. IV-C,
+# Fig. 3b, Table 6)
+# --------------------------------------------------------------------------
+
+def test_morton6_golden(oracle):
+    """Hand-derived: bit 6k + (5 - a) holds bit k of axis a (xx leads, vz last)."""
+    assert oracle.morton6([1, 0, 0, 0, 0, 1], 1) == 32 + 1
+    assert oracle.morton6([0, 1, 0, 0, 0, 0], 2) == 1 << 4
+    assert oracle.morton6([2, 0, 0, 0, 0, 0], 2) == 1 << 11
+    assert oracle.morton6([0, 0, 0, 3, 0, 0], 2) == (1 << 2) | (1 << 8)
+
+
+def test_six_axis_key_reduces_to_three_axis_order(oracle):
+    """With every velocity equal, the 6-D key orders particles exactly as the
+    3-D coordinate key (no bits dropped at this size), and a keyed snapshot
+    with the coordinate key is the best_tradeoff snapshot."""
+    md = synth.md_fcc(cells=6, seed=4)
+    f = [md[k].numpy() for k in ("xx", "yy", "zz")]
+    n = f[0].size
+    vel = [np.full(n, 1.5, np.float32) for _ in range(3)]
+    qs = []
+    for a in f + vel:
+        ea, D = oracle.error_bound(a, 1e-2, 0)
+        qs.append(oracle.lattice(a, D, ea)[0])
+    k3, b3 = oracle.rindex_keys(*qs[:3])
+    k6, b6 = oracle.rindex_keys6(qs)
+    assert b3 <= 10 and b6 == b3
+    assert (oracle.segment_sort(k3, n, 0) == oracle.segment_sort(k6, n, 0)).all()
+    s1, p1 = oracle.compress_snapshot_keyed(f, 1e-3, 1, 8192, 128, 4096, 6, oracle.KEY_XYZ)
+    s2, p2 = oracle.compress_snapshot(f, 1e-3, 1, 8192, 128, 4096, 6)
+    assert s1 == s2 and (p1 == p2).all()
+
+
+def test_table6_per_variable_trend(oracle):
+    """Table 6, per variable (segments of 4096): the velocity key raises the
+    velocity fields' ratios and lowers the coordinates', and the
+    coordinate + velocity key lands between the two single keys for every
+    field.  (The table's overall finding on HACC -- no key helps -- comes from
+    HACC's nearly sorted yy, which the synthetic snapshot does not have.)"""
+    snap = synth.cosmology(1 << 17, 32, 1)
+    fs = [snap[k].numpy() for k in synth.FIELDS]
+    raw = 4 * fs[0].size
+    cr = {}
+    for key, p in ((oracle.KEY_XYZ, 6), (oracle.KEY_V, 6), (oracle.KEY_XYZV, 3)):
+        streams, _ = oracle.compress_snapshot_keyed(fs, 1e-4, 1, 4096, 64, 4096, p, key)
+        cr[key] = [raw / len(s) for s in streams]
+    stored = [raw / len(oracle.compress(a, 1e-4, 1, 4096, 64)) for a in fs]
+    for i in range(3):
+        assert cr[oracle.KEY_V][i] < stored[i]
+        assert cr[oracle.KEY_V][i] < cr[oracle.KEY_XYZV][i] < cr[oracle.KEY_XYZ][i]
+    for i in range(3, 6):
+        assert cr[oracle.KEY_V][i] > stored[i]
+        assert cr[oracle.KEY_XYZ][i] < cr[oracle.KEY_XYZV][i] < cr[oracle.KEY_V][i]
