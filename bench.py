@@ -246,6 +246,48 @@ def rd_points(sz, ctx, xs, ebs=RD_EBS, params=None, md_mode=None):
     return pts
 
 
+def rkeys_bench(sz, device, steps):
+    """Table 6: the plain cosmology snapshot (2^20 particles, 64 halos, six
+    fields) in stored order (SZ-LV) and reordered by the R-index built from
+    the coordinates, the velocities or all six fields (segments of 4096, no
+    ignored digits), rel eb 1e-4: per-field ratios, the overall ratio and the
+    compression rate of the six fields (reordering included)."""
+    import torch
+    import synth
+    snap = synth.cosmology(1 << 20, 64, 1, device="cuda")
+    xs = [snap[f] for f in FIELDS]
+    n = xs[0].numel()
+    raw = 4 * n
+    ctx = sz.Context(device)
+    stream = torch.cuda.current_stream()
+    tags = [sz.SZ_FIELD_XX, sz.SZ_FIELD_YY, sz.SZ_FIELD_ZZ, sz.SZ_FIELD_VX, sz.SZ_FIELD_VY, sz.SZ_FIELD_VZ]
+    out = {"workload": "plain cosmology snapshot, 2^20 particles x 6 fields, rel eb 1e-4, segment 4096, p = 0",
+           "keys": {}}
+    for name, mode, key in (("stored order (SZ-LV)", sz.SZ_MODE_LV, 0), ("coordinates", sz.SZ_MODE_LV_PRX, 0),
+                            ("velocities", sz.SZ_MODE_LV_PRX, 1), ("coordinates + velocities", sz.SZ_MODE_LV_PRX, 2)):
+        prm = sz._params(0, 0, 4096, 0, 0, key) if mode == sz.SZ_MODE_LV_PRX else None
+
+        def run():
+            return sz.sz_compress_snapshot(ctx, tags, xs, n, [1e-4] * 6, sz.SZ_EB_REL, mode, prm)
+
+        for _ in range(2):
+            outs, nb = run()
+            sz.sz_sync(ctx)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for a, b in ev:
+            a.record(stream)
+            outs, nb = run()
+            b.record(stream)
+        sz.sz_sync(ctx)
+        torch.cuda.synchronize()
+        t = sum(a.elapsed_time(b) for a, b in ev) / steps / 1e3
+        sizes = [int(nb[i]) for i in range(6)]
+        out["keys"][name] = {"ratio": 6 * raw / sum(sizes), "compress_gbs": 6 * raw / t / 1e9,
+                             "per_field": {f: raw / b for f, b in zip(FIELDS, sizes)}}
+    ctx.close()
+    return out
+
+
 def rd_bench(sz, device, xs):
     """Fig. 9 sweep: the large cosmology snapshot under LV and LCF, and the
     MD snapshot under best_speed (LV) and best_tradeoff (LV-PRX, p = 6)."""
@@ -696,6 +738,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-lcf", action="store_true")
     ap.add_argument("--no-rd", action="store_true")
+    ap.add_argument("--no-rkeys", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-log2n", type=int, default=24)
     ap.add_argument("--no-serve", action="store_true")
@@ -951,6 +994,11 @@ def main():
     if rank == 0 and not args.no_md:
         md = md_bench(sz, local, args.steps)
 
+    # ---- R-index keys from coordinates / velocities (rank 0; Table 6) -------------
+    rkeys = None
+    if rank == 0 and not args.no_rkeys:
+        rkeys = rkeys_bench(sz, local, args.steps)
+
     # ---- rate-distortion sweep (rank 0; Fig. 9) ----------------------------------
     rd = None
     if rank == 0 and not args.no_rd:
@@ -981,7 +1029,8 @@ def main():
             "compress_frac_hbm": comp_gbs / peak, "decompress_frac_hbm": decomp_gbs / peak,
             "ratio": ratio, "roofline": roofline, "kernels": kernels, "kernels_plain_path": kernels_plain,
             "gpu_launches": launches,
-            "plain_path": plain, "lcf": lcf, "batched": batched, "md": md, "rd": rd, "served": served,
+            "plain_path": plain, "lcf": lcf, "batched": batched, "md": md, "rkeys": rkeys, "rd": rd,
+            "served": served,
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "wall_s_timed": t_wall,
         }
         print(json.dumps(line))

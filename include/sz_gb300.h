@@ -86,14 +86,24 @@ typedef enum { SZ_PRED_DEFAULT = 0, SZ_PRED_LV = 1, SZ_PRED_LCF = 2 } sz_predict
  *                  too; set segment explicitly to request 0).
  *   predictor      an sz_predictor (0 = SZ_PRED_LV).  SZ_PRED_LCF runs the
  *                  per-array kernels: sz_compress_batch takes those arrays
- *                  one by one. */
+ *                  one by one.
+ *   key_fields     MD best_tradeoff mode: an sz_key_fields, the fields the
+ *                  R-index is built from (0 = SZ_KEY_XYZ). */
 typedef struct {
     uint32_t chunk_elems;
     uint32_t sub_elems;
     uint32_t segment;
     uint32_t ignored_digits;
     uint32_t predictor;
+    uint32_t key_fields;
 } sz_params;
+
+/* Sec. IV-C, Fig. 3, Table 6: the R-index of the best_tradeoff reordering from
+ * the coordinates (SZ_KEY_XYZ, Fig. 3a), the velocities (SZ_KEY_V: fields
+ * 3..5 must be VX, VY, VZ; 3-bit digits) or all six (SZ_KEY_XYZV, Fig. 3b:
+ * one bit of each of xx, yy, zz, vx, vy, vz per 6-bit digit, xx leading, at
+ * most 10 bits per axis kept; ignored_digits then counts 6-bit digits, 0..10). */
+typedef enum { SZ_KEY_XYZ = 0, SZ_KEY_V = 1, SZ_KEY_XYZV = 2 } sz_key_fields;
 
 /* Create a context on CUDA device `device`.  hbm_budget_bytes caps the device
  * memory the serving loop may admit at once (0 = no cap).  The workspace grows

@@ -28,6 +28,7 @@ SZ_OK, SZ_ERR_ARG, SZ_ERR_NOMEM, SZ_ERR_CAPACITY, SZ_ERR_CORRUPT, SZ_ERR_CUDA, S
 SZ_EB_ABS, SZ_EB_REL = 0, 1
 SZ_MODE_LV, SZ_MODE_LV_PRX, SZ_MODE_CPC2000 = 0, 1, 2
 SZ_PRED_DEFAULT, SZ_PRED_LV, SZ_PRED_LCF = 0, 1, 2
+SZ_KEY_XYZ, SZ_KEY_V, SZ_KEY_XYZV = 0, 1, 2
 SZ_FIELD_XX, SZ_FIELD_YY, SZ_FIELD_ZZ, SZ_FIELD_VX, SZ_FIELD_VY, SZ_FIELD_VZ, SZ_FIELD_OTHER = range(7)
 SZ_OP_COMPRESS, SZ_OP_DECOMPRESS = 0, 1
 HEADER_BYTES = 160
@@ -43,7 +44,8 @@ PHASES = ("range", "quant", "codebook", "encode", "decode_setup", "decode", "reo
 
 class sz_params(C.Structure):
     _fields_ = [("chunk_elems", C.c_uint32), ("sub_elems", C.c_uint32),
-                ("segment", C.c_uint32), ("ignored_digits", C.c_uint32), ("predictor", C.c_uint32)]
+                ("segment", C.c_uint32), ("ignored_digits", C.c_uint32), ("predictor", C.c_uint32),
+                ("key_fields", C.c_uint32)]
 
 
 class sz_request(C.Structure):
@@ -123,8 +125,9 @@ def _stream(stream):
     return C.c_void_p(int(torch.cuda.current_stream().cuda_stream))
 
 
-def _params(chunk: int = 0, sub: int = 0, segment: int = 0, ignored_digits: int = 0, predictor: int = 0):
-    return sz_params(chunk, sub, segment, ignored_digits, predictor)
+def _params(chunk: int = 0, sub: int = 0, segment: int = 0, ignored_digits: int = 0, predictor: int = 0,
+            key_fields: int = 0):
+    return sz_params(chunk, sub, segment, ignored_digits, predictor, key_fields)
 
 
 class Context:

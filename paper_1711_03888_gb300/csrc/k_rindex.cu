@@ -12,7 +12,11 @@
 //      digits on the low 32 key bits and, only when needed, the high bits.
 // a14  The permutation (position j holds original index perm[j]) is applied
 //      to every field of the snapshot by a gather.  No index array is stored.
+// Keys may also come from the velocities (the same kernels on fields 3..5) or
+// from all six fields (Sec. IV-C, Fig. 3b): one bit of each axis per 6-bit
+// digit, xx leading, at most 10 bits per axis.
 #include "sz_blocksort.cuh"
+#include "sz_ctx.h"
 
 namespace szg {
 
@@ -152,6 +156,79 @@ __global__ void gather_kernel(const float* __restrict__ src, float* __restrict__
         dst[j] = __ldg(src + __ldg(perm + j));
 }
 
+// ---- keys from six fields (Fig. 3b) -------------------------------------------
+
+__device__ __forceinline__ long long axis_q6(float x, const LatticeParams& P) {
+    if (P.raw) return 0;
+    long long q;
+    bool v;
+    lattice_q(x, P, q, v);
+    return q;
+}
+
+__global__ void __launch_bounds__(kKeyThreads) rindex6_range_kernel(Reorder6Args a) {
+    LatticeParams P[6];
+#pragma unroll
+    for (int ax = 0; ax < 6; ++ax) P[ax] = a.st[ax]->P;
+    unsigned long long lo[6], hi[6];
+#pragma unroll
+    for (int ax = 0; ax < 6; ++ax) { lo[ax] = ~0ull; hi[ax] = 0ull; }
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (uint64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int ax = 0; ax < 6; ++ax) {
+            const unsigned long long u = q_order(axis_q6(__ldg(a.pos[ax] + i), P[ax]));
+            lo[ax] = lo[ax] < u ? lo[ax] : u;
+            hi[ax] = hi[ax] > u ? hi[ax] : u;
+        }
+    }
+#pragma unroll
+    for (int ax = 0; ax < 6; ++ax) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long l2 = __shfl_xor_sync(0xffffffffu, lo[ax], o);
+            const unsigned long long h2 = __shfl_xor_sync(0xffffffffu, hi[ax], o);
+            lo[ax] = lo[ax] < l2 ? lo[ax] : l2;
+            hi[ax] = hi[ax] > h2 ? hi[ax] : h2;
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicMin(&a.qrange[ax], lo[ax]);
+            atomicMax(&a.qrange[6 + ax], hi[ax]);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kKeyThreads) rindex6_key_kernel(Reorder6Args a) {
+    LatticeParams P[6];
+    long long qmin[6];
+    unsigned long long umax = 0;
+#pragma unroll
+    for (int ax = 0; ax < 6; ++ax) {
+        P[ax] = a.st[ax]->P;
+        qmin[ax] = q_unorder(a.qrange[ax]);
+        const unsigned long long span = (unsigned long long)(q_unorder(a.qrange[6 + ax]) - qmin[ax]);
+        umax = umax > span ? umax : span;
+    }
+    const int bits = 64 - __clzll((long long)umax);
+    const int drop = bits > 10 ? bits - 10 : 0, b = bits - drop;
+    const int shift = 6 * (int)a.p;
+    uint32_t any_hi = 0;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += (uint64_t)gridDim.x * blockDim.x) {
+        unsigned long long key = 0;
+#pragma unroll
+        for (int ax = 0; ax < 6; ++ax) {
+            const unsigned long long u = (unsigned long long)(axis_q6(__ldg(a.pos[ax] + i), P[ax]) - qmin[ax]) >> drop;
+            for (int k = 0; k < b; ++k) key |= ((u >> k) & 1ull) << (6 * k + (5 - ax));
+        }
+        key = shift < 64 ? (key >> shift) : 0ull;
+        a.key_lo[i] = (uint32_t)key;
+        a.key_hi[i] = (uint32_t)(key >> 32);
+        a.idx[i] = (uint32_t)(i % a.segment);
+        any_hi |= (uint32_t)(key >> 32);
+    }
+    any_hi = __reduce_or_sync(0xffffffffu, any_hi);
+    if ((threadIdx.x & 31) == 0 && any_hi) atomicOr(a.any_hi, 1u);
+}
+
 static int sm_count() {
     static int sms = 0;
     if (!sms) {
@@ -168,6 +245,13 @@ void launch_rindex_keys(const ReorderArgs& a, void* stream) {
     const uint32_t grid = (uint32_t)umin64((a.n + kKeyThreads - 1) / kKeyThreads, (uint64_t)sm_count() * 8u);
     rindex_range_kernel<<<grid ? grid : 1, kKeyThreads, 0, s>>>(a);
     rindex_key_kernel<<<grid ? grid : 1, kKeyThreads, 0, s>>>(a);
+}
+
+void launch_rindex_keys6(const Reorder6Args& a, void* stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    const uint32_t grid = (uint32_t)umin64((a.n + kKeyThreads - 1) / kKeyThreads, (uint64_t)sm_count() * 8u);
+    rindex6_range_kernel<<<grid ? grid : 1, kKeyThreads, 0, s>>>(a);
+    rindex6_key_kernel<<<grid ? grid : 1, kKeyThreads, 0, s>>>(a);
 }
 
 void launch_segment_sort(const ReorderArgs& a, void* stream) {

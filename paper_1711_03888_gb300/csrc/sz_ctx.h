@@ -94,6 +94,22 @@ uint32_t tune_chunk(uint64_t n);
 sz_status resolve_params(const sz_params* p, uint64_t n, uint32_t* C, uint32_t* G);
 uint32_t params_pred(const sz_params* p);     // kPredLV or kPredLCF
 size_t cpc_max_bytes(uint64_t n);
+// R-index keys from six fields (xx, yy, zz, vx, vy, vz; Fig. 3b): per-axis
+// lattice range into qrange (12 words, order-mapped min then max), then keys
+// of at most 10 bits per axis, shifted right by 6p, into key_lo / key_hi with
+// the index within the segment in idx.
+struct Reorder6Args {
+    const float* pos[6];
+    const ArrayState* st[6];
+    uint64_t n;
+    uint32_t segment, p;
+    unsigned long long* qrange;
+    uint32_t* key_lo;
+    uint32_t* key_hi;
+    uint32_t* idx;
+    uint32_t* any_hi;
+};
+void launch_rindex_keys6(const Reorder6Args& a, void* stream);
 sz_status cpc_compress_coords(sz_ctx* ctx, const ReorderArgs& r, uint64_t n, void* d_out, size_t out_cap,
                               size_t* out_bytes, uint32_t* perm_out, cudaStream_t s);
 sz_status ctx_reserve(sz_ctx* ctx, int arrays, uint64_t max_chunks, uint64_t max_code_elems);

@@ -86,16 +86,23 @@ extern "C" sz_status sz_compress_snapshot(sz_ctx* ctx, int nfields, const sz_fie
     // ---- best_tradeoff (SZ-LV-PRX) and best_compression (SZ-CPC2000) -----------
     if (nfields < 3 || !fields || fields[0] != SZ_FIELD_XX || fields[1] != SZ_FIELD_YY || fields[2] != SZ_FIELD_ZZ)
         return SZ_ERR_ARG;
+    // the fields the R-index is built from (Fig. 3): coordinates, velocities or all six
+    const uint32_t keyf = params ? params->key_fields : (uint32_t)SZ_KEY_XYZ;
+    if (keyf > (uint32_t)SZ_KEY_XYZV || (cpc && keyf != SZ_KEY_XYZ)) return SZ_ERR_ARG;
+    if (keyf != SZ_KEY_XYZ &&
+        (nfields < 6 || fields[3] != SZ_FIELD_VX || fields[4] != SZ_FIELD_VY || fields[5] != SZ_FIELD_VZ))
+        return SZ_ERR_ARG;
+    const int ax0 = keyf == SZ_KEY_V ? 3 : 0, nax = keyf == SZ_KEY_XYZV ? 6 : 3;
     // best_compression: keys of one segment with no ignored digits (a full sort follows)
     const uint32_t S = cpc ? (uint32_t)(n ? n : 1) : (params && params->segment) ? params->segment : 16384u;
     const uint32_t p = cpc ? 0u : (params && (params->segment || params->ignored_digits)) ? params->ignored_digits : 6u;
-    if ((!cpc && S > 65536u) || p > 21u) return SZ_ERR_ARG;
-    if ((st = ctx_reserve(ctx, 3, (n + C - 1) / C, (uint64_t)((n + C - 1) / C) * C)) != SZ_OK) return st;
+    if ((!cpc && S > 65536u) || p > (keyf == SZ_KEY_XYZV ? 10u : 21u)) return SZ_ERR_ARG;
+    if ((st = ctx_reserve(ctx, ax0 + nax, (n + C - 1) / C, (uint64_t)((n + C - 1) / C) * C)) != SZ_OK) return st;
     uint8_t* md = nullptr;
     if ((st = md_reserve(ctx, n, nfields, &md)) != SZ_OK) return st;
 
-    // a1 on the three coordinates (state slots 0..2)
-    for (int ax = 0; ax < 3; ++ax) {
+    // a1 on the key fields (state slot = field index)
+    for (int ax = ax0; ax < ax0 + nax; ++ax) {
         CompressArgs a = make_compress_args(ctx, ax, d_in[ax], n, eb[ax], (int)kind, C, G, 0u, d_out[ax], out_cap[ax]);
         ProfScope pr(ctx, SZ_PHASE_RANGE, s);
         launch_range(&a, 1, s);
@@ -103,9 +110,9 @@ extern "C" sz_status sz_compress_snapshot(sz_ctx* ctx, int nfields, const sz_fie
     ReorderArgs r;
     memset(&r, 0, sizeof(r));
     for (int ax = 0; ax < 3; ++ax) {
-        r.pos[ax] = d_in[ax];
-        r.eb[ax] = eb[ax];
-        r.st[ax] = ctx->d_state + ax;
+        r.pos[ax] = d_in[ax0 + ax];
+        r.eb[ax] = eb[ax0 + ax];
+        r.st[ax] = ctx->d_state + ax0 + ax;
     }
     r.n = n;
     r.eb_kind = (int)kind;
@@ -139,7 +146,30 @@ extern "C" sz_status sz_compress_snapshot(sz_ctx* ctx, int nfields, const sz_fie
         for (int f = 3; f < nfields; ++f) launch_gather(d_in[f], permuted + (size_t)f * n, r.perm, n, s);
     } else {
         ProfScope pr(ctx, SZ_PHASE_REORDER, s);
-        launch_rindex_keys(r, s);
+        if (keyf == SZ_KEY_XYZV) {
+            Reorder6Args r6;
+            memset(&r6, 0, sizeof(r6));
+            for (int ax = 0; ax < 6; ++ax) {
+                r6.pos[ax] = d_in[ax];
+                r6.st[ax] = ctx->d_state + ax;
+            }
+            r6.n = n;
+            r6.segment = S;
+            r6.p = p;
+            r6.qrange = (unsigned long long*)(md + 128);
+            r6.key_lo = r.key_lo;
+            r6.key_hi = r.key_hi;
+            r6.idx = r.idx;
+            r6.any_hi = r.any_hi;
+            const unsigned long long init6[12] = {~0ull, ~0ull, ~0ull, ~0ull, ~0ull, ~0ull, 0ull, 0ull, 0ull, 0ull, 0ull, 0ull};
+            if (cudaMemcpyAsync(r6.qrange, init6, sizeof(init6), cudaMemcpyHostToDevice, s) != cudaSuccess) {
+                cudaGetLastError();
+                return SZ_ERR_CUDA;
+            }
+            launch_rindex_keys6(r6, s);
+        } else {
+            launch_rindex_keys(r, s);
+        }
         launch_segment_sort(r, s);
         for (int f = 0; f < nfields; ++f) launch_gather(d_in[f], permuted + (size_t)f * n, r.perm, n, s);
     }

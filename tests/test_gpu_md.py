@@ -89,12 +89,25 @@ def test_md_best_speed_is_plain_lv(sz, ctx, oracle):
         assert g == oracle.compress(t.numpy(), 1e-4, 1, h["chunk"], h["sub"])
 
 
-def test_md_best_compression_not_built(sz, ctx):
+def test_md_best_compression_round_trip(sz, ctx):
+    """best_compression writes one coordinate stream to the first output;
+    it decodes to the sorted coordinates within every axis's bound (the
+    byte-level parity is in test_gpu_cpc.py)."""
     md = synth.md_fcc(cells=8, seed=2)
     xs = [md[k].cuda() for k in ("xx", "yy", "zz")]
-    with pytest.raises(sz.SzError) as e:
-        sz.sz_compress_snapshot(ctx, [0, 1, 2], xs, xs[0].numel(), [1e-4] * 3, sz.SZ_EB_REL, sz.SZ_MODE_CPC2000)
-    assert e.value.status == sz.SZ_ERR_UNSUPPORTED
+    n = xs[0].numel()
+    perm = torch.empty(n, dtype=torch.int32, device="cuda")
+    outs, nb = sz.sz_compress_snapshot(ctx, [0, 1, 2], xs, n, [1e-4] * 3, sz.SZ_EB_REL, sz.SZ_MODE_CPC2000,
+                                       perm=perm)
+    sz.sz_sync(ctx)
+    assert int(nb[1]) == int(nb[2]) == 0 and int(nb[0]) > 160
+    ys = [torch.empty(n, dtype=torch.float32, device="cuda") for _ in range(3)]
+    no = sz.sz_decompress_cpc(ctx, outs[0], int(nb[0]), ys)
+    sz.sz_sync(ctx)
+    assert no.value == n
+    for x, y in zip(xs, ys):
+        R = (x.max() - x.min()).double().item()
+        assert (x[perm.long()].double() - y.double()).abs().max().item() <= 1e-4 * R * (1 + 1e-12)
 
 
 @pytest.mark.parametrize("eb", [1e-4, 1e-3])
