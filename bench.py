@@ -306,7 +306,7 @@ def rd_bench(sz, device, xs):
     return out
 
 
-def lcf_bench(sz, ctx, stream, step, xs, ys, outs, args, raw_bytes, ratio_lv):
+def lcf_bench(sz, ctx, stream, step, xs, ys, outs, args, raw_bytes, ratio_lv, with_cpu=True):
     """The per-array path with the LCF predictor on the benchmark arrays:
     compress / decompress GB/s from CUDA events, the ratio against LV's, and
     each kernel phase's device time.  Checks the error bound first."""
@@ -335,9 +335,38 @@ def lcf_bench(sz, ctx, stream, step, xs, ys, outs, args, raw_bytes, ratio_lv):
     sz.sz_profile_enable(ctx, False)
     tc = sum(e[0].elapsed_time(e[1]) for e in ev) / 1e3 / k
     td = sum(e[1].elapsed_time(e[2]) for e in ev) / 1e3 / k
+    ms = {ph: ms / k for ph, (c, ms) in prof.items() if c}
+    # the dominant LCF kernel by device time: decode, whose algorithmic bytes
+    # are the streams read plus the floats written
+    peak, peak_kind = _peaks()
+    dec_bytes = sum(sizes) + raw_bytes
+    dec_gbs = dec_bytes / (ms["decode"] / 1e3) / 1e9
+    # the oracle beside it (CPU-baseline leg: rank 0 at N = 1 only): LCF round
+    # trips of the first 2^22 elements of each field, one thread per field
+    cpu = None
+    if with_cpu:
+        import oracle
+        oracle.build()
+        from concurrent.futures import ThreadPoolExecutor
+        samp = [x[: 1 << 22].cpu().numpy() for x in xs]
+
+        def one(a):
+            oracle.decompress(oracle.compress(a, args.eb, 1, 4096, 64, pred=oracle.PRED_LCF))
+
+        t0 = time.perf_counter()
+        with ThreadPoolExecutor(max_workers=len(samp)) as ex:
+            list(ex.map(one, samp))
+        t_or = time.perf_counter() - t0
+        cpu = {"value": 4 * sum(a.size for a in samp) / t_or / 1e9, "unit": "GB/s", "cores": len(samp),
+               "kind": "oracle",
+               "sample": "first 2^22 elements of each field, LCF compress + decompress, one thread per field"}
     return {"compress_gbs": raw_bytes / tc / 1e9, "decompress_gbs": raw_bytes / td / 1e9,
             "round_trip_gbs": raw_bytes / (tc + td) / 1e9, "ratio": raw_bytes / sum(sizes), "ratio_lv": ratio_lv,
-            "ms_per_step": {ph: round(ms / k, 4) for ph, (c, ms) in prof.items() if c},
+            "ms_per_step": {ph: round(v, 4) for ph, v in ms.items()},
+            "roofline": {"kernel": "decode_kernel (LCF team loops)", "bound": "hbm", "achieved": dec_gbs,
+                         "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": dec_gbs / peak,
+                         "algorithmic_bytes_per_step": dec_bytes},
+            "cpu_oracle": cpu,
             "note": "per field: sz_compress / sz_decompress with predictor SZ_PRED_LCF (second differences)"}
 
 
@@ -503,7 +532,7 @@ def batched_bench(sz, device, steps):
 # R-index reordering (Sec. IV-B; Tables 4-5)
 # ---------------------------------------------------------------------------
 
-def md_bench(sz, device, steps):
+def md_bench(sz, device, steps, with_cpu=True):
     """FCC crystal of 100^3 cells (3.92 M atoms after 2 % vacancies, 10 %
     swapped), xx/yy/zz: best_speed (SZ-LV in stored order) against best_tradeoff
     (SZ-LV-PRX: segment 16384, p = 6 ignored digits, and p = 0 = full radix
@@ -564,6 +593,18 @@ def md_bench(sz, device, steps):
                 torch.cuda.synchronize()
                 td = sum(a.elapsed_time(b) for a, b in evd) / steps / 1e3
                 rec["decompress_gbs"] = nbytes / td / 1e9
+                # decoding reads the stream and writes three float arrays; the oracle beside it
+                peak, _ = _peaks()
+                rec["decode_roofline_frac"] = (size + nbytes) / td / 1e9 / peak
+                if eb == 1e-4 and with_cpu:      # CPU-baseline leg: rank 0 at N = 1 only
+                    import oracle
+                    oracle.build()
+                    hx = [x.cpu().numpy() for x in xs]
+                    t0 = time.perf_counter()
+                    s_or, _ = oracle.compress_cpc(*hx, eb, 1)
+                    oracle.decompress_cpc(s_or)
+                    rec["cpu_oracle_gbs"] = nbytes / (time.perf_counter() - t0) / 1e9
+                    rec["cpu_oracle_note"] = "compress + decompress of the same crystal by the oracle, one thread"
             out["modes"][f"{name} @ {eb:g}"] = rec
     ctx.close()
     return out
@@ -894,7 +935,8 @@ def main():
     # ---- the LCF predictor (Sec. IV-A, original SZ) on the same arrays ---------
     lcf = None
     if not args.no_lcf:
-        lcf = lcf_bench(sz, ctx, stream, step, xs, ys, outs, args, raw_bytes, ratio)
+        lcf = lcf_bench(sz, ctx, stream, step, xs, ys, outs, args, raw_bytes, ratio,
+                        with_cpu=not args.no_cpu and rank == 0 and ws == 1)
 
     # ---- roofline of the dominant kernel -----------------------------------
     peak, peak_kind = _peaks()
@@ -992,7 +1034,7 @@ def main():
     # ---- MD snapshot (rank 0): reordering modes ---------------------------------
     md = None
     if rank == 0 and not args.no_md:
-        md = md_bench(sz, local, args.steps)
+        md = md_bench(sz, local, args.steps, with_cpu=not args.no_cpu and ws == 1)
 
     # ---- R-index keys from coordinates / velocities (rank 0; Table 6) -------------
     rkeys = None
