@@ -568,15 +568,19 @@ __device__ __noinline__ void decode_team_lcf_strided(const DecArray d, DecSmem& 
 
 __device__ __noinline__ void decode_team_lcf_counted(const DecArray d, DecSmem& sm, const uint32_t* lut2,
                                                      uint32_t* xs, uint32_t stage_words, int team, int k,
-                                                     uint32_t* ctr, uint32_t nu, uint64_t ahead, uint32_t* s_unit,
-                                                     uint32_t* err) {
-    for (;;) {
-        if (k == 0) s_unit[team] = atomicAdd(ctr, 1u);
+                                                     uint32_t* ctr, uint32_t nu, uint32_t* s_unit, uint32_t* err) {
+    if (k == 0) s_unit[team] = atomicAdd(ctr, 1u);
+    team_sync(team);
+    uint32_t u = s_unit[team];
+    team_sync(team);
+    while (u < nu) {
+        if (k == 0) s_unit[team] = atomicAdd(ctr, 1u);      // the next ticket, prefetched while u decodes
         team_sync(team);
-        const uint32_t u = s_unit[team];
+        const uint32_t un = s_unit[team];
         team_sync(team);
-        if (u >= nu) return;
-        if (!decode_chunk_team<true>(d, sm, lut2, xs, xs + d.C, stage_words, team, k, u, u + ahead, err)) return;
+        if (!decode_chunk_team<true>(d, sm, lut2, xs, xs + d.C, stage_words, team, k, u, un < nu ? un : ~0ull, err))
+            return;
+        u = un;
     }
 }
 
@@ -682,7 +686,10 @@ __device__ __forceinline__ uint32_t find_stream(const uint64_t* uoff, uint32_t k
 // the work -- and sweeps the streams cyclically from there, visiting each
 // once: it loads a stream's tables, its teams drain the stream's counter, and
 // the block moves on.  Streams with fast and slow chunks thus end together.
-// A bad chunk stops its team on that stream only.
+// A team takes its next unit's ticket before decoding the current one and
+// asks L2 to prefetch that unit's payload (a fixed distance ahead would miss:
+// only the blocks on the same stream draw from its counter).  A bad chunk
+// stops its team on that stream only.
 __global__ void __launch_bounds__(kDecBlock, 1) decode_multi_kernel(const DecompressArgs* args, const uint64_t* uoff,
                                                                     uint32_t* ctr, uint32_t k) {
     __shared__ DecSmem sm;
@@ -695,7 +702,6 @@ __global__ void __launch_bounds__(kDecBlock, 1) decode_multi_kernel(const Decomp
     if (F == 0) return;
     uint32_t* lut2 = reinterpret_cast<uint32_t*>(dyn_smem);
     const int team = tid / kDecThreads, kk = tid % kDecThreads;
-    const uint64_t ahead = (uint64_t)gridDim.x * kMaxTeams;     // units in flight across the GPU
     uint32_t i = find_stream(uoff, k, F * blockIdx.x / gridDim.x);
     for (uint32_t v = 0; v < k; ++v, i = (i + 1 == k) ? 0 : i + 1) {
         const uint32_t nu = (uint32_t)(uoff[i + 1] - uoff[i]);
@@ -719,24 +725,30 @@ __global__ void __launch_bounds__(kDecBlock, 1) decode_multi_kernel(const Decomp
         uint32_t stage_words = 0;
         uint32_t* xs = raw ? nullptr : team_region(dyn_smem, teams, team, &stage_words, d.C);
         if (!raw && d.lcf) {
-            decode_team_lcf_counted(d, sm, lut2, xs, stage_words, team, kk, ctr + i, nu, ahead, s_unit, sa.err);
+            decode_team_lcf_counted(d, sm, lut2, xs, stage_words, team, kk, ctr + i, nu, s_unit, sa.err);
             continue;
         }
-        for (;;) {
+        // a team holds two tickets: while it decodes unit u, unit un (its next)
+        // is prefetched into L2
+        if (kk == 0) s_unit[team] = atomicAdd(ctr + i, 1u);
+        team_sync(team);
+        uint32_t u = s_unit[team];
+        team_sync(team);
+        while (u < nu) {
             if (kk == 0) s_unit[team] = atomicAdd(ctr + i, 1u);
             team_sync(team);
-            const uint32_t u = s_unit[team];
+            const uint32_t un = s_unit[team];
             team_sync(team);
-            if (u >= nu) break;
             if (raw) {
                 // a 4096-word piece
                 uint32_t* dst = reinterpret_cast<uint32_t*>(sa.out);
                 const uint64_t e1 = umin64(d.n, ((uint64_t)u + 1) * kRawUnit);
                 for (uint64_t e = (uint64_t)u * kRawUnit + kk; e < e1; e += kDecThreads) dst[e] = __ldg(d.payload + e);
-            } else if (!decode_chunk_team<false>(d, sm, lut2, xs, xs + d.C, stage_words, team, kk, u, u + ahead,
-                                                 sa.err)) {
+            } else if (!decode_chunk_team<false>(d, sm, lut2, xs, xs + d.C, stage_words, team, kk, u,
+                                                 un < nu ? un : ~0ull, sa.err)) {
                 break;
             }
+            u = un;
         }
     }
 }
