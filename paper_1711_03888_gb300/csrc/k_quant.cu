@@ -1,7 +1,8 @@
 // k_quant.cu -- stand-alone launch of the quantize + histogram phase (a2-a4;
 // body in sz_quant.cuh): persistent 256-thread blocks walk the chunks of one
 // array with a block-private window of the histogram, flushed once at exit,
-// the next chunk's input staged into shared memory while one is quantized.
+// each chunk's input staged into shared memory (one stage, so that four
+// blocks fit on an SM).
 #include "sz_quant.cuh"
 
 namespace szg {
@@ -17,7 +18,7 @@ __global__ void __launch_bounds__(kQuantThreads) quant_kernel(CompressArgs a) {
     hist_window_zero(sh);
     __syncthreads();
     if (((uintptr_t)a.in & 15u) == 0)
-        quant_array_staged<STORE, LCF>(a, P, blockIdx.x, gridDim.x, reinterpret_cast<float*>(stage4), sh, s_esc);
+        quant_array_staged<STORE, LCF, 1>(a, P, blockIdx.x, gridDim.x, reinterpret_cast<float*>(stage4), sh, s_esc);
     else
         quant_array_global<STORE, LCF>(a, P, blockIdx.x, gridDim.x, sh, s_esc);
     hist_window_flush(sh, a.hist);
@@ -37,12 +38,12 @@ void launch_quant(const CompressArgs* a, int k, void* stream) {
     static int per_sm[3][4] = {};
     static const uint32_t kCs[4] = {2048u, 4096u, 8192u, 16384u};
     if (!per_sm[0][0]) {
-        const int smax = (int)quant_stage_bytes(16384);
+        const int smax = (int)quant_stage_bytes(16384, 1);
         cudaFuncSetAttribute(quant_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
         cudaFuncSetAttribute(quant_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
         cudaFuncSetAttribute(quant_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
         for (int j = 0; j < 4; ++j) {
-            const size_t sm = quant_stage_bytes(kCs[j]);
+            const size_t sm = quant_stage_bytes(kCs[j], 1);
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[0][j], quant_kernel<false>, kQuantThreads, sm);
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[1][j], quant_kernel<true>, kQuantThreads, sm);
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[2][j], quant_kernel<true, true>, kQuantThreads, sm);
@@ -53,7 +54,7 @@ void launch_quant(const CompressArgs* a, int k, void* stream) {
         // LCF needs the stored codes (its encoder does not recompute them)
         const int v = a[i].codes ? (a[i].pred == kPredLCF ? 2 : 1) : 0;
         const int j = a[i].C == 2048 ? 0 : a[i].C == 4096 ? 1 : a[i].C == 8192 ? 2 : 3;
-        const size_t smem = quant_stage_bytes(a[i].C);
+        const size_t smem = quant_stage_bytes(a[i].C, 1);
         const uint32_t div = a[i].grid_div > 1 ? a[i].grid_div : 1u;
         uint32_t grid = umin32(a[i].n_chunks, (uint32_t)(sms * per_sm[v][j]) / div);
         if (grid == 0) grid = 1;

@@ -38,8 +38,12 @@ constexpr int kWinWords = kWin / 2;
 constexpr uint32_t kWinLo = kRadius - kWin / 2;
 __host__ __device__ constexpr uint32_t quant_flush_every(uint32_t C) { return 65535u / C; }
 
-// dynamic shared memory of the staged quantize loop: two stages of C + 4 floats
-constexpr size_t quant_stage_bytes(uint32_t C) { return 2u * 4u * ((size_t)C + 4u); }
+// dynamic shared memory of the staged quantize loop: NSTAGE stages of C + 4 floats.
+// Measured on GB300 (2^27 elements, C = 4096): the stand-alone kernel (64
+// registers) runs 4 blocks per SM with one stage (48 KB per block) against 3
+// with two, 0.306 vs 0.329 ms; the batched kernel (80 registers, 3 blocks
+// whatever the stage count) keeps two.
+constexpr size_t quant_stage_bytes(uint32_t C, int NSTAGE = 2) { return (size_t)NSTAGE * 4u * ((size_t)C + 4u); }
 
 __device__ __forceinline__ void hist_add(uint32_t code, uint32_t* sh, uint32_t* gh) {
     const uint32_t w = code - kWinLo;
@@ -378,11 +382,29 @@ __device__ __forceinline__ void quant_array_global(const CompressArgs& a, const 
 }
 
 // The persistent quantize loop of one array over chunks first, first + step,
-// ...: chunk c + step is copied into one stage while chunk c is quantized from
-// the other.  stage: 2 (C + 4) floats, 16-byte aligned.
-template <bool STORE, bool LCF = false>
+// ...: with two stages chunk c + step is copied into one while chunk c is
+// quantized from the other; with one stage the copy of each chunk waits for
+// the previous chunk (other resident blocks cover the latency).  stage:
+// NSTAGE (C + 4) floats, 16-byte aligned.
+template <bool STORE, bool LCF = false, int NSTAGE = 2>
 __device__ __forceinline__ void quant_array_staged(const CompressArgs& a, const LatticeParams& P, uint32_t first,
                                                    uint32_t step, float* stage, uint32_t* sh, uint32_t* s_esc) {
+    static_assert(NSTAGE == 1 || NSTAGE == 2, "stages");
+    if (NSTAGE == 1) {
+        uint32_t since = 0;
+        for (uint32_t c = first; c < a.n_chunks; c += step) {
+            quant_issue(a, c, stage);
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+            __syncthreads();          // chunk c is staged
+            quant_chunk_staged<STORE, LCF>(a, P, c, stage, sh, s_esc);   // ends with a block barrier
+            if (++since == quant_flush_every(a.C)) {
+                hist_window_flush(sh, a.hist);
+                __syncthreads();
+                since = 0;
+            }
+        }
+        return;
+    }
     float* buf[2] = {stage, stage + a.C + 4};
     uint32_t c = first, since = 0;
     if (c < a.n_chunks) quant_issue(a, c, buf[0]);
