@@ -419,13 +419,36 @@ __device__ void codebook_body(const CompressArgs& a, CbSmem<NT>& sm, uint32_t* f
     // -------- 6. escape bases (exclusive scan, in place) ----------------------
     const uint32_t nc = a.n_chunks;
     uint32_t carry = 0;
-    for (uint32_t t0 = 0; t0 < nc; t0 += kCbThreads) {
-        uint32_t i = t0 + tid;
-        uint32_t v = (i < nc) ? a.chunk_esc[i] : 0u;
+    if (fast != nullptr && (uint64_t)nc + (nc >> 5) <= 4ull * fast_cap) {
+        // staged in the (now free) shared buffer by coalesced loads, skewed by
+        // one word per 32 so that runs of consecutive chunks hit distinct banks;
+        // each thread scans its run, one block scan joins the runs
+        uint32_t* e = fast;
+        for (uint32_t i = tid; i < nc; i += kCbThreads) e[i + (i >> 5)] = a.chunk_esc[i];
+        __syncthreads();
+        const uint32_t per = (nc + kCbThreads - 1) / kCbThreads;
+        const uint32_t c0 = umin32(nc, tid * per), c1 = umin32(nc, c0 + per);
+        uint32_t run = 0;
+        for (uint32_t c = c0; c < c1; ++c) run += e[c + (c >> 5)];
         uint32_t tot;
-        uint32_t ex = block_exclusive_scan<kCbThreads>(v, sm.ws32, &tot);
-        if (i < nc) a.chunk_esc[i] = carry + ex;
-        carry += tot;
+        run = block_exclusive_scan<kCbThreads>(run, sm.ws32, &tot);
+        for (uint32_t c = c0; c < c1; ++c) {
+            const uint32_t v = e[c + (c >> 5)];
+            e[c + (c >> 5)] = run;
+            run += v;
+        }
+        __syncthreads();
+        for (uint32_t i = tid; i < nc; i += kCbThreads) a.chunk_esc[i] = e[i + (i >> 5)];
+        carry = tot;
+    } else {
+        for (uint32_t t0 = 0; t0 < nc; t0 += kCbThreads) {
+            uint32_t i = t0 + tid;
+            uint32_t v = (i < nc) ? a.chunk_esc[i] : 0u;
+            uint32_t tot;
+            uint32_t ex = block_exclusive_scan<kCbThreads>(v, sm.ws32, &tot);
+            if (i < nc) a.chunk_esc[i] = carry + ex;
+            carry += tot;
+        }
     }
     const uint64_t E = carry;
 
