@@ -121,3 +121,29 @@ def test_cpc_errors(sz, ctx):
     assert _gpu_decode(sz, ctx, bytes(4096), n)[0] == sz.SZ_ERR_CORRUPT
     # the context still works
     assert _gpu_decode(sz, ctx, g, n)[0] == sz.SZ_OK
+
+
+def test_cpc_decoder_capacity_and_foreign_formats(sz, ctx):
+    """A coordinate stream decoded into too small an array reports capacity
+    with the particle count; each decoder rejects the other format's stream
+    (SZ-LV vs SZ-CPC2000 magic) and the context keeps working."""
+    md = synth.md_fcc(cells=6, seed=5)
+    f = [md[k].numpy() for k in ("xx", "yy", "zz")]
+    n = f[0].size
+    st, outs, nb, _ = _gpu_cpc(sz, ctx, f, 1e-3)
+    assert st == sz.SZ_OK
+    g = outs[0][: nb[0]]
+    small = [torch.empty(n - 1, dtype=torch.float32, device="cuda") for _ in range(3)]
+    no = sz.sz_decompress_cpc(ctx, g, nb[0], small)
+    assert sz.sz_sync(ctx, check=False) == sz.SZ_ERR_CAPACITY
+    assert no.value == n
+    # an SZ-LV stream into the coordinate decoder, and the coordinate stream into the SZ-LV decoder
+    lv, lnb = sz.sz_compress(ctx, torch.from_numpy(f[0]).cuda(), 1e-3, sz.SZ_EB_REL)
+    sz.sz_sync(ctx)
+    ys = [torch.empty(n, dtype=torch.float32, device="cuda") for _ in range(3)]
+    sz.sz_decompress_cpc(ctx, lv, lnb.value, ys)
+    assert sz.sz_sync(ctx, check=False) == sz.SZ_ERR_CORRUPT
+    sz.sz_decompress(ctx, g, nb[0], ys[0])
+    assert sz.sz_sync(ctx, check=False) == sz.SZ_ERR_CORRUPT
+    st, no2, back = _gpu_decode(sz, ctx, g.cpu().numpy().tobytes(), n)
+    assert st == sz.SZ_OK and no2 == n
