@@ -20,18 +20,18 @@ __global__ void __launch_bounds__(EncShape<C>::kThreads, EncShape<C>::kMinBlocks
         return;
     }
     uint32_t* smem = reinterpret_cast<uint32_t*>(dyn_smem);
-    if (FROM_CODES) {
+    if constexpr (FROM_CODES) {
         encode_array_pipelined<C, NT, LCF>(a, smem, esm, s_c, s_prev);
-        return;
-    }
-    // codes recomputed from the input: one chunk per ticket
-    for (;;) {
-        if (threadIdx.x == 0) s_c[0] = atomicAdd(&st->ticket, 1u);
-        __syncthreads();          // also: the last chunk's buffer is free
-        const uint32_t c = s_c[0];
-        __syncthreads();
-        if (c >= a.n_chunks) return;
-        encode_chunk<NT, EncShape<C>::kRun, false>(a, c, smem, esm);
+    } else {
+        // codes recomputed from the input: one chunk per ticket
+        for (;;) {
+            if (threadIdx.x == 0) s_c[0] = atomicAdd(&st->ticket, 1u);
+            __syncthreads();          // also: the last chunk's buffer is free
+            const uint32_t c = s_c[0];
+            __syncthreads();
+            if (c >= a.n_chunks) return;
+            encode_chunk<NT, EncShape<C>::kRun, false>(a, c, smem, esm);
+        }
     }
 }
 

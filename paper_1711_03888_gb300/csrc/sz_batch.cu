@@ -227,8 +227,7 @@ sz_status batch_compress(sz_ctx* ctx, int k, const float* const* d_in, const siz
         ms.elementSize = 4;
         ms.width = cnt_bytes / 4;
         ms.height = 1;
-        cudaKernelNodeParams kp;
-        memset(&kp, 0, sizeof(kp));
+        cudaKernelNodeParams kp{};
         void* kargs[] = {&plan};
         kp.func = func;
         kp.gridDim = dim3(grid);
@@ -251,8 +250,7 @@ sz_status batch_compress(sz_ctx* ctx, int k, const float* const* d_in, const siz
         cudaGraphNode_t prev = n_copy;
         for (int i = 0; nodes_ok && i < nml; ++i) {
             // range -> quantize -> codebook in a chain; the encoders after the codebook
-            cudaKernelNodeParams mp;
-            memset(&mp, 0, sizeof(mp));
+            cudaKernelNodeParams mp{};
             void* margs[] = {&ml[i].args};
             mp.func = const_cast<void*>(ml[i].func);
             mp.gridDim = dim3(ml[i].grid[0], ml[i].grid[1], ml[i].grid[2]);
