@@ -781,7 +781,7 @@ def main():
     ap.add_argument("--no-rd", action="store_true")
     ap.add_argument("--no-rkeys", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--cpu-log2n", type=int, default=24)
+    ap.add_argument("--cpu-log2n", type=int, default=26)
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-md", action="store_true")
@@ -1057,14 +1057,15 @@ def main():
         served = served_bench(sz, snap, args.eb, args.serve_rate, args.serve_seconds, args.serve_stress,
                               args.serve_stress_seconds, args.serve_slots, args.serve_budget_gb, local)
 
-    # ---- CPU oracle on a bounded sample (rank 0) -------------------------------
+    # ---- CPU oracle on a bounded sample (rank 0, N = 1 only) -----------------
     cpu = None
-    if rank == 0 and not args.no_cpu:
+    if rank == 0 and ws == 1 and not args.no_cpu:
         arrays = cpu_sample(snap, 1 << args.cpu_log2n)
         t, b = oracle_round_trip(arrays, args.eb)
         cpu = {"value": b / t / 1e9, "unit": "GB/s", "cores": len(arrays), "kind": "oracle",
                "sample": f"first 2^{args.cpu_log2n} elements of each of the 6 fields, compress + decompress, "
-                         f"one thread per field"}
+                         f"one thread per field",
+               "wall_s": t, "cpu_seconds_approx": t * len(arrays)}
 
     if rank == 0:
         line = {
