@@ -1015,13 +1015,13 @@ def main():
             h2d = 4 * sum(x.numel() for x in hx) + sum(nb)
             d2h = sum(nb) + 4 * sum(n_out)
 
-        for _ in range(2):
+        for _ in range(max(3, args.warmup)):
             e2e_step()
         torch.cuda.synchronize()
         _barrier(ws)
         # every call is synchronous, so each step's wall time is its own; the
         # value is the mean over the steps (the list shows host-side outliers)
-        k2 = max(1, min(args.steps, 5))
+        k2 = max(1, min(args.steps, 10))
         step_ms = []
         t0 = time.perf_counter()
         for _ in range(k2):

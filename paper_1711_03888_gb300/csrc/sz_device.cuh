@@ -132,14 +132,19 @@ __device__ __forceinline__ uint32_t swz(uint32_t e, uint32_t gshift) {
 }
 
 // ---------------------------------------------------------------------------
-// Memory-ordering helpers for the decoupled look-back
+// Status-word access for the decoupled look-back.  A chunk's status word holds
+// its flag and its value in one 64-bit word, and no other data is handed over
+// through it, so relaxed device-scope accesses suffice: a release store would
+// make the publishing thread wait for its earlier global writes first.
+// Measured on GB300 (six 2^27-element arrays, batched encode): acquire loads
+// with release stores 2.60 ms, relaxed loads 2.51 ms, both relaxed 2.23 ms.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void st_release(unsigned long long* p, unsigned long long v) {
-    asm volatile("st.release.gpu.global.u64 [%0], %1;" :: "l"(p), "l"(v) : "memory");
+__device__ __forceinline__ void st_status(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" :: "l"(p), "l"(v) : "memory");
 }
-__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
+__device__ __forceinline__ unsigned long long ld_status(const unsigned long long* p) {
     unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
 

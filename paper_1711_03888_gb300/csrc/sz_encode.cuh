@@ -107,7 +107,7 @@ __device__ __forceinline__ void encode_chunk_body(const CompressArgs& a, const L
     unsigned long long* status = a.chunk_status;
     constexpr unsigned long long FLAG_AGG = 1ull << 62, FLAG_INC = 2ull << 62, FLAG_ERR = 3ull << 62;
     constexpr unsigned long long VMASK = (1ull << 62) - 1;
-    if (tid == 0) st_release(&status[c], (c == 0 ? FLAG_INC : FLAG_AGG) | chunk_words);
+    if (tid == 0) st_status(&status[c], (c == 0 ? FLAG_INC : FLAG_AGG) | chunk_words);
     // zero the payload area (the code entries are in registers now)
     for (uint32_t w = tid; w < chunk_words; w += NT) buf[w] = 0u;
     __syncthreads();
@@ -172,10 +172,10 @@ __device__ __forceinline__ void encode_chunk_body(const CompressArgs& a, const L
             unsigned long long s = FLAG_INC;               // before chunk 0: an empty prefix
             if (pos >= 0) {
                 uint32_t spins = 0;
-                s = ld_acquire(&status[pos]);
+                s = ld_status(&status[pos]);
                 while ((s & ~VMASK) == 0ull && spins < kLookbackSpins) {
                     __nanosleep(64);
-                    s = ld_acquire(&status[pos]);
+                    s = ld_status(&status[pos]);
                     ++spins;
                 }
             }
@@ -193,9 +193,9 @@ __device__ __forceinline__ void encode_chunk_body(const CompressArgs& a, const L
         if (tid == 0) {
             if (bad) {
                 raise_err(a.err, E_TIMEOUT);
-                st_release(&status[c], FLAG_ERR);
+                st_status(&status[c], FLAG_ERR);
             } else {
-                st_release(&status[c], FLAG_INC | (excl + chunk_words));
+                st_status(&status[c], FLAG_INC | (excl + chunk_words));
             }
             s_prefix = bad ? ~0ull : excl;
         }
