@@ -1,0 +1,98 @@
+"""bench.py's host-side bookkeeping on CPU: the committed per-launch DRAM
+traffic is used only while the kernel's sources hash as they did when it was
+captured, and the nvidia-smi clock log is parsed into the median SM clock and
+the throttle reasons seen."""
+import json
+import os
+import shutil
+import subprocess
+import sys
+import tempfile
+import time
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def _copy_tree(tmp_path):
+    """A throwaway copy of what the traffic lookup reads."""
+    root = tmp_path / "repo"
+    shutil.copytree(os.path.join(ROOT, "profiles"), root / "profiles")
+    shutil.copytree(os.path.join(ROOT, "paper_1711_03888_gb300", "csrc"), root / "paper_1711_03888_gb300" / "csrc",
+                    ignore=shutil.ignore_patterns("*.o", "*.so"))
+    return root
+
+
+def test_traffic_entries_match_the_committed_sources():
+    d = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    kernels = [k for k in d if not k.startswith("_")]
+    assert kernels
+    for k in kernels:
+        t = bench._traffic(k)
+        assert t is not None, f"{k}: sources changed since the capture"
+        assert t == pytest.approx(d[k]["dram_read"] + d[k]["dram_write"])
+    assert bench._traffic("no_such_kernel") is None
+
+
+def test_traffic_is_dropped_once_a_source_changes(tmp_path, monkeypatch):
+    root = _copy_tree(tmp_path)
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    d = json.load(open(root / "profiles" / "traffic.json"))
+    k = next(k for k in d if not k.startswith("_"))
+    assert bench._traffic(k) is not None
+    src = root / "paper_1711_03888_gb300" / "csrc" / d[k]["sources"][-1]
+    src.write_bytes(src.read_bytes() + b"\n// edited\n")
+    assert bench._traffic(k) is None
+    # a missing or unreadable table gives no traffic either
+    (root / "profiles" / "traffic.json").write_text("{")
+    assert bench._traffic(k) is None
+    os.unlink(root / "profiles" / "traffic.json")
+    assert bench._traffic(k) is None
+
+
+def _fake_log(lines):
+    """A ClockSampler on its nvidia-smi path, fed by a process that prints
+    `lines` in nvidia-smi's CSV form and then waits to be terminated."""
+    s = bench.ClockSampler(0)
+    s.f = tempfile.NamedTemporaryFile("w", prefix="sz_clocks_", suffix=".csv", delete=False)
+    s.path = s.f.name
+    script = "".join(f"echo '{ln}'; " for ln in lines) + "sleep 30"
+    s.proc = subprocess.Popen(["bash", "-c", script], stdout=s.f)
+    deadline = time.time() + 10
+    while os.path.getsize(s.path) < sum(len(ln) + 1 for ln in lines) and time.time() < deadline:
+        time.sleep(0.02)
+    return s
+
+
+def test_clock_log_median_and_reasons():
+    lines = [
+        "0, 2070, 2070, 900.5, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 1980, 2070, 1399.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 1100.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "garbage line",
+        "0, [N/A], 2070, 0, 0x0, Not Active, Not Active, Not Active, Not Active",
+    ]
+    s = _fake_log(lines)
+    path = s.path
+    r = s.stop()
+    assert r["source"] == "nvidia-smi"
+    assert r["samples"] == 3
+    assert r["sm_mhz"] == 2070.0 and r["sm_max_mhz"] == 2070.0
+    assert r["reasons"] == ["sw_power_cap"]
+    assert not os.path.exists(path)
+
+
+def test_clock_log_reports_every_slowdown_reason():
+    lines = ["0, 1200, 2070, 500, 0x68, Active, Active, Active, Not Active"]
+    r = _fake_log(lines).stop()
+    assert r["sm_mhz"] == 1200.0
+    assert r["reasons"] == ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"]
+
+
+def test_unsampled_clocks_say_so():
+    s = bench.ClockSampler(0)
+    assert s.stop() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
