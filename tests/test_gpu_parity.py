@@ -108,6 +108,39 @@ def test_stream_parity_absolute(sz, ctx, oracle, eb_abs):
     _check(sz, ctx, oracle, _make("spiky", 30000), eb_abs, 0, 2048)
 
 
+def _degenerate(kind, n):
+    i = np.arange(n)
+    if kind == "all_nan":
+        return np.full(n, np.nan, np.float32)
+    if kind == "all_inf":
+        return np.where(i % 2 == 0, np.inf, -np.inf).astype(np.float32)
+    if kind == "nan_payloads":      # quiet and signalling NaNs of both signs, distinct payloads
+        bits = np.where(i % 2 == 0, 0x7FC00000, 0xFF800000).astype(np.uint32) | ((i % 4093) + 1).astype(np.uint32)
+        return bits.view(np.float32)
+    if kind == "two_values":
+        return np.where(i % 3 == 0, 1.0, -1.0).astype(np.float32)
+    if kind == "one_finite":        # the value range is one point among non-finite values
+        x = np.full(n, np.nan, np.float32)
+        x[n // 2] = 7.25
+        return x
+    raise ValueError(kind)
+
+
+@pytest.mark.parametrize("kind", ["all_nan", "all_inf", "nan_payloads", "two_values", "one_finite"])
+@pytest.mark.parametrize("n", [1, 7, 2049, 9000])
+@pytest.mark.parametrize("eb,ek", [(1e-4, 1), (1e-3, 0)])
+def test_degenerate_arrays(sz, ctx, oracle, kind, n, eb, ek):
+    """Arrays without a finite value range (every value NaN or infinite, or one
+    finite value among them), NaN payloads, and a two-symbol codebook: the
+    stream equals the oracle's and the decode is bit-exact, NaN payloads included."""
+    x = torch.from_numpy(_degenerate(kind, n))
+    ref = _check(sz, ctx, oracle, x, eb, ek, 2048)
+    if kind != "two_values":
+        # stored raw: the decode reproduces every input bit, NaN payloads included
+        assert oracle.parse_header(ref)["flags"] == 1
+        assert np.array_equal(_bits(oracle.decompress(ref)), _bits(x.numpy()))
+
+
 def test_empty_array(sz, ctx, oracle):
     x = torch.zeros(0, dtype=torch.float32)
     ref = oracle.compress(x.numpy(), 1e-4, 1, 2048, 32)
