@@ -118,6 +118,36 @@ def _ptr(t) -> int:
     return 0 if t is None else int(t.data_ptr())
 
 
+_F32, _U8, _I32 = "float32", "uint8", "int32"
+
+
+def _arg(t, dtype: str, device: str, what: str, min_numel: int = 0):
+    """Check a tensor before its address crosses the C ABI, which takes raw
+    pointers and element counts: the element type, one contiguous block, the
+    memory the call expects ("cuda" for device calls, "cpu" for the host-memory
+    calls) and, where a count is passed beside it, enough elements."""
+    if str(t.dtype) != "torch." + dtype:
+        raise SzError(SZ_ERR_ARG, f"{what}: {t.dtype}, expected torch.{dtype}")
+    if not t.is_contiguous():
+        raise SzError(SZ_ERR_ARG, f"{what}: not contiguous")
+    if t.device.type != device:
+        raise SzError(SZ_ERR_ARG, f"{what}: on {t.device}, expected {device} memory")
+    min_numel = int(getattr(min_numel, "value", min_numel))
+    if t.numel() < min_numel:
+        raise SzError(SZ_ERR_ARG, f"{what}: {t.numel()} elements, {min_numel} needed")
+    return t
+
+
+def _cap(t, cap, what: str) -> int:
+    """An explicit capacity may not pass the tensor's own size."""
+    if cap is None:
+        return t.numel()
+    cap = int(getattr(cap, "value", cap))
+    if cap < 0 or cap > t.numel():
+        raise SzError(SZ_ERR_ARG, f"{what}: capacity {cap} outside 0..{t.numel()}")
+    return int(cap)
+
+
 def _stream(stream):
     if stream is not None:
         return C.c_void_p(int(stream))
@@ -174,10 +204,12 @@ def sz_compress(ctx: Context, x, eb: float, kind: int = SZ_EB_REL, params=None, 
     tensor; allocated with the maximum size when None).  Returns
     (out, size_holder); size_holder.value is valid after sz_sync."""
     import torch
+    _arg(x, _F32, "cuda", "sz_compress x")
     n = x.numel()
     if out is None:
         out = torch.empty(sz_max_compressed_bytes(n), dtype=torch.uint8, device=x.device)
-    cap = out.numel() if out_cap is None else out_cap
+    _arg(out, _U8, "cuda", "sz_compress out")
+    cap = _cap(out, out_cap, "sz_compress out")
     nb = ctx.hold(C.c_size_t(0))
     p = params if params is not None else _params()
     _check(_lib.sz_compress(ctx.handle, _ptr(x), n, eb, kind, C.byref(p), _ptr(out), cap, C.byref(nb),
@@ -188,8 +220,10 @@ def sz_compress(ctx: Context, x, eb: float, kind: int = SZ_EB_REL, params=None, 
 def sz_decompress(ctx: Context, stream_buf, in_bytes: int, out, n_cap=None, stream=None):
     """Enqueue decompression of a stream (uint8 CUDA tensor) into the float32
     CUDA tensor `out`.  Returns a holder whose .value is n after sz_sync."""
+    _arg(stream_buf, _U8, "cuda", "sz_decompress stream", in_bytes)
+    _arg(out, _F32, "cuda", "sz_decompress out")
+    cap = _cap(out, n_cap, "sz_decompress out")
     no = ctx.hold(C.c_size_t(0))
-    cap = out.numel() if n_cap is None else n_cap
     _check(_lib.sz_decompress(ctx.handle, _ptr(stream_buf), in_bytes, _ptr(out), cap, C.byref(no),
                               _stream(stream)), "sz_decompress")
     return no
@@ -198,8 +232,12 @@ def sz_decompress(ctx: Context, stream_buf, in_bytes: int, out, n_cap=None, stre
 def sz_compress_batch(ctx: Context, xs, ebs, kind: int = SZ_EB_REL, params=None, outs=None, stream=None):
     import torch
     k = len(xs)
+    for i in range(k):
+        _arg(xs[i], _F32, "cuda", f"sz_compress_batch xs[{i}]")
     if outs is None:
         outs = [torch.empty(sz_max_compressed_bytes(x.numel()), dtype=torch.uint8, device=x.device) for x in xs]
+    for i in range(k):
+        _arg(outs[i], _U8, "cuda", f"sz_compress_batch outs[{i}]")
     ins = (C.c_void_p * k)(*[_ptr(x) for x in xs])
     ns = (C.c_size_t * k)(*[x.numel() for x in xs])
     e = (C.c_double * k)(*ebs)
@@ -214,6 +252,9 @@ def sz_compress_batch(ctx: Context, xs, ebs, kind: int = SZ_EB_REL, params=None,
 
 def sz_decompress_batch(ctx: Context, streams, in_bytes, outs, stream=None):
     k = len(streams)
+    for i in range(k):
+        _arg(streams[i], _U8, "cuda", f"sz_decompress_batch streams[{i}]", in_bytes[i])
+        _arg(outs[i], _F32, "cuda", f"sz_decompress_batch outs[{i}]")
     ins = (C.c_void_p * k)(*[_ptr(s) for s in streams])
     ib = (C.c_size_t * k)(*in_bytes)
     o = (C.c_void_p * k)(*[_ptr(t) for t in outs])
@@ -229,8 +270,12 @@ def sz_compress_host(ctx: Context, xs, ebs, kind: int = SZ_EB_REL, params=None, 
     outs, sizes); raises on failure when `check`."""
     import torch
     k = len(xs)
+    for i in range(k):
+        _arg(xs[i], _F32, "cpu", f"sz_compress_host xs[{i}]")
     if outs is None:
         outs = [torch.empty(sz_max_compressed_bytes(x.numel()), dtype=torch.uint8).pin_memory() for x in xs]
+    for i in range(k):
+        _arg(outs[i], _U8, "cpu", f"sz_compress_host outs[{i}]")
     ins = (C.c_void_p * k)(*[_ptr(x) for x in xs])
     ns = (C.c_size_t * k)(*[x.numel() for x in xs])
     e = (C.c_double * k)(*ebs)
@@ -248,6 +293,9 @@ def sz_decompress_host(ctx: Context, streams, in_bytes, outs, stream=None, check
     """Host streams in, host float32 tensors out (synchronous).  Returns
     (status, element counts); raises on failure when `check`."""
     k = len(streams)
+    for i in range(k):
+        _arg(streams[i], _U8, "cpu", f"sz_decompress_host streams[{i}]", in_bytes[i])
+        _arg(outs[i], _F32, "cpu", f"sz_decompress_host outs[{i}]")
     ins = (C.c_void_p * k)(*[_ptr(s) for s in streams])
     ib = (C.c_size_t * k)(*in_bytes)
     o = (C.c_void_p * k)(*[_ptr(t) for t in outs])
@@ -263,10 +311,16 @@ def sz_compress_snapshot(ctx: Context, fields, xs, n: int, ebs, kind: int = SZ_E
                          params=None, outs=None, perm=None, stream=None):
     import torch
     k = len(xs)
+    for i in range(k):
+        _arg(xs[i], _F32, "cuda", f"sz_compress_snapshot xs[{i}]", n)
     if outs is None:
         outs = [torch.empty(sz_max_compressed_bytes(n), dtype=torch.uint8, device=xs[0].device) for _ in xs]
         if mode == SZ_MODE_CPC2000:
             outs[0] = torch.empty(sz_cpc_max_bytes(n), dtype=torch.uint8, device=xs[0].device)
+    for i in range(k):
+        _arg(outs[i], _U8, "cuda", f"sz_compress_snapshot outs[{i}]")
+    if perm is not None:
+        _arg(perm, _I32, "cuda", "sz_compress_snapshot perm", n)
     f = (C.c_int * k)(*fields)
     ins = (C.c_void_p * k)(*[_ptr(x) for x in xs])
     e = (C.c_double * k)(*ebs)
@@ -286,6 +340,11 @@ def sz_cpc_max_bytes(n: int) -> int:
 def sz_decompress_cpc(ctx: Context, stream_buf, in_bytes: int, outs, n_cap=None, stream=None):
     """Enqueue decoding of an SZ-CPC2000 coordinate stream into three float32
     CUDA tensors (x, y, z).  Returns a holder whose .value is n after sz_sync."""
+    _arg(stream_buf, _U8, "cuda", "sz_decompress_cpc stream", in_bytes)
+    if len(outs) != 3:
+        raise SzError(SZ_ERR_ARG, "sz_decompress_cpc: three output arrays (x, y, z)")
+    for i, t in enumerate(outs):
+        _arg(t, _F32, "cuda", f"sz_decompress_cpc outs[{i}]", 0 if n_cap is None else n_cap)
     no = ctx.hold(C.c_size_t(0))
     o = ctx.hold((C.c_void_p * 3)(*[_ptr(t) for t in outs]))
     cap = min(t.numel() for t in outs) if n_cap is None else n_cap
@@ -311,10 +370,12 @@ def sz_compress_noalloc(x, eb: float, kind: int = SZ_EB_REL, out=None, out_cap=N
     n <= 2^26).  Synchronous; returns (status, out, out_bytes).  `out` is
     allocated here by torch when None -- pass it to allocate nothing at all."""
     import torch
+    _arg(x, _F32, "cuda", "sz_compress_noalloc x")
     n = x.numel()
     if out is None:
         out = torch.empty(sz_max_compressed_bytes(n), dtype=torch.uint8, device=x.device)
-    cap = out.numel() if out_cap is None else out_cap
+    _arg(out, _U8, "cuda", "sz_compress_noalloc out")
+    cap = _cap(out, out_cap, "sz_compress_noalloc out")
     nb = C.c_size_t(0)
     st = _lib.sz_compress_noalloc(_ptr(x), n, eb, kind, _ptr(out), cap, C.byref(nb), _stream(stream))
     return st, out, nb.value
