@@ -407,9 +407,10 @@ def link_rates(hx, hy):
     return {"h2d_gbs": nb / t_in / 1e9, "d2h_gbs": nb / t_out / 1e9, "both_gbs": 2 * nb / t_both / 1e9}
 
 
-def _traffic(kernel: str):
-    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if the
-    kernel source is unchanged since the capture; else None."""
+def _ncu_entry(kernel: str):
+    """The committed ncu record of `kernel` (per-launch DRAM bytes and device
+    time on the full workload), if the kernel's sources are unchanged since
+    the capture; else None."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -423,9 +424,33 @@ def _traffic(kernel: str):
             h.update(open(os.path.join(ROOT, "paper_1711_03888_gb300", "csrc", f), "rb").read())
         if h.hexdigest()[:16] != e["sources_sha256_16"]:
             return None
-        return float(e["bytes_per_launch_full"])
+        return e
     except Exception:
         return None
+
+
+def _traffic(kernel: str):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if the
+    kernel source is unchanged since the capture; else None."""
+    e = _ncu_entry(kernel)
+    try:
+        return None if e is None else float(e["bytes_per_launch_full"])
+    except (KeyError, TypeError, ValueError):
+        return None
+
+
+def ncu_dram_rate(kernel: str, peak: float):
+    """The DRAM rate ncu measured for one launch of `kernel` (bytes read and
+    written over its serialised device time), and its fraction of `peak`."""
+    e = _ncu_entry(kernel)
+    try:
+        b, ns = float(e["bytes_per_launch_full"]), float(e["ncu_duration_ns"])
+    except (KeyError, TypeError, ValueError):
+        return None
+    if ns <= 0:
+        return None
+    gbs = b / ns
+    return {"dram_bytes": b, "duration_ms": ns / 1e6, "dram_gbs": gbs, "dram_frac": gbs / peak}
 
 
 # ---------------------------------------------------------------------------
@@ -983,6 +1008,19 @@ def main():
 
     kernels = kernel_table(prof, args.steps, algo_batched)
     kernels_plain = kernel_table(prof_plain, args.steps, algo_plain)
+    for ph, kname in kernel_multi.items():
+        if ph in kernels:
+            kernels[ph]["ncu"] = ncu_dram_rate(kname, peak)
+    # The bytes the pass structure forces, per step: with a relative bound the
+    # range and quantize passes each read the input, the u16 codes go out and
+    # back, and the stream is written; decompression reads the stream and
+    # writes the floats.
+    dep_c, dep_d = 12 * n * k6 + stream_bytes, stream_bytes + 4 * n * k6
+    dependency = {"compress_bytes_per_step": dep_c, "decompress_bytes_per_step": dep_d,
+                  "compress_gbs": dep_c / (t_c / args.steps) / 1e9,
+                  "decompress_gbs": dep_d / (t_d / args.steps) / 1e9}
+    dependency["compress_frac"] = dependency["compress_gbs"] / peak
+    dependency["decompress_frac"] = dependency["decompress_gbs"] / peak
     # The dominant single kernel of the batched step by device time per step.
     # While tracing is on, the batch's graph work runs as direct launches of the
     # same per-phase kernels, each between two events on the step's stream.
@@ -1079,6 +1117,7 @@ def main():
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config,
             "compress_gbs": comp_gbs, "decompress_gbs": decomp_gbs,
             "compress_frac_hbm": comp_gbs / peak, "decompress_frac_hbm": decomp_gbs / peak,
+            "dependency_bytes": dependency,
             "ratio": ratio, "roofline": roofline, "kernels": kernels, "kernels_plain_path": kernels_plain,
             "gpu_launches": launches,
             "plain_path": plain, "lcf": lcf, "batched": batched, "md": md, "rkeys": rkeys, "rd": rd,

@@ -96,3 +96,20 @@ def test_clock_log_reports_every_slowdown_reason():
 def test_unsampled_clocks_say_so():
     s = bench.ClockSampler(0)
     assert s.stop() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+
+
+def test_ncu_dram_rate_from_the_committed_capture(tmp_path, monkeypatch):
+    d = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    for k in (k for k in d if not k.startswith("_")):
+        r = bench.ncu_dram_rate(k, 1000.0)
+        b = d[k]["dram_read"] + d[k]["dram_write"]
+        assert r["dram_bytes"] == pytest.approx(b)
+        assert r["dram_gbs"] == pytest.approx(b / d[k]["ncu_duration_ns"])
+        assert r["dram_frac"] == pytest.approx(r["dram_gbs"] / 1000.0)
+        assert r["duration_ms"] == pytest.approx(d[k]["ncu_duration_ns"] / 1e6)
+    root = _copy_tree(tmp_path)
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    k = next(k for k in d if not k.startswith("_"))
+    src = root / "paper_1711_03888_gb300" / "csrc" / d[k]["sources"][0]
+    src.write_bytes(b"// edited\n" + src.read_bytes())
+    assert bench.ncu_dram_rate(k, 1000.0) is None
