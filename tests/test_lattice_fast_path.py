@@ -140,3 +140,16 @@ def test_candidate_alone_is_not_enough(oracle):
     assert wrong.mean() > 0.01
     taken, q, _ = _fast_path(x[wrong], D, eb_abs)
     assert (q[taken] == qo[wrong][taken]).all() and taken.mean() > 0.99
+
+
+@pytest.mark.parametrize("D", [F32(2.0 ** -9), F32(0.0512), F32(3.0), F32(2.0 ** -140), F32(1e30)])
+def test_reconstruction_shortcut_every_small_q(D):
+    """The decoder's shortcut (sz_device.cuh, recon_f; the 32-bit loop of
+    k_decode.cu): for |q| <= 2^24 one float multiply RN32(float(q) * D)
+    equals the definition RN32(RN64(q * D)), for every such q, a subnormal
+    step and a step whose products overflow included."""
+    q = np.arange(-(1 << 24), (1 << 24) + 1, dtype=np.int64)
+    with np.errstate(over="ignore"):
+        short = q.astype(F32) * D
+        ref = (q.astype(F64) * F64(D)).astype(F32)
+    assert np.array_equal(short.view(np.uint32), ref.view(np.uint32))
