@@ -429,7 +429,24 @@ def sz_serve_stats(ctx: Context) -> dict:
 def request(op: int, inp, n: int, out=None, out_cap: int = 0, in_bytes: int = 0, eb: float = 0.0,
             kind: int = SZ_EB_REL) -> sz_request:
     """Build an sz_request from CUDA tensors or raw device addresses (out=None:
-    the service allocates the output)."""
+    the service allocates the output).  Tensors are checked like the other
+    entry points' (raw addresses are the caller's responsibility): a compress
+    request takes n float32 values in and writes uint8 stream bytes, within
+    out_cap; a decompress request reads in_bytes stream bytes and writes up to
+    n float32 values."""
+    comp = op == SZ_OP_COMPRESS
+    if not isinstance(inp, int) and inp is not None:
+        if comp:
+            _arg(inp, _F32, "cuda", "request input", n)
+        else:
+            _arg(inp, _U8, "cuda", "request stream", in_bytes)
+    if not isinstance(out, int) and out is not None:
+        if comp:
+            _arg(out, _U8, "cuda", "request output")
+            _cap(out, out_cap, "request output")
+        else:
+            _arg(out, _F32, "cuda", "request output", n)
+
     def addr(t):
         return None if t is None else (t if isinstance(t, int) else t.data_ptr())
     return sz_request(op, addr(inp), n, in_bytes, addr(out), out_cap, eb, kind)

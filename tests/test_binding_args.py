@@ -73,3 +73,41 @@ def test_coordinate_decoder_takes_three_arrays():
     x = torch.zeros(8, dtype=torch.float32)
     # the memory check of the stream comes first on CPU; with two arrays the count is refused
     _refused(sz.sz_decompress_cpc, CTX, s, 8, [x, x])
+
+
+class _DevT:
+    """Stands in for a contiguous CUDA tensor (dtype, memory kind, size,
+    address) so the acceptance side of the checks runs on CPU."""
+
+    def __init__(self, dtype, numel):
+        self.dtype, self._n = dtype, numel
+        self.device = types.SimpleNamespace(type="cuda")
+
+    def numel(self):
+        return self._n
+
+    def is_contiguous(self):
+        return True
+
+    def data_ptr(self):
+        return 1 << 20
+
+
+def test_serving_requests_are_checked_like_the_calls():
+    n = 5000
+    x, st = _DevT(torch.float32, n), _DevT(torch.uint8, 1234)
+    out_c, out_d = _DevT(torch.uint8, sz.sz_max_compressed_bytes(n)), _DevT(torch.float32, n)
+    # the shapes the serving tests and the bench submit are accepted
+    sz.request(sz.SZ_OP_COMPRESS, x, n, eb=1e-4)
+    sz.request(sz.SZ_OP_COMPRESS, x, n, out=out_c, out_cap=out_c.numel(), eb=1e-4)
+    sz.request(sz.SZ_OP_DECOMPRESS, st, n, in_bytes=st.numel())
+    sz.request(sz.SZ_OP_DECOMPRESS, st, n, out=out_d, in_bytes=st.numel())
+    r = sz.request(sz.SZ_OP_COMPRESS, 123456, n, out=654321, out_cap=10)     # raw addresses pass
+    assert r.input == 123456 and r.out == 654321
+    # and the ones that do not fit are refused
+    _refused(sz.request, sz.SZ_OP_COMPRESS, torch.zeros(n), n)                # host memory
+    _refused(sz.request, sz.SZ_OP_COMPRESS, _DevT(torch.uint8, n), n)         # a stream as input
+    _refused(sz.request, sz.SZ_OP_COMPRESS, _DevT(torch.float32, n - 1), n)   # too short
+    _refused(sz.request, sz.SZ_OP_COMPRESS, x, n, out=out_c, out_cap=out_c.numel() + 1)
+    _refused(sz.request, sz.SZ_OP_DECOMPRESS, st, n, in_bytes=st.numel() + 1)
+    _refused(sz.request, sz.SZ_OP_DECOMPRESS, st, n, out=_DevT(torch.float32, n - 1), in_bytes=10)
