@@ -486,12 +486,96 @@ class _Holder:
         return int(self.arr[self.i])
 
 
+def _stats_ms(seconds):
+    """best / median / mean of per-step times (seconds in, ms out)."""
+    import numpy as np
+    v = 1e3 * np.asarray(seconds, dtype=np.float64)
+    return {"best": float(v.min()), "median": float(np.median(v)), "mean": float(v.mean())}
+
+
 def cpu_sample(snap, n_sample):
     import numpy as np
     return [np.ascontiguousarray(snap[f][:n_sample].cpu().numpy()) for f in FIELDS]
 
 
 # ---------------------------------------------------------------------------
+
+def _round_trip_timed(sz, ctx, stream, xs, ebs, outs, ys, steps, traced=False):
+    """steps x (sz_compress_batch + sz_decompress_batch) with CUDA events around
+    each half; returns (compress seconds per step, decompress seconds per step,
+    stream sizes, per-phase trace or None)."""
+    import torch
+    if traced:
+        sz.sz_profile_enable(ctx, True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for a, b, c in ev:
+        a.record(stream)
+        _, nb = sz.sz_compress_batch(ctx, xs, ebs, sz.SZ_EB_REL, outs=outs)
+        b.record(stream)
+        sz.sz_decompress_batch(ctx, outs, [o.numel() for o in outs], ys)
+        c.record(stream)
+    sz.sz_sync(ctx)
+    torch.cuda.synchronize()
+    prof = None
+    if traced:
+        prof = sz.sz_profile_read(ctx)
+        sz.sz_profile_enable(ctx, False)
+    tc = sum(a.elapsed_time(b) for a, b, _ in ev) / steps / 1e3
+    td = sum(b.elapsed_time(c) for _, b, c in ev) / steps / 1e3
+    return tc, td, [int(nb[i]) for i in range(len(xs))], prof
+
+
+def bounds_bench(sz, ctx, stream, xs, ys, outs, raw_bytes, steps, peak):
+    """The large snapshot at its other relative bounds (1e-3 and 1e-5), through
+    the same batched calls: round-trip rates, ratio, and the traced decoder's
+    rate of its algorithmic bytes against the HBM peak."""
+    res = {}
+    for eb in (1e-3, 1e-5):
+        ebs = [eb] * len(xs)
+        for _ in range(2):
+            _round_trip_timed(sz, ctx, stream, xs, ebs, outs, ys, 1)
+        tc, td, sizes, _ = _round_trip_timed(sz, ctx, stream, xs, ebs, outs, ys, steps)
+        _, _, _, prof = _round_trip_timed(sz, ctx, stream, xs, ebs, outs, ys, steps, traced=True)
+        sb = sum(sizes)
+        rec = {"compress_gbs": raw_bytes / tc / 1e9, "decompress_gbs": raw_bytes / td / 1e9,
+               "round_trip_gbs": raw_bytes / (tc + td) / 1e9, "ratio": raw_bytes / sb,
+               "compress_frac_hbm": raw_bytes / tc / 1e9 / peak, "decompress_frac_hbm": raw_bytes / td / 1e9 / peak}
+        for ph, algo in (("decode", sb + raw_bytes), ("encode", raw_bytes // 2 + sb), ("quant", raw_bytes * 3 // 2)):
+            cnt, ms = prof.get(ph, (0, 0.0))
+            if cnt:
+                avg = ms / cnt / 1e3
+                per_launch = algo * steps / cnt
+                rec[ph] = {"avg_ms": 1e3 * avg, "achieved_gbs": per_launch / avg / 1e9,
+                           "frac": per_launch / avg / 1e9 / peak}
+        res[f"{eb:g}"] = rec
+    return res
+
+
+def small_bench(sz, device, eb, steps, peak):
+    """The plain cosmology snapshot of 2^20 particles x 6 fields (4 MiB arrays,
+    64 halos) through the batched calls: round-trip rates and ratio."""
+    import torch
+    import synth
+    snap = synth.cosmology(1 << 20, 64, 1, device="cuda")
+    xs = [snap[f] for f in FIELDS]
+    raw = 4 * sum(x.numel() for x in xs)
+    ctx = sz.Context(device)
+    outs = [torch.empty(sz.sz_max_compressed_bytes(x.numel()), dtype=torch.uint8, device="cuda") for x in xs]
+    ys = [torch.empty(x.numel(), dtype=torch.float32, device="cuda") for x in xs]
+    stream = torch.cuda.current_stream()
+    ebs = [eb] * len(xs)
+    for _ in range(3):
+        _round_trip_timed(sz, ctx, stream, xs, ebs, outs, ys, 1)
+    tc, td, sizes, _ = _round_trip_timed(sz, ctx, stream, xs, ebs, outs, ys, steps)
+    res = {"workload": f"plain cosmology snapshot: 2^20 particles x 6 float32 fields, 64 halos, rel eb {eb:g}",
+           "compress_gbs": raw / tc / 1e9, "decompress_gbs": raw / td / 1e9, "round_trip_gbs": raw / (tc + td) / 1e9,
+           "compress_ms": 1e3 * tc, "decompress_ms": 1e3 * td, "ratio": raw / sum(sizes),
+           "compress_frac_hbm": raw / tc / 1e9 / peak, "decompress_frac_hbm": raw / td / 1e9 / peak,
+           "tuned_chunk": sz.sz_batch_tuning(ctx, 1 << 20)["chunk_elems"]}
+    ctx.close()
+    return res
+
 
 # ---------------------------------------------------------------------------
 # Batched form: 128 simulated ranks x 6 fields of uneven sizes
@@ -545,13 +629,40 @@ def batched_bench(sz, device, steps):
     decomp()
     sz.sz_sync(ctx)
     t_dec = timed(decomp, steps)
+    # what the autotuner chose (one entry per size class present) ...
+    classes = {}
+    for x in xs:
+        t = sz.sz_batch_tuning(ctx, x.numel())
+        key = f"{t['class'][0]}..{t['class'][1]}"
+        if key not in classes:
+            classes[key] = {"chunk": t["chunk_elems"], "fixed_rule_chunk": t["fixed_chunk_elems"],
+                            "trial_ms": t["trial_ms"], "arrays": 0}
+        classes[key]["arrays"] += 1
+    t0 = sz.sz_batch_tuning(ctx, xs[0].numel())
+    tuned = {"classes": classes, "range_tile": t0["range_tile"], "quant_group": t0["quant_group"],
+             "tile_trial_ms": t0["tile_trial_ms"],
+             "note": "chosen by timing compress + decompress of the batch on the device for each candidate "
+                     "chunk size (first sight of a size class), then the persistent kernel's item sizes"}
+    # ... against the fixed rule (2048 up to 2^16 elements, else 4096; default item sizes)
+    sz.sz_ctx_set_autotune(ctx, False)
+    for _ in range(2):
+        nbf = batch()
+        sz.sz_sync(ctx)
+    sizes_f = [int(nbf[i]) for i in range(len(xs))]
+    t_batch_f = timed(batch, steps)
+    decomp()
+    sz.sz_sync(ctx)
+    t_dec_f = timed(decomp, steps)
+    tuned["fixed_rule"] = {"compress_ms": 1e3 * t_batch_f, "decompress_ms": 1e3 * t_dec_f,
+                           "round_trip_ms": 1e3 * (t_batch_f + t_dec_f), "ratio": nbytes / sum(sizes_f)}
+    tuned["tuned_round_trip_ms"] = 1e3 * (t_batch + t_dec)
     res = {"workload": "768 float32 arrays (128 ranks x 6 fields), 2^U[14,24] elements each, per-array rel eb "
                        "from {1e-3, 1e-4}; cosmology generator per rank sub-box",
            "arrays": len(xs), "gbytes": nbytes / 1e9, "ratio": nbytes / sum(sizes),
            "batched_compress_gbs": nbytes / t_batch / 1e9, "batched_compress_ms": 1e3 * t_batch,
            "plain_compress_gbs": nbytes / t_plain / 1e9, "plain_compress_ms": 1e3 * t_plain,
            "speedup": t_plain / t_batch,
-           "decompress_gbs": nbytes / t_dec / 1e9, "decompress_ms": 1e3 * t_dec}
+           "decompress_gbs": nbytes / t_dec / 1e9, "decompress_ms": 1e3 * t_dec, "autotuner": tuned}
     ctx.close()
     return res
 
@@ -716,29 +827,35 @@ def run_served(sz, ctx, reqs, eb):
 
 
 def run_serial_plain(sz, ctx, reqs, eb, out_c, out_d):
-    """The same requests back to back through sz_compress / sz_decompress on
-    one stream; per-request device time from CUDA events.  Latency under the
-    same arrivals follows the single-server queue: c_i = max(a_i, c_{i-1}) + s_i."""
+    """The same requests issued at their arrival times, one after another,
+    through the plain calls: each sz_compress / sz_decompress is followed by
+    sz_sync, so a request that arrives while the previous one runs waits for
+    it.  Latency = completion - arrival (host clock); the device time of each
+    call from CUDA events."""
     import torch
     stream = torch.cuda.current_stream()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in reqs]
     torch.cuda.synchronize()
+    lat = []
     t0 = time.perf_counter()
     for e, (ta, op, x, n, nb) in zip(ev, reqs):
+        while True:
+            d = ta - (time.perf_counter() - t0)
+            if d <= 0:
+                break
+            if d > 3e-4:
+                time.sleep(d - 2e-4)
         e[0].record(stream)
         if op == "c":
             sz.sz_compress(ctx, x, eb, sz.SZ_EB_REL, None, out_c)
         else:
             sz.sz_decompress(ctx, x, nb, out_d, n)
         e[1].record(stream)
-    sz.sz_sync(ctx)
+        sz.sz_sync(ctx)
+        lat.append(time.perf_counter() - t0 - ta)
     torch.cuda.synchronize()
     span = time.perf_counter() - t0
     svc = [a.elapsed_time(b) / 1e3 for a, b in ev]
-    c, lat = 0.0, []
-    for (ta, *_), s in zip(reqs, svc):
-        c = max(ta, c) + s
-        lat.append(c - ta)
     return lat, sum(svc), span
 
 
@@ -793,6 +910,21 @@ def served_bench(sz, snap, eb, rate, seconds, stress, stress_seconds, slots, bud
     res["counters"] = sz.sz_serve_stats(ctx)
     sz.sz_serve_stop(ctx)
     ctx.close()
+    # the stress arrivals under a budget below what they keep in flight, so
+    # that admission waits for budget (a 2^27-element compress holds ~1.3 GB)
+    small_gb = 3.0
+    ctx = sz.Context(device, budget=int(small_gb * (1 << 30)))
+    sz.sz_serve_start(ctx, slots)
+    run_served(sz, ctx, [(0.0, "c", big[: 1 << 27], 1 << 27, 0)] + [(0.0, "d", st, n, nb) for st, n, nb in streams[:2]],
+               eb)
+    reqs = make_requests(rng, rate * stress, stress_seconds, pools, streams)
+    lat, span = run_served(sz, ctx, reqs, eb)
+    nbytes = sum(4 * r[3] for r in reqs)
+    res["stress_small_budget"] = {"budget_gb": small_gb, "rate_per_s": rate * stress, "requests": len(reqs),
+                                  "p50_ms": 1e3 * _percentile(lat, 50), "p99_ms": 1e3 * _percentile(lat, 99),
+                                  "gbs": nbytes / span / 1e9, "counters": sz.sz_serve_stats(ctx)}
+    sz.sz_serve_stop(ctx)
+    ctx.close()
     plain.close()
     return res
 
@@ -814,6 +946,8 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-md", action="store_true")
+    ap.add_argument("--no-bounds", action="store_true")
+    ap.add_argument("--no-small", action="store_true")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--serve-stress", type=float, default=10.0)
@@ -906,14 +1040,17 @@ def main():
         assert err <= args.eb * R * (1 + 1e-12), f"error bound violated: {err} > {args.eb * R}"
     ratio = raw_bytes / sum(sizes)
 
+    tuning = sz.sz_batch_tuning(ctx, n)     # the autotuner ran on the guard call (first sight)
+
     clocks = ClockSampler(local)
-    clocks.start()            # sampling from the warm-up through the timed region
+    clocks.start()            # sampling from the warm-up through the timed regions
     for _ in range(args.warmup):
         step()
         sz.sz_sync(ctx)
     torch.cuda.synchronize()
-    _barrier(ws)
-    sz.sz_profile_enable(ctx, True)
+    # ---- headline: the product's calls as a user makes them -- the batch's CUDA
+    # graph replay and the batched decoder -- with no tracing; CUDA events on
+    # the stream around the compress half and the decompress half of each step
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
            torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     torch.cuda.synchronize()
@@ -928,15 +1065,37 @@ def main():
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall0
     _barrier(ws)
-    prof = sz.sz_profile_read(ctx)
-    sz.sz_profile_enable(ctx, False)
-    clk = clocks.stop()
-    t_c = sum(e[0].elapsed_time(e[1]) for e in ev) / 1e3
-    t_d = sum(e[1].elapsed_time(e[2]) for e in ev) / 1e3
+    tc_steps = [e[0].elapsed_time(e[1]) / 1e3 for e in ev]
+    td_steps = [e[1].elapsed_time(e[2]) / 1e3 for e in ev]
+    t_c = sum(tc_steps)
+    t_d = sum(td_steps)
     t_step = (t_c + t_d) / args.steps
     value, t_step_max, total_bytes = weak_scaling_value(raw_bytes, t_step, ws)
     comp_gbs = raw_bytes / (t_c / args.steps) / 1e9
     decomp_gbs = raw_bytes / (t_d / args.steps) / 1e9
+    stats = {"timing": "CUDA events on the stream, graph replay (no tracing), per step",
+             "compress_ms": _stats_ms(tc_steps), "decompress_ms": _stats_ms(td_steps),
+             "step_ms": _stats_ms([a + b for a, b in zip(tc_steps, td_steps)])}
+    stats["compress_gbs_best"] = raw_bytes / (stats["compress_ms"]["best"] / 1e3) / 1e9
+    stats["decompress_gbs_best"] = raw_bytes / (stats["decompress_ms"]["best"] / 1e3) / 1e9
+    stats["round_trip_gbs_median"] = raw_bytes / (stats["step_ms"]["median"] / 1e3) / 1e9
+
+    # ---- breakdown: the same steps traced, each kernel between two events on
+    # the step's stream (the batch's graph work then runs as direct launches
+    # of the same kernels in the same order)
+    sz.sz_profile_enable(ctx, True)
+    evt = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        evt[i][0].record(stream)
+        step()
+        evt[i][1].record(stream)
+    sz.sz_sync(ctx)
+    torch.cuda.synchronize()
+    prof = sz.sz_profile_read(ctx)
+    sz.sz_profile_enable(ctx, False)
+    clk = clocks.stop()
+    traced_step_ms = _stats_ms([a.elapsed_time(b) for a, b in evt])
 
     # ---- the per-array (plain) path on the same arrays, for comparison ------------
     for _ in range(2):
@@ -1070,8 +1229,21 @@ def main():
         te = _max_over_ranks((time.perf_counter() - t0) / k2, ws)
         assert np.array_equal(hy[0][: 1 << 16].numpy().view(np.uint32), ys[0][: 1 << 16].cpu().numpy().view(np.uint32))
         e2e = {"value": total_bytes / te / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-               "ms_per_step": 1e3 * te, "step_ms": [round(v, 2) for v in step_ms], "link": link_rates(hx, hy)}
+               "ms_per_step": 1e3 * te, "step_ms": [round(v, 2) for v in step_ms],
+               "stats_ms": _stats_ms([v / 1e3 for v in step_ms]),
+               "gbs_median_step": raw_bytes / (float(np.median(step_ms)) / 1e3) / 1e9,
+               "link": link_rates(hx, hy)}
         del hx, hs, hy
+
+    # ---- the workload's other bounds (1e-3, 1e-5) on the same arrays ------------
+    bounds = None
+    if not args.no_bounds:
+        bounds = bounds_bench(sz, ctx, stream, xs, ys, outs, raw_bytes, max(3, min(args.steps, 5)), peak)
+
+    # ---- the small plain snapshot (2^20 x 6) -------------------------------------
+    small = None
+    if rank == 0 and not args.no_small:
+        small = small_bench(sz, local, args.eb, args.steps, peak)
 
     # ---- batched form (rank 0): 768 uneven arrays, one graph vs 768 calls --------
     batched = None
@@ -1118,8 +1290,9 @@ def main():
             "compress_gbs": comp_gbs, "decompress_gbs": decomp_gbs,
             "compress_frac_hbm": comp_gbs / peak, "decompress_frac_hbm": decomp_gbs / peak,
             "dependency_bytes": dependency,
-            "ratio": ratio, "roofline": roofline, "kernels": kernels, "kernels_plain_path": kernels_plain,
-            "gpu_launches": launches,
+            "ratio": ratio, "stats": stats, "traced_step_ms": traced_step_ms, "tuning": tuning,
+            "roofline": roofline, "kernels": kernels, "kernels_plain_path": kernels_plain,
+            "gpu_launches": launches, "other_bounds": bounds, "small_snapshot": small,
             "plain_path": plain, "lcf": lcf, "batched": batched, "md": md, "rkeys": rkeys, "rd": rd,
             "served": served,
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "wall_s_timed": t_wall,

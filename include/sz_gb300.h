@@ -77,7 +77,9 @@ typedef enum { SZ_PRED_DEFAULT = 0, SZ_PRED_LV = 1, SZ_PRED_LCF = 2 } sz_predict
 
 /* Tuning parameters; a NULL pointer or a zero field selects the default.
  *   chunk_elems    elements per chunk: 2048, 4096, 8192 or 16384
- *                  (0 = chosen from n by the built-in tuner).
+ *                  (0 = the fixed rule from n: 2048 up to 2^16 elements,
+ *                  else 4096; sz_compress_batch measures instead, see
+ *                  sz_ctx_set_autotune).
  *   sub_elems      elements per sub-stream; must be chunk_elems / 64 (or 0).
  *   segment        MD mode: elements per sorted segment (Table 4), 1..65536
  *                  (0 = 16384).
@@ -139,12 +141,53 @@ sz_status sz_decompress(sz_ctx* ctx, const void* d_in, size_t in_bytes, float* d
 /* Compress k independent arrays (the per-rank fields of a snapshot; Sec. V
  * compresses each in-memory array independently).  Arrays may have different
  * sizes and bounds; each stream is byte-identical to sz_compress on that
- * array.  Arrays are processed together so per-array fixed costs overlap.
- * Arguments are host arrays of k entries; out_bytes[i] is set by sz_sync(). */
+ * array with the same chunk size (the autotuner below may pick another chunk
+ * size than sz_compress's fixed rule).  Arrays are processed together so
+ * per-array fixed costs overlap: one CUDA graph per batch shape, replayed on
+ * later calls.  Arguments are host arrays of k entries; out_bytes[i] is set
+ * by sz_sync(). */
 sz_status sz_compress_batch(sz_ctx* ctx, int k, const float* const* d_in, const size_t* n,
                             const double* eb, sz_eb_kind kind, const sz_params* params,
                             void* const* d_out, const size_t* out_cap, size_t* out_bytes,
                             void* stream);
+
+/* Autotuning of the batched form.  When params leave chunk_elems and
+ * sub_elems at 0 (and the predictor is LV), sz_compress_batch picks the chunk
+ * size of each size class of arrays (n <= 2^16, <= 2^20, < 2^22, < 2^26, and
+ * larger) and the item sizes of its persistent kernel by measurement: the
+ * first time a class (or a batch shape) is seen, it compresses the batch --
+ * or its first arrays, up to 2^30 elements -- with each candidate chunk size
+ * (2048, 4096, 8192, 16384) into the caller's output buffers, decodes the
+ * result into a temporary buffer, times both on the device with CUDA events
+ * and keeps the fastest round trip.  The choice is cached in the context, so
+ * later calls replay it; a tuning call synchronizes `stream` and allocates,
+ * so make it outside stream capture.  Streams stay byte-identical to
+ * sz_compress of the same array at the chosen chunk size (the header records
+ * it).  sz_ctx_set_autotune(ctx, 0) switches the tuner off: the fixed rule
+ * (2048 up to 2^16 elements, else 4096) then applies, as in sz_compress.
+ * Errors: SZ_ERR_ARG (NULL ctx). */
+sz_status sz_ctx_set_autotune(sz_ctx* ctx, int on);
+
+/* What the autotuner chose for arrays of n elements (host struct).
+ *   chunk_elems        the tuned chunk size of n's size class, 0 if not tuned yet
+ *   fixed_chunk_elems  the fixed rule's chunk size for n
+ *   class_lo, class_hi the size class, in elements (inclusive)
+ *   trial_ms[j]        device ms of the trial round trip with chunk size
+ *                      2048 << j (0 = not run or failed)
+ *   range_tile, quant_group, tile_trial_ms[j]
+ *                      the persistent kernel's item sizes (range elements,
+ *                      quantize chunks) for the last tuned batch shape and the
+ *                      compression ms of each candidate pair (0 if none)
+ * Errors: SZ_ERR_ARG (NULL pointer). */
+typedef struct {
+    uint32_t chunk_elems;
+    uint32_t fixed_chunk_elems;
+    uint64_t class_lo, class_hi;
+    float trial_ms[4];
+    uint32_t range_tile, quant_group;
+    float tile_trial_ms[4];
+} sz_tuning;
+sz_status sz_batch_tuning(sz_ctx* ctx, size_t n, sz_tuning* out);
 
 /* Decompress k streams; each result equals sz_decompress of that stream. */
 sz_status sz_decompress_batch(sz_ctx* ctx, int k, const void* const* d_in, const size_t* in_bytes,
@@ -220,6 +263,19 @@ sz_status sz_decompress_cpc(sz_ctx* ctx, const void* d_in, size_t in_bytes, floa
  * (SZ_OK if none), then clear it. */
 sz_status sz_sync(sz_ctx* ctx, void* stream);
 
+/* Exercise the timeout path of the device-side waits.  Every wait in the
+ * kernels (the encoder's look-back on the chunks before its own, the batched
+ * kernel's wait for an earlier phase) polls a bounded number of times and
+ * then latches SZ_ERR_TIMEOUT instead of hanging.  This call enqueues on
+ * `stream` one warp that runs the encoder's look-back wait against a
+ * predecessor chunk that never publishes its size, polling at most `spins`
+ * times (1 .. 2^20, a short sleep between polls).  The wait runs out, the
+ * kernel latches SZ_ERR_TIMEOUT and returns; the next sz_sync() reports and
+ * clears it, and the context stays usable.  The paper has no counterpart: the
+ * waits belong to this library's parallel encoder.  Errors now: SZ_ERR_ARG
+ * (NULL ctx, spins out of range), SZ_ERR_CUDA. */
+sz_status sz_check_wait_timeout(sz_ctx* ctx, uint32_t spins, void* stream);
+
 /* Human-readable name of a status code (static string). */
 const char* sz_status_string(sz_status s);
 
@@ -238,9 +294,11 @@ const char* sz_status_string(sz_status s);
  *     them and sets *out_bytes (host) before returning; device errors come
  *     back as its return value (SZ_ERR_CAPACITY: out_cap too small, with the
  *     required size in *out_bytes).
- *   - The first call on a device also looks up the scratch array's device
- *     address and initializes it; make that first call before any stream
- *     capture.
+ *   - Every call looks up the scratch array's device address (the first call
+ *     on a device is also where the array is set up; make that first call
+ *     before any stream capture) and re-arms the array's state with one small
+ *     kernel ahead of its own, so a device whose context was reset, which
+ *     moves and zero-fills the array, is handled like a fresh one.
  *   - All calls on a device share the one array, which keeps the previous
  *     call's contents.  Calls that overlap on the GPU (other host threads or
  *     streams) race on it and must be serialized by the caller. */

@@ -36,7 +36,8 @@ HEADER_BYTES = 160
 EXPORTS = ("sz_ctx_create", "sz_ctx_destroy", "sz_max_compressed_bytes", "sz_compress", "sz_decompress",
            "sz_compress_batch", "sz_decompress_batch", "sz_compress_host", "sz_decompress_host", "sz_compress_snapshot",
            "sz_cpc_max_bytes", "sz_decompress_cpc", "sz_sync", "sz_status_string",
-           "sz_profile_enable", "sz_profile_read", "sz_compress_noalloc",
+           "sz_profile_enable", "sz_profile_read", "sz_compress_noalloc", "sz_check_wait_timeout",
+           "sz_ctx_set_autotune", "sz_batch_tuning",
            "sz_serve_start", "sz_serve_submit", "sz_serve_poll", "sz_serve_wait", "sz_serve_release",
            "sz_serve_stats", "sz_serve_stop")
 PHASES = ("range", "quant", "codebook", "encode", "decode_setup", "decode", "reorder", "batch")
@@ -46,6 +47,12 @@ class sz_params(C.Structure):
     _fields_ = [("chunk_elems", C.c_uint32), ("sub_elems", C.c_uint32),
                 ("segment", C.c_uint32), ("ignored_digits", C.c_uint32), ("predictor", C.c_uint32),
                 ("key_fields", C.c_uint32)]
+
+
+class sz_tuning(C.Structure):
+    _fields_ = [("chunk_elems", C.c_uint32), ("fixed_chunk_elems", C.c_uint32), ("class_lo", C.c_uint64),
+                ("class_hi", C.c_uint64), ("trial_ms", C.c_float * 4), ("range_tile", C.c_uint32),
+                ("quant_group", C.c_uint32), ("tile_trial_ms", C.c_float * 4)]
 
 
 class sz_request(C.Structure):
@@ -86,6 +93,9 @@ _sig = {
     "sz_sync": (_st, [_vp, _vp]),
     "sz_status_string": (C.c_char_p, [C.c_int]),
     "sz_compress_noalloc": (_st, [_vp, _sz, C.c_double, C.c_int, _vp, _sz, C.POINTER(_sz), _vp]),
+    "sz_check_wait_timeout": (_st, [_vp, C.c_uint32, _vp]),
+    "sz_ctx_set_autotune": (_st, [_vp, C.c_int]),
+    "sz_batch_tuning": (_st, [_vp, _sz, C.POINTER(sz_tuning)]),
     "sz_profile_enable": (_st, [_vp, C.c_int]),
     "sz_profile_read": (_st, [_vp, C.POINTER(C.c_uint64), C.POINTER(C.c_double), C.c_int]),
     "sz_serve_start": (_st, [_vp, C.c_int]),
@@ -379,6 +389,26 @@ def sz_compress_noalloc(x, eb: float, kind: int = SZ_EB_REL, out=None, out_cap=N
     nb = C.c_size_t(0)
     st = _lib.sz_compress_noalloc(_ptr(x), n, eb, kind, _ptr(out), cap, C.byref(nb), _stream(stream))
     return st, out, nb.value
+
+
+def sz_ctx_set_autotune(ctx: Context, on: bool = True):
+    _check(_lib.sz_ctx_set_autotune(ctx.handle, 1 if on else 0), "sz_ctx_set_autotune")
+
+
+def sz_batch_tuning(ctx: Context, n: int) -> dict:
+    """The batched form's autotuner choice for arrays of n elements."""
+    t = sz_tuning()
+    _check(_lib.sz_batch_tuning(ctx.handle, int(n), C.byref(t)), "sz_batch_tuning")
+    return {"chunk_elems": t.chunk_elems, "fixed_chunk_elems": t.fixed_chunk_elems,
+            "class": (t.class_lo, t.class_hi), "trial_ms": {2048 << j: t.trial_ms[j] for j in range(4)},
+            "range_tile": t.range_tile, "quant_group": t.quant_group,
+            "tile_trial_ms": list(t.tile_trial_ms)}
+
+
+def sz_check_wait_timeout(ctx: Context, spins: int, stream=None):
+    """Enqueue one warp whose look-back wait runs out after `spins` polls; the
+    next sz_sync() reports SZ_ERR_TIMEOUT."""
+    _check(_lib.sz_check_wait_timeout(ctx.handle, int(spins), _stream(stream)), "sz_check_wait_timeout")
 
 
 def sz_profile_enable(ctx: Context, on: bool = True):

@@ -3,8 +3,8 @@
 // every in-memory array independently).
 //
 // The work list holds every array's items in dependency order:
-//   range tiles (64 Ki elements)  -> quantize groups (8 chunks)
-//   -> one codebook per array     -> encode chunks
+//   range tiles (plan.range_tile elements) -> quantize groups (plan.quant_group
+//   chunks) -> one codebook per array -> encode chunks
 // Blocks of 256 threads take items from one atomic counter.  Before running
 // an item a block waits (bounded) on the per-array counters its phase needs.
 // Every item a block can wait on was taken earlier by a running block, whose
@@ -21,8 +21,7 @@ namespace szg {
 
 constexpr int kBatchThreads = 256;
 // a quantize item flushes its histogram window once: its elements must fit
-// the window's 16-bit counters (batched arrays use C <= 4096)
-static_assert(kQuantGroup * 4096u <= 65535u, "quantize group too large for the 16-bit window");
+// the window's 16-bit counters, so quant_group * C <= 65535 (the host checks)
 constexpr uint32_t kWaitSpins = 1u << 24;
 
 union BatchSmem {
@@ -76,14 +75,14 @@ __device__ __forceinline__ uint32_t find_array(const uint32_t* off, uint32_t k, 
 }
 
 __device__ void batch_range_tile(const CompressArgs& a, BatchCounters* cnt, uint32_t t, uint32_t ntiles,
-                                 BatchSmem& sm) {
+                                 uint32_t tile, BatchSmem& sm) {
     const int tid = threadIdx.x;
     // share of the histogram to clear
     const uint32_t per = (kNumCodes + ntiles - 1) / ntiles;
     for (uint32_t i = t * per + tid; i < umin32((t + 1) * per, kNumCodes); i += kBatchThreads) a.hist[i] = 0u;
     uint32_t kmin = 0xffffffffu, kmax = 0u, any = 0u;
     if (a.eb_kind == 1) {
-        const uint64_t b = (uint64_t)t * kRangeTile, e = umin64(a.n, b + kRangeTile);
+        const uint64_t b = (uint64_t)t * tile, e = umin64(a.n, b + tile);
         for (uint64_t i = b + tid; i < e; i += kBatchThreads) {
             float x = __ldg(a.in + i);
             if (finite_f(x)) {
@@ -163,15 +162,16 @@ __global__ void __launch_bounds__(kBatchThreads) batch_compress_kernel(BatchPlan
         if (!ctl.ok) continue;
         // ---- the item ---------------------------------------------------------------
         if (phase == 0) {
-            batch_range_tile(a, cnt, idx, plan.range_tiles[arr], sm);
+            batch_range_tile(a, cnt, idx, plan.range_tiles[arr], plan.range_tile, sm);
         } else if (phase == 1) {
             const ArrayState* st = a.st;
             const LatticeParams P = st->P;
             if (!P.raw && a.n) {
                 hist_window_zero(sm.q.win);
                 __syncthreads();
-                const uint32_t c1 = umin32((idx + 1) * kQuantGroup, a.n_chunks);
-                for (uint32_t c = idx * kQuantGroup; c < c1; ++c) quant_chunk<true>(a, P, c, sm.q.win, sm.q.esc);
+                const uint32_t g = plan.quant_group;
+                const uint32_t c1 = umin32((idx + 1) * g, a.n_chunks);
+                for (uint32_t c = idx * g; c < c1; ++c) quant_chunk<true>(a, P, c, sm.q.win, sm.q.esc);
                 hist_window_flush(sm.q.win, a.hist);
             }
             __threadfence();      // codes, escape counts and histogram before the group is counted

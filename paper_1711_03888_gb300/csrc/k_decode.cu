@@ -89,7 +89,7 @@ __device__ __forceinline__ void decode_setup_body(const DecompressArgs& a, Setup
                              off[S_ANCHOR] - off[S_CWORD] < 8 * (nc + 1) || off[S_CESC] - off[S_ANCHOR] < 8 * na * nc ||
                              off[S_SUBLEN] - off[S_CESC] < 8 * (nc + 1) ||
                              off[S_ESC] - off[S_SUBLEN] < 2 * nc * kSubPerChunk ||
-                             off[S_PAYLOAD] - off[S_ESC] < (uint64_t)kEscBytes * E)
+                             E > n || E > (off[S_PAYLOAD] - off[S_ESC]) / kEscBytes)
                         status = E_CORRUPT;
                     sm.m = (uint32_t)m;
                 }

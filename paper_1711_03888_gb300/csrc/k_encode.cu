@@ -65,6 +65,21 @@ static void launch_encode_t(const CompressArgs& a, cudaStream_t s) {
     else encode_kernel<C, false><<<grid, NT, smem, s>>>(a);
 }
 
+// The timeout path of the look-back wait: one warp waits, as the encoder of
+// chunk 1 would, on chunk 0's status word, which nothing publishes.  After
+// `spins` polls the wait gives up and the kernel latches E_TIMEOUT.
+__global__ void __launch_bounds__(32) wait_timeout_kernel(unsigned long long* status, uint32_t* err, uint32_t spins) {
+    if (threadIdx.x == 0) st_status(&status[0], 0ull);
+    __syncwarp();
+    unsigned long long excl = 0;
+    const bool ok = lookback_prefix(status, 1, spins, &excl);
+    if (threadIdx.x == 0 && !ok) raise_err(err, E_TIMEOUT);
+}
+
+void launch_wait_timeout(unsigned long long* status, uint32_t* err, uint32_t spins, void* stream) {
+    wait_timeout_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(status, err, spins);
+}
+
 void launch_encode(const CompressArgs* a, int k, void* stream) {
     cudaStream_t s = (cudaStream_t)stream;
     for (int i = 0; i < k; ++i) {

@@ -75,8 +75,11 @@ __global__ void __launch_bounds__(EncShape<C>::kThreads, EncShape<C>::kMinBlocks
     encode_array_pipelined<C, NT>(sa, reinterpret_cast<uint32_t*>(dyn_smem), esm, s_c, &s_prev);
 }
 
-constexpr int kEncSmem2048 = (int)enc_smem_bytes(2048);
-constexpr int kEncSmem4096 = (int)enc_smem_bytes(4096);
+constexpr uint32_t kMultiC[4] = {2048u, 4096u, 8192u, 16384u};
+const void* const kEncMulti[4] = {(const void*)encode_multi_kernel<2048>, (const void*)encode_multi_kernel<4096>,
+                                  (const void*)encode_multi_kernel<8192>, (const void*)encode_multi_kernel<16384>};
+constexpr int kEncThreads[4] = {EncShape<2048>::kThreads, EncShape<4096>::kThreads, EncShape<8192>::kThreads,
+                                EncShape<16384>::kThreads};
 
 int sm_count() {
     static int sms = 0;
@@ -102,22 +105,23 @@ int multi_compress_launches(const CompressArgs* d_args, const MultiGroup* groups
         if (groups[i].max_chunks > max_nc) max_nc = groups[i].max_chunks;
         if (groups[i].C > maxC) maxC = groups[i].C;
     }
-    static int per_sm = 0, enc_res[2] = {0, 0};
+    static int quant_res[4] = {0, 0, 0, 0}, enc_res[4] = {0, 0, 0, 0};
     static bool configured = false;
     if (!configured) {
         cudaFuncSetAttribute(codebook_multi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCbFastBytes);
         cudaFuncSetAttribute(quant_multi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)quant_stage_bytes(4096));
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, quant_multi_kernel, kQuantThreads,
-                                                      quant_stage_bytes(4096));
-        if (per_sm <= 0) per_sm = 1;
-        cudaFuncSetAttribute(encode_multi_kernel<2048>, cudaFuncAttributeMaxDynamicSharedMemorySize, kEncSmem2048);
-        cudaFuncSetAttribute(encode_multi_kernel<4096>, cudaFuncAttributeMaxDynamicSharedMemorySize, kEncSmem4096);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&enc_res[0], encode_multi_kernel<2048>,
-                                                      EncShape<2048>::kThreads, kEncSmem2048);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&enc_res[1], encode_multi_kernel<4096>,
-                                                      EncShape<4096>::kThreads, kEncSmem4096);
-        for (int j = 0; j < 2; ++j) enc_res[j] = (enc_res[j] > 0 ? enc_res[j] : 1) * sm_count();
+                             (int)quant_stage_bytes(16384));
+        for (int j = 0; j < 4; ++j) {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&quant_res[j], quant_multi_kernel, kQuantThreads,
+                                                          quant_stage_bytes(kMultiC[j]));
+            quant_res[j] = (quant_res[j] > 0 ? quant_res[j] : 1) * sm_count();
+        }
+        for (int j = 0; j < 4; ++j) {
+            const int sm = (int)enc_smem_bytes((int)kMultiC[j]);
+            cudaFuncSetAttribute(kEncMulti[j], cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&enc_res[j], kEncMulti[j], kEncThreads[j], sm);
+            enc_res[j] = (enc_res[j] > 0 ? enc_res[j] : 1) * sm_count();
+        }
         configured = true;
     }
     auto set = [](KernelLaunch& L, const void* f, uint32_t gx, uint32_t gy, uint32_t bx, size_t smem, int phase,
@@ -131,23 +135,21 @@ int multi_compress_launches(const CompressArgs* d_args, const MultiGroup* groups
     };
     int k = 0;
     set(out[k++], (const void*)range_multi_kernel, kRangeBlocks, count, 256, 0, SZ_PHASE_RANGE, d_args, first);
-    set(out[k++], (const void*)quant_multi_kernel, umin32(max_nc, (uint32_t)(sm_count() * per_sm)), count,
+    const int jq = maxC == 2048 ? 0 : maxC == 4096 ? 1 : maxC == 8192 ? 2 : 3;
+    set(out[k++], (const void*)quant_multi_kernel, umin32(max_nc, (uint32_t)quant_res[jq]), count,
         kQuantThreads, quant_stage_bytes(maxC), SZ_PHASE_QUANT, d_args, first);
     set(out[k++], (const void*)codebook_multi_kernel, 1, count, kCbBlock, kCbFastBytes, SZ_PHASE_CODEBOOK, d_args,
         first);
     for (int i = 0; i < ngroups; ++i) {
         // persistent encoders: the resident blocks shared out over the group's arrays
-        const int j = groups[i].C == 2048 ? 0 : 1;
+        int j = -1;
+        for (int t = 0; t < 4; ++t)
+            if (groups[i].C == kMultiC[t]) j = t;
+        if (j < 0) return -1;
         const int share = enc_res[j] / (int)groups[i].count;
         const uint32_t per = umin32(groups[i].max_chunks ? groups[i].max_chunks : 1u, (uint32_t)(share > 0 ? share : 1));
-        if (groups[i].C == 2048)
-            set(out[k++], (const void*)encode_multi_kernel<2048>, per, groups[i].count, EncShape<2048>::kThreads,
-                kEncSmem2048, SZ_PHASE_ENCODE, d_args, groups[i].first);
-        else if (groups[i].C == 4096)
-            set(out[k++], (const void*)encode_multi_kernel<4096>, per, groups[i].count, EncShape<4096>::kThreads,
-                kEncSmem4096, SZ_PHASE_ENCODE, d_args, groups[i].first);
-        else
-            return -1;
+        set(out[k++], kEncMulti[j], per, groups[i].count, kEncThreads[j], enc_smem_bytes((int)kMultiC[j]),
+            SZ_PHASE_ENCODE, d_args, groups[i].first);
     }
     return k;
 }

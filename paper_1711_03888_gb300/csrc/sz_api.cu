@@ -19,9 +19,11 @@ namespace szg {
 
 static const uint32_t kChunkChoices[] = {2048u, 4096u, 8192u, 16384u};
 
-// Built-in tuner: a pure function of n (never of load), so streams are
-// reproducible.  4096-element chunks (64-element sub-streams) let eight
-// decoder teams share an SM; small arrays use 2048 to keep every SM busy.
+// The fixed chunk-size rule (not measured at run time): a pure function of n,
+// so streams are reproducible.  4096-element chunks (64-element sub-streams)
+// let eight decoder teams share an SM; small arrays use 2048 to keep every SM
+// busy.  The plain and served calls use it; the batched form's autotuner
+// replaces it there (sz_batch.cu).
 uint32_t tune_chunk(uint64_t n) {
     if (n <= (1ull << 16)) return 2048u;
     return 4096u;
@@ -299,6 +301,42 @@ sz_status sz_sync(sz_ctx* ctx, void* stream) {
     if (err & E_UNSUPPORTED) return SZ_ERR_UNSUPPORTED;
     if (err & E_CAPACITY) return SZ_ERR_CAPACITY;
     if (err) return SZ_ERR_CUDA;
+    return SZ_OK;
+}
+
+sz_status sz_ctx_set_autotune(sz_ctx* ctx, int on) {
+    if (!ctx) return SZ_ERR_ARG;
+    ctx->autotune = on != 0;
+    return SZ_OK;
+}
+
+sz_status sz_batch_tuning(sz_ctx* ctx, size_t n, sz_tuning* out) {
+    if (!ctx || !out) return SZ_ERR_ARG;
+    memset(out, 0, sizeof(*out));
+    static const uint64_t lo[kTuneClasses] = {0, (1ull << 16) + 1, (1ull << 20) + 1, 1ull << 22, 1ull << 26};
+    static const uint64_t hi[kTuneClasses] = {1ull << 16, 1ull << 20, (1ull << 22) - 1, (1ull << 26) - 1,
+                                              (1ull << 32) - 1};
+    const int c = tune_class(n);
+    out->chunk_elems = ctx->tune_C[c];
+    out->fixed_chunk_elems = tune_chunk(n);
+    out->class_lo = lo[c];
+    out->class_hi = hi[c];
+    for (int j = 0; j < kTuneCands; ++j) {
+        out->trial_ms[j] = ctx->tune_ms[c][j];
+        out->tile_trial_ms[j] = ctx->tile_ms[j];
+    }
+    out->range_tile = ctx->tile_range;
+    out->quant_group = ctx->tile_group;
+    return SZ_OK;
+}
+
+sz_status sz_check_wait_timeout(sz_ctx* ctx, uint32_t spins, void* stream) {
+    if (!ctx || spins < 1 || spins > (1u << 20)) return SZ_ERR_ARG;
+    cudaSetDevice(ctx->device);
+    // the status word sits in the error word's block, past the error word
+    unsigned long long* status = reinterpret_cast<unsigned long long*>(ctx->d_err + 32);
+    launch_wait_timeout(status, ctx->d_err, spins, stream);
+    if (cudaPeekAtLastError() != cudaSuccess) { cudaGetLastError(); return SZ_ERR_CUDA; }
     return SZ_OK;
 }
 

@@ -8,8 +8,13 @@
 // The context keeps a batch pool with each array's own state, histogram,
 // codeword table, codebook scratch and per-chunk tables, sliced by that
 // array's size.  Each stream is byte-identical to sz_compress on the same
-// array.  Arrays whose chunk size is above 4096 (set explicitly through
-// params) go through the per-array path instead.
+// array with the same chunk size.  Arrays with chunks above 4096 elements go
+// to the per-phase launches whatever their size; LCF prediction takes the
+// per-array path.
+// Autotuning (chunk_elems 0, the context's autotuner on): the chunk size of
+// each size class of arrays and the persistent kernel's item sizes are picked
+// by timing the candidates on the batch itself, the first time a size class
+// (or a batch shape) is seen, and cached in the context.
 // Decompression (k > 1): one setup launch (a block per stream), a scan of the
 // streams' decode units, and one decode launch whose blocks take contiguous
 // ranges of all streams' chunks (k_decode.cu).
@@ -40,9 +45,12 @@ sz_status pool_reserve(sz_ctx* ctx, size_t bytes) {
 
 }  // namespace
 
-sz_status batch_compress(sz_ctx* ctx, int k, const float* const* d_in, const size_t* n, const double* eb,
-                         sz_eb_kind kind, const sz_params* params, void* const* d_out, const size_t* out_cap,
-                         size_t* out_bytes, cudaStream_t s) {
+// One batched compression with the chunk size of every array given (Cs, or
+// the fixed rule when null) and the persistent kernel's item sizes.
+static sz_status batch_compress_run(sz_ctx* ctx, int k, const float* const* d_in, const size_t* n,
+                                    const double* eb, sz_eb_kind kind, const sz_params* params,
+                                    const uint32_t* Cs_in, uint32_t range_tile, uint32_t quant_group,
+                                    void* const* d_out, const size_t* out_cap, size_t* out_bytes, cudaStream_t s) {
     cudaSetDevice(ctx->device);
     std::vector<uint32_t> Cs(k), Gs(k);
     std::vector<int> batched;
@@ -51,11 +59,15 @@ sz_status batch_compress(sz_ctx* ctx, int k, const float* const* d_in, const siz
         sz_status st = validate_compress(d_in[i], n[i], eb[i], kind, d_out[i]);
         if (st != SZ_OK) return st;
         if ((st = resolve_params(params, n[i], &Cs[i], &Gs[i])) != SZ_OK) return st;
-        if (Cs[i] <= 4096 && !lcf) batched.push_back(i);
+        if (Cs_in) {
+            Cs[i] = Cs_in[i];
+            Gs[i] = Cs_in[i] / kSubPerChunk;
+        }
+        if (!lcf) batched.push_back(i);
     }
-    // arrays with large explicit chunks or LCF prediction: the per-array path
+    // arrays with LCF prediction: the per-array path
     for (int i = 0; i < k; ++i) {
-        if (Cs[i] <= 4096 && !lcf) continue;
+        if (!lcf) continue;
         sz_status st = sz_compress(ctx, d_in[i], n[i], eb[i], kind, params, d_out[i], out_cap[i],
                                    out_bytes ? &out_bytes[i] : nullptr, s);
         if (st != SZ_OK) return st;
@@ -70,7 +82,7 @@ sz_status batch_compress(sz_ctx* ctx, int k, const float* const* d_in, const siz
     uint32_t ks = 0;
     {
         std::vector<int> small, large;
-        for (int i : batched) (n[i] < kBatchLargeElems ? small : large).push_back(i);
+        for (int i : batched) (n[i] < kBatchLargeElems && Cs[i] <= 4096 ? small : large).push_back(i);
         if (small.size() <= kBatchFewSmall) {
             large.insert(large.begin(), small.begin(), small.end());
             small.clear();
@@ -125,21 +137,30 @@ sz_status batch_compress(sz_ctx* ctx, int k, const float* const* d_in, const siz
             const uint64_t nc = (n[i] + Cs[i] - 1) / Cs[i];
             off[ph * (ks + 1) + j] = item;
             uint32_t cnt;
-            if (ph == 0) cnt = tiles[j] = (uint32_t)((n[i] + kRangeTile - 1) / kRangeTile) + (n[i] == 0 ? 1u : 0u);
-            else if (ph == 1) cnt = qgroups[j] = (uint32_t)((nc + kQuantGroup - 1) / kQuantGroup);
+            if (ph == 0) cnt = tiles[j] = (uint32_t)((n[i] + range_tile - 1) / range_tile) + (n[i] == 0 ? 1u : 0u);
+            else if (ph == 1) cnt = qgroups[j] = (uint32_t)((nc + quant_group - 1) / quant_group);
             else if (ph == 2) cnt = 1;
             else cnt = (uint32_t)nc;
             item += cnt;
         }
         off[ph * (ks + 1) + ks] = item;
     }
-    uint64_t key = 1469598103934665603ull;      // FNV-1a over everything the graph bakes in
+    // The graph's identity: everything it bakes in (pool address and layout,
+    // every array's arguments).  A cached graph is replayed only when these
+    // bytes equal the ones it was built from; the FNV-1a hash is the quick
+    // test in front of the full comparison.
+    uint64_t key = 1469598103934665603ull;
+    std::vector<uint8_t> ident;
+    ident.reserve(sizeof(base) + sizeof(bytes) + sizeof(CompressArgs) * kb);
     auto mix = [&](const void* p, size_t b) {
         const uint8_t* c = (const uint8_t*)p;
         for (size_t t = 0; t < b; ++t) key = (key ^ c[t]) * 1099511628211ull;
+        ident.insert(ident.end(), c, c + b);
     };
     mix(&base, sizeof(base));
     mix(&bytes, sizeof(bytes));
+    mix(&range_tile, sizeof(range_tile));
+    mix(&quant_group, sizeof(quant_group));
     for (uint32_t j = 0; j < kb; ++j) {
         const int i = batched[j];
         CompressArgs& a = args[j];
@@ -164,7 +185,7 @@ sz_status batch_compress(sz_ctx* ctx, int k, const float* const* d_in, const siz
         mix(&a, sizeof(a));
     }
 
-    if (key != ctx->bg_key || !ctx->bg_exec) {
+    if (key != ctx->bg_key || !ctx->bg_exec || ident != ctx->bg_ident) {
         // a new batch: wait for the previous graph before reusing its staging
         if (ctx->bg_done && cudaEventSynchronize(ctx->bg_done) != cudaSuccess) { cudaGetLastError(); return SZ_ERR_CUDA; }
         if (!ctx->bg_done && cudaEventCreateWithFlags(&ctx->bg_done, cudaEventDisableTiming) != cudaSuccess) {
@@ -205,6 +226,8 @@ sz_status batch_compress(sz_ctx* ctx, int k, const float* const* d_in, const siz
         plan.quant_groups = (const uint32_t*)(base + o_groups);
         plan.item_off = (const uint32_t*)(base + o_off);
         plan.k = ks;
+        plan.range_tile = range_tile;
+        plan.quant_group = quant_group;
         plan.next = (uint32_t*)(base + o_cnt + sizeof(BatchCounters) * ks);
         plan.err = ctx->d_err;
         // graph: plan copy and counter reset, then the persistent kernel (small
@@ -214,6 +237,7 @@ sz_status batch_compress(sz_ctx* ctx, int k, const float* const* d_in, const siz
         ctx->bg_exec = nullptr;
         ctx->bg_graph = nullptr;
         ctx->bg_key = 0;
+        ctx->bg_ident.clear();
         cudaGraph_t g = nullptr;
         cudaGraphNode_t n_copy, n_reset, n_kern;
         void* func;
@@ -270,6 +294,7 @@ sz_status batch_compress(sz_ctx* ctx, int k, const float* const* d_in, const siz
         }
         ctx->bg_graph = g;
         ctx->bg_key = key;
+        ctx->bg_ident.swap(ident);
     }
     if (!ctx->prof_on) {
         if (cudaGraphLaunch(ctx->bg_exec, s) != cudaSuccess) { cudaGetLastError(); return SZ_ERR_CUDA; }
@@ -290,6 +315,8 @@ sz_status batch_compress(sz_ctx* ctx, int k, const float* const* d_in, const siz
             plan.quant_groups = (const uint32_t*)(base + o_groups);
             plan.item_off = (const uint32_t*)(base + o_off);
             plan.k = ks;
+            plan.range_tile = range_tile;
+            plan.quant_group = quant_group;
             plan.next = (uint32_t*)(base + o_cnt + sizeof(BatchCounters) * ks);
             plan.err = ctx->d_err;
             ProfScope pr(ctx, SZ_PHASE_BATCH, s);
@@ -403,6 +430,226 @@ sz_status batch_decompress(sz_ctx* ctx, int k, const void* const* d_in, const si
             if (st != SZ_OK) return st;
         }
     return SZ_OK;
+}
+
+// ---- autotuner of the batched compression ----------------------------------
+namespace {
+
+constexpr uint32_t kTuneC[kTuneCands] = {2048u, 4096u, 8192u, 16384u};
+// Persistent-kernel item sizes tried (range tile elements, quantize group
+// chunks); the first is the default.  quant_group * 4096 stays below 2^16.
+constexpr uint32_t kTuneTile[kTuneCands][2] = {{1u << 16, 8u}, {1u << 15, 4u}, {1u << 17, 8u}, {1u << 16, 4u}};
+constexpr uint64_t kTuneMaxElems = 1ull << 30;   // largest trial batch
+constexpr uint64_t kTuneMaxArray = 1ull << 28;   // larger arrays are not run as trials
+
+uint32_t fixed_chunk(uint64_t n) { return tune_chunk(n); }
+
+// arrays of a batch that the persistent kernel takes (the rest go to the per-phase launches)
+uint64_t small_shape_key(int k, const size_t* n, const uint32_t* Cs, uint32_t* count) {
+    uint64_t key = 0;
+    uint32_t c = 0;
+    for (int i = 0; i < k; ++i)
+        if (n[i] < kBatchLargeElems && Cs[i] <= 4096) {
+            ++c;
+            key += n[i];
+        }
+    *count = c;
+    return c <= kBatchFewSmall ? 0 : (((uint64_t)c << 40) ^ key);
+}
+
+}  // namespace
+
+int tune_class(uint64_t n) {
+    if (n <= (1ull << 16)) return 0;
+    if (n <= (1ull << 20)) return 1;
+    if (n < (1ull << 22)) return 2;
+    if (n < (1ull << 26)) return 3;
+    return 4;
+}
+
+// Times candidate choices on (a prefix of) the batch.  Each trial compresses
+// the trial arrays into the caller's output buffers and decodes them into a
+// temporary buffer, twice (the first run builds the graph), and takes the
+// device time of the second run from CUDA events on the call's stream.  The
+// stream is synchronized first; the context's error word is saved and
+// restored, and a trial that latches an error is discarded.
+static sz_status tune_batch(sz_ctx* ctx, int k, const float* const* d_in, const size_t* n, const double* eb,
+                            sz_eb_kind kind, const sz_params* params, void* const* d_out, const size_t* out_cap,
+                            cudaStream_t s) {
+    // the trial batch: the arrays of at most kTuneMaxArray elements, in order,
+    // up to kTuneMaxElems in all (a class without such an array keeps the fixed rule)
+    std::vector<const float*> tin;
+    std::vector<size_t> tn, tcap;
+    std::vector<double> teb;
+    std::vector<void*> tout;
+    uint64_t tot = 0;
+    for (int i = 0; i < k; ++i) {
+        if (n[i] > kTuneMaxArray || tot + n[i] > kTuneMaxElems) continue;
+        tot += n[i];
+        tin.push_back(d_in[i]);
+        tn.push_back(n[i]);
+        teb.push_back(eb[i]);
+        tout.push_back(d_out[i]);
+        tcap.push_back(out_cap[i]);
+    }
+    const int kt = (int)tin.size();
+    bool need[kTuneClasses] = {};
+    bool any = false;
+    for (int i = 0; i < kt; ++i) {
+        const int c = tune_class(tn[i]);
+        if (!ctx->tune_C[c]) need[c] = any = true;
+    }
+    // trial chunk sizes: tuned classes keep their choice, the others the fixed rule
+    std::vector<uint32_t> Ct(kt);
+    for (int i = 0; i < kt; ++i) {
+        const uint32_t c = ctx->tune_C[tune_class(tn[i])];
+        Ct[i] = c ? c : fixed_chunk(tn[i]);
+    }
+    uint32_t nsmall = 0;
+    const uint64_t skey = small_shape_key(kt, tn.data(), Ct.data(), &nsmall);
+    const bool need_tiles = skey && ctx->tile_key != skey;
+    if (!any && !need_tiles) return SZ_OK;
+
+    if (cudaStreamSynchronize(s) != cudaSuccess) { cudaGetLastError(); return SZ_ERR_CUDA; }
+    uint32_t saved_err = 0;
+    if (cudaMemcpy(&saved_err, ctx->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemset(ctx->d_err, 0, sizeof(uint32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        return SZ_ERR_CUDA;
+    }
+    const bool prof = ctx->prof_on;
+    ctx->prof_on = false;
+    // decode targets of the trial arrays (16-byte aligned slices of one block)
+    std::vector<float*> dec(kt, nullptr);
+    std::vector<size_t> ncap(kt);
+    size_t dec_bytes = 0;
+    for (int i = 0; i < kt; ++i) dec_bytes += (4 * (tn[i] ? tn[i] : 1) + 255) & ~(size_t)255;
+    uint8_t* dec_mem = nullptr;
+    if (cudaMalloc(&dec_mem, dec_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        dec_mem = nullptr;           // trials then time compression only
+    } else {
+        size_t o = 0;
+        for (int i = 0; i < kt; ++i) {
+            dec[i] = reinterpret_cast<float*>(dec_mem + o);
+            ncap[i] = tn[i];
+            o += (4 * (tn[i] ? tn[i] : 1) + 255) & ~(size_t)255;
+        }
+    }
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    for (auto& e : ev) cudaEventCreate(&e);
+    sz_status status = SZ_OK;
+    auto trial = [&](const uint32_t* C, uint32_t tl, uint32_t gr, bool decode, float* ms) -> bool {
+        float best = 0.f;
+        for (int rep = 0; rep < 2; ++rep) {
+            cudaEventRecord(ev[0], s);
+            sz_status st = batch_compress_run(ctx, kt, tin.data(), tn.data(), teb.data(), kind, params, C, tl, gr, tout.data(), tcap.data(), nullptr, s);
+            cudaEventRecord(ev[1], s);
+            if (st == SZ_OK && decode && dec_mem)
+                st = batch_decompress(ctx, kt, reinterpret_cast<const void* const*>(tout.data()), tcap.data(), dec.data(),
+                                      ncap.data(), nullptr, s);
+            cudaEventRecord(ev[2], s);
+            if (cudaEventSynchronize(ev[2]) != cudaSuccess) { cudaGetLastError(); status = SZ_ERR_CUDA; return false; }
+            if (st != SZ_OK) { status = st; return false; }
+            float tc = 0.f, td = 0.f;
+            cudaEventElapsedTime(&tc, ev[0], ev[1]);
+            cudaEventElapsedTime(&td, ev[1], ev[2]);
+            if (rep) best = tc + td;
+        }
+        uint32_t err = 0;
+        cudaMemcpy(&err, ctx->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost);
+        if (err) {
+            cudaMemset(ctx->d_err, 0, sizeof(uint32_t));
+            return false;
+        }
+        *ms = best;
+        return true;
+    };
+    const uint32_t tl0 = kTuneTile[0][0], gr0 = kTuneTile[0][1];
+    for (int c = 0; c < kTuneClasses && status == SZ_OK; ++c) {
+        if (!need[c]) continue;
+        float best = 0.f;
+        uint32_t pick = 0;
+        for (int j = 0; j < kTuneCands; ++j) {
+            std::vector<uint32_t> Cc(Ct);
+            for (int i = 0; i < kt; ++i)
+                if (tune_class(tn[i]) == c) Cc[i] = kTuneC[j];
+            float ms = 0.f;
+            ctx->tune_ms[c][j] = 0.f;
+            if (!trial(Cc.data(), tl0, gr0, true, &ms)) {
+                if (status != SZ_OK) break;
+                continue;
+            }
+            ctx->tune_ms[c][j] = ms;
+            if (!pick || ms < best) { best = ms; pick = kTuneC[j]; }
+        }
+        if (status != SZ_OK) break;
+        ctx->tune_C[c] = pick ? pick : 4096u;
+        for (int i = 0; i < kt; ++i)
+            if (tune_class(tn[i]) == c) Ct[i] = ctx->tune_C[c];
+    }
+    if (status == SZ_OK) {
+        const uint64_t key2 = small_shape_key(kt, tn.data(), Ct.data(), &nsmall);
+        if (key2 && ctx->tile_key != key2) {
+            float best = 0.f;
+            int pick = 0;
+            for (int j = 0; j < kTuneCands; ++j) {
+                float ms = 0.f;
+                ctx->tile_ms[j] = 0.f;
+                if (!trial(Ct.data(), kTuneTile[j][0], kTuneTile[j][1], false, &ms)) {
+                    if (status != SZ_OK) break;
+                    continue;
+                }
+                ctx->tile_ms[j] = ms;
+                if (j == 0 || ms < best) { best = ms; pick = j; }
+            }
+            if (status == SZ_OK) {
+                ctx->tile_key = key2;
+                ctx->tile_range = kTuneTile[pick][0];
+                ctx->tile_group = kTuneTile[pick][1];
+            }
+        }
+    }
+    for (auto& e : ev) if (e) cudaEventDestroy(e);
+    if (dec_mem) cudaFree(dec_mem);
+    ctx->prof_on = prof;
+    if (cudaMemcpy(ctx->d_err, &saved_err, sizeof(uint32_t), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGetLastError();
+        if (status == SZ_OK) status = SZ_ERR_CUDA;
+    }
+    return status;
+}
+
+sz_status batch_compress(sz_ctx* ctx, int k, const float* const* d_in, const size_t* n, const double* eb,
+                         sz_eb_kind kind, const sz_params* params, void* const* d_out, const size_t* out_cap,
+                         size_t* out_bytes, cudaStream_t s) {
+    cudaSetDevice(ctx->device);
+    const bool tuned = ctx->autotune && !(params && (params->chunk_elems || params->sub_elems)) &&
+                       params_pred(params) != kPredLCF;
+    if (!tuned)
+        return batch_compress_run(ctx, k, d_in, n, eb, kind, params, nullptr, kRangeTile, kQuantGroup, d_out, out_cap,
+                                  out_bytes, s);
+    for (int i = 0; i < k; ++i) {
+        sz_status st = validate_compress(d_in[i], n[i], eb[i], kind, d_out[i]);
+        if (st != SZ_OK) return st;
+        uint32_t C, G;
+        if ((st = resolve_params(params, n[i], &C, &G)) != SZ_OK) return st;
+    }
+    std::vector<uint32_t> Cs(k);
+    uint32_t tile = kRangeTile, group = kQuantGroup;
+    sz_status st = tune_batch(ctx, k, d_in, n, eb, kind, params, d_out, out_cap, s);
+    if (st != SZ_OK) return st;
+    for (int i = 0; i < k; ++i) {
+        const uint32_t c = ctx->tune_C[tune_class(n[i])];
+        Cs[i] = c ? c : tune_chunk(n[i]);
+    }
+    uint32_t nsmall = 0;
+    const uint64_t skey = small_shape_key(k, n, Cs.data(), &nsmall);
+    if (skey && skey == ctx->tile_key) {
+        tile = ctx->tile_range;
+        group = ctx->tile_group;
+    }
+    return batch_compress_run(ctx, k, d_in, n, eb, kind, params, Cs.data(), tile, group, d_out, out_cap, out_bytes, s);
 }
 
 }  // namespace szg

@@ -44,6 +44,7 @@ struct sz_ctx {
     int batch_states_armed = 0;
     // cached CUDA graph of the last batch (plan copy + counter reset + persistent kernel)
     uint64_t bg_key = 0;
+    std::vector<uint8_t> bg_ident;      // the bytes the cached graph was built from
     cudaGraph_t bg_graph = nullptr;
     cudaGraphExec_t bg_exec = nullptr;
     cudaEvent_t bg_done = nullptr;
@@ -66,6 +67,15 @@ struct sz_ctx {
     // SZ-CPC2000: sort buffers and per-block tables
     uint8_t* cpc = nullptr;
     size_t cpc_bytes = 0;
+    // batched-form autotuner: chosen chunk size per size class of arrays (0 =
+    // not tuned yet) with the trial times of the candidates, and the
+    // persistent kernel's item sizes for the last tuned batch shape
+    int autotune = 1;
+    uint32_t tune_C[szg::kTuneClasses] = {};
+    float tune_ms[szg::kTuneClasses][szg::kTuneCands] = {};
+    uint64_t tile_key = 0;
+    uint32_t tile_range = 0, tile_group = 0;
+    float tile_ms[szg::kTuneCands] = {};
     // serving loop
     sz_serve_state* serve = nullptr;
     // tracing: event pairs around launches
@@ -91,6 +101,7 @@ struct ProfScope {
     ~ProfScope();
 };
 uint32_t tune_chunk(uint64_t n);
+int tune_class(uint64_t n);   // size class of the batched form's autotuner (0 .. kTuneClasses-1)
 sz_status resolve_params(const sz_params* p, uint64_t n, uint32_t* C, uint32_t* G);
 uint32_t params_pred(const sz_params* p);     // kPredLV or kPredLCF
 size_t cpc_max_bytes(uint64_t n);

@@ -148,6 +148,48 @@ __device__ __forceinline__ unsigned long long ld_status(const unsigned long long
     return v;
 }
 
+// Decoupled look-back over the chunks before chunk c, by one full warp.
+// status[j] holds a 2-bit flag and a 62-bit value: AGG (chunk j's own word
+// count), INC (the words of chunks 0 .. j) or ERR (chunk j gave up).  Lane l
+// reads chunk j - l, 32 predecessors per step, and the warp sums back to the
+// nearest INC.  A word still unpublished is polled at most spin_limit times
+// (with a short sleep between polls); after that, or on an ERR, the warp
+// returns false.  On success every lane gets the exclusive prefix in *excl.
+constexpr unsigned long long kLbAgg = 1ull << 62, kLbInc = 2ull << 62, kLbErr = 3ull << 62;
+constexpr unsigned long long kLbValue = (1ull << 62) - 1;
+
+__device__ __forceinline__ bool lookback_prefix(const unsigned long long* status, uint64_t c, uint32_t spin_limit,
+                                                unsigned long long* excl) {
+    const int lane = threadIdx.x & 31;
+    unsigned long long sum = 0;
+    long long j = (long long)c - 1;
+    while (j >= 0) {
+        const long long pos = j - lane;
+        unsigned long long s = kLbInc;                 // before chunk 0: an empty prefix
+        if (pos >= 0) {
+            uint32_t spins = 0;
+            s = ld_status(&status[pos]);
+            while ((s & ~kLbValue) == 0ull && spins < spin_limit) {
+                __nanosleep(64);
+                s = ld_status(&status[pos]);
+                ++spins;
+            }
+        }
+        const unsigned long long f = s & ~kLbValue;
+        if (__any_sync(0xffffffffu, f == 0ull || f == kLbErr)) return false;
+        const uint32_t inc = __ballot_sync(0xffffffffu, f == kLbInc);
+        const int lim = inc ? (__ffs(inc) - 1) : 31;  // lanes 0 .. lim contribute
+        unsigned long long v = (lane <= lim) ? (s & kLbValue) : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        sum += v;
+        if (inc) break;
+        j -= 32;
+    }
+    *excl = sum;
+    return true;
+}
+
 // ---------------------------------------------------------------------------
 // Scans
 // ---------------------------------------------------------------------------

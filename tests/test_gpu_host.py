@@ -22,6 +22,9 @@ def sz():
 @pytest.fixture(scope="module")
 def ctx(sz):
     c = sz.Context(0)
+    # the host calls use the fixed chunk-size rule; the batched device calls
+    # they are compared with use it too when the autotuner is off
+    sz.sz_ctx_set_autotune(c, False)
     yield c
     c.close()
 

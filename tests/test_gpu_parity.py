@@ -224,6 +224,11 @@ def test_corrupt_streams_are_rejected(sz, ctx, oracle):
     assert run(bad) == sz.SZ_ERR_CORRUPT                       # chunk offset out of range
     bad = bytearray(ref); bad[h["off_sublen"]: h["off_sublen"] + 2] = (60000).to_bytes(2, "little")
     assert run(bad) == sz.SZ_ERR_CORRUPT                       # sub-stream length inconsistent
+    for E in ((1 << 60) + 5, (1 << 64) - 1, (1 << 15) + 1):
+        # an escape count whose record size would wrap, or beyond the element count:
+        # rejected by the header check before any chunk is decoded
+        bad = bytearray(ref); bad[64:72] = E.to_bytes(8, "little")
+        assert run(bad) == sz.SZ_ERR_CORRUPT
     rng = np.random.default_rng(1)
     for trial in range(8):                                      # random payload damage: no fault, no hang
         bad = bytearray(ref)

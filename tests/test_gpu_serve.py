@@ -1,7 +1,8 @@
 """GPU tests of the serving loop (continuous batching of compress and
-decompress requests): every result is byte-identical to the plain call on the
-same input, alone and in the mix, whatever the admission order, budget and
-output ownership; a failing request fails alone."""
+decompress requests): every result is byte-identical to the CPU oracle's on
+the same input (compressed streams byte for byte, reconstructions bit for
+bit), alone and in the mix, whatever the admission order, budget and output
+ownership; the plain call agrees too; a failing request fails alone."""
 import time
 
 import numpy as np
@@ -46,9 +47,19 @@ def _pool(n_total, seed):
     return [snap["xx"], snap["vz"]]
 
 
+def _chunk(n):
+    # the served and plain calls' chunk size: 2048 elements up to 2^16, else 4096
+    return 2048 if n <= (1 << 16) else 4096
+
+
 def _mix(sz, plain_ctx, seed, sizes):
     """Requests over slices of a device pool: (op, input tensor, n, eb, kind,
-    expected bytes)."""
+    expected bytes).  The expected bytes are the oracle's: its stream for a
+    compress request, its reconstruction for a decompress request, whose input
+    stream the oracle made too.  The plain call is checked against the same
+    bytes."""
+    import oracle
+    oracle.build()
     rng = np.random.default_rng(seed)
     pool = _pool(1 << 22, seed)
     reqs = []
@@ -60,12 +71,16 @@ def _mix(sz, plain_ctx, seed, sizes):
         kind = sz.SZ_EB_REL if i % 3 else sz.SZ_EB_ABS
         if kind == sz.SZ_EB_ABS:
             eb = eb * 100.0
-        if i % 4 == 3:                        # decompress request of a stream made alone
-            s = _plain_compress(sz, plain_ctx, x, eb, kind)
-            st = torch.frombuffer(bytearray(s), dtype=torch.uint8).cuda()
-            reqs.append(("d", st, n, eb, kind, _plain_decompress(sz, plain_ctx, st, n)))
+        C = _chunk(n)
+        ref = oracle.compress(x.cpu().numpy(), eb, kind, C, C // 64)
+        if i % 4 == 3:                        # decompress request of a stream the oracle made
+            st = torch.frombuffer(bytearray(ref), dtype=torch.uint8).cuda()
+            y = oracle.decompress(ref).tobytes()
+            assert _plain_decompress(sz, plain_ctx, st, n) == y
+            reqs.append(("d", st, n, eb, kind, y))
         else:
-            reqs.append(("c", x, n, eb, kind, _plain_compress(sz, plain_ctx, x, eb, kind)))
+            assert _plain_compress(sz, plain_ctx, x, eb, kind) == ref
+            reqs.append(("c", x, n, eb, kind, ref))
     torch.cuda.synchronize()
     return reqs
 
@@ -183,7 +198,7 @@ def test_serve_held_outputs_block_until_released(sz, plain_ctx):
     n = 1 << 18
     reqs = _mix(sz, plain_ctx, 14, [n] * 3)
     keep = (sz.sz_max_compressed_bytes(n) + 255) // 256 * 256
-    per = 4 * n + keep + 2 * n
+    per = 4 * n + keep + 2 * n + (64 << 10)   # input, output, codes and chunk tables (with slack)
     budget = per + keep          # room for one request in flight plus one held output
     ctx = sz.Context(0, budget=budget)
     try:
