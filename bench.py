@@ -213,8 +213,11 @@ def rd_points(sz, ctx, xs, ebs=RD_EBS, params=None, md_mode=None):
     md_mode = SZ_MODE_LV_PRX compresses xs (xx, yy, zz) as one reordered MD
     snapshot and compares each decoded field with the reordered original.
     Also the closed form -20 log10(eb / sqrt 3) of uniform quantization noise
-    and the worst |x - x'| / (eb R) over the fields."""
+    and the worst |x - x'| / (eb R) over the fields.  The streams use the
+    fixed chunk-size rule (the batched form's autotuner is switched off on
+    ctx), so a point's rate does not depend on run-time measurements."""
     import torch
+    sz.sz_ctx_set_autotune(ctx, False)
     pts = []
     n_tot = sum(x.numel() for x in xs)
     for eb in ebs:

@@ -309,12 +309,13 @@ sz_status sz_compress_noalloc(const float* d_in, size_t n, double eb, sz_eb_kind
 
 /* Kernel phases of the path: range (a1), lattice + histogram (a2-a4),
  * codebook + layout (a5, a8), encode (a6-a7), decoder setup, decode
- * (a9-a11), MD reordering (R-index keys + segment sort + gather), and the
- * batched persistent kernel. */
+ * (a9-a11), MD reordering (R-index keys + segment sort + gather), the
+ * batched persistent kernel, and the chunk-size pass of the batched form's
+ * two-pass encoder (the per-array calls count it under encode). */
 typedef enum {
     SZ_PHASE_RANGE = 0, SZ_PHASE_QUANT = 1, SZ_PHASE_CODEBOOK = 2, SZ_PHASE_ENCODE = 3,
     SZ_PHASE_DECODE_SETUP = 4, SZ_PHASE_DECODE = 5, SZ_PHASE_REORDER = 6, SZ_PHASE_BATCH = 7,
-    SZ_NUM_PHASES = 8
+    SZ_PHASE_ENCODE_SIZES = 8, SZ_NUM_PHASES = 9
 } sz_phase;
 
 /* Enable (on != 0) or disable tracing.  While enabled, the context records a

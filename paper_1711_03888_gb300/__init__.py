@@ -40,7 +40,7 @@ EXPORTS = ("sz_ctx_create", "sz_ctx_destroy", "sz_max_compressed_bytes", "sz_com
            "sz_ctx_set_autotune", "sz_batch_tuning",
            "sz_serve_start", "sz_serve_submit", "sz_serve_poll", "sz_serve_wait", "sz_serve_release",
            "sz_serve_stats", "sz_serve_stop")
-PHASES = ("range", "quant", "codebook", "encode", "decode_setup", "decode", "reorder", "batch")
+PHASES = ("range", "quant", "codebook", "encode", "decode_setup", "decode", "reorder", "batch", "encode_sizes")
 
 
 class sz_params(C.Structure):

@@ -3,13 +3,19 @@
 // decode_setup (one block): validates the header against in_bytes, rebuilds
 // the canonical code from the (symbol, length) list -- first code, count and
 // base per length, left-justified limits, symbols in (length, symbol) order --
-// and fills a 12-bit direct lookup table.
+// and fills the lookup tables: a 12-bit first level (sym << 8 | len, or, for
+// a prefix of longer codes, the shortest length under it << 8) and a second
+// level over up to kLut2Max 16-bit prefixes past the first level's codes
+// (codes of 13..16 bits, or the shortest longer length).  A code neither
+// resolves is found by a short walk up the limits from that shortest length.
+// It also records the stream's largest chunk payload.
 //
 // decode (one persistent block per SM, split into independent 64-thread
 // "chunk teams" with their own named barrier): a team takes one chunk at a
 // time.  It stages the chunk's payload in shared memory (coalesced 128-bit
-// copies; chunks too large for the stage are read from global memory) and
-// asks L2 to prefetch its next chunk.  Thread k decodes sub-stream k (G
+// copies) and asks L2 to prefetch its next chunk; a block runs as many teams
+// as leave each a stage that holds the stream's largest chunk (a chunk larger
+// even for one team is read from global memory).  Thread k decodes sub-stream k (G
 // symbols) from its start bit (team scan of the sub-stream bit lengths) into
 // a swizzled shared buffer of deltas.  A team scan of the per-thread delta
 // sums plus the chunk anchor gives each thread its starting lattice value
@@ -30,12 +36,11 @@ constexpr int kDecThreads = kSubPerChunk;    // 64 threads per team
 constexpr int kMaxTeams = 8;
 constexpr int kDecBlock = kMaxTeams * kDecThreads;   // 512
 constexpr size_t kDecDynSmem = 208u * 1024u;         // second-level table (32 KB) + team regions
-constexpr uint32_t kEscMark = 0x80000000u;           // delta slot of an escape
 
 struct SetupSmem {
     RadixSmem rs;
     uint32_t cnt[kMaxLen + 2];
-    uint32_t ok, m;
+    uint32_t ok, m, maxw;
     unsigned long long kraft;
 };
 
@@ -118,7 +123,10 @@ __device__ __forceinline__ void decode_setup_body(const DecompressArgs& a, Setup
     const uint8_t* lens = in + st->off[S_LENS];
     uint32_t* scr = a.cb_scratch;
     for (int l = tid; l < kMaxLen + 2; l += kSetupThreads) sm.cnt[l] = 0;
-    if (tid == 0) sm.kraft = 0;
+    if (tid == 0) {
+        sm.kraft = 0;
+        sm.maxw = 0;
+    }
     __syncthreads();
     unsigned long long kr = 0;
     for (uint32_t k = tid; k < m; k += kSetupThreads) {
@@ -156,15 +164,37 @@ __device__ __forceinline__ void decode_setup_body(const DecompressArgs& a, Setup
         st->lim[kMaxLen + 1] = 0xffffffffu;
     }
     __syncthreads();
-    // second level: codes of 13..16 bits by their 16-bit prefix, over the
-    // prefixes [lim[12], lim[16]) >> 8 (those of longer codes read 0)
+    // First level: 12-bit prefixes.  Codes of up to 12 bits fill their
+    // prefixes with sym << 8 | len; every prefix of longer codes holds the
+    // shortest length under it, lmin << 8 (len field 0; lmin 25 = no code).
+    // Second level: the 16-bit prefixes from lim[12] on, at most kLut2Max of
+    // them -- codes of 13..16 bits as sym << 8 | len, prefixes of longer
+    // codes as lmin << 8.  lmin(x) = the first l with x < lim[l], because the
+    // codes of length l occupy [lim[l-1], lim[l]) in left-justified order.
     constexpr int kSh = kMaxLen - kLut2Bits;
     const uint32_t l2_lo = st->lim[kLutBits] >> kSh;
-    const uint32_t l2_hi = st->lim[kLut2Bits] >> kSh;
-    const uint32_t l2_n = (l2_hi > l2_lo && l2_hi - l2_lo <= kLut2Max) ? l2_hi - l2_lo : 0u;
+    const uint32_t l2_n = umin32(kLut2Max, 65536u - l2_lo);
+    const uint32_t l2_short = (st->lim[kLut2Bits] >> kSh) - l2_lo;   // entries of codes <= 16 bits
     uint32_t* lut2 = a.lut + (1u << kLutBits);
-    for (uint32_t i = tid; i < (1u << kLutBits); i += kSetupThreads) a.lut[i] = 0u;
-    for (uint32_t i = tid; i < l2_n; i += kSetupThreads) lut2[i] = 0u;
+    const uint32_t p1_lo = st->lim[kLutBits] >> (kMaxLen - kLutBits);
+    for (uint32_t i = tid; i < (1u << kLutBits); i += kSetupThreads) {
+        uint32_t v = 0u;
+        if (i >= p1_lo) {
+            uint32_t l = kLutBits + 1;
+            while (l <= (uint32_t)kMaxLen && (i << (kMaxLen - kLutBits)) >= st->lim[l]) ++l;
+            v = l << 8;
+        }
+        a.lut[i] = v;
+    }
+    for (uint32_t i = tid; i < l2_n; i += kSetupThreads) {
+        uint32_t v = 0u;
+        if (i >= l2_short) {
+            uint32_t l = kLut2Bits + 1;
+            while (l <= (uint32_t)kMaxLen && ((l2_lo + i) << kSh) >= st->lim[l]) ++l;
+            v = l << 8;
+        }
+        lut2[i] = v;
+    }
     __syncthreads();
     for (uint32_t p = tid; p < m; p += kSetupThreads) {
         uint32_t l = kl[p], s = vl[p];
@@ -173,15 +203,30 @@ __device__ __forceinline__ void decode_setup_body(const DecompressArgs& a, Setup
         if (l <= (uint32_t)kLutBits) {
             uint32_t lo = code << (kLutBits - l), hi = (code + 1) << (kLutBits - l);
             for (uint32_t e = lo; e < hi; ++e) a.lut[e] = (s << 8) | l;
-        } else if (l2_n && l <= (uint32_t)kLut2Bits) {
+        } else if (l <= (uint32_t)kLut2Bits) {
             uint32_t lo = (code << (kLut2Bits - l)) - l2_lo, hi = ((code + 1) << (kLut2Bits - l)) - l2_lo;
             for (uint32_t e = lo; e < hi && e < l2_n; ++e) lut2[e] = (s << 8) | l;
         }
+    }
+    // the largest chunk payload, which sets how many teams a block runs (the
+    // stage of each must hold it); malformed offsets count as empty chunks here
+    // and are rejected where the chunk is decoded
+    {
+        const uint64_t* cw = reinterpret_cast<const uint64_t*>(in + st->off[S_CWORD]);
+        const uint64_t nc = rd64(in + H_NCHUNKS);
+        uint32_t mx = 0;
+        for (uint64_t c = tid; c < nc; c += kSetupThreads) {
+            const uint64_t wb = cw[c], we = cw[c + 1];
+            if (we > wb) mx = max(mx, (uint32_t)umin64(we - wb, 1u << 24));
+        }
+        for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if ((tid & 31) == 0) atomicMax(&sm.maxw, mx);
     }
     __syncthreads();
     if (tid == 0) {
         st->l2_lo = l2_lo;
         st->l2_n = l2_n;
+        st->max_cw = sm.maxw;
         st->dec_ok = 1;
     }
 }
@@ -251,14 +296,21 @@ struct DecSmem {
 // dynamic shared memory: the second-level table, then one region per team
 constexpr size_t kLut2Bytes = sizeof(uint32_t) * kLut2Max;
 
-__device__ __forceinline__ int teams_for(uint32_t C) {
-    return C <= 4096 ? 8 : (C == 8192 ? 4 : 2);
+// Teams per block for chunks of C elements whose largest payload is max_cw
+// words: the most (up to 8 for C <= 4096, 4 for 8192, 2 for 16384) whose
+// region -- C value slots and the stage -- still stages the largest chunk;
+// a stream with chunks larger even for one team reads those from global memory.
+__device__ __forceinline__ int teams_for(uint32_t C, uint32_t max_cw) {
+    int t = C <= 4096 ? 8 : (C == 8192 ? 4 : 2);
+    while (t > 1 && ((uint32_t)((kDecDynSmem - kLut2Bytes) / 4) / (uint32_t)t & ~3u) < C + max_cw + 4u) --t;
+    return t;
 }
 
-// A code longer than the second level covers: walk the left-justified limits.
-__device__ __noinline__ uint32_t decode_long(uint32_t w24, const DecSmem& sm, const uint16_t* by_len, bool& bad) {
-    uint32_t len = kLutBits + 1;
-    while (w24 >= sm.lim[len]) ++len;   // lim[25] = ~0 stops the walk
+// A code longer than the second level covers: walk the left-justified limits
+// from `len` (the shortest length under the code's prefix).
+__device__ __noinline__ uint32_t decode_long(uint32_t w24, uint32_t len, const DecSmem& sm, const uint16_t* by_len,
+                                             bool& bad) {
+    while (len <= (uint32_t)kMaxLen && w24 >= sm.lim[len]) ++len;
     if (len > (uint32_t)kMaxLen) {
         bad = true;
         return 0u;
@@ -274,9 +326,9 @@ __device__ __forceinline__ uint32_t decode_symbol(BitReader& br, const DecSmem& 
     const uint32_t w = br.peek();
     const uint32_t e1 = sm.lut[w >> (32 - kLutBits)];
     const uint32_t i2 = (w >> (32 - kLut2Bits)) - l2_lo;   // wraps above l2_n below the range
-    const uint32_t e2 = i2 < l2_n ? lut2[i2] : 0u;
-    uint32_t ent = e1 ? e1 : e2;
-    if (ent == 0u) ent = decode_long(w >> (32 - kMaxLen), sm, by_len, bad);
+    const uint32_t e2 = i2 < l2_n ? lut2[i2] : e1;
+    uint32_t ent = (e1 & 255u) ? e1 : e2;
+    if ((ent & 255u) == 0u) ent = decode_long(w >> (32 - kMaxLen), ent >> 8, sm, by_len, bad);
     br.consume(ent & 255u);
     return ent >> 8;
 }
@@ -315,7 +367,7 @@ struct DecArray {
     const uint16_t* by_len;
     float* out;
     uint64_t n, nc, E, pw;
-    uint32_t C, G, gshift, l2_lo, l2_n;
+    uint32_t C, G, gshift, l2_lo, l2_n, max_cw;
     float D;
     bool vec;
     bool lcf;          // second-difference (LCF) stream: two anchors per chunk
@@ -344,6 +396,7 @@ __device__ __forceinline__ void dec_array(const DecompressArgs& a, DecArray& d) 
     d.by_len = a.by_len;
     d.l2_lo = st->l2_lo;
     d.l2_n = st->l2_n;
+    d.max_cw = st->max_cw;
     d.lcf = st->pred == kPredLCF;
 }
 
@@ -498,7 +551,7 @@ __device__ __forceinline__ bool decode_chunk_team(const DecArray& d, DecSmem& sm
     const long long q_fast = (1ll << 24) - (long long)G * (kRadius - 1);
     const long long q0 = d.anchor[c] + pre;
     if (nesc == 0 && q0 >= -q_fast && q0 <= q_fast) {
-        // 32-bit: q stays within 2^24, one exact int -> float and one fmul each
+        // 32-bit: q stays within the exact range, one int -> float and one fmul each
         int q = (int)q0;
         for (uint32_t j4 = 0; j4 < nsym; j4 += 4) {
             uint4* slot = reinterpret_cast<uint4*>(&xs[swz(e0 + j4, gshift)]);
@@ -588,7 +641,7 @@ __device__ __noinline__ void decode_team_lcf_counted(const DecArray d, DecSmem& 
 // payload stage
 __device__ __forceinline__ uint32_t* team_region(uint4* dyn, int teams, int team, uint32_t* stage_words,
                                                  uint32_t C) {
-    const uint32_t region_words = (uint32_t)((kDecDynSmem - kLut2Bytes) / 4) / teams;
+    const uint32_t region_words = ((uint32_t)((kDecDynSmem - kLut2Bytes) / 4) / teams) & ~3u;
     *stage_words = region_words - C;      // multiple of 4
     return reinterpret_cast<uint32_t*>(dyn) + kLut2Max + (size_t)team * region_words;
 }
@@ -612,7 +665,7 @@ __global__ void __launch_bounds__(kDecBlock, 1) decode_kernel(DecompressArgs a) 
     uint32_t* lut2 = reinterpret_cast<uint32_t*>(dyn_smem);
     load_dec_tables(a, d, sm, lut2);
     __syncthreads();
-    const int teams = teams_for(d.C);
+    const int teams = teams_for(d.C, d.max_cw);
     const int team = tid / kDecThreads, k = tid % kDecThreads;
     if (team >= teams) return;
     uint32_t stage_words;
@@ -720,7 +773,7 @@ __global__ void __launch_bounds__(kDecBlock, 1) decode_multi_kernel(const Decomp
             load_dec_tables(sa, d, sm, lut2);
             __syncthreads();
         }
-        const int teams = raw ? kMaxTeams : teams_for(d.C);
+        const int teams = raw ? kMaxTeams : teams_for(d.C, d.max_cw);
         if (team >= teams) continue;
         uint32_t stage_words = 0;
         uint32_t* xs = raw ? nullptr : team_region(dyn_smem, teams, team, &stage_words, d.C);

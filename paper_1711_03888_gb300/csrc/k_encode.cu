@@ -1,11 +1,26 @@
-// k_encode.cu -- stand-alone launch of the encode phase (a6-a7; body in
-// sz_encode.cuh): one block of C/32 threads per chunk, chunks taken in ticket
-// order so the decoupled look-back only waits on running blocks.
+// k_encode.cu -- stand-alone launch of the encode phase (a6-a7; bodies in
+// sz_encode.cuh).  Arrays of kTwoPassChunks chunks or more take the two-pass
+// encoder: pass 1 (encode_sizes_kernel) writes the chunk-word table, pass 2
+// (encode_kernel, LOOKBACK = false) packs every chunk at its offset with no
+// waits.  Smaller arrays, and codes recomputed from the input, take one pass:
+// persistent blocks take chunks in ticket order and find their offsets by the
+// decoupled look-back, which only waits on running blocks.
 #include "sz_encode.cuh"
 
 namespace szg {
 
-template <int C, bool FROM_CODES, bool LCF = false>
+#ifndef SZ_ENC_TWOPASS
+#define SZ_ENC_TWOPASS 0
+#endif
+constexpr uint32_t kTwoPassChunks = SZ_ENC_TWOPASS ? 64u : 0xffffffffu;
+
+template <int C>
+__global__ void __launch_bounds__(kSizeThreads) encode_sizes_kernel(CompressArgs a, uint32_t nblocks) {
+    __shared__ EncSizesSmem sm;
+    encode_sizes_body<C>(a, nblocks, sm);
+}
+
+template <int C, bool FROM_CODES, bool LCF = false, bool LOOKBACK = true>
 __global__ void __launch_bounds__(EncShape<C>::kThreads, EncShape<C>::kMinBlocks) encode_kernel(CompressArgs a) {
     static_assert(FROM_CODES || !LCF, "LCF encodes the stored codes");
     constexpr int NT = EncShape<C>::kThreads;
@@ -21,7 +36,7 @@ __global__ void __launch_bounds__(EncShape<C>::kThreads, EncShape<C>::kMinBlocks
     }
     uint32_t* smem = reinterpret_cast<uint32_t*>(dyn_smem);
     if constexpr (FROM_CODES) {
-        encode_array_pipelined<C, NT, LCF>(a, smem, esm, s_c, s_prev);
+        encode_array_pipelined<C, NT, LCF, LOOKBACK>(a, smem, esm, s_c, s_prev);
     } else {
         // codes recomputed from the input: one chunk per ticket
         for (;;) {
@@ -39,30 +54,46 @@ template <int C>
 static void launch_encode_t(const CompressArgs& a, cudaStream_t s) {
     const size_t smem = enc_smem_bytes(C);
     constexpr int NT = EncShape<C>::kThreads;
-    // variants: 0 codes recomputed, 1 stored codes, 2 stored codes with LCF
-    static int resident[3] = {0, 0, 0};
+    // variants: 0 codes recomputed, 1 stored codes, 2 stored codes with LCF; then
+    // 3 and 4: the packing pass of the two-pass encoder (LV, LCF)
+    static int resident[5] = {0, 0, 0, 0, 0};
+    static int sms = 0, size_res = 0;
     if (!resident[0]) {
-        int dev = 0, sms = 0;
+        int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaFuncSetAttribute(encode_kernel<C, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(encode_kernel<C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(encode_kernel<C, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        int b[3] = {0, 0, 0};
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b[0], encode_kernel<C, false>, NT, smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b[1], encode_kernel<C, true>, NT, smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b[2], encode_kernel<C, true, true>, NT, smem);
-        for (int v = 0; v < 3; ++v) resident[v] = (b[v] > 0 ? b[v] : 1) * (sms > 0 ? sms : 148);
+        if (sms <= 0) sms = 148;
+        const void* f[5] = {(const void*)encode_kernel<C, false>, (const void*)encode_kernel<C, true>,
+                            (const void*)encode_kernel<C, true, true>, (const void*)encode_kernel<C, true, false, false>,
+                            (const void*)encode_kernel<C, true, true, false>};
+        for (int v = 0; v < 5; ++v) {
+            cudaFuncSetAttribute(f[v], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            int b = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f[v], NT, smem);
+            resident[v] = (b > 0 ? b : 1) * sms;
+        }
+        int b = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, encode_sizes_kernel<C>, kSizeThreads, 0);
+        size_res = (b > 0 ? b : 1) * sms;
     }
     // persistent: at most the resident blocks, each taking chunks by ticket
     // (the quantizer stores the codes whenever the prediction is LCF)
-    const int v = a.codes ? (a.pred == kPredLCF ? 2 : 1) : 0;
+    int v = a.codes ? (a.pred == kPredLCF ? 2 : 1) : 0;
     const uint32_t div = a.grid_div > 1 ? a.grid_div : 1u;
+    if (v && a.n_chunks >= kTwoPassChunks) {
+        const uint32_t nb = umin32(a.n_chunks, umax32(1u, (uint32_t)size_res / div));
+        encode_sizes_kernel<C><<<nb, kSizeThreads, 0, s>>>(a, nb);
+        v += 2;
+    }
     uint32_t grid = umin32(a.n_chunks, (uint32_t)resident[v] / div);
     if (grid == 0) grid = 1;
-    if (v == 2) encode_kernel<C, true, true><<<grid, NT, smem, s>>>(a);
-    else if (v) encode_kernel<C, true><<<grid, NT, smem, s>>>(a);
-    else encode_kernel<C, false><<<grid, NT, smem, s>>>(a);
+    switch (v) {
+        case 0: encode_kernel<C, false><<<grid, NT, smem, s>>>(a); break;
+        case 1: encode_kernel<C, true><<<grid, NT, smem, s>>>(a); break;
+        case 2: encode_kernel<C, true, true><<<grid, NT, smem, s>>>(a); break;
+        case 3: encode_kernel<C, true, false, false><<<grid, NT, smem, s>>>(a); break;
+        default: encode_kernel<C, true, true, false><<<grid, NT, smem, s>>>(a); break;
+    }
 }
 
 // The timeout path of the look-back wait: one warp waits, as the encoder of

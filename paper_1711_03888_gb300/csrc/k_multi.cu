@@ -1,6 +1,7 @@
 // k_multi.cu -- the batched form's path for large arrays: each phase (a1
-// range, a2-a4 quantize + histogram, a5 codebook, a6-a7 encode) is one launch
-// over all large arrays of the batch, blockIdx.y selecting the array.  The
+// range, a2-a4 quantize + histogram, a5 codebook, a6-a7 encode in two passes:
+// chunk sizes, then packing) is one launch over all large arrays of the batch,
+// blockIdx.y selecting the array.  The
 // bodies are the stand-alone kernels' (sz_range.cuh, sz_quant.cuh,
 // sz_codebook.cuh, sz_encode.cuh), so every stream is byte-identical to
 // sz_compress; the gain is that the arrays' single-block codebooks run side by
@@ -56,6 +57,20 @@ __global__ void __launch_bounds__(kCbBlock) codebook_multi_kernel(MultiArgs m) {
     codebook_body<kCbBlock>(sa, sm, fast, kCbFastSyms);
 }
 
+// pass 1 of the two-pass encoder over the group's arrays (gridDim.x blocks each)
+template <int C>
+__global__ void __launch_bounds__(kSizeThreads) encode_sizes_multi_kernel(MultiArgs m) {
+    __shared__ EncSizesSmem sm;
+    __shared__ CompressArgs sa;
+    stage_args(m, sa);
+    encode_sizes_body<C>(sa, gridDim.x, sm);
+}
+
+// pass 2: persistent packing of the group's arrays at the offsets of pass 1
+// (or, LOOKBACK, one pass with the chunks' look-back)
+#ifndef SZ_ENC_TWOPASS
+#define SZ_ENC_TWOPASS 0
+#endif
 template <int C>
 __global__ void __launch_bounds__(EncShape<C>::kThreads, EncShape<C>::kMinBlocks) encode_multi_kernel(MultiArgs m) {
     constexpr int NT = EncShape<C>::kThreads;
@@ -72,7 +87,8 @@ __global__ void __launch_bounds__(EncShape<C>::kThreads, EncShape<C>::kMinBlocks
         raw_copy_words(sa, 0, words, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, (uint64_t)gridDim.x * blockDim.x);
         return;
     }
-    encode_array_pipelined<C, NT>(sa, reinterpret_cast<uint32_t*>(dyn_smem), esm, s_c, &s_prev);
+    encode_array_pipelined<C, NT, false, !SZ_ENC_TWOPASS>(sa, reinterpret_cast<uint32_t*>(dyn_smem), esm, s_c,
+                                                          &s_prev);
 }
 
 constexpr uint32_t kMultiC[4] = {2048u, 4096u, 8192u, 16384u};
@@ -80,6 +96,10 @@ const void* const kEncMulti[4] = {(const void*)encode_multi_kernel<2048>, (const
                                   (const void*)encode_multi_kernel<8192>, (const void*)encode_multi_kernel<16384>};
 constexpr int kEncThreads[4] = {EncShape<2048>::kThreads, EncShape<4096>::kThreads, EncShape<8192>::kThreads,
                                 EncShape<16384>::kThreads};
+const void* const kSizesMulti[4] = {(const void*)encode_sizes_multi_kernel<2048>,
+                                    (const void*)encode_sizes_multi_kernel<4096>,
+                                    (const void*)encode_sizes_multi_kernel<8192>,
+                                    (const void*)encode_sizes_multi_kernel<16384>};
 
 int sm_count() {
     static int sms = 0;
@@ -97,7 +117,7 @@ int sm_count() {
 int multi_compress_launches(const CompressArgs* d_args, const MultiGroup* groups, int ngroups, KernelLaunch* out,
                             int max_out) {
     if (ngroups <= 0) return 0;
-    if (max_out < 3 + ngroups) return -1;
+    if (max_out < 3 + 2 * ngroups) return -1;
     const uint32_t first = groups[0].first;
     uint32_t count = 0, max_nc = 1, maxC = 2048;
     for (int i = 0; i < ngroups; ++i) {
@@ -105,7 +125,7 @@ int multi_compress_launches(const CompressArgs* d_args, const MultiGroup* groups
         if (groups[i].max_chunks > max_nc) max_nc = groups[i].max_chunks;
         if (groups[i].C > maxC) maxC = groups[i].C;
     }
-    static int quant_res[4] = {0, 0, 0, 0}, enc_res[4] = {0, 0, 0, 0};
+    static int quant_res[4] = {0, 0, 0, 0}, enc_res[4] = {0, 0, 0, 0}, size_res = 0;
     static bool configured = false;
     if (!configured) {
         cudaFuncSetAttribute(codebook_multi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCbFastBytes);
@@ -122,6 +142,8 @@ int multi_compress_launches(const CompressArgs* d_args, const MultiGroup* groups
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&enc_res[j], kEncMulti[j], kEncThreads[j], sm);
             enc_res[j] = (enc_res[j] > 0 ? enc_res[j] : 1) * sm_count();
         }
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&size_res, kSizesMulti[1], kSizeThreads, 0);
+        size_res = (size_res > 0 ? size_res : 1) * sm_count();
         configured = true;
     }
     auto set = [](KernelLaunch& L, const void* f, uint32_t gx, uint32_t gy, uint32_t bx, size_t smem, int phase,
@@ -146,8 +168,15 @@ int multi_compress_launches(const CompressArgs* d_args, const MultiGroup* groups
         for (int t = 0; t < 4; ++t)
             if (groups[i].C == kMultiC[t]) j = t;
         if (j < 0) return -1;
+        const uint32_t mc = groups[i].max_chunks ? groups[i].max_chunks : 1u;
+        const int sshare = size_res / (int)groups[i].count;
+        if (k >= max_out) return -1;
+        if (SZ_ENC_TWOPASS)
+            set(out[k++], kSizesMulti[j], umin32(mc, (uint32_t)(sshare > 0 ? sshare : 1)), groups[i].count,
+                kSizeThreads, 0, SZ_PHASE_ENCODE_SIZES, d_args, groups[i].first);
         const int share = enc_res[j] / (int)groups[i].count;
-        const uint32_t per = umin32(groups[i].max_chunks ? groups[i].max_chunks : 1u, (uint32_t)(share > 0 ? share : 1));
+        const uint32_t per = umin32(mc, (uint32_t)(share > 0 ? share : 1));
+        if (k >= max_out) return -1;
         set(out[k++], kEncMulti[j], per, groups[i].count, kEncThreads[j], enc_smem_bytes((int)kMultiC[j]),
             SZ_PHASE_ENCODE, d_args, groups[i].first);
     }

@@ -268,12 +268,12 @@ static sz_status batch_compress_run(sz_ctx* ctx, int k, const float* const* d_in
         }
         deps[0] = n_copy;
         deps[1] = n_reset;
-        KernelLaunch ml[8];
-        const int nml = multi_compress_launches(plan.args, groups.data(), (int)groups.size(), ml, 8);
+        KernelLaunch ml[16];
+        const int nml = multi_compress_launches(plan.args, groups.data(), (int)groups.size(), ml, 16);
         bool nodes_ok = nml >= 0;
         cudaGraphNode_t prev = n_copy;
         for (int i = 0; nodes_ok && i < nml; ++i) {
-            // range -> quantize -> codebook in a chain; the encoders after the codebook
+            // range -> quantize -> codebook -> each group's two encode passes, in a chain
             cudaKernelNodeParams mp{};
             void* margs[] = {&ml[i].args};
             mp.func = const_cast<void*>(ml[i].func);
@@ -283,7 +283,7 @@ static sz_status batch_compress_run(sz_ctx* ctx, int k, const float* const* d_in
             mp.kernelParams = margs;
             cudaGraphNode_t node;
             nodes_ok = cudaGraphAddKernelNode(&node, g, &prev, 1, &mp) == cudaSuccess;
-            if (i < 3) prev = node;
+            prev = node;
         }
         if (!nodes_ok || (ks && cudaGraphAddKernelNode(&n_kern, g, deps, 2, &kp) != cudaSuccess) ||
             cudaGraphInstantiate(&ctx->bg_exec, g, 0) != cudaSuccess) {
@@ -322,9 +322,9 @@ static sz_status batch_compress_run(sz_ctx* ctx, int k, const float* const* d_in
             ProfScope pr(ctx, SZ_PHASE_BATCH, s);
             launch_batch_compress(plan, s);
         }
-        KernelLaunch ml[8];
+        KernelLaunch ml[16];
         const int nml = multi_compress_launches((const CompressArgs*)(base + o_args), groups.data(), (int)groups.size(),
-                                                ml, 8);
+                                                ml, 16);
         if (nml < 0) return SZ_ERR_ARG;
         for (int i = 0; i < nml; ++i) {
             ProfScope pr(ctx, ml[i].phase, s);

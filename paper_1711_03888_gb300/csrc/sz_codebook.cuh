@@ -141,6 +141,7 @@ __device__ void codebook_body(const CompressArgs& a, CbSmem<NT>& sm, uint32_t* f
             st->raw = n ? 1u : 0u;
             st->total_bytes = total;
             st->ticket = 0u;
+            st->size_ticket = 0u;
             for (int s = 0; s < 8; ++s) st->off[s] = off[s];
         }
         return;
@@ -189,6 +190,7 @@ __device__ void codebook_body(const CompressArgs& a, CbSmem<NT>& sm, uint32_t* f
             st->raw = 1u;                        // the encoders' raw copy then finds no room and writes nothing
             st->total_bytes = a.out_cap + 1;
             st->ticket = 0u;
+            st->size_ticket = 0u;
             for (int s2 = 0; s2 < 8; ++s2) st->off[s2] = a.out_cap + 1;
         }
         return;
@@ -399,7 +401,9 @@ __device__ void codebook_body(const CompressArgs& a, CbSmem<NT>& sm, uint32_t* f
     for (uint32_t p = tid; p < m; p += kCbThreads) {
         uint32_t l = kl[p], k = vlx[p];
         uint32_t code = sm.first[l] + (p - sm.base[l]);
-        a.enc[sym[k]] = (code << 5) | l;
+        // the codeword left-justified, the escape flag (symbol 0) and the length:
+        // the encoder packs the entry as it stands
+        a.enc[sym[k]] = (code << (32u - l)) | (sym[k] == 0u ? 32u : 0u) | l;
     }
 
     // -------- total code bits --------------------------------------------------
@@ -488,6 +492,7 @@ __device__ void codebook_body(const CompressArgs& a, CbSmem<NT>& sm, uint32_t* f
         st->n_used = m;
         st->bound_bits = B;
         st->ticket = 0u;
+        st->size_ticket = 0u;
     }
     __syncthreads();
     if (sm.raw || !sm.tables_ok) return;

@@ -1,21 +1,23 @@
 // sz_encode.cuh -- a6 + a7: Huffman encoding of the codes into chunked
 // sub-streams, the chunk tables and the escape records.
 //
-// One block of C/32 threads per chunk of C elements (chunks are taken in
-// ticket order so the decoupled look-back always waits on running blocks).
-//  pass 1 (coalesced): each thread takes one float4 per 4*blockDim step,
-//    recomputes the lattice codes (a2-a3; the predecessor comes from the
-//    neighbouring lane), looks up (codeword, length) and stores the packed
-//    entry in shared memory, swizzled so the next pass is conflict-free;
-//  pass 2: thread t loads the 32 consecutive entries t*32 .. t*32+31 into
-//    registers; block scans give its start bit and escape index; the chunk's
-//    word offset comes from the look-back over preceding chunks;
-//  pass 3: thread t packs its 32 codewords MSB-first into the (now free)
-//    shared buffer -- interior words by plain stores, its first and last
-//    word by atomicOr -- and the chunk leaves with 128-bit stores.
-// Sub-stream k (G = C/64 elements) is threads [kG/32, (k+1)G/32), so its bit
-// length is a shuffle reduction over G/32 lanes.  Escape records are rebuilt
-// from global memory (rare).
+// A chunk of C elements is encoded by one block of NT = C / kRun threads;
+// thread t holds the codeword-table entries of elements t*kRun .. t*kRun +
+// kRun - 1 (entries: codeword << (32 - length) | escape << 5 | length, so a
+// thread packs them as they stand).  One block scan gives each thread its
+// start bit and escape index; each thread packs its codewords MSB-first into
+// a zeroed shared buffer by funnel shifts (its first and last words, which it
+// may share with its neighbours, by shared atomic OR; the words between by
+// plain stores), and the chunk leaves with 128-bit stores.  Sub-stream k (G =
+// C/64 elements) is threads [kG/kRun, (k+1)G/kRun), so its bit length is a
+// shuffle reduction.  Escape records are rebuilt from global memory (rare).
+// The chunk's word offset in the payload comes either
+//   - from a decoupled look-back over the chunks before it, chunks being
+//     taken in ticket order so that the look-back waits only on running
+//     blocks (one pass; the batched kernel's small arrays), or
+//   - from pass 1 of the two-pass encoder (encode_sizes_body): every chunk's
+//     word count, scanned into the stream's chunk-word table with a look-back
+//     over blocks instead of chunks; pass 2 then packs with no waits at all.
 #pragma once
 #include "sz_device.cuh"
 
@@ -64,14 +66,14 @@ struct EncSmem {
     unsigned long long prefix;
 };
 
-// The part of a chunk's encoding after each thread holds its kRun packed
-// entries r[j] = codeword << 6 | length << 1 | escape (0 past the chunk's
-// end): block scan of bit lengths and escape counts, publication of the
-// chunk size, packing, escape records, look-back for the word offset, the
-// chunk tables and the coalesced copy of the payload.  anchor (thread 0): the
-// lattice value before the chunk; with LCF, anchor2 is the one before that
-// and escapes carry the second difference.
-template <int NT, int kRun, bool LCF = false>
+// The part of a chunk's encoding after each thread holds its kRun table
+// entries r[j] (0 past the chunk's end): block scan of bit lengths and escape
+// counts, packing, escape records, the chunk's word offset (LOOKBACK: by the
+// look-back, after publishing the chunk's size; else from the chunk-word
+// table of pass 1), the chunk tables and the coalesced copy of the payload.
+// anchor (thread 0): the lattice value before the chunk; with LCF, anchor2 is
+// the one before that and escapes carry the second difference.
+template <int NT, int kRun, bool LCF = false, bool LOOKBACK = true>
 __device__ __forceinline__ void encode_chunk_body(const CompressArgs& a, const LatticeParams& P, const uint32_t c,
                                                   const uint32_t (&r)[kRun], const long long anchor, uint32_t* buf,
                                                   EncSmem<NT>& esm, const long long anchor2 = 0) {
@@ -87,8 +89,8 @@ __device__ __forceinline__ void encode_chunk_body(const CompressArgs& a, const L
     uint32_t bits = 0, escs = 0;
 #pragma unroll
     for (int j = 0; j < kRun; ++j) {
-        bits += (r[j] >> 1) & 31u;
-        escs += r[j] & 1u;
+        bits += r[j] & 31u;
+        escs += (r[j] >> 5) & 1u;
     }
     // one block scan of (escapes << 32 | bits)
     unsigned long long tot;
@@ -106,31 +108,33 @@ __device__ __forceinline__ void encode_chunk_body(const CompressArgs& a, const L
     // ---- publish this chunk's size for the look-back of later chunks --------------
     unsigned long long* status = a.chunk_status;
     constexpr unsigned long long FLAG_AGG = kLbAgg, FLAG_INC = kLbInc, FLAG_ERR = kLbErr;
-    if (tid == 0) st_status(&status[c], (c == 0 ? FLAG_INC : FLAG_AGG) | chunk_words);
+    if (LOOKBACK && tid == 0) st_status(&status[c], (c == 0 ? FLAG_INC : FLAG_AGG) | chunk_words);
     // zero the payload area (the code entries are in registers now)
-    for (uint32_t w = tid; w < chunk_words; w += NT) buf[w] = 0u;
+    for (uint32_t w4 = tid; w4 < chunk_words / 4; w4 += NT) reinterpret_cast<uint4*>(buf)[w4] = make_uint4(0u, 0u, 0u, 0u);
     __syncthreads();
 
-    // ---- pass 3: pack into shared memory ------------------------------------------
+    // ---- pack into shared memory ----------------------------------------------------
+    // cur holds the word being filled (fill bits used, from the top); a
+    // codeword t (left-justified) adds t >> fill, and what does not fit is
+    // the next word's start, t << (32 - fill) (a funnel shift: 0 when fill = 0).
+    // A thread's first and last words may be shared with its neighbours
+    // (atomic OR); the words in between are its own (plain stores).
     {
         uint32_t word = start >> 5, fill = start & 31u, cur = 0u;
         bool first = true;
 #pragma unroll
         for (int j = 0; j < kRun; ++j) {
-            const uint32_t len = (r[j] >> 1) & 31u;
-            const uint32_t cw = r[j] >> 6;
-            const uint32_t room = 32u - fill;
-            if (len < room) {
-                cur |= cw << (room - len);   // len == 0 leaves cur unchanged
-                fill += len;
-            } else {
-                const uint32_t spill = len - room;   // 0..23
-                cur |= cw >> spill;
-                if (first) atomicOr(&buf[word], cur); else buf[word] = cur;
+            const uint32_t t = r[j] & ~255u;
+            cur |= t >> fill;
+            const uint32_t nxt = __funnelshift_r(0u, t, fill);
+            fill += r[j] & 31u;
+            if (fill >= 32u) {
+                if (first) atomicOr(&buf[word], cur);
+                else buf[word] = cur;
                 first = false;
                 ++word;
-                cur = spill ? (cw << (32u - spill)) : 0u;
-                fill = spill;
+                cur = nxt;
+                fill -= 32u;
             }
         }
         if (fill) atomicOr(&buf[word], cur);
@@ -145,7 +149,7 @@ __device__ __forceinline__ void encode_chunk_body(const CompressArgs& a, const L
         uint32_t idx = 0;
 #pragma unroll
         for (int j = 0; j < kRun; ++j) {
-            if (r[j] & 1u) {
+            if (r[j] & 32u) {
                 uint64_t i = base + e0 + j;
                 float x = __ldg(in + i);
                 long long q, qp = 0, qpp = 0;
@@ -161,8 +165,11 @@ __device__ __forceinline__ void encode_chunk_body(const CompressArgs& a, const L
         }
     }
 
-    // ---- decoupled look-back, one warp, 32 predecessors per step --------------------
-    if (tid < 32 && c > 0) {
+    // ---- the chunk's word offset ------------------------------------------------------
+    if (!LOOKBACK) {
+        if (tid == 0) s_prefix = tables_ok ? reinterpret_cast<const uint64_t*>(out + st->off[S_CWORD])[c] : ~0ull;
+    } else if (tid < 32 && c > 0) {
+        // decoupled look-back, one warp, 32 predecessors per step
         unsigned long long excl = 0;
         const bool ok = lookback_prefix(status, c, kLookbackSpins, &excl);
         if (tid == 0) {
@@ -190,7 +197,7 @@ __device__ __forceinline__ void encode_chunk_body(const CompressArgs& a, const L
                 (uint16_t)(e0 < cnt ? sub_bits : 0u);
         }
         if (tid == 0) {
-            reinterpret_cast<uint64_t*>(out + st->off[S_CWORD])[c] = prefix;
+            if (LOOKBACK) reinterpret_cast<uint64_t*>(out + st->off[S_CWORD])[c] = prefix;
             long long* anchors = reinterpret_cast<long long*>(out + st->off[S_ANCHOR]);
             if (LCF) {
                 anchors[2 * (uint64_t)c] = anchor;
@@ -198,10 +205,11 @@ __device__ __forceinline__ void encode_chunk_body(const CompressArgs& a, const L
             } else {
                 anchors[c] = anchor;
             }
-            if (c == a.n_chunks - 1) reinterpret_cast<uint64_t*>(out + st->off[S_CWORD])[c + 1] = prefix + chunk_words;
+            if (LOOKBACK && c == a.n_chunks - 1)
+                reinterpret_cast<uint64_t*>(out + st->off[S_CWORD])[c + 1] = prefix + chunk_words;
         }
     }
-    if (c == a.n_chunks - 1 && tid == 0) {
+    if (LOOKBACK && c == a.n_chunks - 1 && tid == 0) {
         st->total_bytes = chunk_end;
         if (a.out_cap >= kHeaderBytes) {
             *reinterpret_cast<uint64_t*>(out + H_PWORDS) = prefix + chunk_words;
@@ -256,8 +264,7 @@ __device__ void encode_chunk(const CompressArgs& a, const uint32_t c, uint32_t* 
 #pragma unroll
         for (int j = 0; j < kRun; ++j) {
             const uint32_t code = (j & 1) ? (w[j >> 1] >> 16) : (w[j >> 1] & 0xffffu);
-            const uint32_t ent = __ldg(enc + code);
-            r[j] = (e0 + j < cnt) ? (((ent >> 5) << 6) | ((ent & 31u) << 1) | (code == 0u ? 1u : 0u)) : 0u;
+            r[j] = (e0 + j < cnt) ? __ldg(enc + code) : 0u;
         }
         if (tid == 0 && base > 0) {
             bool vv;
@@ -294,8 +301,7 @@ __device__ void encode_chunk(const CompressArgs& a, const uint32_t c, uint32_t* 
             pk[j] = 0u;
             if (e + j < cnt) {
                 uint32_t code = make_code(q[j], j == 0 ? qprev : q[j - 1], vb[j]);
-                uint32_t ent = __ldg(enc + code);
-                pk[j] = ((ent >> 5) << 6) | ((ent & 31u) << 1) | (code == 0u ? 1u : 0u);
+                pk[j] = __ldg(enc + code);
             }
         }
         *reinterpret_cast<uint4*>(&buf[swz(e, kRunShift)]) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
@@ -321,7 +327,7 @@ __device__ void encode_chunk(const CompressArgs& a, const uint32_t c, uint32_t* 
 // unfinished ticket is always being encoded, so the look-back still only
 // waits on chunks that make progress.  s_prev: the element before the chunk
 // (and, with LCF, the one before that in s_prev[1]).
-template <int C, int NT, bool LCF = false>
+template <int C, int NT, bool LCF = false, bool LOOKBACK = true>
 __device__ __forceinline__ void encode_array_pipelined(const CompressArgs& a, uint32_t* smem, EncSmem<NT>& esm,
                                                        uint32_t* s_ticket, float* s_prev) {
     constexpr int kRun = C / NT;
@@ -377,14 +383,124 @@ __device__ __forceinline__ void encode_array_pipelined(const CompressArgs& a, ui
 #pragma unroll
         for (int j = 0; j < kRun; ++j) {
             const uint32_t code = (j & 1) ? (w[j >> 1] >> 16) : (w[j >> 1] & 0xffffu);
-            const uint32_t ent = __ldg(a.enc + code);
-            r[j] = (e0 + j < cnt) ? (((ent >> 5) << 6) | ((ent & 31u) << 1) | (code == 0u ? 1u : 0u)) : 0u;
+            r[j] = (e0 + j < cnt) ? __ldg(a.enc + code) : 0u;
         }
         __syncthreads();          // the stage is read; the next ticket is known
         const uint32_t cn = s_ticket[1];
         if (cn < a.n_chunks) issue(cn);
-        encode_chunk_body<NT, kRun, LCF>(a, P, c, r, anchor, buf, esm, anchor2);
+        encode_chunk_body<NT, kRun, LCF, LOOKBACK>(a, P, c, r, anchor, buf, esm, anchor2);
         c = cn;
+    }
+}
+
+// ---- two-pass encoding, pass 1 --------------------------------------------------------
+// The word count of every chunk (its codes' lengths summed, padded to 128
+// bits) and their exclusive scan: the stream's chunk-word table.  A block
+// takes the next range of chunks by ticket (range t of nblocks: chunks
+// [t nc / nblocks, (t + 1) nc / nblocks)), so it waits only on blocks that
+// took their tickets earlier and are running: it sums its range one chunk per
+// warp, publishes the range's total in the status word of its ticket, looks
+// back over the earlier tickets for its prefix, and turns its range's counts
+// into offsets.  The block of the last ticket writes the table's end, the
+// header's payload size and total, and the stream size.  Reads the stored
+// codes (the code buffer holds whole chunks).
+constexpr int kSizeThreads = 256;
+
+struct EncSizesSmem {
+    unsigned long long wsum[kSizeThreads / 32];
+    unsigned long long ws64[kSizeThreads / 32 + 1];
+    unsigned long long prefix, total;
+    uint32_t ticket;
+};
+
+// summed lengths of the eight codes in q (entries of codes past cnt, counted
+// from the group's first element e, excluded)
+__device__ __forceinline__ uint32_t code_bits8(const uint4 q, const uint32_t* enc, uint32_t e, uint32_t cnt) {
+    const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+    uint32_t bits = 0;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const uint32_t lo = __ldg(enc + (w[m] & 0xffffu)) & 31u, hi = __ldg(enc + (w[m] >> 16)) & 31u;
+        bits += (e + 2 * m < cnt ? lo : 0u) + (e + 2 * m + 1 < cnt ? hi : 0u);
+    }
+    return bits;
+}
+
+template <int C>
+__device__ void encode_sizes_body(const CompressArgs& a, uint32_t nblocks, EncSizesSmem& sm) {
+    ArrayState* st = a.st;
+    if (st->raw || a.n == 0) return;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t nc = a.n_chunks;
+    if (nblocks > nc) nblocks = nc;
+    if (tid == 0) sm.ticket = atomicAdd(&st->size_ticket, 1u);
+    __syncthreads();
+    const uint32_t t = sm.ticket;
+    if (t >= nblocks) return;
+    const uint32_t c0 = (uint32_t)((uint64_t)t * nc / nblocks), c1 = (uint32_t)((uint64_t)(t + 1) * nc / nblocks);
+    const uint64_t off_payload = st->off[S_PAYLOAD];
+    const bool tables_ok = off_payload <= a.out_cap;
+    uint64_t* cword = reinterpret_cast<uint64_t*>(a.out + st->off[S_CWORD]);
+    // ---- the range's chunks: words of each, one warp per chunk ---------------------
+    unsigned long long wacc = 0;
+    for (uint32_t c = c0 + warp; c < c1; c += kSizeThreads / 32) {
+        const uint64_t base = (uint64_t)c * C;
+        const uint32_t cnt = (uint32_t)umin64(C, a.n - base);
+        const uint4* cp = reinterpret_cast<const uint4*>(a.codes + base);
+        uint32_t bits = 0;
+#pragma unroll 4
+        for (uint32_t v = lane; v < (uint32_t)C / 8; v += 32) bits += code_bits8(__ldg(cp + v), a.enc, 8 * v, cnt);
+        bits = warp_reduce_sum(bits);
+        const uint32_t words = ((bits + 127u) >> 7) << 2;
+        if (lane == 0 && tables_ok) cword[c] = words;
+        wacc += words;
+    }
+    if (lane == 0) sm.wsum[warp] = wacc;
+    __syncthreads();
+    // ---- the range's total, published; the prefix by the look-back over blocks ------
+    if (warp == 0) {
+        unsigned long long tot = lane < kSizeThreads / 32 ? sm.wsum[lane] : 0ull;
+        tot = warp_reduce_sum(tot);
+        unsigned long long* status = a.chunk_status;
+        if (lane == 0) st_status(&status[t], (t == 0 ? kLbInc : kLbAgg) | tot);
+        unsigned long long excl = 0;
+        const bool ok = t == 0 || lookback_prefix(status, t, kLookbackSpins, &excl);
+        if (lane == 0) {
+            if (!ok) {
+                raise_err(a.err, E_TIMEOUT);
+                st_status(&status[t], kLbErr);
+            } else if (t > 0) {
+                st_status(&status[t], kLbInc | (excl + tot));
+            }
+            sm.prefix = ok ? excl : ~0ull;
+            sm.total = tot;
+        }
+    }
+    __syncthreads();
+    const unsigned long long prefix = sm.prefix;
+    if (prefix == ~0ull) return;
+    // ---- counts -> offsets over the range, kSizeThreads chunks at a time -------------
+    if (tables_ok) {
+        unsigned long long run = prefix;
+        for (uint32_t c = c0; c < c1; c += kSizeThreads) {
+            const uint32_t ci = c + tid;
+            const unsigned long long w = ci < c1 ? cword[ci] : 0ull;
+            unsigned long long tot2;
+            const unsigned long long ex = block_exclusive_scan<kSizeThreads>(w, sm.ws64, &tot2);
+            if (ci < c1) cword[ci] = run + ex;
+            run += tot2;
+        }
+    }
+    if (t == nblocks - 1 && tid == 0) {
+        const uint64_t pw = prefix + sm.total;
+        const uint64_t end = off_payload + 4ull * pw;
+        st->total_bytes = end;
+        if (a.out_cap >= kHeaderBytes) {
+            *reinterpret_cast<uint64_t*>(a.out + H_PWORDS) = pw;
+            *reinterpret_cast<uint64_t*>(a.out + H_TOTAL) = end;
+        }
+        if (tables_ok) cword[nc] = pw;
+        if (end > a.out_cap) raise_err(a.err, E_CAPACITY);
     }
 }
 

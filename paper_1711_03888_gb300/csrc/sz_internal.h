@@ -26,7 +26,7 @@ constexpr int kSubPerChunk = 64;                  // sub-streams per chunk on th
 constexpr int kRangeBlocks = 1216;                // 8 x 152 SMs
 constexpr int kLutBits = 12;                      // decoder direct-lookup width
 constexpr int kLut2Bits = 16;                     // second level: codes of 13..16 bits by 16-bit prefix
-constexpr uint32_t kLut2Max = 8192;               // second-level entries (above: limit walk only)
+constexpr uint32_t kLut2Max = 8192;               // second-level entries (further prefixes: limit walk)
 constexpr uint32_t kLutWords = (1u << kLutBits) + kLut2Max;   // both levels, per array
 
 // header byte offsets
@@ -78,7 +78,9 @@ struct ArrayState {
     uint32_t dec_ok;
     uint32_t l2_lo;            // decoder: first 16-bit prefix of the second-level table
     uint32_t l2_n;             // decoder: its entries (0 = no second level)
-    uint32_t pad1;
+    uint32_t max_cw;           // decoder: the largest chunk payload of the stream, in words
+    uint32_t size_ticket;      // encoder pass 1 block ticket (reset by the codebook kernel)
+    uint32_t pad1[3];
 };
 
 // Arguments of one array's compression (passed by value to kernels).
@@ -94,7 +96,7 @@ struct CompressArgs {
     uint32_t extra_flags;
     ArrayState* st;
     uint32_t* hist;             // 65536
-    uint32_t* enc;              // 65536: codeword << 5 | length
+    uint32_t* enc;              // 65536: codeword << (32 - length) | escape << 5 | length
     uint32_t* chunk_esc;        // n_chunks: escapes per chunk
     unsigned long long* chunk_status;  // n_chunks: look-back words
     uint32_t* cb_scratch;       // codebook scratch (kCbScratchWords words)
