@@ -10,7 +10,7 @@
 namespace szg {
 
 #ifndef SZ_ENC_TWOPASS
-#define SZ_ENC_TWOPASS 0
+#define SZ_ENC_TWOPASS 1
 #endif
 constexpr uint32_t kTwoPassChunks = SZ_ENC_TWOPASS ? 64u : 0xffffffffu;
 
@@ -18,6 +18,18 @@ template <int C>
 __global__ void __launch_bounds__(kSizeThreads) encode_sizes_kernel(CompressArgs a, uint32_t nblocks) {
     __shared__ EncSizesSmem sm;
     encode_sizes_body<C>(a, nblocks, sm);
+}
+
+template <int C, bool LCF>
+__global__ void __launch_bounds__(kPackWarps * 32, kPackMinBlocks) encode_pack_kernel(CompressArgs a) {
+    extern __shared__ uint4 pack_smem[];
+    uint32_t* sm = reinterpret_cast<uint32_t*>(pack_smem);
+    if (a.st->raw) {
+        const uint64_t words = (a.n + 3u) & ~(uint64_t)3u;
+        raw_copy_words(a, 0, words, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, (uint64_t)gridDim.x * blockDim.x);
+        return;
+    }
+    encode_pack_warp<C, LCF>(a, sm + (threadIdx.x >> 5) * kRoundBufWords);
 }
 
 template <int C, bool FROM_CODES, bool LCF = false, bool LOOKBACK = true>
@@ -57,7 +69,7 @@ static void launch_encode_t(const CompressArgs& a, cudaStream_t s) {
     // variants: 0 codes recomputed, 1 stored codes, 2 stored codes with LCF; then
     // 3 and 4: the packing pass of the two-pass encoder (LV, LCF)
     static int resident[5] = {0, 0, 0, 0, 0};
-    static int sms = 0, size_res = 0;
+    static int sms = 0, size_res = 0, pack_res[2] = {0, 0};
     if (!resident[0]) {
         int dev = 0;
         cudaGetDevice(&dev);
@@ -75,6 +87,16 @@ static void launch_encode_t(const CompressArgs& a, cudaStream_t s) {
         int b = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, encode_sizes_kernel<C>, kSizeThreads, 0);
         size_res = (b > 0 ? b : 1) * sms;
+        cudaFuncSetAttribute(encode_pack_kernel<C, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)pack_smem_bytes());
+        cudaFuncSetAttribute(encode_pack_kernel<C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)pack_smem_bytes());
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, encode_pack_kernel<C, false>, kPackWarps * 32,
+                                                      pack_smem_bytes());
+        pack_res[0] = (b > 0 ? b : 1) * sms;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, encode_pack_kernel<C, true>, kPackWarps * 32,
+                                                      pack_smem_bytes());
+        pack_res[1] = (b > 0 ? b : 1) * sms;
     }
     // persistent: at most the resident blocks, each taking chunks by ticket
     // (the quantizer stores the codes whenever the prediction is LCF)
@@ -83,7 +105,11 @@ static void launch_encode_t(const CompressArgs& a, cudaStream_t s) {
     if (v && a.n_chunks >= kTwoPassChunks) {
         const uint32_t nb = umin32(a.n_chunks, umax32(1u, (uint32_t)size_res / div));
         encode_sizes_kernel<C><<<nb, kSizeThreads, 0, s>>>(a, nb);
-        v += 2;
+        const int l = v == 2 ? 1 : 0;
+        const uint32_t np = umin32((a.n_chunks + kPackWarps - 1) / kPackWarps, umax32(1u, (uint32_t)pack_res[l] / div));
+        if (l) encode_pack_kernel<C, true><<<np, kPackWarps * 32, pack_smem_bytes(), s>>>(a);
+        else encode_pack_kernel<C, false><<<np, kPackWarps * 32, pack_smem_bytes(), s>>>(a);
+        return;
     }
     uint32_t grid = umin32(a.n_chunks, (uint32_t)resident[v] / div);
     if (grid == 0) grid = 1;

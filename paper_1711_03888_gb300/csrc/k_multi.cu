@@ -66,10 +66,25 @@ __global__ void __launch_bounds__(kSizeThreads) encode_sizes_multi_kernel(MultiA
     encode_sizes_body<C>(sa, gridDim.x, sm);
 }
 
-// pass 2: persistent packing of the group's arrays at the offsets of pass 1
-// (or, LOOKBACK, one pass with the chunks' look-back)
+// pass 2: one warp per chunk at the offsets of pass 1
+template <int C>
+__global__ void __launch_bounds__(kPackWarps * 32, kPackMinBlocks) encode_pack_multi_kernel(MultiArgs m) {
+    extern __shared__ uint4 pack_smem[];
+    uint32_t* sm = reinterpret_cast<uint32_t*>(pack_smem);
+    __shared__ CompressArgs sa;
+    stage_args(m, sa);
+    if (sa.n == 0) return;
+    if (sa.st->raw) {
+        const uint64_t words = (sa.n + 3u) & ~(uint64_t)3u;
+        raw_copy_words(sa, 0, words, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, (uint64_t)gridDim.x * blockDim.x);
+        return;
+    }
+    encode_pack_warp<C, false>(sa, sm + (threadIdx.x >> 5) * kRoundBufWords);
+}
+
+// one pass: persistent blocks with the chunks' look-back
 #ifndef SZ_ENC_TWOPASS
-#define SZ_ENC_TWOPASS 0
+#define SZ_ENC_TWOPASS 1
 #endif
 template <int C>
 __global__ void __launch_bounds__(EncShape<C>::kThreads, EncShape<C>::kMinBlocks) encode_multi_kernel(MultiArgs m) {
@@ -87,8 +102,7 @@ __global__ void __launch_bounds__(EncShape<C>::kThreads, EncShape<C>::kMinBlocks
         raw_copy_words(sa, 0, words, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, (uint64_t)gridDim.x * blockDim.x);
         return;
     }
-    encode_array_pipelined<C, NT, false, !SZ_ENC_TWOPASS>(sa, reinterpret_cast<uint32_t*>(dyn_smem), esm, s_c,
-                                                          &s_prev);
+    encode_array_pipelined<C, NT, false, true>(sa, reinterpret_cast<uint32_t*>(dyn_smem), esm, s_c, &s_prev);
 }
 
 constexpr uint32_t kMultiC[4] = {2048u, 4096u, 8192u, 16384u};
@@ -96,6 +110,10 @@ const void* const kEncMulti[4] = {(const void*)encode_multi_kernel<2048>, (const
                                   (const void*)encode_multi_kernel<8192>, (const void*)encode_multi_kernel<16384>};
 constexpr int kEncThreads[4] = {EncShape<2048>::kThreads, EncShape<4096>::kThreads, EncShape<8192>::kThreads,
                                 EncShape<16384>::kThreads};
+const void* const kPackMulti[4] = {(const void*)encode_pack_multi_kernel<2048>,
+                                   (const void*)encode_pack_multi_kernel<4096>,
+                                   (const void*)encode_pack_multi_kernel<8192>,
+                                   (const void*)encode_pack_multi_kernel<16384>};
 const void* const kSizesMulti[4] = {(const void*)encode_sizes_multi_kernel<2048>,
                                     (const void*)encode_sizes_multi_kernel<4096>,
                                     (const void*)encode_sizes_multi_kernel<8192>,
@@ -125,7 +143,7 @@ int multi_compress_launches(const CompressArgs* d_args, const MultiGroup* groups
         if (groups[i].max_chunks > max_nc) max_nc = groups[i].max_chunks;
         if (groups[i].C > maxC) maxC = groups[i].C;
     }
-    static int quant_res[4] = {0, 0, 0, 0}, enc_res[4] = {0, 0, 0, 0}, size_res = 0;
+    static int quant_res[4] = {0, 0, 0, 0}, enc_res[4] = {0, 0, 0, 0}, size_res = 0, pack_res = 0;
     static bool configured = false;
     if (!configured) {
         cudaFuncSetAttribute(codebook_multi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCbFastBytes);
@@ -144,6 +162,10 @@ int multi_compress_launches(const CompressArgs* d_args, const MultiGroup* groups
         }
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&size_res, kSizesMulti[1], kSizeThreads, 0);
         size_res = (size_res > 0 ? size_res : 1) * sm_count();
+        for (int j = 0; j < 4; ++j)
+            cudaFuncSetAttribute(kPackMulti[j], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pack_smem_bytes());
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pack_res, kPackMulti[1], kPackWarps * 32, pack_smem_bytes());
+        pack_res = (pack_res > 0 ? pack_res : 1) * sm_count();
         configured = true;
     }
     auto set = [](KernelLaunch& L, const void* f, uint32_t gx, uint32_t gy, uint32_t bx, size_t smem, int phase,
@@ -174,11 +196,17 @@ int multi_compress_launches(const CompressArgs* d_args, const MultiGroup* groups
         if (SZ_ENC_TWOPASS)
             set(out[k++], kSizesMulti[j], umin32(mc, (uint32_t)(sshare > 0 ? sshare : 1)), groups[i].count,
                 kSizeThreads, 0, SZ_PHASE_ENCODE_SIZES, d_args, groups[i].first);
-        const int share = enc_res[j] / (int)groups[i].count;
-        const uint32_t per = umin32(mc, (uint32_t)(share > 0 ? share : 1));
         if (k >= max_out) return -1;
-        set(out[k++], kEncMulti[j], per, groups[i].count, kEncThreads[j], enc_smem_bytes((int)kMultiC[j]),
-            SZ_PHASE_ENCODE, d_args, groups[i].first);
+        if (SZ_ENC_TWOPASS) {
+            const int pshare = pack_res / (int)groups[i].count;
+            set(out[k++], kPackMulti[j], umin32((mc + kPackWarps - 1) / kPackWarps, (uint32_t)(pshare > 0 ? pshare : 1)),
+                groups[i].count, kPackWarps * 32, pack_smem_bytes(), SZ_PHASE_ENCODE, d_args, groups[i].first);
+        } else {
+            const int share = enc_res[j] / (int)groups[i].count;
+            const uint32_t per = umin32(mc, (uint32_t)(share > 0 ? share : 1));
+            set(out[k++], kEncMulti[j], per, groups[i].count, kEncThreads[j], enc_smem_bytes((int)kMultiC[j]),
+                SZ_PHASE_ENCODE, d_args, groups[i].first);
+        }
     }
     return k;
 }
