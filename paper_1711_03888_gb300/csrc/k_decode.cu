@@ -33,8 +33,13 @@ namespace szg {
 
 constexpr int kSetupThreads = 1024;
 constexpr int kDecThreads = kSubPerChunk;    // 64 threads per team
-constexpr int kMaxTeams = 8;
-constexpr int kDecBlock = kMaxTeams * kDecThreads;   // 512
+#ifndef SZ_DEC_TEAMS
+#define SZ_DEC_TEAMS 12
+#endif
+constexpr int kMaxTeams = SZ_DEC_TEAMS;
+// team t synchronises on named barrier t + 1; a CTA has barriers 0..15
+static_assert(kMaxTeams >= 1 && kMaxTeams <= 15, "one named barrier per team");
+constexpr int kDecBlock = kMaxTeams * kDecThreads;
 constexpr size_t kDecDynSmem = 208u * 1024u;         // second-level table (32 KB) + team regions
 
 struct SetupSmem {
@@ -291,18 +296,88 @@ struct DecSmem {
     uint32_t first[kMaxLen + 2], base[kMaxLen + 2];
     uint32_t ws32[kMaxTeams][2], ws32b[kMaxTeams][2];
     long long ws64[kMaxTeams][2];
+    unsigned long long mbar[kMaxTeams];   // each team's payload barrier
+    uint32_t mph[kMaxTeams];              // its current phase parity
 };
+
+// polls of a team's payload barrier before the copy counts as lost
+constexpr uint32_t kStageSpins = 1u << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// One arrival (the thread that issues the copy) plus the copy's bytes complete
+// a phase of a team's payload barrier.  The caller synchronises the block
+// before a team stages.
+__device__ __forceinline__ void init_stage_barriers(DecSmem& sm, int tid) {
+    if (tid < kMaxTeams) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&sm.mbar[tid])) : "memory");
+        sm.mph[tid] = 0u;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    for (uint32_t i = 0; i < kStageSpins; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// A chunk's payload (words: a multiple of 4, 16-byte aligned in global and
+// shared memory alike, as every chunk is padded to 128 bits) into the team's
+// stage: one thread issues a single 1-D bulk copy that completes on the team's
+// barrier, and the team waits for the barrier's phase.  The caller
+// team-synchronises afterwards and then calls stage_done.  Returns false
+// (E_TIMEOUT raised) if the copy never landed; the team then waits once more,
+// bounded, for it before giving up.
+__device__ __forceinline__ bool stage_chunk(const uint32_t* src, uint32_t* stage, uint32_t words, DecSmem& sm,
+                                            int team, int k, uint32_t* err) {
+    const uint32_t bar = smem_u32(&sm.mbar[team]);
+    const uint32_t ph = sm.mph[team];
+    if (k == 0) {
+        const uint32_t bytes = 4u * words;
+        // the team's earlier generic accesses to the stage come before the copy's writes
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+        if (bytes)
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    smem_u32(stage)),
+                "l"(__cvta_generic_to_global(src)), "r"(bytes), "r"(bar)
+                : "memory");
+    }
+    if (mbar_wait(bar, ph)) return true;
+    if (k == 0) raise_err(err, E_TIMEOUT);
+    mbar_wait(bar, ph);
+    return false;
+}
+
+// After the team barrier that follows stage_chunk: the next copy waits on the
+// barrier's other phase.
+__device__ __forceinline__ void stage_done(DecSmem& sm, int team, int k) {
+    if (k == 0) sm.mph[team] ^= 1u;
+}
 
 // dynamic shared memory: the second-level table, then one region per team
 constexpr size_t kLut2Bytes = sizeof(uint32_t) * kLut2Max;
 
 // Teams per block for chunks of C elements whose largest payload is max_cw
-// words: the most (up to 8 for C <= 4096, 4 for 8192, 2 for 16384) whose
-// region -- C value slots and the stage -- still stages the largest chunk;
-// a stream with chunks larger even for one team reads those from global memory.
-__device__ __forceinline__ int teams_for(uint32_t C, uint32_t max_cw) {
-    int t = C <= 4096 ? 8 : (C == 8192 ? 4 : 2);
-    while (t > 1 && ((uint32_t)((kDecDynSmem - kLut2Bytes) / 4) / (uint32_t)t & ~3u) < C + max_cw + 4u) --t;
+// words: the most (up to kMaxTeams) whose region -- the symbol or value slots
+// and the stage -- still stages the largest chunk; a stream with chunks larger
+// even for one team reads those from global memory.
+// LV streams keep the symbols as 16-bit words (C / 2 words) and need a stage
+// of at least C / 4 words, which carries the values out; LCF streams keep C
+// 32-bit slots.
+__device__ __forceinline__ int teams_for(uint32_t C, uint32_t max_cw, bool lcf) {
+    const uint32_t need = lcf ? C + max_cw + 4u : C / 2u + umax32(max_cw, C / 4u) + 4u;
+    int t = kMaxTeams;
+    while (t > 1 && (((uint32_t)((kDecDynSmem - kLut2Bytes) / 4) / (uint32_t)t) & ~3u) < need) --t;
     return t;
 }
 
@@ -352,6 +427,43 @@ __device__ __forceinline__ uint32_t decode_run(BitReader& br, const DecSmem& sm,
             }
         }
         *reinterpret_cast<uint4*>(&xs[swz(e0 + j4, gshift)]) = make_uint4(s[0], s[1], s[2], s[3]);
+    }
+    return ssum;
+}
+
+// The LV path's 16-bit symbol rows: row k (sub-stream k) holds G symbols as
+// G / 4 units of 8 bytes; unit u sits at u ^ (k / max(1, 16 / NU)) mod NU, so
+// the 16 rows a half-warp writes or reads at one unit index hit distinct banks.
+// (sh = log2(max(1, 16 / NU)), precomputed per stream)
+__device__ __forceinline__ uint32_t sym_unit(uint32_t u, uint32_t k, uint32_t NU, uint32_t sh) {
+    return u ^ ((k >> sh) & (NU - 1u));
+}
+// The value rows of a round: row k holds F 16-byte groups; group m sits at
+// m ^ (k / max(1, 8 / F)) mod F, free of conflicts for the row writes and for
+// the copy-out's reads alike.
+// (sh = log2(max(1, 8 / F)))
+__device__ __forceinline__ uint32_t val_unit(uint32_t m, uint32_t row, uint32_t F, uint32_t sh) {
+    return m ^ ((row >> sh) & (F - 1u));
+}
+
+// Phase 1 of one LV sub-stream: nsym symbols into the thread's 16-bit row.
+template <bool FULL>
+__device__ __forceinline__ uint32_t decode_run16(BitReader& br, const DecSmem& sm, const uint32_t* lut2,
+                                                 uint32_t l2_lo, uint32_t l2_n, const uint16_t* by_len, uint2* srow,
+                                                 uint32_t NU, uint32_t ush, uint32_t k, uint32_t nsym, uint32_t& nesc,
+                                                 bool& bad) {
+    uint32_t ssum = 0;
+    for (uint32_t j4 = 0; j4 < nsym; j4 += 4) {
+        uint32_t s[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            if (FULL || j4 + t < nsym) {
+                s[t] = decode_symbol(br, sm, lut2, l2_lo, l2_n, by_len, bad);
+                ssum += s[t];
+                nesc += (s[t] == 0u);
+            }
+        }
+        srow[sym_unit(j4 >> 2, k, NU, ush)] = make_uint2(s[0] | (s[1] << 16), s[2] | (s[3] << 16));
     }
     return ssum;
 }
@@ -418,7 +530,8 @@ __device__ __forceinline__ void load_dec_tables(const DecompressArgs& a, const D
 
 // One chunk by one team of 64 threads (thread k = sub-stream k): stage, decode,
 // escapes and prefix, reconstruct, store.  next: the chunk this team takes next
-// (L2 prefetch), or >= nc.  Returns false (and raises E_CORRUPT) on a bad chunk.
+// (L2 prefetch), or >= nc.  Returns false (and raises E_CORRUPT, or E_TIMEOUT
+// for a lost copy) on a bad chunk.
 // LCF: the symbols are second differences; see the reconstruction below.
 template <bool LCF>
 __device__ __forceinline__ bool decode_chunk_team(const DecArray& d, DecSmem& sm, const uint32_t* lut2,
@@ -429,7 +542,7 @@ __device__ __forceinline__ bool decode_chunk_team(const DecArray& d, DecSmem& sm
     const uint32_t cnt = (uint32_t)umin64(C, d.n - base);
     const uint64_t wb = d.cword[c], we = d.cword[c + 1];
     const uint64_t eb = d.cesc[c], ee = d.cesc[c + 1];
-    const bool hdr_bad = (wb > we || we > d.pw || eb > ee || ee > d.E || (wb & 3u));
+    const bool hdr_bad = (wb > we || we > d.pw || eb > ee || ee > d.E || ((wb | we) & 3u));
     const uint32_t e0 = k * G;
     const uint32_t nsym = e0 < cnt ? umin32(G, cnt - e0) : 0u;
     const uint32_t sl = d.sublen[c * kSubPerChunk + k];
@@ -442,16 +555,7 @@ __device__ __forceinline__ bool decode_chunk_team(const DecArray& d, DecSmem& sm
     // ---- stage the chunk payload; prefetch the team's next chunk into L2 --------
     const uint32_t cw_words = (uint32_t)(we - wb);
     const bool staged = cw_words <= stage_words;
-    if (staged) {
-        // asynchronous 16-byte copies, all in flight at once
-        const uint4* g4 = reinterpret_cast<const uint4*>(d.payload + wb);
-        const uint32_t s_base = (uint32_t)__cvta_generic_to_shared(stage);
-        for (uint32_t w4 = k; w4 < cw_words / 4; w4 += kDecThreads)
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s_base + 16u * w4),
-                         "l"(__cvta_generic_to_global(g4 + w4))
-                         : "memory");
-        asm volatile("cp.async.wait_all;" ::: "memory");
-    }
+    if (staged && !stage_chunk(d.payload + wb, stage, cw_words, sm, team, k, err)) return false;
     if (k == 0 && next < d.nc) {
         const uint64_t nb = d.cword[next], ne = d.cword[next + 1];
         if (nb < ne && ne <= d.pw && !(nb & 3u) && !(ne & 3u) && ne - nb < (1u << 24)) {
@@ -461,6 +565,7 @@ __device__ __forceinline__ bool decode_chunk_team(const DecArray& d, DecSmem& sm
         }
     }
     team_sync(team);
+    if (staged) stage_done(sm, team, k);
     // ---- phase 1: decode the sub-stream into symbols ----------------------------
     // (separate calls for the staged and the global source, so that the staged
     // reader's loads are shared-memory loads)
@@ -607,6 +712,143 @@ __device__ __forceinline__ bool decode_chunk_team(const DecArray& d, DecSmem& sm
     return true;
 }
 
+// One LV chunk by one team through 16-bit symbol rows (sym16: C / 2 words)
+// and the stage (stage_words >= C / 4): stage the payload (stage_chunk; a
+// chunk larger than the stage is read from global memory), decode
+// each sub-stream into its row, scan the escapes and the delta sums, then four
+// rounds: each thread rebuilds G / 4 values into its row of the stage (free
+// once the payload is decoded) and the team stores the quarter chunk with
+// coalesced 16-byte stores.  next: the chunk this team takes next (L2
+// prefetch), or >= nc.  Returns false (and raises E_CORRUPT) on a bad chunk.
+__device__ __forceinline__ bool decode_chunk_lv16(const DecArray& d, DecSmem& sm, const uint32_t* lut2,
+                                                  uint32_t* sym16, uint32_t* stage, uint32_t stage_words, int team,
+                                                  int k, uint64_t c, uint64_t next, uint32_t* err) {
+    const uint32_t C = d.C, G = d.G;
+    const uint32_t NU = G / 4u, F = G / 16u, VR = G / 4u;
+    const uint32_t gsh = d.gshift;                       // log2 G (5 .. 8)
+    const uint32_t ush = gsh >= 6 ? 0u : 6u - gsh;       // log2 max(1, 16 / NU)
+    const uint32_t vsh = gsh >= 7 ? 0u : 7u - gsh;       // log2 max(1, 8 / F)
+    const uint64_t base = c * C;
+    const uint32_t cnt = (uint32_t)umin64(C, d.n - base);
+    const uint64_t wb = d.cword[c], we = d.cword[c + 1];
+    const uint64_t eb = d.cesc[c], ee = d.cesc[c + 1];
+    const bool hdr_bad = (wb > we || we > d.pw || eb > ee || ee > d.E || ((wb | we) & 3u));
+    const uint32_t e0 = k * G;
+    const uint32_t nsym = e0 < cnt ? umin32(G, cnt - e0) : 0u;
+    const uint32_t sl = d.sublen[c * kSubPerChunk + k];
+    uint32_t tot_bits;
+    const uint32_t start = team_exclusive_scan<uint32_t>(sl, sm.ws32[team], team, k, &tot_bits);
+    if (hdr_bad || (uint64_t)tot_bits > 32ull * (we - wb)) {
+        if (k == 0) raise_err(err, E_CORRUPT);
+        return false;
+    }
+    // ---- stage the chunk payload; prefetch the team's next chunk into L2 --------
+    const uint32_t cw_words = (uint32_t)(we - wb);
+    const bool staged = cw_words <= stage_words;
+    if (staged && !stage_chunk(d.payload + wb, stage, cw_words, sm, team, k, err)) return false;
+    if (k == 0 && next < d.nc) {
+        const uint64_t nb = d.cword[next], ne = d.cword[next + 1];
+        if (nb < ne && ne <= d.pw && !(nb & 3u) && !(ne & 3u) && ne - nb < (1u << 24)) {
+            const uint32_t* p = d.payload + nb;
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(__cvta_generic_to_global(p)),
+                         "r"((uint32_t)(4 * (ne - nb)))
+                         : "memory");
+        }
+    }
+    team_sync(team);
+    if (staged) stage_done(sm, team, k);
+    // ---- phase 1: the sub-stream's symbols into the thread's row -----------------
+    uint2* srow = reinterpret_cast<uint2*>(sym16) + (size_t)k * NU;
+    uint32_t nesc = 0, ssum, end_bit;
+    bool bad = false;
+    if (staged) {
+        BitReader br;
+        br.init(stage, start, cw_words);
+        ssum = nsym == G ? decode_run16<true>(br, sm, lut2, d.l2_lo, d.l2_n, d.by_len, srow, NU, ush, k, nsym, nesc, bad)
+                         : decode_run16<false>(br, sm, lut2, d.l2_lo, d.l2_n, d.by_len, srow, NU, ush, k, nsym, nesc, bad);
+        end_bit = br.bit_pos();
+    } else {
+        BitReader br;
+        br.init(d.payload + wb, start, cw_words);
+        ssum = decode_run16<false>(br, sm, lut2, d.l2_lo, d.l2_n, d.by_len, srow, NU, ush, k, nsym, nesc, bad);
+        end_bit = br.bit_pos();
+    }
+    bad = bad || end_bit - start != sl;
+    // ---- escapes and the team-wide prefix (the stage is free after these barriers) --
+    uint32_t tot_esc;
+    const uint32_t eoff =
+        team_exclusive_scan<uint32_t>(nesc + (bad ? 0x10000u : 0u), sm.ws32b[team], team, k, &tot_esc);
+    if ((tot_esc >> 16) || eb + tot_esc != ee) {
+        if (k == 0) raise_err(err, E_CORRUPT);
+        return false;
+    }
+    long long sum = (long long)ssum - (long long)kRadius * (long long)(nsym - nesc);
+    for (uint32_t t = 0; t < nesc; ++t)
+        sum += *reinterpret_cast<const long long*>(d.escs + (uint64_t)kEscBytes * (eb + eoff + t));
+    long long tot_sum;
+    const long long pre = team_exclusive_scan<long long>(sum, sm.ws64[team], team, k, &tot_sum);
+    // ---- phase 2: four rounds of G / 4 values through the stage -------------------
+    const float D = d.D;
+    const long long q_fast = (1ll << 24) - (long long)G * (kRadius - 1);
+    long long q = d.anchor[c] + pre;
+    const bool fast = nesc == 0 && q >= -q_fast && q <= q_fast;
+    uint64_t ecur = eb + eoff;
+    float* dst = d.out + base;
+    const bool full_vec = d.vec && cnt == C;
+    float4* tr = reinterpret_cast<float4*>(stage);
+    const uint32_t fsh = 31 - __clz(F);
+    for (uint32_t r = 0; r < 4; ++r) {
+        if (fast) {
+            // |q| stays within 2^24: exact in 32-bit integers and in one int -> float
+            int qi = (int)q;
+            for (uint32_t m = 0; m < F; ++m) {
+                const uint2 u = srow[sym_unit(r * F + m, k, NU, ush)];
+                qi += (int)(u.x & 0xffffu) - kRadius; const float v0 = __fmul_rn((float)qi, D);
+                qi += (int)(u.x >> 16) - kRadius;     const float v1 = __fmul_rn((float)qi, D);
+                qi += (int)(u.y & 0xffffu) - kRadius; const float v2 = __fmul_rn((float)qi, D);
+                qi += (int)(u.y >> 16) - kRadius;     const float v3 = __fmul_rn((float)qi, D);
+                tr[(k << fsh) + val_unit(m, k, F, vsh)] = make_float4(v0, v1, v2, v3);
+            }
+            q = qi;
+        } else {
+            for (uint32_t m = 0; m < F; ++m) {
+                const uint2 u = srow[sym_unit(r * F + m, k, NU, ush)];
+                const uint32_t sy[4] = {u.x & 0xffffu, u.x >> 16, u.y & 0xffffu, u.y >> 16};
+                float v[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    v[t] = 0.0f;
+                    if (r * VR + 4 * m + t < nsym) {
+                        if (sy[t] != 0u) {
+                            q += (long long)sy[t] - kRadius;
+                            v[t] = recon_f(q, D);
+                        } else {
+                            const uint8_t* rec = d.escs + (uint64_t)kEscBytes * ecur++;
+                            q += *reinterpret_cast<const long long*>(rec);
+                            v[t] = (rd32(rec + 12) & 1u) ? __uint_as_float(rd32(rec + 8)) : recon_f(q, D);
+                        }
+                    }
+                }
+                tr[(k << fsh) + val_unit(m, k, F, vsh)] = make_float4(v[0], v[1], v[2], v[3]);
+            }
+        }
+        team_sync(team);
+        for (uint32_t g = k; g < kDecThreads * F; g += kDecThreads) {
+            const uint32_t row = g >> fsh, m = g & (F - 1u);
+            const float4 val = tr[(row << fsh) + val_unit(m, row, F, vsh)];
+            const uint32_t e = row * G + r * VR + 4 * m;
+            if (full_vec) {
+                *reinterpret_cast<float4*>(dst + e) = val;
+            } else {
+                const float vv[4] = {val.x, val.y, val.z, val.w};
+                for (int j = 0; j < 4 && e + j < cnt; ++j) dst[e + j] = vv[j];
+            }
+        }
+        team_sync(team);
+    }
+    return true;
+}
+
 // LCF streams run their team loops in separate, non-inlined functions, so the
 // LV path the kernels inline keeps its own code and registers (the stream
 // parameters are passed by value: a reference would pin the caller's copy in
@@ -637,12 +879,12 @@ __device__ __noinline__ void decode_team_lcf_counted(const DecArray d, DecSmem& 
     }
 }
 
-// team region of a block decoding chunks of C elements: C value slots and the
-// payload stage
+// team region of a block: `slots` words of symbol (or value) slots -- C / 2
+// for LV streams' 16-bit rows, C for LCF -- then the payload stage
 __device__ __forceinline__ uint32_t* team_region(uint4* dyn, int teams, int team, uint32_t* stage_words,
-                                                 uint32_t C) {
+                                                 uint32_t slots) {
     const uint32_t region_words = ((uint32_t)((kDecDynSmem - kLut2Bytes) / 4) / teams) & ~3u;
-    *stage_words = region_words - C;      // multiple of 4
+    *stage_words = region_words - slots;  // multiple of 4
     return reinterpret_cast<uint32_t*>(dyn) + kLut2Max + (size_t)team * region_words;
 }
 
@@ -663,13 +905,15 @@ __global__ void __launch_bounds__(kDecBlock, 1) decode_kernel(DecompressArgs a) 
         return;
     }
     uint32_t* lut2 = reinterpret_cast<uint32_t*>(dyn_smem);
+    init_stage_barriers(sm, tid);
     load_dec_tables(a, d, sm, lut2);
     __syncthreads();
-    const int teams = teams_for(d.C, d.max_cw);
+    const int teams = teams_for(d.C, d.max_cw, d.lcf);
     const int team = tid / kDecThreads, k = tid % kDecThreads;
     if (team >= teams) return;
     uint32_t stage_words;
-    uint32_t* xs = team_region(dyn_smem, teams, team, &stage_words, d.C);
+    const uint32_t slots = d.lcf ? d.C : d.C / 2;
+    uint32_t* xs = team_region(dyn_smem, teams, team, &stage_words, slots);
     const uint64_t stride = (uint64_t)gridDim.x * teams;
     if (d.lcf) {
         decode_team_lcf_strided(d, sm, lut2, xs, stage_words, team, k, (uint64_t)blockIdx.x * teams + team, stride,
@@ -677,8 +921,7 @@ __global__ void __launch_bounds__(kDecBlock, 1) decode_kernel(DecompressArgs a) 
         return;
     }
     for (uint64_t c = (uint64_t)blockIdx.x * teams + team; c < d.nc; c += stride)
-        if (!decode_chunk_team<false>(d, sm, lut2, xs, xs + d.C, stage_words, team, k, c, c + stride, a.err))
-            return;
+        if (!decode_chunk_lv16(d, sm, lut2, xs, xs + slots, stage_words, team, k, c, c + stride, a.err)) return;
 }
 
 // ---- batched decompression ---------------------------------------------------
@@ -753,6 +996,7 @@ __global__ void __launch_bounds__(kDecBlock, 1) decode_multi_kernel(const Decomp
     const int tid = threadIdx.x;
     const uint64_t F = uoff[k];
     if (F == 0) return;
+    init_stage_barriers(sm, tid);      // the stream loop's first block barrier publishes them
     uint32_t* lut2 = reinterpret_cast<uint32_t*>(dyn_smem);
     const int team = tid / kDecThreads, kk = tid % kDecThreads;
     uint32_t i = find_stream(uoff, k, F * blockIdx.x / gridDim.x);
@@ -773,10 +1017,11 @@ __global__ void __launch_bounds__(kDecBlock, 1) decode_multi_kernel(const Decomp
             load_dec_tables(sa, d, sm, lut2);
             __syncthreads();
         }
-        const int teams = raw ? kMaxTeams : teams_for(d.C, d.max_cw);
+        const int teams = raw ? kMaxTeams : teams_for(d.C, d.max_cw, d.lcf);
         if (team >= teams) continue;
         uint32_t stage_words = 0;
-        uint32_t* xs = raw ? nullptr : team_region(dyn_smem, teams, team, &stage_words, d.C);
+        const uint32_t slots = d.lcf ? d.C : d.C / 2;
+        uint32_t* xs = raw ? nullptr : team_region(dyn_smem, teams, team, &stage_words, slots);
         if (!raw && d.lcf) {
             decode_team_lcf_counted(d, sm, lut2, xs, stage_words, team, kk, ctr + i, nu, s_unit, sa.err);
             continue;
@@ -797,8 +1042,8 @@ __global__ void __launch_bounds__(kDecBlock, 1) decode_multi_kernel(const Decomp
                 uint32_t* dst = reinterpret_cast<uint32_t*>(sa.out);
                 const uint64_t e1 = umin64(d.n, ((uint64_t)u + 1) * kRawUnit);
                 for (uint64_t e = (uint64_t)u * kRawUnit + kk; e < e1; e += kDecThreads) dst[e] = __ldg(d.payload + e);
-            } else if (!decode_chunk_team<false>(d, sm, lut2, xs, xs + d.C, stage_words, team, kk, u,
-                                                 un < nu ? un : ~0ull, sa.err)) {
+            } else if (!decode_chunk_lv16(d, sm, lut2, xs, xs + slots, stage_words, team, kk, u,
+                                          un < nu ? un : ~0ull, sa.err)) {
                 break;
             }
             u = un;
