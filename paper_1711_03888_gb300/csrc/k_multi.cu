@@ -31,7 +31,18 @@ __global__ void __launch_bounds__(256) range_multi_kernel(MultiArgs m) {
     range_body<256>(sa, blockIdx.x, gridDim.x);
 }
 
-__global__ void __launch_bounds__(kQuantThreads) quant_multi_kernel(MultiArgs m) {
+// One input stage and four blocks per SM (64 registers, a few spills).
+// Measured on GB300, six 2^27 arrays at rel eb 1e-3 / 1e-4 / 1e-5, quantize ms:
+// 1.80 / 1.82 / 4.14 against 2.17 / 2.20 / 4.55 with two stages and no
+// register bound (94 registers, two blocks per SM) and 1.87 / 1.88 / 4.48 with
+// two stages at three blocks per SM.
+#ifndef SZ_QMULTI_STAGES
+#define SZ_QMULTI_STAGES 1
+#endif
+#ifndef SZ_QMULTI_MINB
+#define SZ_QMULTI_MINB 4
+#endif
+__global__ void __launch_bounds__(kQuantThreads, SZ_QMULTI_MINB) quant_multi_kernel(MultiArgs m) {
     __shared__ uint32_t sh[kWinWords];
     __shared__ uint32_t s_esc[kQuantThreads / 32];
     __shared__ CompressArgs sa;
@@ -43,7 +54,8 @@ __global__ void __launch_bounds__(kQuantThreads) quant_multi_kernel(MultiArgs m)
     hist_window_zero(sh);
     __syncthreads();
     if (((uintptr_t)sa.in & 15u) == 0)
-        quant_array_staged<true>(sa, P, blockIdx.x, gridDim.x, reinterpret_cast<float*>(stage4), sh, s_esc);
+        quant_array_staged<true, false, SZ_QMULTI_STAGES>(sa, P, blockIdx.x, gridDim.x, reinterpret_cast<float*>(stage4),
+                                                            sh, s_esc);
     else
         quant_array_global<true>(sa, P, blockIdx.x, gridDim.x, sh, s_esc);
     hist_window_flush(sh, sa.hist);
@@ -148,10 +160,10 @@ int multi_compress_launches(const CompressArgs* d_args, const MultiGroup* groups
     if (!configured) {
         cudaFuncSetAttribute(codebook_multi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCbFastBytes);
         cudaFuncSetAttribute(quant_multi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)quant_stage_bytes(16384));
+                             (int)quant_stage_bytes(16384, SZ_QMULTI_STAGES));
         for (int j = 0; j < 4; ++j) {
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&quant_res[j], quant_multi_kernel, kQuantThreads,
-                                                          quant_stage_bytes(kMultiC[j]));
+                                                          quant_stage_bytes(kMultiC[j], SZ_QMULTI_STAGES));
             quant_res[j] = (quant_res[j] > 0 ? quant_res[j] : 1) * sm_count();
         }
         for (int j = 0; j < 4; ++j) {
@@ -181,7 +193,7 @@ int multi_compress_launches(const CompressArgs* d_args, const MultiGroup* groups
     set(out[k++], (const void*)range_multi_kernel, kRangeBlocks, count, 256, 0, SZ_PHASE_RANGE, d_args, first);
     const int jq = maxC == 2048 ? 0 : maxC == 4096 ? 1 : maxC == 8192 ? 2 : 3;
     set(out[k++], (const void*)quant_multi_kernel, umin32(max_nc, (uint32_t)quant_res[jq]), count,
-        kQuantThreads, quant_stage_bytes(maxC), SZ_PHASE_QUANT, d_args, first);
+        kQuantThreads, quant_stage_bytes(maxC, SZ_QMULTI_STAGES), SZ_PHASE_QUANT, d_args, first);
     set(out[k++], (const void*)codebook_multi_kernel, 1, count, kCbBlock, kCbFastBytes, SZ_PHASE_CODEBOOK, d_args,
         first);
     for (int i = 0; i < ngroups; ++i) {

@@ -41,8 +41,8 @@ __host__ __device__ constexpr uint32_t quant_flush_every(uint32_t C) { return 65
 // dynamic shared memory of the staged quantize loop: NSTAGE stages of C + 4 floats.
 // Measured on GB300 (2^27 elements, C = 4096): the stand-alone kernel (64
 // registers) runs 4 blocks per SM with one stage (48 KB per block) against 3
-// with two, 0.306 vs 0.329 ms; the batched kernel (80 registers, 3 blocks
-// whatever the stage count) keeps two.
+// with two, 0.306 vs 0.329 ms; the batched kernel does the same under a
+// launch bound for four blocks.
 constexpr size_t quant_stage_bytes(uint32_t C, int NSTAGE = 2) { return (size_t)NSTAGE * 4u * ((size_t)C + 4u); }
 
 __device__ __forceinline__ void hist_add(uint32_t code, uint32_t* sh, uint32_t* gh) {
