@@ -10,23 +10,25 @@
 // resolves is found by a short walk up the limits from that shortest length.
 // It also records the stream's largest chunk payload.
 //
-// decode (one persistent block per SM, split into independent 64-thread
-// "chunk teams" with their own named barrier): a team takes one chunk at a
-// time.  It stages the chunk's payload in shared memory (coalesced 128-bit
-// copies) and asks L2 to prefetch its next chunk; a block runs as many teams
-// as leave each a stage that holds the stream's largest chunk (a chunk larger
-// even for one team is read from global memory).  Thread k decodes sub-stream k (G
-// symbols) from its start bit (team scan of the sub-stream bit lengths) into
-// a swizzled shared buffer of deltas.  A team scan of the per-thread delta
-// sums plus the chunk anchor gives each thread its starting lattice value
-// (a10: the block-wide prefix scan; the anchor replaces the device-wide
-// part).  Each thread then rebuilds its values x' = RN32(q*D) (a11) -- in
-// 32-bit integers when no escape occurs and |q| provably stays within 2^24 --
-// and the chunk leaves with 128-bit coalesced stores.  Every table entry and
-// payload word is bounds-checked against in_bytes; a bad stream sets
-// E_CORRUPT.  Streams with the LCF predictor (second differences, two anchors
-// per chunk) take a second team scan for the entry state of each sub-stream
-// and 64-bit reconstruction, in non-inlined functions of their own.
+// decode (one persistent block per SM, split into up to twelve independent
+// 64-thread "chunk teams", each with its own named barrier and mbarrier): a
+// team takes one chunk at a time.  One thread stages the chunk's payload in
+// shared memory with a single 1-D bulk copy and asks L2 to prefetch the team's
+// next chunk; a block runs as many teams as leave each a stage that holds the
+// stream's largest chunk (a chunk larger even for one team is read from
+// global memory).  Thread k decodes sub-stream k (G symbols) from its start
+// bit (team scan of the sub-stream bit lengths) into a row of 16-bit symbols,
+// one table load per symbol.  A team scan of the per-thread delta sums plus
+// the chunk anchor gives each thread its starting lattice value (a10: the
+// block-wide prefix scan; the anchor replaces the device-wide part).  Each
+// thread then rebuilds its values x' = RN32(q*D) (a11) -- in 32-bit integers
+// when no escape occurs and |q| provably stays within 2^24 -- a quarter of its
+// run at a time into the now free stage, from which the team stores the
+// quarter chunk with 128-bit coalesced stores.  Every table entry and payload
+// word is bounds-checked against in_bytes; a bad stream sets E_CORRUPT.
+// Streams with the LCF predictor (second differences, two anchors per chunk)
+// keep 32-bit slots, take a second team scan for the entry state of each
+// sub-stream and 64-bit reconstruction, in non-inlined functions of their own.
 #include "sz_blocksort.cuh"
 
 namespace szg {
@@ -40,7 +42,7 @@ constexpr int kMaxTeams = SZ_DEC_TEAMS;
 // team t synchronises on named barrier t + 1; a CTA has barriers 0..15
 static_assert(kMaxTeams >= 1 && kMaxTeams <= 15, "one named barrier per team");
 constexpr int kDecBlock = kMaxTeams * kDecThreads;
-constexpr size_t kDecDynSmem = 208u * 1024u;         // second-level table (32 KB) + team regions
+constexpr size_t kDecDynSmem = 224u * 1024u;         // both lookup tables (48 KB) + team regions
 
 struct SetupSmem {
     RadixSmem rs;
@@ -291,7 +293,6 @@ __device__ __forceinline__ T team_exclusive_scan(T v, T* ws, int team, int k, T*
 }
 
 struct DecSmem {
-    uint32_t lut[1 << kLutBits];          // sym << 8 | len for codes of <= 12 bits, else 0
     uint32_t lim[kMaxLen + 2];            // left-justified (24-bit) end of each length's codes
     uint32_t first[kMaxLen + 2], base[kMaxLen + 2];
     uint32_t ws32[kMaxTeams][2], ws32b[kMaxTeams][2];
@@ -364,8 +365,12 @@ __device__ __forceinline__ void stage_done(DecSmem& sm, int team, int k) {
     if (k == 0) sm.mph[team] ^= 1u;
 }
 
-// dynamic shared memory: the second-level table, then one region per team
-constexpr size_t kLut2Bytes = sizeof(uint32_t) * kLut2Max;
+// dynamic shared memory: the lookup tables (the 12-bit first level, then the
+// second level's window, as the codebook lays them out in global memory),
+// then one region per team
+constexpr uint32_t kTabWords = (1u << kLutBits) + kLut2Max;
+constexpr size_t kTabBytes = sizeof(uint32_t) * kTabWords;
+constexpr uint32_t kRegionPool = (uint32_t)((kDecDynSmem - kTabBytes) / 4);   // words for the team regions
 
 // Teams per block for chunks of C elements whose largest payload is max_cw
 // words: the most (up to kMaxTeams) whose region -- the symbol or value slots
@@ -377,33 +382,33 @@ constexpr size_t kLut2Bytes = sizeof(uint32_t) * kLut2Max;
 __device__ __forceinline__ int teams_for(uint32_t C, uint32_t max_cw, bool lcf) {
     const uint32_t need = lcf ? C + max_cw + 4u : C / 2u + umax32(max_cw, C / 4u) + 4u;
     int t = kMaxTeams;
-    while (t > 1 && (((uint32_t)((kDecDynSmem - kLut2Bytes) / 4) / (uint32_t)t) & ~3u) < need) --t;
+    while (t > 1 && ((kRegionPool / (uint32_t)t) & ~3u) < need) --t;
     return t;
 }
 
 // A code longer than the second level covers: walk the left-justified limits
-// from `len` (the shortest length under the code's prefix).
-__device__ __noinline__ uint32_t decode_long(uint32_t w24, uint32_t len, const DecSmem& sm, const uint16_t* by_len,
-                                             bool& bad) {
+// from `len` (the shortest length under the code's prefix).  Returns
+// sym << 8 | len, or 0 for a window that starts no code (len is never 0).
+__device__ __noinline__ uint32_t decode_long(uint32_t w24, uint32_t len, const DecSmem& sm, const uint16_t* by_len) {
     while (len <= (uint32_t)kMaxLen && w24 >= sm.lim[len]) ++len;
-    if (len > (uint32_t)kMaxLen) {
-        bad = true;
-        return 0u;
-    }
+    if (len > (uint32_t)kMaxLen) return 0u;
     return ((uint32_t)by_len[sm.base[len] + (w24 >> (kMaxLen - len)) - sm.first[len]] << 8) | len;
 }
 
-// One symbol: the 12-bit direct lookup and the 16-bit second level are read
-// together (independent loads, no divergent branch for the tenth of symbols
-// with longer codes); the walk takes codes beyond 16 bits.
-__device__ __forceinline__ uint32_t decode_symbol(BitReader& br, const DecSmem& sm, const uint32_t* lut2,
+// One symbol, one table load: a window whose 16-bit prefix falls in the
+// second level's range (which starts where the codes of up to 12 bits end)
+// reads the second level, any other the first; both resolve codes of up to
+// 16 bits and mark longer ones with the shortest length under the prefix, for
+// the walk.
+__device__ __forceinline__ uint32_t decode_symbol(BitReader& br, const DecSmem& sm, const uint32_t* tab,
                                                   uint32_t l2_lo, uint32_t l2_n, const uint16_t* by_len, bool& bad) {
     const uint32_t w = br.peek();
-    const uint32_t e1 = sm.lut[w >> (32 - kLutBits)];
     const uint32_t i2 = (w >> (32 - kLut2Bits)) - l2_lo;   // wraps above l2_n below the range
-    const uint32_t e2 = i2 < l2_n ? lut2[i2] : e1;
-    uint32_t ent = (e1 & 255u) ? e1 : e2;
-    if ((ent & 255u) == 0u) ent = decode_long(w >> (32 - kMaxLen), ent >> 8, sm, by_len, bad);
+    uint32_t ent = tab[i2 < l2_n ? (1u << kLutBits) + i2 : (w >> (32 - kLutBits))];
+    if ((ent & 255u) == 0u) {
+        ent = decode_long(w >> (32 - kMaxLen), ent >> 8, sm, by_len);
+        bad = bad || ent == 0u;
+    }
     br.consume(ent & 255u);
     return ent >> 8;
 }
@@ -412,7 +417,7 @@ __device__ __forceinline__ uint32_t decode_symbol(BitReader& br, const DecSmem& 
 // symbols: 0 marks an escape).  Returns the sum of the symbols and counts the
 // escapes; the reader's end position checks the sub-stream length.
 template <bool FULL>
-__device__ __forceinline__ uint32_t decode_run(BitReader& br, const DecSmem& sm, const uint32_t* lut2, uint32_t l2_lo,
+__device__ __forceinline__ uint32_t decode_run(BitReader& br, const DecSmem& sm, const uint32_t* tab, uint32_t l2_lo,
                                                uint32_t l2_n, const uint16_t* by_len, uint32_t* xs, uint32_t e0,
                                                uint32_t gshift, uint32_t nsym, uint32_t& nesc, bool& bad) {
     uint32_t ssum = 0;
@@ -421,7 +426,7 @@ __device__ __forceinline__ uint32_t decode_run(BitReader& br, const DecSmem& sm,
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
             if (FULL || j4 + t < nsym) {
-                s[t] = decode_symbol(br, sm, lut2, l2_lo, l2_n, by_len, bad);
+                s[t] = decode_symbol(br, sm, tab, l2_lo, l2_n, by_len, bad);
                 ssum += s[t];
                 nesc += (s[t] == 0u);
             }
@@ -448,7 +453,7 @@ __device__ __forceinline__ uint32_t val_unit(uint32_t m, uint32_t row, uint32_t 
 
 // Phase 1 of one LV sub-stream: nsym symbols into the thread's 16-bit row.
 template <bool FULL>
-__device__ __forceinline__ uint32_t decode_run16(BitReader& br, const DecSmem& sm, const uint32_t* lut2,
+__device__ __forceinline__ uint32_t decode_run16(BitReader& br, const DecSmem& sm, const uint32_t* tab,
                                                  uint32_t l2_lo, uint32_t l2_n, const uint16_t* by_len, uint2* srow,
                                                  uint32_t NU, uint32_t ush, uint32_t k, uint32_t nsym, uint32_t& nesc,
                                                  bool& bad) {
@@ -458,7 +463,7 @@ __device__ __forceinline__ uint32_t decode_run16(BitReader& br, const DecSmem& s
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
             if (FULL || j4 + t < nsym) {
-                s[t] = decode_symbol(br, sm, lut2, l2_lo, l2_n, by_len, bad);
+                s[t] = decode_symbol(br, sm, tab, l2_lo, l2_n, by_len, bad);
                 ssum += s[t];
                 nesc += (s[t] == 0u);
             }
@@ -515,12 +520,10 @@ __device__ __forceinline__ void dec_array(const DecompressArgs& a, DecArray& d) 
 // Block-wide: the stream's first- and second-level tables and limits into
 // shared memory.
 __device__ __forceinline__ void load_dec_tables(const DecompressArgs& a, const DecArray& d, DecSmem& sm,
-                                                uint32_t* lut2) {
+                                                uint32_t* tab) {
     const int tid = threadIdx.x;
     const ArrayState* st = a.st;
-    for (uint32_t i = tid; i < (1u << kLutBits) / 4; i += blockDim.x)
-        reinterpret_cast<uint4*>(sm.lut)[i] = __ldg(reinterpret_cast<const uint4*>(a.lut) + i);
-    for (uint32_t i = tid; i < d.l2_n; i += blockDim.x) lut2[i] = __ldg(a.lut + (1u << kLutBits) + i);
+    for (uint32_t i = tid; i < (1u << kLutBits) + d.l2_n; i += blockDim.x) tab[i] = __ldg(a.lut + i);
     if (tid < kMaxLen + 2) {
         sm.first[tid] = st->first[tid];
         sm.base[tid] = st->base[tid];
@@ -534,7 +537,7 @@ __device__ __forceinline__ void load_dec_tables(const DecompressArgs& a, const D
 // for a lost copy) on a bad chunk.
 // LCF: the symbols are second differences; see the reconstruction below.
 template <bool LCF>
-__device__ __forceinline__ bool decode_chunk_team(const DecArray& d, DecSmem& sm, const uint32_t* lut2,
+__device__ __forceinline__ bool decode_chunk_team(const DecArray& d, DecSmem& sm, const uint32_t* tab,
                                                   uint32_t* xs, uint32_t* stage, uint32_t stage_words, int team,
                                                   int k, uint64_t c, uint64_t next, uint32_t* err) {
     const uint32_t C = d.C, G = d.G, gshift = d.gshift;
@@ -574,13 +577,13 @@ __device__ __forceinline__ bool decode_chunk_team(const DecArray& d, DecSmem& sm
     if (staged) {
         BitReader br;
         br.init(stage, start, cw_words);
-        ssum = nsym == G ? decode_run<true>(br, sm, lut2, d.l2_lo, d.l2_n, d.by_len, xs, e0, gshift, nsym, nesc, bad)
-                         : decode_run<false>(br, sm, lut2, d.l2_lo, d.l2_n, d.by_len, xs, e0, gshift, nsym, nesc, bad);
+        ssum = nsym == G ? decode_run<true>(br, sm, tab, d.l2_lo, d.l2_n, d.by_len, xs, e0, gshift, nsym, nesc, bad)
+                         : decode_run<false>(br, sm, tab, d.l2_lo, d.l2_n, d.by_len, xs, e0, gshift, nsym, nesc, bad);
         end_bit = br.bit_pos();
     } else {
         BitReader br;
         br.init(d.payload + wb, start, cw_words);
-        ssum = decode_run<false>(br, sm, lut2, d.l2_lo, d.l2_n, d.by_len, xs, e0, gshift, nsym, nesc, bad);
+        ssum = decode_run<false>(br, sm, tab, d.l2_lo, d.l2_n, d.by_len, xs, e0, gshift, nsym, nesc, bad);
         end_bit = br.bit_pos();
     }
     bad = bad || end_bit - start != sl;
@@ -720,7 +723,7 @@ __device__ __forceinline__ bool decode_chunk_team(const DecArray& d, DecSmem& sm
 // once the payload is decoded) and the team stores the quarter chunk with
 // coalesced 16-byte stores.  next: the chunk this team takes next (L2
 // prefetch), or >= nc.  Returns false (and raises E_CORRUPT) on a bad chunk.
-__device__ __forceinline__ bool decode_chunk_lv16(const DecArray& d, DecSmem& sm, const uint32_t* lut2,
+__device__ __forceinline__ bool decode_chunk_lv16(const DecArray& d, DecSmem& sm, const uint32_t* tab,
                                                   uint32_t* sym16, uint32_t* stage, uint32_t stage_words, int team,
                                                   int k, uint64_t c, uint64_t next, uint32_t* err) {
     const uint32_t C = d.C, G = d.G;
@@ -764,13 +767,13 @@ __device__ __forceinline__ bool decode_chunk_lv16(const DecArray& d, DecSmem& sm
     if (staged) {
         BitReader br;
         br.init(stage, start, cw_words);
-        ssum = nsym == G ? decode_run16<true>(br, sm, lut2, d.l2_lo, d.l2_n, d.by_len, srow, NU, ush, k, nsym, nesc, bad)
-                         : decode_run16<false>(br, sm, lut2, d.l2_lo, d.l2_n, d.by_len, srow, NU, ush, k, nsym, nesc, bad);
+        ssum = nsym == G ? decode_run16<true>(br, sm, tab, d.l2_lo, d.l2_n, d.by_len, srow, NU, ush, k, nsym, nesc, bad)
+                         : decode_run16<false>(br, sm, tab, d.l2_lo, d.l2_n, d.by_len, srow, NU, ush, k, nsym, nesc, bad);
         end_bit = br.bit_pos();
     } else {
         BitReader br;
         br.init(d.payload + wb, start, cw_words);
-        ssum = decode_run16<false>(br, sm, lut2, d.l2_lo, d.l2_n, d.by_len, srow, NU, ush, k, nsym, nesc, bad);
+        ssum = decode_run16<false>(br, sm, tab, d.l2_lo, d.l2_n, d.by_len, srow, NU, ush, k, nsym, nesc, bad);
         end_bit = br.bit_pos();
     }
     bad = bad || end_bit - start != sl;
@@ -854,14 +857,14 @@ __device__ __forceinline__ bool decode_chunk_lv16(const DecArray& d, DecSmem& sm
 // parameters are passed by value: a reference would pin the caller's copy in
 // local memory).  Strided chunks (decode_kernel) and counted units
 // (decode_multi_kernel, s_unit: the block's per-team unit slots).
-__device__ __noinline__ void decode_team_lcf_strided(const DecArray d, DecSmem& sm, const uint32_t* lut2,
+__device__ __noinline__ void decode_team_lcf_strided(const DecArray d, DecSmem& sm, const uint32_t* tab,
                                                      uint32_t* xs, uint32_t stage_words, int team, int k,
                                                      uint64_t c0, uint64_t stride, uint32_t* err) {
     for (uint64_t c = c0; c < d.nc; c += stride)
-        if (!decode_chunk_team<true>(d, sm, lut2, xs, xs + d.C, stage_words, team, k, c, c + stride, err)) return;
+        if (!decode_chunk_team<true>(d, sm, tab, xs, xs + d.C, stage_words, team, k, c, c + stride, err)) return;
 }
 
-__device__ __noinline__ void decode_team_lcf_counted(const DecArray d, DecSmem& sm, const uint32_t* lut2,
+__device__ __noinline__ void decode_team_lcf_counted(const DecArray d, DecSmem& sm, const uint32_t* tab,
                                                      uint32_t* xs, uint32_t stage_words, int team, int k,
                                                      uint32_t* ctr, uint32_t nu, uint32_t* s_unit, uint32_t* err) {
     if (k == 0) s_unit[team] = atomicAdd(ctr, 1u);
@@ -873,7 +876,7 @@ __device__ __noinline__ void decode_team_lcf_counted(const DecArray d, DecSmem& 
         team_sync(team);
         const uint32_t un = s_unit[team];
         team_sync(team);
-        if (!decode_chunk_team<true>(d, sm, lut2, xs, xs + d.C, stage_words, team, k, u, un < nu ? un : ~0ull, err))
+        if (!decode_chunk_team<true>(d, sm, tab, xs, xs + d.C, stage_words, team, k, u, un < nu ? un : ~0ull, err))
             return;
         u = un;
     }
@@ -883,9 +886,9 @@ __device__ __noinline__ void decode_team_lcf_counted(const DecArray d, DecSmem& 
 // for LV streams' 16-bit rows, C for LCF -- then the payload stage
 __device__ __forceinline__ uint32_t* team_region(uint4* dyn, int teams, int team, uint32_t* stage_words,
                                                  uint32_t slots) {
-    const uint32_t region_words = ((uint32_t)((kDecDynSmem - kLut2Bytes) / 4) / teams) & ~3u;
+    const uint32_t region_words = (kRegionPool / teams) & ~3u;
     *stage_words = region_words - slots;  // multiple of 4
-    return reinterpret_cast<uint32_t*>(dyn) + kLut2Max + (size_t)team * region_words;
+    return reinterpret_cast<uint32_t*>(dyn) + kTabWords + (size_t)team * region_words;
 }
 
 __global__ void __launch_bounds__(kDecBlock, 1) decode_kernel(DecompressArgs a) {
@@ -904,9 +907,9 @@ __global__ void __launch_bounds__(kDecBlock, 1) decode_kernel(DecompressArgs a) 
             dst[i] = __ldg(src + i);
         return;
     }
-    uint32_t* lut2 = reinterpret_cast<uint32_t*>(dyn_smem);
+    uint32_t* tab = reinterpret_cast<uint32_t*>(dyn_smem);
     init_stage_barriers(sm, tid);
-    load_dec_tables(a, d, sm, lut2);
+    load_dec_tables(a, d, sm, tab);
     __syncthreads();
     const int teams = teams_for(d.C, d.max_cw, d.lcf);
     const int team = tid / kDecThreads, k = tid % kDecThreads;
@@ -916,12 +919,12 @@ __global__ void __launch_bounds__(kDecBlock, 1) decode_kernel(DecompressArgs a) 
     uint32_t* xs = team_region(dyn_smem, teams, team, &stage_words, slots);
     const uint64_t stride = (uint64_t)gridDim.x * teams;
     if (d.lcf) {
-        decode_team_lcf_strided(d, sm, lut2, xs, stage_words, team, k, (uint64_t)blockIdx.x * teams + team, stride,
+        decode_team_lcf_strided(d, sm, tab, xs, stage_words, team, k, (uint64_t)blockIdx.x * teams + team, stride,
                                 a.err);
         return;
     }
     for (uint64_t c = (uint64_t)blockIdx.x * teams + team; c < d.nc; c += stride)
-        if (!decode_chunk_lv16(d, sm, lut2, xs, xs + slots, stage_words, team, k, c, c + stride, a.err)) return;
+        if (!decode_chunk_lv16(d, sm, tab, xs, xs + slots, stage_words, team, k, c, c + stride, a.err)) return;
 }
 
 // ---- batched decompression ---------------------------------------------------
@@ -997,7 +1000,7 @@ __global__ void __launch_bounds__(kDecBlock, 1) decode_multi_kernel(const Decomp
     const uint64_t F = uoff[k];
     if (F == 0) return;
     init_stage_barriers(sm, tid);      // the stream loop's first block barrier publishes them
-    uint32_t* lut2 = reinterpret_cast<uint32_t*>(dyn_smem);
+    uint32_t* tab = reinterpret_cast<uint32_t*>(dyn_smem);
     const int team = tid / kDecThreads, kk = tid % kDecThreads;
     uint32_t i = find_stream(uoff, k, F * blockIdx.x / gridDim.x);
     for (uint32_t v = 0; v < k; ++v, i = (i + 1 == k) ? 0 : i + 1) {
@@ -1014,7 +1017,7 @@ __global__ void __launch_bounds__(kDecBlock, 1) decode_multi_kernel(const Decomp
         dec_array(sa, d);
         const bool raw = sa.st->raw != 0;
         if (!raw) {
-            load_dec_tables(sa, d, sm, lut2);
+            load_dec_tables(sa, d, sm, tab);
             __syncthreads();
         }
         const int teams = raw ? kMaxTeams : teams_for(d.C, d.max_cw, d.lcf);
@@ -1023,7 +1026,7 @@ __global__ void __launch_bounds__(kDecBlock, 1) decode_multi_kernel(const Decomp
         const uint32_t slots = d.lcf ? d.C : d.C / 2;
         uint32_t* xs = raw ? nullptr : team_region(dyn_smem, teams, team, &stage_words, slots);
         if (!raw && d.lcf) {
-            decode_team_lcf_counted(d, sm, lut2, xs, stage_words, team, kk, ctr + i, nu, s_unit, sa.err);
+            decode_team_lcf_counted(d, sm, tab, xs, stage_words, team, kk, ctr + i, nu, s_unit, sa.err);
             continue;
         }
         // a team holds two tickets: while it decodes unit u, unit un (its next)
@@ -1042,7 +1045,7 @@ __global__ void __launch_bounds__(kDecBlock, 1) decode_multi_kernel(const Decomp
                 uint32_t* dst = reinterpret_cast<uint32_t*>(sa.out);
                 const uint64_t e1 = umin64(d.n, ((uint64_t)u + 1) * kRawUnit);
                 for (uint64_t e = (uint64_t)u * kRawUnit + kk; e < e1; e += kDecThreads) dst[e] = __ldg(d.payload + e);
-            } else if (!decode_chunk_lv16(d, sm, lut2, xs, xs + slots, stage_words, team, kk, u,
+            } else if (!decode_chunk_lv16(d, sm, tab, xs, xs + slots, stage_words, team, kk, u,
                                           un < nu ? un : ~0ull, sa.err)) {
                 break;
             }
