@@ -56,11 +56,15 @@ __device__ __forceinline__ bool lattice_fast32(float x, const LatticeParams& P, 
     float t1 = x * P.inv;
     float e = fmaf(-t1, P.D, x);
     float t = fmaf(e, P.inv, t1);
-    float qc = rintf(t);
+    // nearest integer, ties to even, by one rounded add of 1.5 * 2^23: for
+    // |t| < 2^22 (the only case this path accepts) the sum's low mantissa
+    // bits hold the integer, and subtracting the constant again is exact
+    const float big = __fadd_rn(t, 12582912.0f);
+    const float qc = __fsub_rn(big, 12582912.0f);
+    q = __float_as_int(big) - 0x4B400000;
     float r = fmaf(-qc, P.D, x);
     float xr = __fmul_rn(qc, P.D);
     verb = fabsf(__fsub_rn(x, xr)) > P.ebf;
-    q = __float2int_rz(qc);
     return (fabsf(r) <= P.thr_lo) & (fabsf(t) < 4194304.0f);
 }
 
