@@ -29,6 +29,7 @@ import hashlib
 import json
 import math
 import os
+import re
 import subprocess
 import sys
 import tempfile
@@ -440,28 +441,92 @@ def _ncu_entry(kernel: str):
         return None
 
 
+def _ncu_sum(kernel: str):
+    """(DRAM bytes, device ns) per launch of `kernel` -- or of every kernel of
+    "a + b", summed -- from the committed ncu summary; None if any part is
+    missing or stale."""
+    b = ns = 0.0
+    for k in kernel.split(" + "):
+        e = _ncu_entry(k.strip())
+        try:
+            b += float(e["bytes_per_launch_full"])
+            ns += float(e["ncu_duration_ns"])
+        except (KeyError, TypeError, ValueError):
+            return None
+    return b, ns
+
+
 def _traffic(kernel: str):
     """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if the
     kernel source is unchanged since the capture; else None."""
-    e = _ncu_entry(kernel)
-    try:
-        return None if e is None else float(e["bytes_per_launch_full"])
-    except (KeyError, TypeError, ValueError):
-        return None
+    r = _ncu_sum(kernel)
+    return None if r is None else r[0]
 
 
 def ncu_dram_rate(kernel: str, peak: float):
     """The DRAM rate ncu measured for one launch of `kernel` (bytes read and
     written over its serialised device time), and its fraction of `peak`."""
-    e = _ncu_entry(kernel)
-    try:
-        b, ns = float(e["bytes_per_launch_full"]), float(e["ncu_duration_ns"])
-    except (KeyError, TypeError, ValueError):
+    r = _ncu_sum(kernel)
+    if r is None or r[1] <= 0:
         return None
-    if ns <= 0:
-        return None
+    b, ns = r
     gbs = b / ns
     return {"dram_bytes": b, "duration_ms": ns / 1e6, "dram_gbs": gbs, "dram_frac": gbs / peak}
+
+
+# The batched step's kernels whose DRAM traffic bench.py reports, and the
+# sources each is built from (an entry counts only while these hash alike).
+NCU_KERNELS = {
+    "range_multi_kernel": ["k_multi.cu", "sz_range.cuh", "sz_device.cuh", "sz_internal.h"],
+    "quant_multi_kernel": ["k_multi.cu", "sz_quant.cuh", "sz_device.cuh", "sz_internal.h"],
+    "encode_sizes_multi_kernel": ["k_multi.cu", "sz_encode.cuh", "sz_device.cuh", "sz_internal.h"],
+    "encode_pack_multi_kernel": ["k_multi.cu", "sz_encode.cuh", "sz_device.cuh", "sz_internal.h"],
+    "decode_multi_kernel": ["k_decode.cu", "sz_blocksort.cuh", "sz_device.cuh", "sz_internal.h"],
+}
+_UNIT = {"byte": 1.0, "kbyte": 1e3, "mbyte": 1e6, "gbyte": 1e9, "tbyte": 1e12,
+         "nsecond": 1.0, "usecond": 1e3, "msecond": 1e6, "second": 1e9}
+
+
+def write_traffic(csv_path: str, command: str) -> dict:
+    """profiles/traffic.json from an ncu CSV log (--metrics gpu__time_duration.sum,
+    dram__bytes_read.sum,dram__bytes_write.sum --csv): per kernel of
+    NCU_KERNELS, the mean over its captured launches, with the hash of its
+    sources.  Host only."""
+    import csv
+    rows = [r for r in csv.reader(open(csv_path)) if r]
+    hdr_i = next(i for i, r in enumerate(rows) if "Metric Name" in r and "Kernel Name" in r)
+    hdr = rows[hdr_i]
+    col = {h: hdr.index(h) for h in ("ID", "Kernel Name", "Metric Name", "Metric Unit", "Metric Value")}
+    launches = {}
+    for r in rows[hdr_i + 1:]:
+        if len(r) < len(hdr):
+            continue
+        unit = r[col["Metric Unit"]].strip().lower()
+        v = float(r[col["Metric Value"]].replace(",", "")) * _UNIT.get(unit, 1.0)
+        d = launches.setdefault(r[col["ID"]], {"name": r[col["Kernel Name"]]})
+        d[r[col["Metric Name"]]] = v
+    out = {"_about": ("Per-launch DRAM traffic (ncu dram__bytes_read.sum + dram__bytes_write.sum, one pass) "
+                      "of the batched step's kernels on the large cosmology snapshot: 6 arrays of 2^27 float32 "
+                      "per launch, rel eb 1e-4. Command: " + command + ". Written by bench.py --write-traffic; "
+                      "bench.py uses an entry only while the listed sources hash to sources_sha256_16.")}
+    csrc = os.path.join(ROOT, "paper_1711_03888_gb300", "csrc")
+    for k, srcs in NCU_KERNELS.items():
+        ls = [d for d in launches.values() if re.search(r"\b" + k + r"\b", d["name"])]
+        ls = [d for d in ls if "dram__bytes_read.sum" in d and "dram__bytes_write.sum" in d]
+        if not ls:
+            continue
+        h = hashlib.sha256()
+        for f in srcs:
+            h.update(open(os.path.join(csrc, f), "rb").read())
+        rd = sum(d["dram__bytes_read.sum"] for d in ls) / len(ls)
+        wr = sum(d["dram__bytes_write.sum"] for d in ls) / len(ls)
+        ns = sum(d.get("gpu__time_duration.sum", 0.0) for d in ls) / len(ls)
+        out[k] = {"sources": srcs, "sources_sha256_16": h.hexdigest()[:16], "bytes_per_launch_full": rd + wr,
+                  "dram_read": rd, "dram_write": wr, "ncu_duration_ns": ns, "launches_captured": len(ls)}
+    with open(os.path.join(ROOT, "profiles", "traffic.json"), "w") as f:
+        json.dump(out, f, indent=1)
+        f.write("\n")
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -968,7 +1033,13 @@ def main():
     ap.add_argument("--serve-stress-seconds", type=float, default=0.25)
     ap.add_argument("--serve-slots", type=int, default=16)
     ap.add_argument("--serve-budget-gb", type=float, default=48.0)
+    ap.add_argument("--write-traffic", metavar="NCU_CSV",
+                    help="host only: write profiles/traffic.json from an ncu CSV log and exit")
+    ap.add_argument("--traffic-command", default="", help="the ncu command line recorded with --write-traffic")
     args = ap.parse_args()
+    if args.write_traffic:
+        print(json.dumps(write_traffic(args.write_traffic, args.traffic_command), indent=1))
+        return
 
     ws, rank, local = _dist()
     n = 1 << args.log2n

@@ -69,6 +69,45 @@ def test_traffic_is_dropped_once_a_source_changes(tmp_path, monkeypatch):
     assert bench._traffic(k) is None
 
 
+_NCU_CSV_HEADER = ('"ID","Process ID","Process Name","Host Name","Kernel Name","Context","Stream","Block Size",'
+                   '"Grid Size","Device","CC","Section Name","Metric Name","Metric Unit","Metric Value"')
+
+
+def _ncu_row(i, kernel, metric, unit, value):
+    return (f'"{i}","1","python","h","{kernel}","1","7","(256, 1, 1)","(456, 6, 1)","0","10.3",'
+            f'"Command line profiler metrics","{metric}","{unit}","{value}"')
+
+
+def test_write_traffic_from_an_ncu_log(tmp_path, monkeypatch):
+    """--write-traffic averages each kernel's launches, converts ncu's units,
+    pins the current source hashes, and an "a + b" name sums both kernels."""
+    root = _copy_tree(tmp_path)
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    sizes = "void szg::(anonymous namespace)::encode_sizes_multi_kernel<4096>(szg::MultiArgs)"
+    pack = "void szg::(anonymous namespace)::encode_pack_multi_kernel<4096>(szg::MultiArgs)"
+    rows = [_NCU_CSV_HEADER]
+    for i, (k, rd, wr, us) in enumerate([(sizes, "1,600,000,000", "0.001", 430.0),
+                                         (pack, "1,500,000,000", "1.0", 1400.0),
+                                         (pack, "1,700,000,000", "1.2", 1600.0)]):
+        rows += [_ncu_row(i, k, "dram__bytes_read.sum", "byte", rd),
+                 _ncu_row(i, k, "dram__bytes_write.sum", "Gbyte", wr),
+                 _ncu_row(i, k, "gpu__time_duration.sum", "usecond", us)]
+    log = tmp_path / "launches.csv"
+    log.write_text("==PROF== a line before the table\n" + "\n".join(rows) + "\n")
+    out = bench.write_traffic(str(log), "ncu --metrics ...")
+    assert set(k for k in out if not k.startswith("_")) == {"encode_sizes_multi_kernel", "encode_pack_multi_kernel"}
+    p = out["encode_pack_multi_kernel"]
+    assert p["launches_captured"] == 2
+    assert p["dram_read"] == pytest.approx(1.6e9) and p["dram_write"] == pytest.approx(1.1e9)
+    assert p["ncu_duration_ns"] == pytest.approx(1.5e6)
+    assert bench._traffic("encode_pack_multi_kernel") == pytest.approx(2.7e9)
+    assert bench._traffic("encode_sizes_multi_kernel + encode_pack_multi_kernel") == pytest.approx(2.7e9 + 1.601e9)
+    r = bench.ncu_dram_rate("encode_sizes_multi_kernel + encode_pack_multi_kernel", 1000.0)
+    assert r["duration_ms"] == pytest.approx(1.93)
+    # a part that is missing leaves the sum unknown
+    assert bench._traffic("encode_pack_multi_kernel + decode_multi_kernel") is None
+
+
 def _fake_log(lines):
     """A ClockSampler on its nvidia-smi path, fed by a process that prints
     `lines` in nvidia-smi's CSV form and then waits to be terminated."""
