@@ -484,7 +484,9 @@ NCU_KERNELS = {
     "decode_multi_kernel": ["k_decode.cu", "sz_blocksort.cuh", "sz_device.cuh", "sz_internal.h"],
 }
 _UNIT = {"byte": 1.0, "kbyte": 1e3, "mbyte": 1e6, "gbyte": 1e9, "tbyte": 1e12,
-         "nsecond": 1.0, "usecond": 1e3, "msecond": 1e6, "second": 1e9}
+         "b": 1.0, "kb": 1e3, "mb": 1e6, "gb": 1e9, "tb": 1e12,
+         "nsecond": 1.0, "usecond": 1e3, "msecond": 1e6, "second": 1e9,
+         "ns": 1.0, "us": 1e3, "ms": 1e6, "s": 1e9}
 
 
 def write_traffic(csv_path: str, command: str) -> dict:
@@ -1033,6 +1035,8 @@ def main():
     ap.add_argument("--serve-stress-seconds", type=float, default=0.25)
     ap.add_argument("--serve-slots", type=int, default=16)
     ap.add_argument("--serve-budget-gb", type=float, default=48.0)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="headline batch at the fixed chunk-size rule (for runs under a profiler)")
     ap.add_argument("--write-traffic", metavar="NCU_CSV",
                     help="host only: write profiles/traffic.json from an ncu CSV log and exit")
     ap.add_argument("--traffic-command", default="", help="the ncu command line recorded with --write-traffic")
@@ -1087,6 +1091,10 @@ def main():
     xs = [snap[f] for f in FIELDS]
     raw_bytes = 4 * n * len(xs)
     ctx = sz.Context(local)
+    if args.no_autotune:
+        # the fixed chunk-size rule; the autotuner's own trials are timings,
+        # which a profiler that serialises launches would distort
+        sz.sz_ctx_set_autotune(ctx, False)
     outs = [torch.empty(sz.sz_max_compressed_bytes(n), dtype=torch.uint8, device="cuda") for _ in xs]
     ys = [torch.empty(n, dtype=torch.float32, device="cuda") for _ in xs]
     stream = torch.cuda.current_stream()
