@@ -27,8 +27,9 @@
 // quarter chunk with 128-bit coalesced stores.  Every table entry and payload
 // word is bounds-checked against in_bytes; a bad stream sets E_CORRUPT.
 // Streams with the LCF predictor (second differences, two anchors per chunk)
-// keep 32-bit slots, take a second team scan for the entry state of each
-// sub-stream and 64-bit reconstruction, in non-inlined functions of their own.
+// take the same layout plus a second team scan for the entry state of each
+// sub-stream, and rebuild in 32-bit integers only where a bound proves it
+// exact, in non-inlined functions of their own.
 #include "sz_blocksort.cuh"
 
 namespace szg {
@@ -380,7 +381,8 @@ constexpr uint32_t kRegionPool = (uint32_t)((kDecDynSmem - kTabBytes) / 4);   //
 // of at least C / 4 words, which carries the values out; LCF streams keep C
 // 32-bit slots.
 __device__ __forceinline__ int teams_for(uint32_t C, uint32_t max_cw, bool lcf) {
-    const uint32_t need = lcf ? C + max_cw + 4u : C / 2u + umax32(max_cw, C / 4u) + 4u;
+    (void)lcf;   // LV and LCF streams alike keep 16-bit symbol rows
+    const uint32_t need = C / 2u + umax32(max_cw, C / 4u) + 4u;
     int t = kMaxTeams;
     while (t > 1 && ((kRegionPool / (uint32_t)t) & ~3u) < need) --t;
     return t;
@@ -411,29 +413,6 @@ __device__ __forceinline__ uint32_t decode_symbol(BitReader& br, const DecSmem& 
     }
     br.consume(ent & 255u);
     return ent >> 8;
-}
-
-// Phase 1 of one sub-stream: decode nsym symbols into the team's slots (raw
-// symbols: 0 marks an escape).  Returns the sum of the symbols and counts the
-// escapes; the reader's end position checks the sub-stream length.
-template <bool FULL>
-__device__ __forceinline__ uint32_t decode_run(BitReader& br, const DecSmem& sm, const uint32_t* tab, uint32_t l2_lo,
-                                               uint32_t l2_n, const uint16_t* by_len, uint32_t* xs, uint32_t e0,
-                                               uint32_t gshift, uint32_t nsym, uint32_t& nesc, bool& bad) {
-    uint32_t ssum = 0;
-    for (uint32_t j4 = 0; j4 < nsym; j4 += 4) {
-        uint32_t s[4] = {0u, 0u, 0u, 0u};
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            if (FULL || j4 + t < nsym) {
-                s[t] = decode_symbol(br, sm, tab, l2_lo, l2_n, by_len, bad);
-                ssum += s[t];
-                nesc += (s[t] == 0u);
-            }
-        }
-        *reinterpret_cast<uint4*>(&xs[swz(e0 + j4, gshift)]) = make_uint4(s[0], s[1], s[2], s[3]);
-    }
-    return ssum;
 }
 
 // The LV path's 16-bit symbol rows: row k (sub-stream k) holds G symbols as
@@ -531,189 +510,6 @@ __device__ __forceinline__ void load_dec_tables(const DecompressArgs& a, const D
     }
 }
 
-// One chunk by one team of 64 threads (thread k = sub-stream k): stage, decode,
-// escapes and prefix, reconstruct, store.  next: the chunk this team takes next
-// (L2 prefetch), or >= nc.  Returns false (and raises E_CORRUPT, or E_TIMEOUT
-// for a lost copy) on a bad chunk.
-// LCF: the symbols are second differences; see the reconstruction below.
-template <bool LCF>
-__device__ __forceinline__ bool decode_chunk_team(const DecArray& d, DecSmem& sm, const uint32_t* tab,
-                                                  uint32_t* xs, uint32_t* stage, uint32_t stage_words, int team,
-                                                  int k, uint64_t c, uint64_t next, uint32_t* err) {
-    const uint32_t C = d.C, G = d.G, gshift = d.gshift;
-    const uint64_t base = c * C;
-    const uint32_t cnt = (uint32_t)umin64(C, d.n - base);
-    const uint64_t wb = d.cword[c], we = d.cword[c + 1];
-    const uint64_t eb = d.cesc[c], ee = d.cesc[c + 1];
-    const bool hdr_bad = (wb > we || we > d.pw || eb > ee || ee > d.E || ((wb | we) & 3u));
-    const uint32_t e0 = k * G;
-    const uint32_t nsym = e0 < cnt ? umin32(G, cnt - e0) : 0u;
-    const uint32_t sl = d.sublen[c * kSubPerChunk + k];
-    uint32_t tot_bits;
-    const uint32_t start = team_exclusive_scan<uint32_t>(sl, sm.ws32[team], team, k, &tot_bits);
-    if (hdr_bad || (uint64_t)tot_bits > 32ull * (we - wb)) {
-        if (k == 0) raise_err(err, E_CORRUPT);
-        return false;
-    }
-    // ---- stage the chunk payload; prefetch the team's next chunk into L2 --------
-    const uint32_t cw_words = (uint32_t)(we - wb);
-    const bool staged = cw_words <= stage_words;
-    if (staged && !stage_chunk(d.payload + wb, stage, cw_words, sm, team, k, err)) return false;
-    if (k == 0 && next < d.nc) {
-        const uint64_t nb = d.cword[next], ne = d.cword[next + 1];
-        if (nb < ne && ne <= d.pw && !(nb & 3u) && !(ne & 3u) && ne - nb < (1u << 24)) {
-            const uint32_t* p = d.payload + nb;
-            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(__cvta_generic_to_global(p)), "r"((uint32_t)(4 * (ne - nb)))
-                         : "memory");
-        }
-    }
-    team_sync(team);
-    if (staged) stage_done(sm, team, k);
-    // ---- phase 1: decode the sub-stream into symbols ----------------------------
-    // (separate calls for the staged and the global source, so that the staged
-    // reader's loads are shared-memory loads)
-    uint32_t nesc = 0, ssum, end_bit;
-    bool bad = false;
-    if (staged) {
-        BitReader br;
-        br.init(stage, start, cw_words);
-        ssum = nsym == G ? decode_run<true>(br, sm, tab, d.l2_lo, d.l2_n, d.by_len, xs, e0, gshift, nsym, nesc, bad)
-                         : decode_run<false>(br, sm, tab, d.l2_lo, d.l2_n, d.by_len, xs, e0, gshift, nsym, nesc, bad);
-        end_bit = br.bit_pos();
-    } else {
-        BitReader br;
-        br.init(d.payload + wb, start, cw_words);
-        ssum = decode_run<false>(br, sm, tab, d.l2_lo, d.l2_n, d.by_len, xs, e0, gshift, nsym, nesc, bad);
-        end_bit = br.bit_pos();
-    }
-    bad = bad || end_bit - start != sl;
-    // ---- escapes and the team-wide prefix ----------------------------------------
-    uint32_t tot_esc;
-    const uint32_t eoff =
-        team_exclusive_scan<uint32_t>(nesc + (bad ? 0x10000u : 0u), sm.ws32b[team], team, k, &tot_esc);
-    if ((tot_esc >> 16) || eb + tot_esc != ee) {
-        if (k == 0) raise_err(err, E_CORRUPT);
-        return false;
-    }
-    // sum of deltas: escape symbols are 0, every other one is delta + radius
-    long long sum = (long long)ssum - (long long)kRadius * (long long)(nsym - nesc);
-    for (uint32_t t = 0; t < nesc; ++t)
-        sum += *reinterpret_cast<const long long*>(d.escs + (uint64_t)kEscBytes * (eb + eoff + t));
-    long long tot_sum;
-    const long long pre = team_exclusive_scan<long long>(sum, sm.ws64[team], team, k, &tot_sum);
-    const float D = d.D;
-    if constexpr (LCF) {
-        // ---- phase 2 (LCF): q_i = 2 q_{i-1} - q_{i-2} + delta_i ------------------
-        // With the first difference f_i = q_i - q_{i-1}: f_i = f_{i-1} + delta_i and
-        // q_i = q_{i-1} + f_i.  A sub-stream of L deltas maps (f, q) to
-        // (f + S, q + L f + T), S = sum of its deltas (`sum`, scanned above into
-        // `pre`), T = sum of its running sums of deltas.  A second team scan of
-        // L * pre + T gives each sub-stream its entry state; unsigned arithmetic
-        // wraps like the two's-complement recurrence.
-        uint64_t run = 0, T = 0;
-        uint64_t ecur = eb + eoff;
-        for (uint32_t j = 0; j < nsym; ++j) {
-            const uint32_t sy = xs[swz(e0 + j, gshift)];
-            const uint64_t dl = sy ? (uint64_t)((long long)sy - kRadius)
-                                   : *reinterpret_cast<const uint64_t*>(d.escs + (uint64_t)kEscBytes * ecur++);
-            run += dl;
-            T += run;
-        }
-        long long tot_t;
-        const long long preT = team_exclusive_scan<long long>((long long)((uint64_t)nsym * (uint64_t)pre + T),
-                                                              sm.ws64[team], team, k, &tot_t);
-        const uint64_t qm1 = (uint64_t)d.anchor[2 * c], qm2 = (uint64_t)d.anchor[2 * c + 1];
-        const uint64_t f0 = qm1 - qm2;
-        uint64_t f = f0 + (uint64_t)pre;
-        uint64_t q = qm1 + (uint64_t)e0 * f0 + (uint64_t)preT;
-        ecur = eb + eoff;
-        for (uint32_t j4 = 0; j4 < nsym; j4 += 4) {
-            uint4* slot = reinterpret_cast<uint4*>(&xs[swz(e0 + j4, gshift)]);
-            uint4 s4 = *slot;
-            uint32_t sy[4] = {s4.x, s4.y, s4.z, s4.w};
-            uint32_t ov[4];
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                ov[t] = 0u;
-                if (j4 + t < nsym) {
-                    float v;
-                    if (sy[t] != 0u) {
-                        f += (uint64_t)((long long)sy[t] - kRadius);
-                        q += f;
-                        v = recon_f((long long)q, D);
-                    } else {
-                        const uint8_t* r = d.escs + (uint64_t)kEscBytes * ecur++;
-                        f += *reinterpret_cast<const uint64_t*>(r);
-                        q += f;
-                        v = (rd32(r + 12) & 1u) ? __uint_as_float(rd32(r + 8)) : recon_f((long long)q, D);
-                    }
-                    ov[t] = __float_as_uint(v);
-                }
-            }
-            *slot = make_uint4(ov[0], ov[1], ov[2], ov[3]);
-        }
-    } else {
-    // ---- phase 2: reconstruct in place -----------------------------------------
-    // every partial sum of a sub-stream without escapes stays within
-    // q0 +- G * 32767, so |q0| below this bound keeps all of them within 2^24
-    const long long q_fast = (1ll << 24) - (long long)G * (kRadius - 1);
-    const long long q0 = d.anchor[c] + pre;
-    if (nesc == 0 && q0 >= -q_fast && q0 <= q_fast) {
-        // 32-bit: q stays within the exact range, one int -> float and one fmul each
-        int q = (int)q0;
-        for (uint32_t j4 = 0; j4 < nsym; j4 += 4) {
-            uint4* slot = reinterpret_cast<uint4*>(&xs[swz(e0 + j4, gshift)]);
-            uint4 s4 = *slot;
-            q += (int)s4.x - kRadius; const float v0 = __fmul_rn((float)q, D);
-            q += (int)s4.y - kRadius; const float v1 = __fmul_rn((float)q, D);
-            q += (int)s4.z - kRadius; const float v2 = __fmul_rn((float)q, D);
-            q += (int)s4.w - kRadius; const float v3 = __fmul_rn((float)q, D);
-            *slot = make_uint4(__float_as_uint(v0), __float_as_uint(v1), __float_as_uint(v2), __float_as_uint(v3));
-        }
-    } else {
-        long long q = q0;
-        uint64_t ecur = eb + eoff;
-        for (uint32_t j4 = 0; j4 < nsym; j4 += 4) {
-            uint4* slot = reinterpret_cast<uint4*>(&xs[swz(e0 + j4, gshift)]);
-            uint4 s4 = *slot;
-            uint32_t sy[4] = {s4.x, s4.y, s4.z, s4.w};
-            uint32_t ov[4];
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                ov[t] = 0u;
-                if (j4 + t < nsym) {
-                    float v;
-                    if (sy[t] != 0u) {
-                        q += (long long)sy[t] - kRadius;
-                        v = recon_f(q, D);
-                    } else {
-                        const uint8_t* r = d.escs + (uint64_t)kEscBytes * ecur++;
-                        q += *reinterpret_cast<const long long*>(r);
-                        v = (rd32(r + 12) & 1u) ? __uint_as_float(rd32(r + 8)) : recon_f(q, D);
-                    }
-                    ov[t] = __float_as_uint(v);
-                }
-            }
-            *slot = make_uint4(ov[0], ov[1], ov[2], ov[3]);
-        }
-    }
-    }  // LV
-    team_sync(team);
-    // ---- phase 3: coalesced store ---------------------------------------------
-    float* dst = d.out + base;
-    if (d.vec && cnt == C) {
-        for (uint32_t e = 4 * k; e < C; e += 4 * kDecThreads)
-            *reinterpret_cast<uint4*>(dst + e) = *reinterpret_cast<const uint4*>(&xs[swz(e, gshift)]);
-    } else {
-        for (uint32_t e = 4 * k; e < cnt; e += 4 * kDecThreads) {
-            uint4 v = *reinterpret_cast<const uint4*>(&xs[swz(e, gshift)]);
-            uint32_t vv[4] = {v.x, v.y, v.z, v.w};
-            for (int j = 0; j < 4 && e + j < cnt; ++j) dst[e + j] = __uint_as_float(vv[j]);
-        }
-    }
-    team_sync(team);
-    return true;
-}
 
 // One LV chunk by one team through 16-bit symbol rows (sym16: C / 2 words)
 // and the stage (stage_words >= C / 4): stage the payload (stage_chunk; a
@@ -852,6 +648,175 @@ __device__ __forceinline__ bool decode_chunk_lv16(const DecArray& d, DecSmem& sm
     return true;
 }
 
+// One LCF chunk by one team, in the layout of decode_chunk_lv16 (16-bit symbol
+// rows, then four rounds of values through the stage).  With the first
+// difference f_i = q_i - q_{i-1}: f_i = f_{i-1} + delta_i and q_i = q_{i-1} + f_i.
+// A sub-stream of L deltas maps (f, q) to (f + S, q + L f + T), S the sum of its
+// deltas and T the sum of their running sums; a team scan of S gives each
+// sub-stream its entry f, a second one of L * (S-prefix) + T its entry q
+// (unsigned arithmetic wraps like the two's-complement recurrence).  A
+// sub-stream without escapes whose every partial q provably stays within 2^24
+// (from the largest running sums of its deltas) rebuilds in 32-bit integers.
+__device__ __forceinline__ bool decode_chunk_lcf16(const DecArray& d, DecSmem& sm, const uint32_t* tab,
+                                                   uint32_t* sym16, uint32_t* stage, uint32_t stage_words, int team,
+                                                   int k, uint64_t c, uint64_t next, uint32_t* err) {
+    const uint32_t C = d.C, G = d.G;
+    const uint32_t NU = G / 4u, F = G / 16u, VR = G / 4u;
+    const uint32_t gsh = d.gshift;                       // log2 G (5 .. 8)
+    const uint32_t ush = gsh >= 6 ? 0u : 6u - gsh;       // log2 max(1, 16 / NU)
+    const uint32_t vsh = gsh >= 7 ? 0u : 7u - gsh;       // log2 max(1, 8 / F)
+    const uint64_t base = c * C;
+    const uint32_t cnt = (uint32_t)umin64(C, d.n - base);
+    const uint64_t wb = d.cword[c], we = d.cword[c + 1];
+    const uint64_t eb = d.cesc[c], ee = d.cesc[c + 1];
+    const bool hdr_bad = (wb > we || we > d.pw || eb > ee || ee > d.E || ((wb | we) & 3u));
+    const uint32_t e0 = k * G;
+    const uint32_t nsym = e0 < cnt ? umin32(G, cnt - e0) : 0u;
+    const uint32_t sl = d.sublen[c * kSubPerChunk + k];
+    uint32_t tot_bits;
+    const uint32_t start = team_exclusive_scan<uint32_t>(sl, sm.ws32[team], team, k, &tot_bits);
+    if (hdr_bad || (uint64_t)tot_bits > 32ull * (we - wb)) {
+        if (k == 0) raise_err(err, E_CORRUPT);
+        return false;
+    }
+    // ---- stage the chunk payload; prefetch the team's next chunk into L2 --------
+    const uint32_t cw_words = (uint32_t)(we - wb);
+    const bool staged = cw_words <= stage_words;
+    if (staged && !stage_chunk(d.payload + wb, stage, cw_words, sm, team, k, err)) return false;
+    if (k == 0 && next < d.nc) {
+        const uint64_t nb = d.cword[next], ne = d.cword[next + 1];
+        if (nb < ne && ne <= d.pw && !(nb & 3u) && !(ne & 3u) && ne - nb < (1u << 24)) {
+            const uint32_t* p = d.payload + nb;
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(__cvta_generic_to_global(p)),
+                         "r"((uint32_t)(4 * (ne - nb)))
+                         : "memory");
+        }
+    }
+    team_sync(team);
+    if (staged) stage_done(sm, team, k);
+    // ---- phase 1: the sub-stream's symbols into the thread's row -----------------
+    uint2* srow = reinterpret_cast<uint2*>(sym16) + (size_t)k * NU;
+    uint32_t nesc = 0, ssum, end_bit;
+    bool bad = false;
+    if (staged) {
+        BitReader br;
+        br.init(stage, start, cw_words);
+        ssum = nsym == G ? decode_run16<true>(br, sm, tab, d.l2_lo, d.l2_n, d.by_len, srow, NU, ush, k, nsym, nesc, bad)
+                         : decode_run16<false>(br, sm, tab, d.l2_lo, d.l2_n, d.by_len, srow, NU, ush, k, nsym, nesc, bad);
+        end_bit = br.bit_pos();
+    } else {
+        BitReader br;
+        br.init(d.payload + wb, start, cw_words);
+        ssum = decode_run16<false>(br, sm, tab, d.l2_lo, d.l2_n, d.by_len, srow, NU, ush, k, nsym, nesc, bad);
+        end_bit = br.bit_pos();
+    }
+    bad = bad || end_bit - start != sl;
+    // ---- escapes, S, and the entry f -------------------------------------------
+    uint32_t tot_esc;
+    const uint32_t eoff =
+        team_exclusive_scan<uint32_t>(nesc + (bad ? 0x10000u : 0u), sm.ws32b[team], team, k, &tot_esc);
+    if ((tot_esc >> 16) || eb + tot_esc != ee) {
+        if (k == 0) raise_err(err, E_CORRUPT);
+        return false;
+    }
+    long long S = (long long)ssum - (long long)kRadius * (long long)(nsym - nesc);
+    for (uint32_t t = 0; t < nesc; ++t)
+        S += *reinterpret_cast<const long long*>(d.escs + (uint64_t)kEscBytes * (eb + eoff + t));
+    long long tot_s;
+    const long long pre = team_exclusive_scan<long long>(S, sm.ws64[team], team, k, &tot_s);
+    // ---- T and the largest running sums over the row ---------------------------
+    uint64_t run = 0, T = 0, mr = 0, mt = 0;
+    {
+        uint64_t ec = eb + eoff;
+        for (uint32_t j4 = 0; j4 < nsym; j4 += 4) {
+            const uint2 u = srow[sym_unit(j4 >> 2, k, NU, ush)];
+            const uint32_t sy[4] = {u.x & 0xffffu, u.x >> 16, u.y & 0xffffu, u.y >> 16};
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                if (j4 + t < nsym) {
+                    const uint64_t dl = sy[t] ? (uint64_t)((long long)sy[t] - kRadius)
+                                              : *reinterpret_cast<const uint64_t*>(d.escs + (uint64_t)kEscBytes * ec++);
+                    run += dl;
+                    T += run;
+                    mr = umax64(mr, (uint64_t)llabs((long long)run));
+                    mt = umax64(mt, (uint64_t)llabs((long long)T));
+                }
+            }
+        }
+    }
+    long long tot_t;
+    const long long preT =
+        team_exclusive_scan<long long>((long long)((uint64_t)nsym * (uint64_t)pre + T), sm.ws64[team], team, k, &tot_t);
+    const uint64_t qm1 = (uint64_t)d.anchor[2 * c], qm2 = (uint64_t)d.anchor[2 * c + 1];
+    const uint64_t f0 = qm1 - qm2;
+    uint64_t f = f0 + (uint64_t)pre;
+    uint64_t q = qm1 + (uint64_t)e0 * f0 + (uint64_t)preT;
+    // every q of the row is q + (j + 1) f + (a partial T), every f is f + (a running sum)
+    const uint64_t af = (uint64_t)llabs((long long)f), aq = (uint64_t)llabs((long long)q);
+    const bool fast = nesc == 0 && af <= (1ull << 24) && mr <= (1ull << 24) && mt <= (1ull << 26) &&
+                      aq + (uint64_t)nsym * af + mt <= (1ull << 24);
+    // ---- phase 2: four rounds of G / 4 values through the stage -------------------
+    const float D = d.D;
+    uint64_t ecur = eb + eoff;
+    float* dst = d.out + base;
+    const bool full_vec = d.vec && cnt == C;
+    float4* tr = reinterpret_cast<float4*>(stage);
+    const uint32_t fsh = 31 - __clz(F);
+    for (uint32_t r = 0; r < 4; ++r) {
+        if (fast) {
+            // 32-bit, wrapping past the row's end (those values are not stored)
+            uint32_t fu = (uint32_t)f, qu = (uint32_t)q;
+            for (uint32_t m = 0; m < F; ++m) {
+                const uint2 u = srow[sym_unit(r * F + m, k, NU, ush)];
+                fu += (u.x & 0xffffu) - (uint32_t)kRadius; qu += fu; const float v0 = __fmul_rn((float)(int)qu, D);
+                fu += (u.x >> 16) - (uint32_t)kRadius;     qu += fu; const float v1 = __fmul_rn((float)(int)qu, D);
+                fu += (u.y & 0xffffu) - (uint32_t)kRadius; qu += fu; const float v2 = __fmul_rn((float)(int)qu, D);
+                fu += (u.y >> 16) - (uint32_t)kRadius;     qu += fu; const float v3 = __fmul_rn((float)(int)qu, D);
+                tr[(k << fsh) + val_unit(m, k, F, vsh)] = make_float4(v0, v1, v2, v3);
+            }
+            f = (uint64_t)(long long)(int)fu;
+            q = (uint64_t)(long long)(int)qu;
+        } else {
+            for (uint32_t m = 0; m < F; ++m) {
+                const uint2 u = srow[sym_unit(r * F + m, k, NU, ush)];
+                const uint32_t sy[4] = {u.x & 0xffffu, u.x >> 16, u.y & 0xffffu, u.y >> 16};
+                float v[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    v[t] = 0.0f;
+                    if (r * VR + 4 * m + t < nsym) {
+                        if (sy[t] != 0u) {
+                            f += (uint64_t)((long long)sy[t] - kRadius);
+                            q += f;
+                            v[t] = recon_f((long long)q, D);
+                        } else {
+                            const uint8_t* rec = d.escs + (uint64_t)kEscBytes * ecur++;
+                            f += *reinterpret_cast<const uint64_t*>(rec);
+                            q += f;
+                            v[t] = (rd32(rec + 12) & 1u) ? __uint_as_float(rd32(rec + 8)) : recon_f((long long)q, D);
+                        }
+                    }
+                }
+                tr[(k << fsh) + val_unit(m, k, F, vsh)] = make_float4(v[0], v[1], v[2], v[3]);
+            }
+        }
+        team_sync(team);
+        for (uint32_t g = k; g < kDecThreads * F; g += kDecThreads) {
+            const uint32_t row = g >> fsh, m = g & (F - 1u);
+            const float4 val = tr[(row << fsh) + val_unit(m, row, F, vsh)];
+            const uint32_t e = row * G + r * VR + 4 * m;
+            if (full_vec) {
+                *reinterpret_cast<float4*>(dst + e) = val;
+            } else {
+                const float vv[4] = {val.x, val.y, val.z, val.w};
+                for (int j = 0; j < 4 && e + j < cnt; ++j) dst[e + j] = vv[j];
+            }
+        }
+        team_sync(team);
+    }
+    return true;
+}
+
 // LCF streams run their team loops in separate, non-inlined functions, so the
 // LV path the kernels inline keeps its own code and registers (the stream
 // parameters are passed by value: a reference would pin the caller's copy in
@@ -861,7 +826,7 @@ __device__ __noinline__ void decode_team_lcf_strided(const DecArray d, DecSmem& 
                                                      uint32_t* xs, uint32_t stage_words, int team, int k,
                                                      uint64_t c0, uint64_t stride, uint32_t* err) {
     for (uint64_t c = c0; c < d.nc; c += stride)
-        if (!decode_chunk_team<true>(d, sm, tab, xs, xs + d.C, stage_words, team, k, c, c + stride, err)) return;
+        if (!decode_chunk_lcf16(d, sm, tab, xs, xs + d.C / 2, stage_words, team, k, c, c + stride, err)) return;
 }
 
 __device__ __noinline__ void decode_team_lcf_counted(const DecArray d, DecSmem& sm, const uint32_t* tab,
@@ -876,7 +841,7 @@ __device__ __noinline__ void decode_team_lcf_counted(const DecArray d, DecSmem& 
         team_sync(team);
         const uint32_t un = s_unit[team];
         team_sync(team);
-        if (!decode_chunk_team<true>(d, sm, tab, xs, xs + d.C, stage_words, team, k, u, un < nu ? un : ~0ull, err))
+        if (!decode_chunk_lcf16(d, sm, tab, xs, xs + d.C / 2, stage_words, team, k, u, un < nu ? un : ~0ull, err))
             return;
         u = un;
     }
@@ -915,7 +880,7 @@ __global__ void __launch_bounds__(kDecBlock, 1) decode_kernel(DecompressArgs a) 
     const int team = tid / kDecThreads, k = tid % kDecThreads;
     if (team >= teams) return;
     uint32_t stage_words;
-    const uint32_t slots = d.lcf ? d.C : d.C / 2;
+    const uint32_t slots = d.C / 2;
     uint32_t* xs = team_region(dyn_smem, teams, team, &stage_words, slots);
     const uint64_t stride = (uint64_t)gridDim.x * teams;
     if (d.lcf) {
@@ -1023,7 +988,7 @@ __global__ void __launch_bounds__(kDecBlock, 1) decode_multi_kernel(const Decomp
         const int teams = raw ? kMaxTeams : teams_for(d.C, d.max_cw, d.lcf);
         if (team >= teams) continue;
         uint32_t stage_words = 0;
-        const uint32_t slots = d.lcf ? d.C : d.C / 2;
+        const uint32_t slots = d.C / 2;
         uint32_t* xs = raw ? nullptr : team_region(dyn_smem, teams, team, &stage_words, slots);
         if (!raw && d.lcf) {
             decode_team_lcf_counted(d, sm, tab, xs, stage_words, team, kk, ctr + i, nu, s_unit, sa.err);
