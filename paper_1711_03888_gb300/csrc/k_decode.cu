@@ -292,6 +292,18 @@ __device__ __forceinline__ T team_exclusive_scan(T v, T* ws, int team, int k, T*
     team_sync(team);
     return r;
 }
+// The same without the closing barrier: for a buffer the team writes next
+// only after a later team barrier (each scan of a chunk has its own buffer).
+template <typename T>
+__device__ __forceinline__ T team_exclusive_scan_once(T v, T* ws, int team, int k, T* total) {
+    T inc = warp_inclusive_scan(v);
+    if ((k & 31) == 31) ws[k >> 5] = inc;
+    team_sync(team);
+    T w0 = ws[0];
+    T r = inc - v + ((k >> 5) ? w0 : T(0));
+    *total = w0 + ws[1];
+    return r;
+}
 
 struct DecSmem {
     uint32_t lim[kMaxLen + 2];            // left-justified (24-bit) end of each length's codes
@@ -521,7 +533,17 @@ __device__ __forceinline__ void load_dec_tables(const DecompressArgs& a, const D
 // prefetch), or >= nc.  Returns false (and raises E_CORRUPT) on a bad chunk.
 __device__ __forceinline__ bool decode_chunk_lv16(const DecArray& d, DecSmem& sm, const uint32_t* tab,
                                                   uint32_t* sym16, uint32_t* stage, uint32_t stage_words, int team,
-                                                  int k, uint64_t c, uint64_t next, uint32_t* err) {
+                                                  int k, uint64_t c, uint64_t next, uint32_t* err,
+                                                  uint32_t* ctr = nullptr, uint32_t* slot = nullptr,
+                                                  uint32_t* next_out = nullptr) {
+    // ctr: the stream's unit counter; the team's next ticket is drawn here and
+    // handed out through `slot` after the staging barrier (next_out), and it
+    // is also the chunk whose payload is prefetched into L2
+    if (ctr != nullptr && k == 0) {
+        const uint32_t t = atomicAdd(ctr, 1u);
+        *slot = t;
+        next = t;
+    }
     const uint32_t C = d.C, G = d.G;
     const uint32_t NU = G / 4u, F = G / 16u, VR = G / 4u;
     const uint32_t gsh = d.gshift;                       // log2 G (5 .. 8)
@@ -536,7 +558,7 @@ __device__ __forceinline__ bool decode_chunk_lv16(const DecArray& d, DecSmem& sm
     const uint32_t nsym = e0 < cnt ? umin32(G, cnt - e0) : 0u;
     const uint32_t sl = d.sublen[c * kSubPerChunk + k];
     uint32_t tot_bits;
-    const uint32_t start = team_exclusive_scan<uint32_t>(sl, sm.ws32[team], team, k, &tot_bits);
+    const uint32_t start = team_exclusive_scan_once<uint32_t>(sl, sm.ws32[team], team, k, &tot_bits);
     if (hdr_bad || (uint64_t)tot_bits > 32ull * (we - wb)) {
         if (k == 0) raise_err(err, E_CORRUPT);
         return false;
@@ -556,6 +578,7 @@ __device__ __forceinline__ bool decode_chunk_lv16(const DecArray& d, DecSmem& sm
     }
     team_sync(team);
     if (staged) stage_done(sm, team, k);
+    if (ctr != nullptr) *next_out = *slot;
     // ---- phase 1: the sub-stream's symbols into the thread's row -----------------
     uint2* srow = reinterpret_cast<uint2*>(sym16) + (size_t)k * NU;
     uint32_t nesc = 0, ssum, end_bit;
@@ -576,7 +599,7 @@ __device__ __forceinline__ bool decode_chunk_lv16(const DecArray& d, DecSmem& sm
     // ---- escapes and the team-wide prefix (the stage is free after these barriers) --
     uint32_t tot_esc;
     const uint32_t eoff =
-        team_exclusive_scan<uint32_t>(nesc + (bad ? 0x10000u : 0u), sm.ws32b[team], team, k, &tot_esc);
+        team_exclusive_scan_once<uint32_t>(nesc + (bad ? 0x10000u : 0u), sm.ws32b[team], team, k, &tot_esc);
     if ((tot_esc >> 16) || eb + tot_esc != ee) {
         if (k == 0) raise_err(err, E_CORRUPT);
         return false;
@@ -585,7 +608,7 @@ __device__ __forceinline__ bool decode_chunk_lv16(const DecArray& d, DecSmem& sm
     for (uint32_t t = 0; t < nesc; ++t)
         sum += *reinterpret_cast<const long long*>(d.escs + (uint64_t)kEscBytes * (eb + eoff + t));
     long long tot_sum;
-    const long long pre = team_exclusive_scan<long long>(sum, sm.ws64[team], team, k, &tot_sum);
+    const long long pre = team_exclusive_scan_once<long long>(sum, sm.ws64[team], team, k, &tot_sum);
     // ---- phase 2: four rounds of G / 4 values through the stage -------------------
     const float D = d.D;
     const long long q_fast = (1ll << 24) - (long long)G * (kRadius - 1);
@@ -1001,19 +1024,23 @@ __global__ void __launch_bounds__(kDecBlock, 1) decode_multi_kernel(const Decomp
         uint32_t u = s_unit[team];
         team_sync(team);
         while (u < nu) {
+            if (!raw) {
+                // the next ticket travels with the chunk's staging barrier
+                uint32_t un = 0;
+                if (!decode_chunk_lv16(d, sm, tab, xs, xs + slots, stage_words, team, kk, u, ~0ull, sa.err, ctr + i,
+                                       &s_unit[team], &un))
+                    break;
+                u = un;
+                continue;
+            }
+            // a raw stream: a 4096-word piece per unit
             if (kk == 0) s_unit[team] = atomicAdd(ctr + i, 1u);
             team_sync(team);
             const uint32_t un = s_unit[team];
             team_sync(team);
-            if (raw) {
-                // a 4096-word piece
-                uint32_t* dst = reinterpret_cast<uint32_t*>(sa.out);
-                const uint64_t e1 = umin64(d.n, ((uint64_t)u + 1) * kRawUnit);
-                for (uint64_t e = (uint64_t)u * kRawUnit + kk; e < e1; e += kDecThreads) dst[e] = __ldg(d.payload + e);
-            } else if (!decode_chunk_lv16(d, sm, tab, xs, xs + slots, stage_words, team, kk, u,
-                                          un < nu ? un : ~0ull, sa.err)) {
-                break;
-            }
+            uint32_t* dst = reinterpret_cast<uint32_t*>(sa.out);
+            const uint64_t e1 = umin64(d.n, ((uint64_t)u + 1) * kRawUnit);
+            for (uint64_t e = (uint64_t)u * kRawUnit + kk; e < e1; e += kDecThreads) dst[e] = __ldg(d.payload + e);
             u = un;
         }
     }
