@@ -531,6 +531,10 @@ __device__ __forceinline__ void load_dec_tables(const DecompressArgs& a, const D
 // once the payload is decoded) and the team stores the quarter chunk with
 // coalesced 16-byte stores.  next: the chunk this team takes next (L2
 // prefetch), or >= nc.  Returns false (and raises E_CORRUPT) on a bad chunk.
+// GT: the sub-stream length when known at compile time (64, i.e. C = 4096, the
+// fixed rule for arrays above 2^16 elements), so that the row and swizzle
+// arithmetic folds to constants; 0 takes it from the stream.
+template <uint32_t GT>
 __device__ __forceinline__ bool decode_chunk_lv16(const DecArray& d, DecSmem& sm, const uint32_t* tab,
                                                   uint32_t* sym16, uint32_t* stage, uint32_t stage_words, int team,
                                                   int k, uint64_t c, uint64_t next, uint32_t* err,
@@ -544,9 +548,9 @@ __device__ __forceinline__ bool decode_chunk_lv16(const DecArray& d, DecSmem& sm
         *slot = t;
         next = t;
     }
-    const uint32_t C = d.C, G = d.G;
+    const uint32_t G = GT ? GT : d.G, C = GT ? GT * kSubPerChunk : d.C;
     const uint32_t NU = G / 4u, F = G / 16u, VR = G / 4u;
-    const uint32_t gsh = d.gshift;                       // log2 G (5 .. 8)
+    const uint32_t gsh = GT ? (31u - __clz(GT)) : d.gshift;   // log2 G (5 .. 8)
     const uint32_t ush = gsh >= 6 ? 0u : 6u - gsh;       // log2 max(1, 16 / NU)
     const uint32_t vsh = gsh >= 7 ? 0u : 7u - gsh;       // log2 max(1, 8 / F)
     const uint64_t base = c * C;
@@ -618,7 +622,7 @@ __device__ __forceinline__ bool decode_chunk_lv16(const DecArray& d, DecSmem& sm
     float* dst = d.out + base;
     const bool full_vec = d.vec && cnt == C;
     float4* tr = reinterpret_cast<float4*>(stage);
-    const uint32_t fsh = 31 - __clz(F);
+    const uint32_t fsh = gsh - 4u;                       // log2 F
     for (uint32_t r = 0; r < 4; ++r) {
         if (fast) {
             // |q| stays within 2^24: exact in 32-bit integers and in one int -> float
@@ -912,7 +916,10 @@ __global__ void __launch_bounds__(kDecBlock, 1) decode_kernel(DecompressArgs a) 
         return;
     }
     for (uint64_t c = (uint64_t)blockIdx.x * teams + team; c < d.nc; c += stride)
-        if (!decode_chunk_lv16(d, sm, tab, xs, xs + slots, stage_words, team, k, c, c + stride, a.err)) return;
+        if (!(d.G == 64u
+                  ? decode_chunk_lv16<64>(d, sm, tab, xs, xs + slots, stage_words, team, k, c, c + stride, a.err)
+                  : decode_chunk_lv16<0>(d, sm, tab, xs, xs + slots, stage_words, team, k, c, c + stride, a.err)))
+            return;
 }
 
 // ---- batched decompression ---------------------------------------------------
@@ -1027,8 +1034,11 @@ __global__ void __launch_bounds__(kDecBlock, 1) decode_multi_kernel(const Decomp
             if (!raw) {
                 // the next ticket travels with the chunk's staging barrier
                 uint32_t un = 0;
-                if (!decode_chunk_lv16(d, sm, tab, xs, xs + slots, stage_words, team, kk, u, ~0ull, sa.err, ctr + i,
-                                       &s_unit[team], &un))
+                if (!(d.G == 64u
+                          ? decode_chunk_lv16<64>(d, sm, tab, xs, xs + slots, stage_words, team, kk, u, ~0ull, sa.err,
+                                                  ctr + i, &s_unit[team], &un)
+                          : decode_chunk_lv16<0>(d, sm, tab, xs, xs + slots, stage_words, team, kk, u, ~0ull, sa.err,
+                                                 ctr + i, &s_unit[team], &un)))
                     break;
                 u = un;
                 continue;
