@@ -684,12 +684,13 @@ __device__ __forceinline__ bool decode_chunk_lv16(const DecArray& d, DecSmem& sm
 // (unsigned arithmetic wraps like the two's-complement recurrence).  A
 // sub-stream without escapes whose every partial q provably stays within 2^24
 // (from the largest running sums of its deltas) rebuilds in 32-bit integers.
+template <uint32_t GT>
 __device__ __forceinline__ bool decode_chunk_lcf16(const DecArray& d, DecSmem& sm, const uint32_t* tab,
                                                    uint32_t* sym16, uint32_t* stage, uint32_t stage_words, int team,
                                                    int k, uint64_t c, uint64_t next, uint32_t* err) {
-    const uint32_t C = d.C, G = d.G;
+    const uint32_t G = GT ? GT : d.G, C = GT ? GT * kSubPerChunk : d.C;
     const uint32_t NU = G / 4u, F = G / 16u, VR = G / 4u;
-    const uint32_t gsh = d.gshift;                       // log2 G (5 .. 8)
+    const uint32_t gsh = GT ? (31u - __clz(GT)) : d.gshift;   // log2 G (5 .. 8)
     const uint32_t ush = gsh >= 6 ? 0u : 6u - gsh;       // log2 max(1, 16 / NU)
     const uint32_t vsh = gsh >= 7 ? 0u : 7u - gsh;       // log2 max(1, 8 / F)
     const uint64_t base = c * C;
@@ -788,7 +789,7 @@ __device__ __forceinline__ bool decode_chunk_lcf16(const DecArray& d, DecSmem& s
     float* dst = d.out + base;
     const bool full_vec = d.vec && cnt == C;
     float4* tr = reinterpret_cast<float4*>(stage);
-    const uint32_t fsh = 31 - __clz(F);
+    const uint32_t fsh = gsh - 4u;                       // log2 F
     for (uint32_t r = 0; r < 4; ++r) {
         if (fast) {
             // 32-bit, wrapping past the row's end (those values are not stored)
@@ -853,7 +854,9 @@ __device__ __noinline__ void decode_team_lcf_strided(const DecArray d, DecSmem& 
                                                      uint32_t* xs, uint32_t stage_words, int team, int k,
                                                      uint64_t c0, uint64_t stride, uint32_t* err) {
     for (uint64_t c = c0; c < d.nc; c += stride)
-        if (!decode_chunk_lcf16(d, sm, tab, xs, xs + d.C / 2, stage_words, team, k, c, c + stride, err)) return;
+        if (!(d.G == 64u ? decode_chunk_lcf16<64>(d, sm, tab, xs, xs + d.C / 2, stage_words, team, k, c, c + stride, err)
+                         : decode_chunk_lcf16<0>(d, sm, tab, xs, xs + d.C / 2, stage_words, team, k, c, c + stride, err)))
+            return;
 }
 
 __device__ __noinline__ void decode_team_lcf_counted(const DecArray d, DecSmem& sm, const uint32_t* tab,
@@ -868,7 +871,9 @@ __device__ __noinline__ void decode_team_lcf_counted(const DecArray d, DecSmem& 
         team_sync(team);
         const uint32_t un = s_unit[team];
         team_sync(team);
-        if (!decode_chunk_lcf16(d, sm, tab, xs, xs + d.C / 2, stage_words, team, k, u, un < nu ? un : ~0ull, err))
+        const uint64_t nx = un < nu ? un : ~0ull;
+        if (!(d.G == 64u ? decode_chunk_lcf16<64>(d, sm, tab, xs, xs + d.C / 2, stage_words, team, k, u, nx, err)
+                         : decode_chunk_lcf16<0>(d, sm, tab, xs, xs + d.C / 2, stage_words, team, k, u, nx, err)))
             return;
         u = un;
     }
