@@ -21,8 +21,9 @@
 //     blocks (one pass: smaller arrays, the batched kernel's small arrays,
 //     and codes recomputed from the input).
 // Measured on GB300 (encode step of six 2^27-element arrays, rel eb 1e-4):
-// one pass 2.18 ms; two passes 0.43 + 1.57 ms, and 0.43 + 1.48 ms with the
-// branch-free packing of pass 2 (1.63 with a branch per completed word).
+// one pass 2.18 ms; two passes 0.43 + 1.57 ms, 0.43 + 1.48 ms with the
+// branch-free packing of pass 2 (1.63 with a branch per completed word), and
+// 0.43 + 1.20 ms with sixteen codes per lane and round.
 #pragma once
 #include "sz_device.cuh"
 
@@ -538,9 +539,9 @@ __device__ void encode_sizes_body(const CompressArgs& a, uint32_t nblocks, EncSi
 }
 
 // ---- two-pass encoding, pass 2: one warp per chunk ------------------------------------
-// A warp takes a chunk by ticket and packs it in rounds of 256 codes, lane l
-// holding codes 8l .. 8l+7 of the round: one 16-byte load of codes (the next
-// round's is in flight meanwhile), eight table lookups, one warp scan of
+// A warp takes a chunk by ticket and packs it in rounds of 512 codes, lane l
+// holding codes 16l .. 16l+15 of the round: two 16-byte loads of codes (the
+// next round's are in flight meanwhile), sixteen table lookups, one warp scan of
 // (escapes, bits) for the lane's bit offset, funnel-shift packing into the
 // warp's zeroed round buffer in shared memory (each completed word OR-ed in by
 // a predicated shared reduction, so the lanes never diverge: a lane's first
@@ -552,17 +553,30 @@ __device__ void encode_sizes_body(const CompressArgs& a, uint32_t nblocks, EncSi
 // word and zero padding to 128 bits.  Warps never wait for one another.
 constexpr int kPackWarps = 8;
 // dynamic shared memory of a packing block: the warps' round buffers
-constexpr size_t pack_smem_bytes() { return 4u * (size_t)kPackWarps * 256u; }
+constexpr size_t pack_smem_bytes();
 // three blocks per SM (80 registers; measured against 2 and 4 on GB300: two
 // blocks of 94 registers pack six 2^27 arrays in 1.86 ms against 1.43 at rel
 // eb 1e-4)
 constexpr int kPackMinBlocks = 3;
-constexpr uint32_t kRoundBufWords = 256;     // 8 codes x 32 lanes x 24 bits = 192 words, plus the carried word
+// Codes per lane and round.  Measured on GB300 (six 2^27 arrays, rel eb 1e-3 /
+// 1e-4 / 1e-5, packing pass): 16 codes 1.11 / 1.20 / 2.33 ms, 8 codes 1.36 /
+// 1.43 / 2.39 ms (the round's scan, sub-stream sums, buffer clearing and
+// copy-out are paid per round); 32 codes spill 312 bytes per thread.
+#ifndef SZ_PACK_K
+#define SZ_PACK_K 16
+#endif
+constexpr int kPackK = SZ_PACK_K;
+static_assert(kPackK == 8 || kPackK == 16, "codes per lane");
+// K codes x 32 lanes x 24 bits = 24 K words, plus the carried word
+constexpr uint32_t kRoundBufWords = 32u * kPackK;
+constexpr size_t pack_smem_bytes() { return 4u * (size_t)kPackWarps * kRoundBufWords; }
+static_assert(kRoundBufWords >= 24u * kPackK + 2u, "a round's words and the carried one fit the buffer");
 
 template <int C, bool LCF>
 __device__ void encode_pack_warp(const CompressArgs& a, uint32_t* rbuf) {
     constexpr int G = C / kSubPerChunk;
-    constexpr int L = G / 8;                 // lanes per sub-stream
+    constexpr int K = kPackK, RS = 32 * K;   // codes per lane, per round
+    constexpr int L = G / K;                 // lanes per sub-stream
     static_assert(L >= 1 && L <= 32, "sub-stream width");
     ArrayState* st = a.st;
     if (st->raw || a.n == 0) return;
@@ -599,39 +613,47 @@ __device__ void encode_pack_warp(const CompressArgs& a, uint32_t* rbuf) {
             }
         }
         const uint4* cp = reinterpret_cast<const uint4*>(a.codes + base);
-        uint4 q4 = __ldg(cp + lane);
+        uint4 q4[K / 8];
+#pragma unroll
+        for (int i = 0; i < K / 8; ++i) q4[i] = __ldg(cp + (K / 8) * lane + i);
         uint32_t carry = 0u, carry_bits = 0u;
         uint64_t wout = wbeg;
         uint64_t esc_run = a.chunk_esc[c];
 #pragma unroll 1
-        for (uint32_t r = 0; r < (uint32_t)C / 256; ++r) {
-            const uint4 cur = q4;
-            if (r + 1 < (uint32_t)C / 256) q4 = __ldg(cp + 32 * (r + 1) + lane);
-            const uint32_t e0 = 256u * r + 8u * lane;
-            const uint32_t w[4] = {cur.x, cur.y, cur.z, cur.w};
-            uint32_t ent[8];
-            uint32_t bits = 0, escs = 0;
-            if ((r + 1u) * 256u <= cnt) {        // a full round (the warp agrees)
+        for (uint32_t r = 0; r < (uint32_t)C / RS; ++r) {
+            uint32_t w[K / 2];
 #pragma unroll
-                for (int j = 0; j < 8; ++j) ent[j] = __ldg(a.enc + ((w[j >> 1] >> ((j & 1) * 16)) & 0xffffu));
+            for (int i = 0; i < K / 8; ++i) {
+                w[4 * i] = q4[i].x; w[4 * i + 1] = q4[i].y; w[4 * i + 2] = q4[i].z; w[4 * i + 3] = q4[i].w;
+            }
+            if (r + 1 < (uint32_t)C / RS) {
+#pragma unroll
+                for (int i = 0; i < K / 8; ++i) q4[i] = __ldg(cp + (RS / 8) * (r + 1) + (K / 8) * lane + i);
+            }
+            const uint32_t e0 = (uint32_t)RS * r + (uint32_t)K * lane;
+            uint32_t ent[K];
+            uint32_t bits = 0, escs = 0;
+            if ((r + 1u) * (uint32_t)RS <= cnt) {        // a full round (the warp agrees)
+#pragma unroll
+                for (int j = 0; j < K; ++j) ent[j] = __ldg(a.enc + ((w[j >> 1] >> ((j & 1) * 16)) & 0xffffu));
             } else {
 #pragma unroll
-                for (int j = 0; j < 8; ++j)
+                for (int j = 0; j < K; ++j)
                     ent[j] = (e0 + j < cnt) ? __ldg(a.enc + ((w[j >> 1] >> ((j & 1) * 16)) & 0xffffu)) : 0u;
             }
             uint32_t any = 0u;
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
+            for (int j = 0; j < K; ++j) {
                 bits += ent[j] & 31u;
                 any |= ent[j];
             }
             uint32_t emask = 0u;                  // the lane's escapes, bit j for code j
             if (any & 32u) {                      // escapes are rare: count them only where there are some
 #pragma unroll
-                for (int j = 0; j < 8; ++j) emask |= ((ent[j] >> 5) & 1u) << j;
+                for (int j = 0; j < K; ++j) emask |= ((ent[j] >> 5) & 1u) << j;
                 escs = __popc(emask);
             }
-            // warp scan of (escapes << 16 | bits): at most 256 escapes and 6144 bits a round
+            // warp scan of (escapes << 16 | bits): at most 32 K escapes and 768 K bits a round
             const uint32_t v = (escs << 16) | bits;
             uint32_t inc = v;
 #pragma unroll
@@ -655,7 +677,7 @@ __device__ void encode_pack_warp(const CompressArgs& a, uint32_t* rbuf) {
                 const uint32_t pos = carry_bits + (ex & 0xffffu);
                 uint32_t addr = (uint32_t)__cvta_generic_to_shared(rbuf) + 4u * (pos >> 5), fill = pos & 31u, cw = 0u;
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
+                for (int j = 0; j < K; ++j) {
                     const uint32_t t = ent[j] & ~255u;
                     cw |= t >> fill;
                     const uint32_t nxt = __funnelshift_r(0u, t, fill);
