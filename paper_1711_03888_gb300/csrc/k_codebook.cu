@@ -6,7 +6,7 @@ namespace szg {
 __global__ void __launch_bounds__(kCbBlock) codebook_kernel(CompressArgs a) {
     __shared__ CbSmem<kCbBlock> sm;
     extern __shared__ uint32_t fast[];
-    codebook_body<kCbBlock>(a, sm, fast, kCbFastSyms);
+    codebook_body<kCbBlock>(a, sm, fast, kCbFastSyms, gridDim.x == 4u);
 }
 
 void launch_codebook(const CompressArgs* a, int k, void* stream) {
@@ -15,7 +15,7 @@ void launch_codebook(const CompressArgs* a, int k, void* stream) {
         cudaFuncSetAttribute(codebook_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCbFastBytes);
         configured = true;
     }
-    for (int i = 0; i < k; ++i) codebook_kernel<<<1, kCbBlock, kCbFastBytes, (cudaStream_t)stream>>>(a[i]);
+    for (int i = 0; i < k; ++i) codebook_kernel<<<kCbBlocks, kCbBlock, kCbFastBytes, (cudaStream_t)stream>>>(a[i]);
 }
 
 }  // namespace szg

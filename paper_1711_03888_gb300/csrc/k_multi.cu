@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(kCbBlock) codebook_multi_kernel(MultiArgs m) {
     __shared__ CompressArgs sa;
     extern __shared__ uint32_t fast[];
     stage_args(m, sa);
-    codebook_body<kCbBlock>(sa, sm, fast, kCbFastSyms);
+    codebook_body<kCbBlock>(sa, sm, fast, kCbFastSyms, gridDim.x == 4u);
 }
 
 // pass 1 of the two-pass encoder over the group's arrays (gridDim.x blocks each)
@@ -194,7 +194,7 @@ int multi_compress_launches(const CompressArgs* d_args, const MultiGroup* groups
     const int jq = maxC == 2048 ? 0 : maxC == 4096 ? 1 : maxC == 8192 ? 2 : 3;
     set(out[k++], (const void*)quant_multi_kernel, umin32(max_nc, (uint32_t)quant_res[jq]), count,
         kQuantThreads, quant_stage_bytes(maxC, SZ_QMULTI_STAGES), SZ_PHASE_QUANT, d_args, first);
-    set(out[k++], (const void*)codebook_multi_kernel, 1, count, kCbBlock, kCbFastBytes, SZ_PHASE_CODEBOOK, d_args,
+    set(out[k++], (const void*)codebook_multi_kernel, kCbBlocks, count, kCbBlock, kCbFastBytes, SZ_PHASE_CODEBOOK, d_args,
         first);
     for (int i = 0; i < ngroups; ++i) {
         // persistent encoders: the resident blocks shared out over the group's arrays

@@ -21,11 +21,17 @@
 namespace szg {
 
 constexpr int kCbBlock = 1024;      // threads of the stand-alone codebook launch
+#ifndef SZ_CB_PAR
+#define SZ_CB_PAR 1
+#endif
+constexpr unsigned kCbBlocks = SZ_CB_PAR ? 4u : 1u;   // blocks per array of the stand-alone launches
 // Alphabets up to this many used symbols sort, merge and take depths in
 // shared memory (4 * kCbFastSyms words of dynamic shared memory).
 constexpr uint32_t kCbFastSyms = 11264;
 constexpr size_t kCbFastBytes = 4u * 4u * kCbFastSyms;
+static_assert(2u * kCbFastSyms <= 32768u, "a parallel build's parent links fit before its lengths");
 constexpr uint32_t kCbMaxRounds = 256;   // merge rounds recorded for the depth sweep
+constexpr uint32_t kCbDepthUnknown = 0xffu;   // a parallel build that would need pointer jumping
 
 // scratch layout (u32 words)
 constexpr size_t SC_SYM = 0;
@@ -57,6 +63,7 @@ struct CbSmem {
     uint32_t base[kMaxLen + 2];
     unsigned long long off[8];
     uint32_t raw, tables_ok;
+    uint32_t pk_last, pk_pick;     // parallel builds: this block finishes; the halvings chosen
 };
 
 __device__ __forceinline__ uint64_t pad16(uint64_t b) { return (b + 15u) & ~(uint64_t)15u; }
@@ -115,9 +122,16 @@ __device__ __forceinline__ uint32_t count_le(const uint32_t* p, uint32_t len, ui
 // (NT = 1024 for the stand-alone launch, 256 inside the batched kernel).
 // fast: optional shared-memory space (4 * fast_cap words); alphabets of at
 // most fast_cap used symbols run the sort, the merge and the depths there.
+// park: the launch runs four blocks for this array.  When the alphabet fits
+// the shared-memory path, block h builds the tree of the frequencies halved h
+// times (f -> (f >> 1) | 1, the length-limit rule) side by side with the
+// others, and the last block to finish keeps the fewest halvings whose tree
+// fits 24 bits -- the tree the one-block loop would end on -- and lays out
+// the stream (or, if none fits, goes on halving alone).  Larger alphabets run
+// on block 0 alone.
 template <int NT>
 __device__ void codebook_body(const CompressArgs& a, CbSmem<NT>& sm, uint32_t* fast = nullptr,
-                              uint32_t fast_cap = 0) {
+                              uint32_t fast_cap = 0, bool park = false) {
     constexpr int kCbThreads = NT;
     const int tid = threadIdx.x;
     ArrayState* st = a.st;
@@ -127,6 +141,7 @@ __device__ void codebook_body(const CompressArgs& a, CbSmem<NT>& sm, uint32_t* f
     const uint32_t flags = a.extra_flags & kFlagReordered;
 
     // -------- degenerate streams: empty, or raw copy ------------------------
+    if (park && blockIdx.x != 0 && (n == 0 || P.raw)) return;     // block 0 writes them
     if (n == 0 || P.raw) {
         if (tid == 0) {
             unsigned long long off[8];
@@ -181,6 +196,8 @@ __device__ void codebook_body(const CompressArgs& a, CbSmem<NT>& sm, uint32_t* f
         __syncthreads();
     }
     const uint32_t m = sm.m;
+    // with four blocks, the others only build trees side by side (below)
+    if (park && blockIdx.x != 0 && !(m > 1 && fast != nullptr && m <= fast_cap)) return;
     // A non-raw array of n > 0 elements always has a used symbol.  An empty
     // histogram would leave the tree without a root: report it and write
     // nothing (the encoder then finds no layout to fill).
@@ -206,18 +223,25 @@ __device__ void codebook_body(const CompressArgs& a, CbSmem<NT>& sm, uint32_t* f
         // between KA / KB and values between VA / VB; the merge keeps the
         // internal-node weights in the key buffer the sort did not end in.
         const bool in_smem = fast != nullptr && m <= fast_cap;
+        const bool par4 = park && in_smem;
+        if (park && !par4 && blockIdx.x != 0) return;     // a large alphabet: block 0 alone
         uint32_t* KA = in_smem ? fast : scr + SC_KA;
         uint32_t* VA = in_smem ? fast + fast_cap : scr + SC_VA;
         uint32_t* KB = in_smem ? fast + 2 * fast_cap : scr + SC_KB;
         uint32_t* VB = in_smem ? fast + 3 * fast_cap : scr + SC_VB;
-        uint32_t* par = scr + SC_PAR;
+        // The tree of the working weights halved `halvings` more times into
+        // par / lenP: once, or (once = false) halving the working weights
+        // until the deepest leaf fits; sm.maxd ends as that depth.
+        auto build = [&](uint32_t* par, uint32_t* lenP, uint32_t halvings, bool once) {
         for (;;) {
             // keys: working weights; values: ascending-symbol index
             uint32_t wmax = 0;
             for (uint32_t k = tid; k < m; k += kCbThreads) {
-                KA[k] = wrk[k];
+                uint32_t w = wrk[k];
+                for (uint32_t h = 0; h < halvings; ++h) w = (w >> 1) | 1u;
+                KA[k] = w;
                 VA[k] = k;
-                wmax = max(wmax, wrk[k]);
+                wmax = max(wmax, w);
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
@@ -306,6 +330,13 @@ __device__ void codebook_body(const CompressArgs& a, CbSmem<NT>& sm, uint32_t* f
             // the leaves'.  Beyond kCbMaxRounds rounds: pointer jumping.
             const uint32_t nodes = 2 * m - 1, root = 2 * m - 2;
             uint32_t* dep;
+            if (once && nr > kCbMaxRounds) {
+                // a parallel build leaves pointer jumping (in the shared global
+                // regions) to the one-block loop: depth unknown
+                if (tid == 0) sm.maxd = kCbDepthUnknown;
+                __syncthreads();
+                return;
+            }
             if (nr <= kCbMaxRounds) {
                 // 2m words: the two key buffers and the values buffer the sort did not end in are free
                 dep = !in_smem ? scr + SC_DA : (vl == VA ? KB : KA);
@@ -362,13 +393,63 @@ __device__ void codebook_body(const CompressArgs& a, CbSmem<NT>& sm, uint32_t* f
                 sm.maxd = mx;
             }
             __syncthreads();
-            if (sm.maxd <= (uint32_t)kMaxLen) {
-                for (uint32_t j = tid; j < m; j += kCbThreads) lenA[vl[j]] = dep[j];
+            if (sm.maxd <= (uint32_t)kMaxLen || once) {
+                for (uint32_t j = tid; j < m; j += kCbThreads) lenP[vl[j]] = dep[j];
                 __syncthreads();
-                break;
+                return;
             }
             for (uint32_t k = tid; k < m; k += kCbThreads) wrk[k] = (wrk[k] >> 1) | 1u;
             __syncthreads();
+        }
+        };
+        if (!par4) {
+            build(scr + SC_PAR, lenA, 0u, false);
+        } else {
+            // this block's build in its own slot of the global key / value
+            // regions (unused by the shared-memory path): parent links (2m - 1
+            // words), then lengths at +32768 (m <= fast_cap words)
+            const uint32_t h = blockIdx.x;
+            uint32_t* slot = scr + SC_KA + (size_t)h * 65536u;
+            build(slot, slot + 32768u, h, true);
+            if (tid == 0)
+                st->cb_ok[h] = sm.maxd == kCbDepthUnknown ? 2u : sm.maxd <= (uint32_t)kMaxLen ? 1u : 0u;
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) sm.pk_last = atomicAdd(&st->cb_done, 1u) == gridDim.x - 1u ? 1u : 0u;
+            __syncthreads();
+            if (!sm.pk_last) return;
+            __threadfence();
+            if (tid == 0) {
+                // the first fitting build; an unknown one before it, or none
+                // fitting: 5 (the one-block loop from the start) or 4 (from
+                // four halvings)
+                uint32_t pick = 4u;
+                for (int q = 0; q < 4; ++q) {
+                    const uint32_t v = *reinterpret_cast<volatile const uint32_t*>(&st->cb_ok[q]);
+                    if (v == 2u) { pick = 5u; break; }
+                    if (v == 1u) { pick = (uint32_t)q; break; }
+                }
+                sm.pk_pick = pick;
+                st->cb_done = 0u;
+            }
+            __syncthreads();
+            const uint32_t pick = sm.pk_pick;
+            if (pick < 4u) {
+                const uint32_t* src = scr + SC_KA + (size_t)pick * 65536u + 32768u;
+                for (uint32_t j = tid; j < m; j += kCbThreads) lenA[j] = __ldcg(src + j);
+                __syncthreads();
+            } else if (pick == 5u) {
+                build(scr + SC_PAR, lenA, 0u, false);
+            } else {
+                // none of 0..3 halvings fits: go on from four, one block
+                for (uint32_t j = tid; j < m; j += kCbThreads) {
+                    uint32_t w = wrk[j];
+                    for (int q = 0; q < 4; ++q) w = (w >> 1) | 1u;
+                    wrk[j] = w;
+                }
+                __syncthreads();
+                build(scr + SC_PAR, lenA, 0u, false);
+            }
         }
     }
 

@@ -80,7 +80,9 @@ struct ArrayState {
     uint32_t l2_n;             // decoder: its entries (0 = no second level)
     uint32_t max_cw;           // decoder: the largest chunk payload of the stream, in words
     uint32_t size_ticket;      // encoder pass 1 block ticket (reset by the codebook kernel)
-    uint32_t pad1[3];
+    uint32_t cb_done;          // codebook: blocks done with their parallel build (re-armed by the range pass)
+    uint32_t cb_ok[4];         // codebook: the build of h halvings fits the length limit
+    uint32_t pad1[2];
 };
 
 // Arguments of one array's compression (passed by value to kernels).

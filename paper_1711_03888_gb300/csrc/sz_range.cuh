@@ -91,6 +91,7 @@ __device__ __forceinline__ void range_body(const CompressArgs& a, uint32_t bid, 
         st->any_finite = any2;
         st->P = make_params(range_eb_abs(a.eb, a.eb_kind, kmin2, kmax2, any2));
         st->acc_blocks = 0u;
+        st->cb_done = 0u;
         st->range_done = 1u;
     }
 }
