@@ -35,13 +35,23 @@ __global__ void __launch_bounds__(256) range_multi_kernel(MultiArgs m) {
 // Measured on GB300, six 2^27 arrays at rel eb 1e-3 / 1e-4 / 1e-5, quantize ms:
 // 1.80 / 1.82 / 4.14 against 2.17 / 2.20 / 4.55 with two stages and no
 // register bound (94 registers, two blocks per SM) and 1.87 / 1.88 / 4.48 with
-// two stages at three blocks per SM.
+// two stages at three blocks per SM.  Chunk-relative 32-bit offsets in the
+// staged loop and the unaligned loop out of line cut the spills from 100 to
+// 44 bytes: 1.60 / 1.62 / 3.91 against 1.71 / 1.73 / 3.99 ms (three blocks
+// per SM without spills: 1.74 / 1.76 / 4.24).
 #ifndef SZ_QMULTI_STAGES
 #define SZ_QMULTI_STAGES 1
 #endif
 #ifndef SZ_QMULTI_MINB
 #define SZ_QMULTI_MINB 4
 #endif
+// the unaligned-input loop, out of line so that its registers do not weigh
+// on the staged loop's
+__device__ __noinline__ void quant_multi_unaligned(const CompressArgs& a, uint32_t* sh, uint32_t* s_esc) {
+    const LatticeParams P = a.st->P;
+    quant_array_global<true>(a, P, blockIdx.x, gridDim.x, sh, s_esc);
+}
+
 __global__ void __launch_bounds__(kQuantThreads, SZ_QMULTI_MINB) quant_multi_kernel(MultiArgs m) {
     __shared__ uint32_t sh[kWinWords];
     __shared__ uint32_t s_esc[kQuantThreads / 32];
@@ -57,7 +67,7 @@ __global__ void __launch_bounds__(kQuantThreads, SZ_QMULTI_MINB) quant_multi_ker
         quant_array_staged<true, false, SZ_QMULTI_STAGES>(sa, P, blockIdx.x, gridDim.x, reinterpret_cast<float*>(stage4),
                                                             sh, s_esc);
     else
-        quant_array_global<true>(sa, P, blockIdx.x, gridDim.x, sh, s_esc);
+        quant_multi_unaligned(sa, sh, s_esc);
     hist_window_flush(sh, sa.hist);
 }
 

@@ -224,40 +224,40 @@ __device__ void quant_chunk_staged(const CompressArgs& a, const LatticeParams& P
                                    uint32_t* sh, uint32_t* s_esc) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint64_t cbase = (uint64_t)c * a.C;
-    const float* sx = stage + 4;           // sx[e - cbase] = x[e]; sx[-4 .. -1] = the elements before the chunk
+    const float* sx = stage + 4;           // sx[o] = x[cbase + o]; sx[-4 .. -1] = the elements before the chunk
     const bool fast_ok = P.fast != 0;
-    const uint64_t n = a.n;
     const uint32_t span = a.C / 8;
-    uint16_t* codes = a.codes;
-    const uint64_t s0 = (uint64_t)c * a.C + (uint64_t)warp * span;
-    const uint64_t s1 = umin64(n, s0 + span);
+    uint16_t* codes = a.codes + cbase;
+    // chunk-relative offsets: this warp's span is s0 .. s1 - 1
+    const uint32_t s0 = (uint32_t)warp * span;
+    const uint32_t s1 = (uint32_t)umin64(a.n - cbase, (uint64_t)s0 + span);
     uint32_t esc = 0;
     long long carry = 0, carry2 = 0;     // q_{s0-1}, and q_{s0-2} for LCF
-    if (s0 < s1 && s0 > 0 && lane == 0) {
+    if (s0 < s1 && cbase + s0 > 0 && lane == 0) {
         bool vv;
-        lattice_q(sx[s0 - 1 - cbase], P, carry, vv);
-        if (LCF && s0 > 1) lattice_q(sx[s0 - 2 - cbase], P, carry2, vv);   // the stage holds 4 before the chunk
+        lattice_q(sx[(int)s0 - 1], P, carry, vv);
+        if (LCF && cbase + s0 > 1) lattice_q(sx[(int)s0 - 2], P, carry2, vv);   // the stage holds 4 before the chunk
     }
     carry = __shfl_sync(0xffffffffu, carry, 0);
     if (LCF) carry2 = __shfl_sync(0xffffffffu, carry2, 0);
-    for (uint64_t ib = s0; ib < s1; ib += 256) {
+    for (uint32_t ib = s0; ib < s1; ib += 256) {
         float xg[2][4];
 #pragma unroll
         for (int g = 0; g < 2; ++g) {
-            const uint64_t i = ib + 128 * g + 4 * (uint64_t)lane;
+            const uint32_t i = ib + 128 * g + 4 * lane;
             if (ib + 128 * g + 128 <= s1) {
-                float4 v = *reinterpret_cast<const float4*>(sx + (i - cbase));
+                float4 v = *reinterpret_cast<const float4*>(sx + i);
                 xg[g][0] = v.x; xg[g][1] = v.y; xg[g][2] = v.z; xg[g][3] = v.w;
             } else {
 #pragma unroll
-                for (int j = 0; j < 4; ++j) xg[g][j] = (i + j < s1) ? sx[i + j - cbase] : 0.0f;
+                for (int j = 0; j < 4; ++j) xg[g][j] = (i + j < s1) ? sx[i + j] : 0.0f;
             }
         }
 #pragma unroll
         for (int g = 0; g < 2; ++g) {
-            const uint64_t i0 = ib + 128 * g;
+            const uint32_t i0 = ib + 128 * g;
             if (i0 >= s1) break;
-            const uint64_t i = i0 + 4 * (uint64_t)lane;
+            const uint32_t i = i0 + 4 * lane;
             const bool full = (i0 + 128 <= s1);
             float x[4] = {xg[g][0], xg[g][1], xg[g][2], xg[g][3]};
             uint32_t cd[4];

@@ -201,3 +201,23 @@ def uniform_f32(n: int, seed: int, lo: float = -1.0, hi: float = 1.0, device="cp
 def random_walk_f32(n: int, seed: int, step: float = 1.0, device="cpu") -> torch.Tensor:
     """Cumulative sum of normal steps: smooth data with a long range."""
     return torch.cumsum(normal(seed, 78, n, device) * step, 0).to(torch.float32)
+
+
+def skewed_steps_f32(m: int = 26, scale: int = 1, ratio: float = 1.62, seed: int = 5,
+                     device="cpu") -> torch.Tensor:
+    """Integer-valued walk whose steps take m distinct values with counts
+    max(1, floor(scale * ratio^k)), k = 0..m-1, in random order.  Counts that
+    grow slightly faster than Fibonacci numbers give the deepest prefix tree a
+    given number of elements allows; the most frequent count goes to step 0,
+    the next ones to +1, -1, +2, -2, ... .  Values stay integers below 2^24, so
+    they are exact in float32."""
+    counts = [max(1, int(scale * ratio ** k)) for k in range(m)]
+    steps = []
+    for rank, k in enumerate(range(m - 1, -1, -1)):
+        s = (rank + 1) // 2 if rank % 2 else -(rank // 2)
+        steps.append(torch.full((counts[k],), s, dtype=torch.int64))
+    seq = torch.cat(steps)
+    perm = torch.argsort(_srl(bits64(seed, 79, seq.numel()), 1))
+    x = torch.cumsum(seq[perm], 0)
+    assert int(x.abs().max()) < (1 << 24)
+    return x.to(torch.float32).to(device)

@@ -3,6 +3,8 @@ oracle on the same seeded inputs.  Integer/byte work must be bit-exact: the
 compressed stream must equal the oracle's byte for byte, and the
 reconstruction must equal the oracle's bit for bit (which implies the error
 bound |x - x'| <= eb_abs the oracle pins establish)."""
+import heapq
+
 import numpy as np
 import pytest
 import torch
@@ -172,6 +174,14 @@ def test_unaligned_input(sz, ctx, oracle):
         out, nb = sz.sz_compress(ctx, x, 1e-4, 1, sz._params(2048))
         sz.sz_sync(ctx)
         assert out[: nb.value].cpu().numpy().tobytes() == ref
+    # the batched kernels take the unaligned views through their global-memory loop
+    offs = (1, 2, 3)
+    outs, nb = sz.sz_compress_batch(ctx, [base.cuda()[off:] for off in offs], [1e-4] * 3, 1)
+    sz.sz_sync(ctx)
+    for i, off in enumerate(offs):
+        got = outs[i][: nb[i]].cpu().numpy().tobytes()
+        h = oracle.parse_header(got)
+        assert got == oracle.compress(base[off:].numpy(), 1e-4, 1, h["chunk"], h["sub"])
 
 
 def test_decoder_reads_oracle_streams_and_reuse(sz, ctx, oracle):
@@ -257,6 +267,45 @@ def test_batch_equals_plain(sz, ctx, oracle):
         assert no[i] == x.numel()
         yr = oracle.decompress(outs[i][: nb[i]].cpu().numpy().tobytes())
         assert np.array_equal(_bits(ys[i][: x.numel()].cpu().numpy()), _bits(yr))
+
+
+def _rebuilds_needed(freq, limit=24):
+    """How many times the (w >> 1) | 1 rescaling must run before the prefix
+    tree of `freq` is at most `limit` deep (tree built by always merging the
+    two lightest nodes, leaves before internal nodes on equal weight)."""
+    f = sorted(int(v) for v in freq)
+    k = 0
+    while True:
+        heap = [(w, 0, i, 0) for i, w in enumerate(f)]
+        heapq.heapify(heap)
+        made = 0
+        while len(heap) > 1:
+            a, b = heapq.heappop(heap), heapq.heappop(heap)
+            heapq.heappush(heap, (a[0] + b[0], 1, made, max(a[3], b[3]) + 1))
+            made += 1
+        if heap[0][3] <= limit:
+            return k
+        f = sorted((w >> 1) | 1 for w in f)
+        k += 1
+
+
+@pytest.mark.parametrize("scale,rebuilds", [(1, 1), (3, 3), (6, 4), (12, 5), (48, 7)])
+def test_length_limit_rebuilds(sz, ctx, oracle, scale, rebuilds):
+    """Step histograms that grow like Fibonacci numbers force the 24-bit code
+    length limit to rescale the counts several times (Sec. III-B's Huffman
+    stage): one to seven rebuilds.  Plain and batched compression must give
+    the oracle's stream byte for byte."""
+    x = synth.skewed_steps_f32(26, scale)
+    _, cnt = np.unique(np.diff(x.numpy()), return_counts=True)
+    assert _rebuilds_needed(cnt) == rebuilds
+    ref = _check(sz, ctx, oracle, x, 0.5, 0, 4096)
+    syms, lens = oracle.stream_codebook(ref)
+    assert lens.max() <= 24 and syms.size == 26
+    outs, nb = sz.sz_compress_batch(ctx, [x.cuda(), synth.random_walk_f32(9000, 3).cuda()], [0.5, 1e-3], 0)
+    sz.sz_sync(ctx)
+    got = outs[0][: nb[0]].cpu().numpy().tobytes()
+    hg = oracle.parse_header(got)
+    assert got == oracle.compress(x.numpy(), 0.5, 0, hg["chunk"], hg["sub"])
 
 
 @pytest.mark.parametrize("field", ["xx", "vz"])
