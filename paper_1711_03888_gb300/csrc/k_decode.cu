@@ -8,7 +8,9 @@
 // level over up to kLut2Max 16-bit prefixes past the first level's codes
 // (codes of 13..16 bits, or the shortest longer length).  A code neither
 // resolves is found by a short walk up the limits from that shortest length.
-// It also records the stream's largest chunk payload.
+// In a stream of 64-symbol sub-streams the escape symbol's entries carry
+// kEscMark instead of 0 (see decode_run16).  It also records the stream's
+// largest chunk payload.
 //
 // decode (one persistent block per SM, split into up to twelve independent
 // 64-thread "chunk teams", each with its own named barrier and mbarrier): a
@@ -35,6 +37,11 @@
 namespace szg {
 
 constexpr int kSetupThreads = 1024;
+// The escape symbol as the lookup tables give it in streams of 64-symbol
+// sub-streams: its low 16 bits (0) mark the escape in the symbol rows, and a
+// sub-stream's sum of symbols counts the escapes from bit 22 up, since 64
+// symbols below 2^16 sum to less than 2^22.
+constexpr uint32_t kEscMark = 1u << 22;
 constexpr int kDecThreads = kSubPerChunk;    // 64 threads per team
 #ifndef SZ_DEC_TEAMS
 #define SZ_DEC_TEAMS 12
@@ -204,10 +211,12 @@ __device__ __forceinline__ void decode_setup_body(const DecompressArgs& a, Setup
         lut2[i] = v;
     }
     __syncthreads();
+    const uint32_t esc_sym = rd32(in + H_G) == 64u ? kEscMark : 0u;   // the header is valid here
     for (uint32_t p = tid; p < m; p += kSetupThreads) {
         uint32_t l = kl[p], s = vl[p];
         a.by_len[p] = (uint16_t)s;
         const uint32_t code = st->first[l] + (p - st->base[l]);
+        if (s == 0u) s = esc_sym;
         if (l <= (uint32_t)kLutBits) {
             uint32_t lo = code << (kLutBits - l), hi = (code + 1) << (kLutBits - l);
             for (uint32_t e = lo; e < hi; ++e) a.lut[e] = (s << 8) | l;
@@ -249,8 +258,12 @@ __global__ void __launch_bounds__(kSetupThreads) decode_setup_kernel(DecompressA
 // b bits into hi.  peek() returns the 32 bits from there by one funnel shift;
 // consume() advances and pulls in one word when b passes 32 (predicated, so
 // lanes do not diverge).  Words at or past `end` read as zero, so a bad
-// stream cannot make it read outside the chunk.
-struct BitReader {
+// stream cannot make it read outside the chunk: PAD = false tests the index
+// and loads only when a word is due; PAD = true (a staged chunk, whose stage
+// holds a zero word at `end`) loads every step from the index clamped to
+// `end`, which costs fewer instructions than the test.
+template <bool PAD>
+struct BitReaderT {
     const uint32_t* words;
     uint32_t pos, end, hi, lo, b;
     __device__ __forceinline__ void init(const uint32_t* w, uint32_t begin_bit, uint32_t end_word) {
@@ -266,7 +279,7 @@ struct BitReader {
     __device__ __forceinline__ void consume(uint32_t len) {
         b += len;
         const bool need = b >= 32u;
-        const uint32_t nxt = (need && pos < end) ? words[pos] : 0u;
+        const uint32_t nxt = PAD ? words[umin32(pos, end)] : ((need && pos < end) ? words[pos] : 0u);
         hi = need ? lo : hi;
         lo = need ? nxt : lo;
         pos += need ? 1u : 0u;
@@ -413,15 +426,18 @@ __device__ __noinline__ uint32_t decode_long(uint32_t w24, uint32_t len, const D
 // second level's range (which starts where the codes of up to 12 bits end)
 // reads the second level, any other the first; both resolve codes of up to
 // 16 bits and mark longer ones with the shortest length under the prefix, for
-// the walk.
-__device__ __forceinline__ uint32_t decode_symbol(BitReader& br, const DecSmem& sm, const uint32_t* tab,
-                                                  uint32_t l2_lo, uint32_t l2_n, const uint16_t* by_len, bool& bad) {
+// the walk.  MARK: the stream's tables give the escape as kEscMark, and so
+// does the walk.
+template <bool MARK, class BR>
+__device__ __forceinline__ uint32_t decode_symbol(BR& br, const DecSmem& sm, const uint32_t* tab, uint32_t l2_lo,
+                                                  uint32_t l2_n, const uint16_t* by_len, bool& bad) {
     const uint32_t w = br.peek();
     const uint32_t i2 = (w >> (32 - kLut2Bits)) - l2_lo;   // wraps above l2_n below the range
     uint32_t ent = tab[i2 < l2_n ? (1u << kLutBits) + i2 : (w >> (32 - kLutBits))];
     if ((ent & 255u) == 0u) {
         ent = decode_long(w >> (32 - kMaxLen), ent >> 8, sm, by_len);
         bad = bad || ent == 0u;
+        if (MARK && ent != 0u && (ent >> 8) == 0u) ent |= kEscMark << 8;
     }
     br.consume(ent & 255u);
     return ent >> 8;
@@ -442,24 +458,30 @@ __device__ __forceinline__ uint32_t val_unit(uint32_t m, uint32_t row, uint32_t 
     return m ^ ((row >> sh) & (F - 1u));
 }
 
-// Phase 1 of one LV sub-stream: nsym symbols into the thread's 16-bit row.
-template <bool FULL>
-__device__ __forceinline__ uint32_t decode_run16(BitReader& br, const DecSmem& sm, const uint32_t* tab,
-                                                 uint32_t l2_lo, uint32_t l2_n, const uint16_t* by_len, uint2* srow,
-                                                 uint32_t NU, uint32_t ush, uint32_t k, uint32_t nsym, uint32_t& nesc,
-                                                 bool& bad) {
+// Phase 1 of one sub-stream: nsym symbols into the thread's 16-bit row.
+// Returns their sum and adds their escapes to nesc: counted one by one, or
+// (MARK) read from bits 22 and up of the sum of the marked symbols.
+template <bool FULL, bool MARK, class BR>
+__device__ __forceinline__ uint32_t decode_run16(BR& br, const DecSmem& sm, const uint32_t* tab, uint32_t l2_lo,
+                                                 uint32_t l2_n, const uint16_t* by_len, uint2* srow, uint32_t NU,
+                                                 uint32_t ush, uint32_t k, uint32_t nsym, uint32_t& nesc, bool& bad) {
     uint32_t ssum = 0;
     for (uint32_t j4 = 0; j4 < nsym; j4 += 4) {
         uint32_t s[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
             if (FULL || j4 + t < nsym) {
-                s[t] = decode_symbol(br, sm, tab, l2_lo, l2_n, by_len, bad);
+                s[t] = decode_symbol<MARK>(br, sm, tab, l2_lo, l2_n, by_len, bad);
                 ssum += s[t];
-                nesc += (s[t] == 0u);
+                if (!MARK) nesc += (s[t] == 0u);
             }
         }
-        srow[sym_unit(j4 >> 2, k, NU, ush)] = make_uint2(s[0] | (s[1] << 16), s[2] | (s[3] << 16));
+        // the low halves: a marked escape stores as 0
+        srow[sym_unit(j4 >> 2, k, NU, ush)] = make_uint2(__byte_perm(s[0], s[1], 0x5410), __byte_perm(s[2], s[3], 0x5410));
+    }
+    if (MARK) {
+        nesc += ssum >> 22;
+        ssum &= kEscMark - 1u;
     }
     return ssum;
 }
@@ -569,8 +591,9 @@ __device__ __forceinline__ bool decode_chunk_lv16(const DecArray& d, DecSmem& sm
     }
     // ---- stage the chunk payload; prefetch the team's next chunk into L2 --------
     const uint32_t cw_words = (uint32_t)(we - wb);
-    const bool staged = cw_words <= stage_words;
+    const bool staged = cw_words < stage_words;     // the stage holds the payload and a zero word after it
     if (staged && !stage_chunk(d.payload + wb, stage, cw_words, sm, team, k, err)) return false;
+    if (staged && k == 0) stage[cw_words] = 0u;
     if (k == 0 && next < d.nc) {
         const uint64_t nb = d.cword[next], ne = d.cword[next + 1];
         if (nb < ne && ne <= d.pw && !(nb & 3u) && !(ne & 3u) && ne - nb < (1u << 24)) {
@@ -588,15 +611,17 @@ __device__ __forceinline__ bool decode_chunk_lv16(const DecArray& d, DecSmem& sm
     uint32_t nesc = 0, ssum, end_bit;
     bool bad = false;
     if (staged) {
-        BitReader br;
+        BitReaderT<true> br;
         br.init(stage, start, cw_words);
-        ssum = nsym == G ? decode_run16<true>(br, sm, tab, d.l2_lo, d.l2_n, d.by_len, srow, NU, ush, k, nsym, nesc, bad)
-                         : decode_run16<false>(br, sm, tab, d.l2_lo, d.l2_n, d.by_len, srow, NU, ush, k, nsym, nesc, bad);
+        ssum = nsym == G
+                   ? decode_run16<true, GT == 64>(br, sm, tab, d.l2_lo, d.l2_n, d.by_len, srow, NU, ush, k, nsym, nesc, bad)
+                   : decode_run16<false, GT == 64>(br, sm, tab, d.l2_lo, d.l2_n, d.by_len, srow, NU, ush, k, nsym, nesc,
+                                                   bad);
         end_bit = br.bit_pos();
     } else {
-        BitReader br;
+        BitReaderT<false> br;
         br.init(d.payload + wb, start, cw_words);
-        ssum = decode_run16<false>(br, sm, tab, d.l2_lo, d.l2_n, d.by_len, srow, NU, ush, k, nsym, nesc, bad);
+        ssum = decode_run16<false, GT == 64>(br, sm, tab, d.l2_lo, d.l2_n, d.by_len, srow, NU, ush, k, nsym, nesc, bad);
         end_bit = br.bit_pos();
     }
     bad = bad || end_bit - start != sl;
@@ -709,8 +734,9 @@ __device__ __forceinline__ bool decode_chunk_lcf16(const DecArray& d, DecSmem& s
     }
     // ---- stage the chunk payload; prefetch the team's next chunk into L2 --------
     const uint32_t cw_words = (uint32_t)(we - wb);
-    const bool staged = cw_words <= stage_words;
+    const bool staged = cw_words < stage_words;     // the stage holds the payload and a zero word after it
     if (staged && !stage_chunk(d.payload + wb, stage, cw_words, sm, team, k, err)) return false;
+    if (staged && k == 0) stage[cw_words] = 0u;
     if (k == 0 && next < d.nc) {
         const uint64_t nb = d.cword[next], ne = d.cword[next + 1];
         if (nb < ne && ne <= d.pw && !(nb & 3u) && !(ne & 3u) && ne - nb < (1u << 24)) {
@@ -727,15 +753,17 @@ __device__ __forceinline__ bool decode_chunk_lcf16(const DecArray& d, DecSmem& s
     uint32_t nesc = 0, ssum, end_bit;
     bool bad = false;
     if (staged) {
-        BitReader br;
+        BitReaderT<true> br;
         br.init(stage, start, cw_words);
-        ssum = nsym == G ? decode_run16<true>(br, sm, tab, d.l2_lo, d.l2_n, d.by_len, srow, NU, ush, k, nsym, nesc, bad)
-                         : decode_run16<false>(br, sm, tab, d.l2_lo, d.l2_n, d.by_len, srow, NU, ush, k, nsym, nesc, bad);
+        ssum = nsym == G
+                   ? decode_run16<true, GT == 64>(br, sm, tab, d.l2_lo, d.l2_n, d.by_len, srow, NU, ush, k, nsym, nesc, bad)
+                   : decode_run16<false, GT == 64>(br, sm, tab, d.l2_lo, d.l2_n, d.by_len, srow, NU, ush, k, nsym, nesc,
+                                                   bad);
         end_bit = br.bit_pos();
     } else {
-        BitReader br;
+        BitReaderT<false> br;
         br.init(d.payload + wb, start, cw_words);
-        ssum = decode_run16<false>(br, sm, tab, d.l2_lo, d.l2_n, d.by_len, srow, NU, ush, k, nsym, nesc, bad);
+        ssum = decode_run16<false, GT == 64>(br, sm, tab, d.l2_lo, d.l2_n, d.by_len, srow, NU, ush, k, nsym, nesc, bad);
         end_bit = br.bit_pos();
     }
     bad = bad || end_bit - start != sl;
