@@ -20,7 +20,8 @@
 // stream's largest chunk (a chunk larger even for one team is read from
 // global memory).  Thread k decodes sub-stream k (G symbols) from its start
 // bit (team scan of the sub-stream bit lengths) into a row of 16-bit symbols,
-// one table load per symbol.  A team scan of the per-thread delta sums plus
+// one table load per symbol and, in a staged full sub-stream, one refill of
+// the 64-bit bit window per two symbols.  A team scan of the per-thread delta sums plus
 // the chunk anchor gives each thread its starting lattice value (a10: the
 // block-wide prefix scan; the anchor replaces the device-wide part).  Each
 // thread then rebuilds its values x' = RN32(q*D) (a11) -- in 32-bit integers
@@ -275,9 +276,19 @@ struct BitReaderT {
         pos = p + 2;
         b = begin_bit & 31u;
     }
+    static constexpr bool kPad = PAD;
     __device__ __forceinline__ uint32_t peek() const { return __funnelshift_l(lo, hi, b); }
+    // the window from bit b for b up to 48 (at least 16 valid bits)
+    __device__ __forceinline__ uint32_t peek16() const {
+        const bool past = b >= 32u;
+        return __funnelshift_l(past ? 0u : lo, past ? lo : hi, b);
+    }
+    __device__ __forceinline__ void advance(uint32_t len) { b += len; }
     __device__ __forceinline__ void consume(uint32_t len) {
         b += len;
+        refill();
+    }
+    __device__ __forceinline__ void refill() {
         const bool need = b >= 32u;
         const uint32_t nxt = PAD ? words[umin32(pos, end)] : ((need && pos < end) ? words[pos] : 0u);
         hi = need ? lo : hi;
@@ -443,6 +454,39 @@ __device__ __forceinline__ uint32_t decode_symbol(BR& br, const DecSmem& sm, con
     return ent >> 8;
 }
 
+// Two symbols with one refill: after a code of at most 16 bits the 64-bit
+// window still holds the 16 bits the tables read; a longer code (the walk)
+// refills before the next symbol, and the walk itself reads a refilled window.
+template <bool MARK, class BR>
+__device__ __forceinline__ void decode_pair(BR& br, const DecSmem& sm, const uint32_t* tab, uint32_t l2_lo,
+                                            uint32_t l2_n, const uint16_t* by_len, uint32_t& s0, uint32_t& s1,
+                                            bool& bad) {
+    uint32_t w = br.peek();
+    uint32_t i2 = (w >> (32 - kLut2Bits)) - l2_lo;
+    uint32_t ent = tab[i2 < l2_n ? (1u << kLutBits) + i2 : (w >> (32 - kLutBits))];
+    if ((ent & 255u) == 0u) {
+        ent = decode_long(w >> (32 - kMaxLen), ent >> 8, sm, by_len);
+        bad = bad || ent == 0u;
+        if (MARK && ent != 0u && (ent >> 8) == 0u) ent |= kEscMark << 8;
+        br.consume(ent & 255u);
+    } else {
+        br.advance(ent & 255u);
+    }
+    s0 = ent >> 8;
+    w = br.peek16();
+    i2 = (w >> (32 - kLut2Bits)) - l2_lo;
+    ent = tab[i2 < l2_n ? (1u << kLutBits) + i2 : (w >> (32 - kLutBits))];
+    if ((ent & 255u) == 0u) {
+        br.refill();
+        w = br.peek();
+        ent = decode_long(w >> (32 - kMaxLen), ent >> 8, sm, by_len);
+        bad = bad || ent == 0u;
+        if (MARK && ent != 0u && (ent >> 8) == 0u) ent |= kEscMark << 8;
+    }
+    br.consume(ent & 255u);
+    s1 = ent >> 8;
+}
+
 // The LV path's 16-bit symbol rows: row k (sub-stream k) holds G symbols as
 // G / 4 units of 8 bytes; unit u sits at u ^ (k / max(1, 16 / NU)) mod NU, so
 // the 16 rows a half-warp writes or reads at one unit index hit distinct banks.
@@ -468,12 +512,22 @@ __device__ __forceinline__ uint32_t decode_run16(BR& br, const DecSmem& sm, cons
     uint32_t ssum = 0;
     for (uint32_t j4 = 0; j4 < nsym; j4 += 4) {
         uint32_t s[4] = {0u, 0u, 0u, 0u};
+        if constexpr (FULL && BR::kPad) {
+            decode_pair<MARK>(br, sm, tab, l2_lo, l2_n, by_len, s[0], s[1], bad);
+            decode_pair<MARK>(br, sm, tab, l2_lo, l2_n, by_len, s[2], s[3], bad);
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            if (FULL || j4 + t < nsym) {
-                s[t] = decode_symbol<MARK>(br, sm, tab, l2_lo, l2_n, by_len, bad);
+            for (int t = 0; t < 4; ++t) {
                 ssum += s[t];
                 if (!MARK) nesc += (s[t] == 0u);
+            }
+        } else {
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                if (FULL || j4 + t < nsym) {
+                    s[t] = decode_symbol<MARK>(br, sm, tab, l2_lo, l2_n, by_len, bad);
+                    ssum += s[t];
+                    if (!MARK) nesc += (s[t] == 0u);
+                }
             }
         }
         // the low halves: a marked escape stores as 0
