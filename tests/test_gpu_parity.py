@@ -292,8 +292,8 @@ def _rebuilds_needed(freq, limit=24):
 @pytest.mark.parametrize("scale,rebuilds", [(1, 1), (3, 3), (6, 4), (12, 5), (48, 7)])
 def test_length_limit_rebuilds(sz, ctx, oracle, scale, rebuilds):
     """Step histograms that grow like Fibonacci numbers force the 24-bit code
-    length limit to rescale the counts several times (Sec. III-B's Huffman
-    stage): one to seven rebuilds.  Plain and batched compression must give
+    length limit to rescale the counts several times (the Huffman stage,
+    Sec. II / IV-B): one to seven rebuilds.  Plain and batched compression must give
     the oracle's stream byte for byte."""
     x = synth.skewed_steps_f32(26, scale)
     _, cnt = np.unique(np.diff(x.numpy()), return_counts=True)
