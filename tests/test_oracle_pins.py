@@ -286,6 +286,17 @@ def test_huffman_limit_matches_heap_construction(oracle, kind):
     assert lens.tolist() == _heap_lengths(freq, sym)
 
 
+@pytest.mark.parametrize("scale", [1, 3, 6, 12, 48])
+def test_huffman_limit_on_repeated_rebuilds(oracle, scale):
+    """The step counts of synth.skewed_steps_f32 (m = 26, ratio 1.62) need one
+    to seven rescalings before the tree fits 24 bits; the oracle must end on
+    the heap construction's tree after every one of them."""
+    freq = np.asarray([max(1, int(scale * 1.62 ** k)) for k in range(26)], np.uint64)
+    sym = np.arange(freq.size, dtype=np.uint32)
+    assert max(_heap_lengths(freq, sym, limit=64)) > 24
+    assert oracle.huffman_lengths(freq, sym).tolist() == _heap_lengths(freq, sym)
+
+
 def _package_merge(freq, L):
     """Optimal lengths under a length limit L (Larmore-Hirschberg)."""
     n = len(freq)
